@@ -1,0 +1,289 @@
+/*
+ * pcx.h -- C ABI of a GB300 (sm_103a) library for the kernel-compensated
+ * Yee-scheme Maxwell eigenproblem of 3D photonic crystals in anisotropic
+ * media (arXiv:2511.17107).
+ *
+ * The discrete problem (Sec. 2.3, eq. kc_formulation): find the smallest
+ * positive eigenvalues w_h^2 of
+ *
+ *     Op = A M A^H + gamma B^H B      on C^{3 N^3},
+ *
+ * A the Bloch-phased Yee curl (Sec. 2.1 eq. yee_ABmatrix, Sec. 2.2
+ * eq. ct_blocks), B the Yee divergence, M the per-cell discrete inverse
+ * permittivity M_Trivial (Sec. 3.2.1 eq. trivial_trivial).  The library works
+ * in the Fourier basis x = F3^H H (Sec. 2.4 eq. matrixfree_kcform), where
+ *
+ *     Op_F x = K_A F3^H M F3 K_A^H x + gamma K_B x.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: N points per axis, N a power of two with 8 <= N <= 256; h = 1/N.
+ * Vector block: `nvec` vectors, each 3 N^3 complex numbers laid out
+ *   [vec][component 0..2][p3 or z][p2 or y][p1 or x], x fastest, complex
+ *   interleaved (re, im).  PCX_FP64 -> double2 (complex128),
+ *   PCX_FP32 -> float2 (complex64).  Fourier mode index p_j in [0, N).
+ * Device pointers: allocated by the caller (e.g. PyTorch), never freed or
+ *   retained by the library; they must be 16-byte aligned.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every device entry point only enqueues work on that stream,
+ *   except where it says it synchronises.
+ * Bloch vector k: Cartesian, 3 doubles (Sec. 1 eq. intro_magneticshifted).
+ * gamma: a value <= 0 selects the practical rule of Remark 2.6
+ *   (eq. kc_settingofgamma1): 4 pi^2 if k = 0 or |k| >= 1, else 4 pi^2/|k|^2.
+ * Errors: every call returns a pcx_status; nothing aborts, nothing traps on
+ *   the device.  pcx_last_error() gives a message for the last failing call
+ *   on a context.  Invalid arguments never reach a kernel.
+ */
+#ifndef PCX_H
+#define PCX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcx_ctx pcx_ctx;
+
+typedef enum {
+  PCX_OK = 0,
+  PCX_EINVAL = -1,   /* invalid argument (sizes, pointers, alignment)        */
+  PCX_ENOMEM = -2,   /* device or host allocation failed                      */
+  PCX_ENOTHPD = -3,  /* a cell block of M is not Hermitian positive definite  */
+  PCX_ENOCONV = -4,  /* eigensolver hit its iteration cap (partial results)   */
+  PCX_ENUMERIC = -5, /* NaN / Inf, or a breakdown the solver cannot repair    */
+  PCX_ECUDA = -6     /* a CUDA runtime call failed                            */
+} pcx_status;
+
+enum { PCX_FP64 = 0, PCX_FP32 = 1 };
+
+/* Shape kinds of a structure description (Cartesian coordinates, the
+ * structure is periodic with the unit cube; see pcx_setup). */
+enum {
+  PCX_SHAPE_SPHERE = 0,  /* p = cx, cy, cz, r                                  */
+  PCX_SHAPE_SEGMENT = 1, /* p = x0, y0, z0, x1, y1, z1, r  (flat-capped rod)   */
+  PCX_SHAPE_BOX = 2,     /* p = lox, loy, loz, hix, hiy, hiz  (lo <= x < hi)   */
+  PCX_SHAPE_GYROID = 3   /* p = t, mode: g(x) > t (mode 0) or |g(x)| > t (1),
+                            g = sin(2pi x)cos(2pi y) + sin(2pi y)cos(2pi z)
+                              + sin(2pi z)cos(2pi x)  (Sec. 4)                 */
+};
+
+typedef struct {
+  int kind;
+  int material;   /* index into pcx_setup_desc.eps */
+  double p[9];
+} pcx_shape;
+
+enum { PCX_CT_SUMMED = 0, PCX_CT_LITERAL = 1 };
+
+typedef struct {
+  int n;                 /* grid points per axis (power of two, 8..256)           */
+  int stencil_m;         /* 1 = Yee (2nd order) ... 5 (10th order), Sec. 2.5      */
+  int ct_reading;        /* PCX_CT_SUMMED (default) or PCX_CT_LITERAL, see below  */
+  double lattice[9];     /* row-major 3x3 matrix A whose COLUMNS are a1, a2, a3   */
+  int n_mat;             /* number of materials                                   */
+  const double* eps;     /* n_mat x 3 x 3 complex PERMITTIVITY, row-major,
+                            (re, im) interleaved: 18 doubles per material (host)  */
+  int background;        /* material of points outside every shape                */
+  int n_shape;
+  const pcx_shape* shapes;      /* host; the first shape containing a point wins  */
+  const double* cell_blocks;    /* optional host array (NULL = sample shapes):
+                            N^3 x 9 already-inverted blocks, cell order z, y, x:
+                            d1, d2, d3, re o12, im o12, re o13, im o13, re o23,
+                            im o23 (M_k = [[d1,o12,o13],[.,d2,o23],[.,.,d3]],
+                            Hermitian)                                           */
+} pcx_setup_desc;
+
+/*
+ * pcx_setup -- build a context: sample the structure and assemble M.
+ *
+ * Sec. 2.1 eqs. yee_edgefacedofs / yee_volumedofs (staggered points, 1-based
+ * i,j,k): E1 at ((i-1/2)h, jh, kh), E2 at (ih, (j-1/2)h, kh), E3 at
+ * (ih, jh, (k-1/2)h), volume centres at ((i-1/2)h, (j-1/2)h, (k-1/2)h), in
+ * fractional coordinates x'; the material is looked up at the physical
+ * point A x' (Sec. 2.2 eq. ct_replacement).  Each material's permittivity is
+ * inverted in FP64 to epsilon_1 (Sec. 1 eq. intro_permittivity).  Cell block
+ * (Sec. 3.1 eq. permittivity_diagonal_case, Sec. 3.2.1 eq. trivial_trivial,
+ * Lemma 3.5): d_c = (epsilon_1 at the E_c point)_cc, o_ij = (epsilon_1 at
+ * the volume centre)_ij.  Every block is checked to be HPD (3x3 Cholesky).
+ *
+ * ct_reading: the printed coordinate-transform blocks (Sec. 2.2
+ * eq. ct_blocks) sum over j without j appearing.  PCX_CT_SUMMED reads
+ * hat D_i = sum_j b_ji (D_{1,j} + i kt_j D_{0,j}), b = A^{-1}, kt = A^T k;
+ * PCX_CT_LITERAL reads sum_j b_ji D_{1,j} + i k_i D_{0,i}.  Both equal
+ * eq. yee_block for the simple cubic lattice.
+ *
+ * Ownership: copies everything it needs; desc and its arrays may be freed
+ * on return.  The context owns M (FP64 and FP32 copies) and all tables on the
+ * current device.  Synchronises the device.
+ * Errors: PCX_EINVAL (N not a power of two in [8,256], stencil_m not in
+ * [1,5] or N < 2 stencil_m, singular lattice, bad material index, NULL
+ * pointers), PCX_ENOTHPD (first failing cell named in pcx_last_error; *out
+ * still receives the context so that the message can be read),
+ * PCX_ENOMEM, PCX_ECUDA.
+ */
+pcx_status pcx_setup(const pcx_setup_desc* desc, pcx_ctx** out);
+
+/*
+ * pcx_sample_host -- the host half of pcx_setup without a device: samples the
+ * structure exactly as pcx_setup does and writes the packed cell blocks
+ * (N^3 x 9 doubles, layout of pcx_setup_desc.cell_blocks) and, if ids_out is
+ * not NULL, the material index of every sample point (4 x N^3 int32: point
+ * sets E1, E2, E3, V, each in cell order z, y, x).  *first_bad receives the
+ * first cell (linear index) whose block is not HPD, or -1.  Needs no GPU.
+ * Errors: as pcx_setup, except that a non-HPD block is reported through
+ * *first_bad, not as an error.
+ */
+pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32_t* ids_out, long long* first_bad);
+
+/* Release a context and its device memory (NULL is ignored). */
+void pcx_destroy(pcx_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none; ctx may be NULL for
+ * errors raised before a context exists). */
+const char* pcx_last_error(const pcx_ctx* ctx);
+
+/* Grid size and number of complex entries 3 N^3 of one vector. */
+int pcx_grid_n(const pcx_ctx* ctx);
+size_t pcx_vector_length(const pcx_ctx* ctx);
+
+/*
+ * pcx_cell_blocks -- copy the packed cell blocks of M to a host array of
+ * N^3 x 9 doubles (layout of pcx_setup_desc.cell_blocks), and the smallest
+ * cell eigenvalue to *lambda_min (may be NULL).  Lemma 3.5: the spectrum of M
+ * is the union of the cell-block spectra.
+ */
+pcx_status pcx_cell_blocks(const pcx_ctx* ctx, double* host_out, double* lambda_min);
+
+/*
+ * pcx_symbols -- the per-k tables the kernels use (host output).
+ * Lemma 2.1 / Prop. 2.8: Lambda_1(p), Lambda_0(p) are the eigenvalues of the
+ * circulant D1, D0 (2m-th order first rows of Sec. 2.5 eq.
+ * kc:highord:stencil).  Output (each may be NULL):
+ *   s_tab  [3][N] complex (6N doubles): S_j(p) = Lambda_1(p) + i kt_j Lambda_0(p)
+ *          (PCX_CT_SUMMED) or Lambda_1(p) (PCX_CT_LITERAL);
+ *   q_tab  [3][N] complex: 0 (SUMMED) or i k_i Lambda_0(p) (LITERAL);
+ *   b      [9] doubles, b = A^{-1} row-major;
+ *   gamma_out: the gamma used (rule above when gamma <= 0).
+ * The mode symbol is kappa_i(p) = sum_j b_ji S_j(p_j) + Q_i(p_i).
+ */
+pcx_status pcx_symbols(const pcx_ctx* ctx, const double k[3], double gamma,
+                       double* s_tab, double* q_tab, double* b, double* gamma_out);
+
+/*
+ * pcx_apply -- Y = Op_F X for a block of nvec vectors (device, stream-ordered).
+ *
+ * Sec. 2.4 eq. matrixfree_kcform with Prop. 2.8:
+ *   u = K_A^H x = -conj(kappa) x x            (per mode)
+ *   e = F3 u,  m = M e (per cell, Sec. 3.2.1),  w = F3^H m
+ *   y = K_A w + gamma K_B x = kappa x w + gamma conj(kappa) (kappa . x)
+ * with F3 = F (x) F (x) F, F_ij = w^{(i-1)(j-1)}/sqrt(N), w = exp(2 pi i/N)
+ * (Lemma 2.1).  X and Y: nvec vectors in `precision`; X and Y must not
+ * overlap.  Y is also the work space: no other device memory is used.
+ * Errors: PCX_EINVAL (NULL or misaligned pointers, nvec < 0, X == Y,
+ * bad precision), PCX_ECUDA (launch failure).  nvec == 0 is a no-op.
+ */
+pcx_status pcx_apply(pcx_ctx* ctx, const double k[3], double gamma, const void* X, void* Y,
+                     int nvec, int precision, void* stream);
+
+/*
+ * pcx_apply_host -- pcx_apply on HOST buffers: copies X to the device, applies,
+ * copies Y back, and synchronises `stream` before returning.  Pinned host
+ * memory gives full copy bandwidth; pageable memory also works.  Staging
+ * buffers are owned by the context and grow on demand.
+ */
+pcx_status pcx_apply_host(pcx_ctx* ctx, const double k[3], double gamma, const void* X_host,
+                          void* Y_host, int nvec, int precision, void* stream);
+
+/*
+ * pcx_precond -- W = K_P^{-1} R per Fourier mode (device, stream-ordered).
+ * Sec. 2.4 eqs. matrixfree_diagP / matrixfree_finalform:
+ *   K_P = K_A K_A^H + gamma K_B = |kappa|^2 I + (gamma - 1) conj(kappa) kappa^T,
+ *   K_P^{-1} = I/|kappa|^2 + (1/gamma - 1) conj(kappa) kappa^T / |kappa|^4
+ * (Sherman-Morrison).  A mode with kappa = 0 (only k = 0, p = 0: the null
+ * space H of Prop. 2.5) maps to 0.  R == W (in place) is allowed.
+ */
+pcx_status pcx_precond(pcx_ctx* ctx, const double k[3], double gamma, const void* R, void* W,
+                       int nvec, int precision, void* stream);
+
+/*
+ * pcx_gram -- G = A^H B for two blocks of columns of length L (complex):
+ * G[i*nb + j] = sum_l conj(A_i[l]) B_j[l], written as na x nb complex128
+ * (interleaved doubles) to the DEVICE buffer G.  The Gram products of the
+ * Rayleigh-Ritz step (Sec. 4: LOBPCG).  Column i of A starts at
+ * A + i * L elements.  precision PCX_FP32: FP32 products on tensor cores
+ * (TF32 with error compensation) accumulated per chunk and summed in FP64;
+ * PCX_FP64: FP64 FMA.  1 <= na, nb <= 128.
+ */
+pcx_status pcx_gram(pcx_ctx* ctx, const void* A, int na, const void* B, int nb, size_t L,
+                    int precision, void* G, void* stream);
+
+/*
+ * pcx_combine -- Y_j = sum_i S_i C[i*ny + j]  (+ beta * Y_j if beta != 0):
+ * tall x small product of the Rayleigh-Ritz update (Sec. 4: LOBPCG).
+ * S: ns columns of length L; C: DEVICE ns x ny complex128; Y: ny columns;
+ * Y must not overlap S.  1 <= ns <= 256, 1 <= ny <= 256.
+ */
+pcx_status pcx_combine(pcx_ctx* ctx, const void* S, int ns, const void* C, int ny, double beta,
+                       void* Y, size_t L, int precision, void* stream);
+
+/*
+ * pcx_residual -- R_j = AX_j - theta_j X_j and the squared norms
+ * out[j] = ||R_j||^2, out[nvec + j] = ||X_j||^2 (DEVICE doubles), giving
+ * Res_j = ||R_j|| / ||X_j|| of Sec. 4 eq. exp_relativeresidual.  theta:
+ * DEVICE doubles.  R may alias AX.
+ */
+pcx_status pcx_residual(pcx_ctx* ctx, const void* X, const void* AX, const double* theta, void* R,
+                        double* norms_out, int nvec, size_t L, int precision, void* stream);
+
+/*
+ * pcx_rr_eig -- the small generalised Hermitian eigenproblem of the
+ * Rayleigh-Ritz step (Sec. 4: LOBPCG), on the HOST in FP64:
+ *   G_A c = theta G_B c,  G_A, G_B m x m Hermitian (row-major complex128,
+ *   interleaved doubles), G_B positive semi-definite.
+ * Directions in which the diagonally scaled G_B has an eigenvalue
+ * <= drop_tol * (its largest) are discarded (rank-revealing orthonormalisation
+ * of the search space); *rank receives the number r kept.  theta[r] ascending;
+ * cvec: m x r row-major complex128 with G_B-orthonormal columns.  Buffers must
+ * hold m values / m*m complex entries.  Errors: PCX_EINVAL (m outside
+ * [1, 512], NULL), PCX_ENUMERIC (G_B has a non-positive diagonal entry).
+ * Needs no GPU.
+ */
+pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol, double* theta, double* cvec,
+                      int* rank);
+
+/* Eigensolver options (pcx_solve).  Zero-initialised fields take defaults. */
+typedef struct {
+  int block;          /* vectors per block (>= nev; default nev + 4)               */
+  int maxit;          /* iteration cap per k (default 1000)                        */
+  int precision;      /* PCX_FP64: all FP64.  PCX_FP32: mixed -- FP32 apply and
+                         storage, FP64 Rayleigh-Ritz, then FP64 refinement         */
+  double switch_tol;  /* mixed: switch to FP64 when all Res_j <= this (default 1e-4) */
+  uint64_t seed;      /* initial block seed (default 20251117)                     */
+  int verbose;        /* print per-iteration residuals to stderr                   */
+} pcx_solve_opts;
+
+/*
+ * pcx_solve -- smallest nev positive eigenvalues w_h^2 at each of nk Bloch
+ * vectors (host kpts, nk x 3), by block LOBPCG with soft locking (Sec. 4;
+ * Knyazev 2001) preconditioned by K_P^{-1}: Rayleigh-Ritz on span{X, W, P},
+ * W = K_P^{-1} R, converged columns keep their place in X but get no new W
+ * or P.  Converged when every Res_j <= tol (eq. exp_relativeresidual).  At
+ * k = 0 the p = 0 mode of every block is deflated (Prop. 2.5: null space H).
+ * Outputs (host, any may be NULL): eig_out[nk*nev] ascending per k,
+ * res_out[nk*nev], iters_out[nk].  vec_out: optional DEVICE buffer for the
+ * eigenvectors (nk*nev vectors, FP64 layout).  Synchronises `stream`.
+ * Errors: PCX_ENOCONV (cap reached; outputs hold the last iterate),
+ * PCX_ENUMERIC (NaN/Inf or unrecoverable breakdown), PCX_EINVAL, PCX_ENOMEM,
+ * PCX_ECUDA.
+ */
+pcx_status pcx_solve(pcx_ctx* ctx, const double* kpts, int nk, int nev, double tol,
+                     const pcx_solve_opts* opts, double* eig_out, double* res_out,
+                     int* iters_out, void* vec_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCX_H */

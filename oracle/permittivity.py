@@ -42,8 +42,15 @@ def fractional_points(n: int, which: str) -> np.ndarray:
     return np.stack([x, y, z], axis=-1)
 
 
+def _dot3(a, b):
+    """a . b over the last axis, summed left to right: (a0 b0 + a1 b1) + a2 b2."""
+    return (a[..., 0] * b[..., 0] + a[..., 1] * b[..., 1]) + a[..., 2] * b[..., 2]
+
+
 def _inside(shape_kind, params, p):
-    """Membership of Cartesian points p (..., 3) in a unit-cube-periodic shape."""
+    """Membership of Cartesian points p (..., 3) in a unit-cube-periodic shape.
+    Distances are evaluated left to right (see _dot3) so that a point on a
+    boundary is classified the same way on every machine."""
     images = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], dtype=np.float64)
     if shape_kind == SHAPE_SPHERE:
         c = np.array(params[:3])
@@ -53,7 +60,7 @@ def _inside(shape_kind, params, p):
         hit = np.zeros(p.shape[:-1], dtype=bool)
         for im in images:
             q = d + im
-            hit |= np.einsum("...i,...i->...", q, q) < r * r
+            hit |= _dot3(q, q) < r * r
         return hit
     if shape_kind == SHAPE_SEGMENT:
         a = np.array(params[:3])
@@ -61,16 +68,16 @@ def _inside(shape_kind, params, p):
         r = params[6]
         mid = 0.5 * (a + b)
         axis = b - a
-        length = np.linalg.norm(axis)
+        length = np.sqrt((axis[0] * axis[0] + axis[1] * axis[1]) + axis[2] * axis[2])
         u = axis / length
         d = p - mid
         d = d - np.round(d)
         hit = np.zeros(p.shape[:-1], dtype=bool)
         for im in images:
             q = d + im
-            t = q @ u
+            t = _dot3(q, u)
             perp = q - t[..., None] * u
-            hit |= (np.abs(t) <= 0.5 * length) & (np.einsum("...i,...i->...", perp, perp) < r * r)
+            hit |= (np.abs(t) <= 0.5 * length) & (_dot3(perp, perp) < r * r)
         return hit
     if shape_kind == SHAPE_BOX:
         lo = np.array(params[:3])
@@ -93,7 +100,8 @@ def material_ids(structure, n: int, which: str) -> np.ndarray:
     """Material index at every point of a staggered point set; the first
     shape containing the point wins, else the background."""
     frac = fractional_points(n, which)
-    phys = frac @ np.asarray(structure.lattice, dtype=np.float64).T   # A x'
+    a = np.asarray(structure.lattice, dtype=np.float64)
+    phys = np.stack([_dot3(a[r], frac) for r in range(3)], axis=-1)   # A x'
     ids = np.full(frac.shape[:-1], structure.background, dtype=np.int64)
     done = np.zeros(frac.shape[:-1], dtype=bool)
     for s in structure.shapes:

@@ -1,0 +1,276 @@
+// extern "C" entry points of libpcx (declared in include/pcx.h): argument
+// validation, error strings and dispatch to the setup code, the kernels and
+// the solver.  Invalid arguments are rejected here, before any launch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "linalg.h"
+#include "pcx_internal.h"
+
+namespace {
+
+thread_local std::string g_err;   // errors raised without a context
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+pcx_status cuda_fail(pcx_ctx* c, const char* where, cudaError_t e) {
+  std::string msg = std::string(where) + ": CUDA error " + cudaGetErrorString(e);
+  if (c) c->err = msg;
+  else g_err = msg;
+  return e == cudaErrorMemoryAllocation ? PCX_ENOMEM : PCX_ECUDA;
+}
+
+pcx_status inval(pcx_ctx* c, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_err = msg;
+  return PCX_EINVAL;
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + nb && y < x + na;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcx_status pcx_setup(const pcx_setup_desc* desc, pcx_ctx** out) {
+  if (!desc || !out) return inval(nullptr, "pcx_setup: NULL argument");
+  *out = nullptr;
+  pcx_ctx* c = new (std::nothrow) pcx_ctx();
+  if (!c) {
+    g_err = "pcx_setup: out of host memory";
+    return PCX_ENOMEM;
+  }
+  pcx_status st;
+  try {
+    st = pcx::setup_context(desc, c);
+  } catch (const std::bad_alloc&) {
+    c->err = "pcx_setup: out of host memory";
+    st = PCX_ENOMEM;
+  }
+  if (st == PCX_OK || st == PCX_ENOTHPD) {
+    *out = c;
+    return st;
+  }
+  g_err = c->err;
+  pcx_destroy(c);
+  return st;
+}
+
+pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32_t* ids_out, long long* first_bad) {
+  if (!desc || !blocks_out) return inval(nullptr, "pcx_sample_host: NULL argument");
+  std::string err;
+  pcx_status st = pcx::validate_desc(desc, err);
+  if (st != PCX_OK) return inval(nullptr, err);
+  std::vector<double> blocks;
+  std::vector<int32_t> ids;
+  try {
+    st = pcx::sample_blocks(desc, desc->lattice, blocks, ids_out ? &ids : nullptr, err);
+  } catch (const std::bad_alloc&) {
+    g_err = "pcx_sample_host: out of host memory";
+    return PCX_ENOMEM;
+  }
+  if (st != PCX_OK) {
+    g_err = err;
+    return st;
+  }
+  std::memcpy(blocks_out, blocks.data(), blocks.size() * sizeof(double));
+  if (ids_out) std::memcpy(ids_out, ids.data(), ids.size() * sizeof(int32_t));
+  if (first_bad) *first_bad = pcx::first_non_hpd(blocks);
+  return PCX_OK;
+}
+
+void pcx_destroy(pcx_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64, c->dev.tw32, c->dev.m64, c->dev.m32, c->stage_x, c->stage_y};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+const char* pcx_last_error(const pcx_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+int pcx_grid_n(const pcx_ctx* c) { return c ? c->n : 0; }
+
+size_t pcx_vector_length(const pcx_ctx* c) { return c ? (size_t)3 * c->n * c->n * c->n : 0; }
+
+pcx_status pcx_cell_blocks(const pcx_ctx* c, double* host_out, double* lambda_min) {
+  if (!c || c->blocks.empty()) return inval(const_cast<pcx_ctx*>(c), "pcx_cell_blocks: no context");
+  if (host_out) std::memcpy(host_out, c->blocks.data(), c->blocks.size() * sizeof(double));
+  if (lambda_min) {
+    // smallest eigenvalue of every Hermitian cell block (Jacobi on 3x3)
+    double lo = INFINITY;
+    const size_t n3 = c->blocks.size() / 9;
+    for (size_t i = 0; i < n3; ++i) {
+      const double* b = &c->blocks[9 * i];
+      std::vector<pcx::cd> a = {b[0], {b[3], b[4]}, {b[5], b[6]}, {b[3], -b[4]}, b[1], {b[7], b[8]},
+                                {b[5], -b[6]}, {b[7], -b[8]}, b[2]};
+      std::vector<double> w;
+      std::vector<pcx::cd> v;
+      pcx::herm_eig(3, a, w, v);
+      lo = std::min(lo, w[0]);
+    }
+    *lambda_min = lo;
+  }
+  return PCX_OK;
+}
+
+pcx_status pcx_symbols(const pcx_ctx* c, const double k[3], double gamma, double* s_tab, double* q_tab, double* b,
+                       double* gamma_out) {
+  if (!c || !k) return inval(const_cast<pcx_ctx*>(c), "pcx_symbols: NULL argument");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  const int n = c->n;
+  for (int j = 0; j < 3; ++j)
+    for (int p = 0; p < n; ++p) {
+      const pcx::cd l1 = c->lam1[p], l0 = c->lam0[p];
+      const pcx::cd s = l1 + pcx::cd(0, kp.kt[j]) * l0;
+      const pcx::cd q = pcx::cd(0, kp.kq[j]) * l0;
+      if (s_tab) {
+        s_tab[2 * (j * n + p)] = s.real();
+        s_tab[2 * (j * n + p) + 1] = s.imag();
+      }
+      if (q_tab) {
+        q_tab[2 * (j * n + p)] = q.real();
+        q_tab[2 * (j * n + p) + 1] = q.imag();
+      }
+    }
+  if (b) std::memcpy(b, c->b, 9 * sizeof(double));
+  if (gamma_out) *gamma_out = kp.gamma;
+  return PCX_OK;
+}
+
+static pcx_status check_block(pcx_ctx* c, const char* who, const void* X, const void* Y, int nvec, int precision) {
+  if (!c) return inval(nullptr, std::string(who) + ": NULL context");
+  if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, std::string(who) + ": bad precision");
+  if (nvec < 0) return inval(c, std::string(who) + ": nvec < 0");
+  if (nvec == 0) return PCX_OK;
+  if (!X || !Y) return inval(c, std::string(who) + ": NULL buffer");
+  if (!aligned16(X) || !aligned16(Y)) return inval(c, std::string(who) + ": buffers must be 16-byte aligned");
+  return PCX_OK;
+}
+
+pcx_status pcx_apply(pcx_ctx* c, const double k[3], double gamma, const void* X, void* Y, int nvec, int precision,
+                     void* stream) {
+  pcx_status st = check_block(c, "pcx_apply", X, Y, nvec, precision);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k) return inval(c, "pcx_apply: NULL k");
+  const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
+  if (ranges_overlap(X, bytes, Y, bytes)) return inval(c, "pcx_apply: X and Y overlap");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  cudaError_t e = pcx::launch_apply(c, kp, X, Y, nvec, precision, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply", e);
+}
+
+pcx_status pcx_apply_host(pcx_ctx* c, const double k[3], double gamma, const void* Xh, void* Yh, int nvec,
+                          int precision, void* stream) {
+  pcx_status st = check_block(c, "pcx_apply_host", Xh, Yh, nvec, precision);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k) return inval(c, "pcx_apply_host: NULL k");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
+  if (bytes > c->stage_bytes) {
+    if (c->stage_x) cudaFree(c->stage_x);
+    if (c->stage_y) cudaFree(c->stage_y);
+    c->stage_x = c->stage_y = nullptr;
+    c->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->stage_x, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->stage_y, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+    c->stage_bytes = bytes;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->stage_x, Xh, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  e = pcx::launch_apply(c, kp, c->stage_x, c->stage_y, nvec, precision, s);
+  if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+  e = cudaMemcpyAsync(Yh, c->stage_y, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply_host", e);
+}
+
+pcx_status pcx_precond(pcx_ctx* c, const double k[3], double gamma, const void* R, void* W, int nvec, int precision,
+                       void* stream) {
+  pcx_status st = check_block(c, "pcx_precond", R, W, nvec, precision);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k) return inval(c, "pcx_precond: NULL k");
+  const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
+  if (R != W && ranges_overlap(R, bytes, W, bytes)) return inval(c, "pcx_precond: R and W partially overlap");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  cudaError_t e = pcx::launch_precond(c, kp, R, W, nvec, precision, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_precond", e);
+}
+
+pcx_status pcx_gram(pcx_ctx* c, const void* A, int na, const void* B, int nb, size_t L, int precision, void* G,
+                    void* stream) {
+  if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, "pcx_gram: bad precision");
+  if (na < 1 || nb < 1 || na > 128 || nb > 128) return inval(c, "pcx_gram: need 1 <= na, nb <= 128");
+  if (!A || !B || !G || !aligned16(A) || !aligned16(B) || !aligned16(G))
+    return inval(c, "pcx_gram: NULL or misaligned buffer");
+  cudaError_t e = pcx::launch_gram(A, na, B, nb, L, precision, static_cast<double*>(G), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_gram", e);
+}
+
+pcx_status pcx_combine(pcx_ctx* c, const void* S, int ns, const void* C, int ny, double beta, void* Y, size_t L,
+                       int precision, void* stream) {
+  if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, "pcx_combine: bad precision");
+  if (ns < 1 || ny < 1 || ns > 256 || ny > 256) return inval(c, "pcx_combine: need 1 <= ns, ny <= 256");
+  if (!S || !C || !Y || !aligned16(S) || !aligned16(Y) || !aligned16(C))
+    return inval(c, "pcx_combine: NULL or misaligned buffer");
+  const size_t es = precision == PCX_FP64 ? 16 : 8;
+  if (ranges_overlap(S, ns * L * es, Y, ny * L * es)) return inval(c, "pcx_combine: S and Y overlap");
+  cudaError_t e = pcx::launch_combine(S, ns, static_cast<const double*>(C), ny, beta, Y, L, precision,
+                                      static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_combine", e);
+}
+
+pcx_status pcx_residual(pcx_ctx* c, const void* X, const void* AX, const double* theta, void* R, double* norms_out,
+                        int nvec, size_t L, int precision, void* stream) {
+  if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, "pcx_residual: bad precision");
+  if (nvec < 0) return inval(c, "pcx_residual: nvec < 0");
+  if (!X || !AX || !theta || !R || !norms_out || !aligned16(X) || !aligned16(AX) || !aligned16(R))
+    return inval(c, "pcx_residual: NULL or misaligned buffer");
+  cudaError_t e = pcx::launch_residual(X, AX, theta, R, norms_out, nvec, L, precision, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_residual", e);
+}
+
+pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol, double* theta, double* cvec,
+                      int* rank) {
+  if (m < 1 || m > 512 || !ga || !gb || !theta || !cvec || !rank) return inval(nullptr, "pcx_rr_eig: bad argument");
+  std::vector<pcx::cd> a((size_t)m * m), b((size_t)m * m);
+  std::memcpy(a.data(), ga, sizeof(double) * 2 * m * m);
+  std::memcpy(b.data(), gb, sizeof(double) * 2 * m * m);
+  std::vector<double> th;
+  std::vector<pcx::cd> cm;
+  const int r = pcx::gen_eig(m, a, b, drop_tol, th, cm);
+  *rank = r;
+  if (r < 0) {
+    g_err = "pcx_rr_eig: metric matrix is not positive definite";
+    return PCX_ENUMERIC;
+  }
+  std::memcpy(theta, th.data(), sizeof(double) * r);
+  std::memcpy(cvec, cm.data(), sizeof(double) * 2 * (size_t)m * r);
+  return PCX_OK;
+}
+
+pcx_status pcx_solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, const pcx_solve_opts* opts,
+                     double* eig_out, double* res_out, int* iters_out, void* vec_out, void* stream) {
+  if (!c) return inval(nullptr, "pcx_solve: NULL context");
+  if (vec_out && !aligned16(vec_out)) return inval(c, "pcx_solve: vec_out must be 16-byte aligned");
+  try {
+    return pcx::solve(c, kpts, nk, nev, tol, opts, eig_out, res_out, iters_out, vec_out,
+                      static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    c->err = "pcx_solve: out of host memory";
+    return PCX_ENOMEM;
+  }
+}
+
+}  // extern "C"

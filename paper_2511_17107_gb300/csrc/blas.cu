@@ -1,0 +1,298 @@
+// Block kernels of the Rayleigh-Ritz eigensolver (Sec. 4: LOBPCG): Gram
+// products of tall-skinny blocks, the tall x small update, residuals and
+// their norms (eq. exp_relativeresidual), random initial blocks and the
+// k = 0 deflation of the constant fields (Prop. 2.5).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "cx.cuh"
+#include "pcx_internal.h"
+
+namespace pcx {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Gram: G[i][j] = sum_l conj(A_i[l]) B_j[l], FP64 output.
+// CTA tile: 32 x 32 outputs, 256 threads each owning a 2 x 2 output block.
+// The row range [l0, l1) of one CTA is walked in chunks of GL rows staged in
+// shared memory; products accumulate in T within a chunk and in FP64 across
+// chunks; CTA partials are added to G with FP64 atomics.
+// ---------------------------------------------------------------------------
+constexpr int GT = 32;
+constexpr int GL = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_kernel(const cx<T>* __restrict__ A, int na, const cx<T>* __restrict__ B,
+                                                   int nb, size_t L, size_t rows_per_cta, double* __restrict__ G) {
+  __shared__ cx<T> sa[GL][GT + 1];
+  __shared__ cx<T> sb[GL][GT + 1];
+  const int ti = blockIdx.x * GT, tj = blockIdx.y * GT;
+  const size_t l0 = (size_t)blockIdx.z * rows_per_cta;
+  const size_t l1 = (l0 + rows_per_cta < L) ? l0 + rows_per_cta : L;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;   // output block (2ty.., 2tx..)
+  double acc[2][2][2] = {};
+  for (size_t base = l0; base < l1; base += GL) {
+    // stage GL rows of 32 columns of A and B (row index fastest across threads)
+    for (int e = threadIdx.x; e < GL * GT; e += 256) {
+      const int r = e % GL, col = e / GL;
+      const size_t l = base + r;
+      const bool ok = l < l1;
+      sa[r][col] = (ok && ti + col < na) ? A[(size_t)(ti + col) * L + l] : mk((T)0, (T)0);
+      sb[r][col] = (ok && tj + col < nb) ? B[(size_t)(tj + col) * L + l] : mk((T)0, (T)0);
+    }
+    __syncthreads();
+    cx<T> part[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) part[a][b] = mk((T)0, (T)0);
+#pragma unroll 8
+    for (int r = 0; r < GL; ++r) {
+      cx<T> av[2] = {sa[r][2 * ty], sa[r][2 * ty + 1]};
+      cx<T> bv[2] = {sb[r][2 * tx], sb[r][2 * tx + 1]};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) part[a][b] = cfma_conj(av[a], bv[b], part[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        acc[a][b][0] += (double)part[a][b].x;
+        acc[a][b][1] += (double)part[a][b].y;
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = ti + 2 * ty + a, j = tj + 2 * tx + b;
+      if (i < na && j < nb) {
+        atomicAdd(&G[2 * ((size_t)i * nb + j)], acc[a][b][0]);
+        atomicAdd(&G[2 * ((size_t)i * nb + j) + 1], acc[a][b][1]);
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Combine: Y_j = sum_i S_i C[i][j] (+ beta Y_j), one row per thread, up to
+// CY output columns per sweep; C staged in shared memory in T.
+// ---------------------------------------------------------------------------
+constexpr int CY = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) combine_kernel(const cx<T>* __restrict__ S, int ns, const double* __restrict__ Cm,
+                                                      int ny, int j0, double beta, cx<T>* __restrict__ Y, size_t L) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  cx<T>* c = reinterpret_cast<cx<T>*>(csm);   // [ns][CY]
+  const int nyl = (ny - j0 < CY) ? ny - j0 : CY;
+  for (int e = threadIdx.x; e < ns * CY; e += blockDim.x) {
+    const int i = e / CY, j = e % CY;
+    c[e] = (j < nyl) ? mk((T)Cm[2 * ((size_t)i * ny + j0 + j)], (T)Cm[2 * ((size_t)i * ny + j0 + j) + 1])
+                     : mk((T)0, (T)0);
+  }
+  __syncthreads();
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (size_t)gridDim.x * blockDim.x) {
+    cx<T> acc[CY];
+#pragma unroll
+    for (int j = 0; j < CY; ++j) acc[j] = mk((T)0, (T)0);
+    for (int i = 0; i < ns; ++i) {
+      const cx<T> sv = S[(size_t)i * L + l];
+#pragma unroll
+      for (int j = 0; j < CY; ++j) acc[j] = cfma(sv, c[i * CY + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < CY; ++j) {
+      if (j < nyl) {
+        cx<T>* yp = Y + (size_t)(j0 + j) * L + l;
+        cx<T> r = acc[j];
+        if (beta != 0.0) r = r + scale(*yp, (T)beta);
+        *yp = r;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Residual R_j = AX_j - theta_j X_j with ||R_j||^2 and ||X_j||^2 (FP64).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) residual_kernel(const cx<T>* __restrict__ X, const cx<T>* AX, const double* theta,
+                                                       cx<T>* R, double* norms, int nvec, size_t L) {
+  const int j = blockIdx.y;
+  const T th = (T)theta[j];
+  double rr = 0.0, xx = 0.0;
+  const cx<T>* x = X + (size_t)j * L;
+  const cx<T>* ax = AX + (size_t)j * L;
+  cx<T>* r = R + (size_t)j * L;
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (size_t)gridDim.x * blockDim.x) {
+    const cx<T> xv = x[l], av = ax[l];
+    const cx<T> rv = mk(fma(-th, xv.x, av.x), fma(-th, xv.y, av.y));
+    r[l] = rv;
+    rr += (double)norm2(rv);
+    xx += (double)norm2(xv);
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    xx += __shfl_down_sync(0xffffffffu, xx, o);
+  }
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  if (lane == 0) {
+    red[0][wid] = rr;
+    red[1][wid] = xx;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x / 32;
+    rr = lane < nw ? red[0][lane] : 0.0;
+    xx = lane < nw ? red[1][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_down_sync(0xffffffffu, rr, o);
+      xx += __shfl_down_sync(0xffffffffu, xx, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&norms[j], rr);
+      atomicAdd(&norms[nvec + j], xx);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Seeded complex Gaussian fill: SplitMix64 hash of (seed, index) -> two
+// uniforms -> Box-Muller (uses the CUDA math library's log, sqrt, sincos).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void fill_random_kernel(cx<T>* X, size_t total, uint64_t seed) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const uint64_t h1 = splitmix(seed ^ splitmix(2 * e)), h2 = splitmix(seed ^ splitmix(2 * e + 1));
+    const double u1 = ((h1 >> 11) + 1) * (1.0 / 9007199254740993.0);   // (0, 1]
+    const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+    const double rad = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    X[e] = mk((T)(rad * cs), (T)(rad * sn));
+  }
+}
+
+template <typename T>
+__global__ void deflate_kernel(cx<T>* X, int nvec, size_t n3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * nvec) X[(size_t)i * n3] = mk((T)0, (T)0);   // mode p = 0 of component i % 3 of vector i / 3
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, size_t count) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (D)src[e];
+}
+
+unsigned grid_for(size_t work, int threads, unsigned cap = 152u * 32u) {
+  return (unsigned)std::max<size_t>(1, std::min<size_t>((work + threads - 1) / threads, cap));
+}
+
+}  // namespace
+
+cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision, double* G,
+                        cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * 2 * (size_t)na * nb, s);
+  if (e != cudaSuccess) return e;
+  if (L == 0) return cudaSuccess;
+  const unsigned gx = (na + GT - 1) / GT, gy = (nb + GT - 1) / GT;
+  // enough CTAs to fill the GPU several times over
+  const size_t want = std::max<size_t>(1, (size_t)152 * 8 / (gx * gy));
+  size_t rows = (L + want - 1) / want;
+  rows = ((rows + GL - 1) / GL) * GL;
+  const unsigned gz = (unsigned)((L + rows - 1) / rows);
+  dim3 grid(gx, gy, gz);
+  if (precision == PCX_FP64)
+    gram_kernel<double><<<grid, 256, 0, s>>>(static_cast<const cx<double>*>(A), na, static_cast<const cx<double>*>(B),
+                                             nb, L, rows, G);
+  else
+    gram_kernel<float><<<grid, 256, 0, s>>>(static_cast<const cx<float>*>(A), na, static_cast<const cx<float>*>(B),
+                                            nb, L, rows, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, double beta, void* Y, size_t L,
+                           int precision, cudaStream_t s) {
+  if (L == 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = grid_for(L, threads, 152u * 8u);
+  for (int j0 = 0; j0 < ny; j0 += CY) {
+    if (precision == PCX_FP64) {
+      const size_t smem = (size_t)ns * CY * sizeof(cx<double>);
+      combine_kernel<double><<<blocks, threads, smem, s>>>(static_cast<const cx<double>*>(S), ns, C, ny, j0, beta,
+                                                           static_cast<cx<double>*>(Y), L);
+    } else {
+      const size_t smem = (size_t)ns * CY * sizeof(cx<float>);
+      combine_kernel<float><<<blocks, threads, smem, s>>>(static_cast<const cx<float>*>(S), ns, C, ny, j0, beta,
+                                                          static_cast<cx<float>*>(Y), L);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_residual(const void* X, const void* AX, const double* theta, void* R, double* norms, int nvec,
+                            size_t L, int precision, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nvec, s);
+  if (e != cudaSuccess || nvec == 0) return e;
+  dim3 grid(grid_for(L, 256, 152u * 4u), nvec);
+  if (precision == PCX_FP64)
+    residual_kernel<double><<<grid, 256, 0, s>>>(static_cast<const cx<double>*>(X), static_cast<const cx<double>*>(AX),
+                                                 theta, static_cast<cx<double>*>(R), norms, nvec, L);
+  else
+    residual_kernel<float><<<grid, 256, 0, s>>>(static_cast<const cx<float>*>(X), static_cast<const cx<float>*>(AX),
+                                                theta, static_cast<cx<float>*>(R), norms, nvec, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_random(void* X, int nvec, size_t L, uint64_t seed, int precision, cudaStream_t s) {
+  const size_t total = (size_t)nvec * L;
+  if (total == 0) return cudaSuccess;
+  if (precision == PCX_FP64)
+    fill_random_kernel<double><<<grid_for(total, 256), 256, 0, s>>>(static_cast<cx<double>*>(X), total, seed);
+  else
+    fill_random_kernel<float><<<grid_for(total, 256), 256, 0, s>>>(static_cast<cx<float>*>(X), total, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deflate_p0(void* X, int nvec, int n, int precision, cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const size_t n3 = (size_t)n * n * n;
+  const unsigned blocks = (3 * nvec + 127) / 128;
+  if (precision == PCX_FP64)
+    deflate_kernel<double><<<blocks, 128, 0, s>>>(static_cast<cx<double>*>(X), nvec, n3);
+  else
+    deflate_kernel<float><<<blocks, 128, 0, s>>>(static_cast<cx<float>*>(X), nvec, n3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t count, cudaStream_t s) {
+  // count = number of complex entries
+  const size_t reals = 2 * count;
+  if (reals == 0) return cudaSuccess;
+  const unsigned blocks = grid_for(reals, 256);
+  if (src_prec == PCX_FP32 && dst_prec == PCX_FP64)
+    convert_kernel<float, double><<<blocks, 256, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), reals);
+  else if (src_prec == PCX_FP64 && dst_prec == PCX_FP32)
+    convert_kernel<double, float><<<blocks, 256, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), reals);
+  else
+    return cudaMemcpyAsync(dst, src, reals * (src_prec == PCX_FP64 ? 8 : 4), cudaMemcpyDeviceToDevice, s);
+  return cudaGetLastError();
+}
+
+}  // namespace pcx

@@ -1,0 +1,94 @@
+// Internal declarations of the pcx library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pcx.h"
+
+namespace pcx {
+
+using cd = std::complex<double>;
+
+// Per-k scalars every Fourier-space kernel needs.  The mode symbol is
+//   kappa_i(p) = sum_j b[j][i] * (L1[p_j] + i kt[j] L0[p_j]) + i kq[i] L0[p_i]
+// (kq = 0 for the summed reading, kt = 0 and kq = k for the literal reading,
+// where the S_j table keeps only L1).  See pcx_symbols in pcx.h.
+struct KParams {
+  double b[9];      // b = A^{-1}, row-major: b[3*j + i] = b_ji
+  double kt[3];     // coefficient of i Lambda_0 inside S_j
+  double kq[3];     // coefficient of i Lambda_0(p_i) added to kappa_i
+  double gamma;
+  int diag_b;       // 1 when b is diagonal (simple cubic fast path)
+};
+
+// Device-resident, k-independent tables of one context.
+struct DeviceTables {
+  void* lam64 = nullptr;   // [2][N] double2: Lambda_1, Lambda_0
+  void* lam32 = nullptr;   // [2][N] float2
+  void* tw64 = nullptr;    // [N] double2: exp(-2 pi i m / N)
+  void* tw32 = nullptr;    // [N] float2
+  void* m64 = nullptr;     // [9][N^3] double: d1 d2 d3 re12 im12 re13 im13 re23 im23
+  void* m32 = nullptr;     // [9][N^3] float
+};
+
+}  // namespace pcx
+
+struct pcx_ctx {
+  int n = 0;
+  int m = 1;
+  int reading = PCX_CT_SUMMED;
+  int device = 0;
+  double A[9] = {0};
+  double b[9] = {0};
+  std::vector<pcx::cd> lam1, lam0;       // host copies of the symbol tables
+  std::vector<double> blocks;            // host N^3 x 9 packed cell blocks
+  double lambda_min = 0.0;
+  pcx::DeviceTables dev;
+  // staging for pcx_apply_host
+  void* stage_x = nullptr;
+  void* stage_y = nullptr;
+  size_t stage_bytes = 0;
+  std::string err;
+};
+
+namespace pcx {
+
+// setup.cpp
+pcx_status validate_desc(const pcx_setup_desc* d, std::string& err);
+pcx_status sample_blocks(const pcx_setup_desc* d, const double* A, std::vector<double>& blocks,
+                         std::vector<int32_t>* ids, std::string& err);
+long long first_non_hpd(const std::vector<double>& blocks);
+pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c);
+KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma);
+double gamma_rule(const double k[3]);
+
+// kernels (fft_apply.cu, blas.cu)
+cudaError_t launch_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
+                         int precision, cudaStream_t s);
+cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec,
+                           int precision, cudaStream_t s);
+cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision,
+                        double* G, cudaStream_t s);
+cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, double beta, void* Y,
+                           size_t L, int precision, cudaStream_t s);
+cudaError_t launch_residual(const void* X, const void* AX, const double* theta, void* R,
+                            double* norms, int nvec, size_t L, int precision, cudaStream_t s);
+cudaError_t launch_fill_random(void* X, int nvec, size_t L, uint64_t seed, int precision,
+                               cudaStream_t s);
+cudaError_t launch_deflate_p0(void* X, int nvec, int n, int precision, cudaStream_t s);
+cudaError_t launch_convert(const void* src, int src_prec, void* dst, int dst_prec, size_t count,
+                           cudaStream_t s);
+
+// solver.cpp
+pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol,
+                 const pcx_solve_opts* opts, double* eig_out, double* res_out, int* iters_out,
+                 void* vec_out, cudaStream_t s);
+
+inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+}  // namespace pcx

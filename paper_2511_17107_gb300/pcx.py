@@ -1,0 +1,334 @@
+"""ctypes binding of libpcx (include/pcx.h).  Argument marshalling only:
+every step of the computation runs inside the CUDA library.  The library
+must have been built (``paper_2511_17107_gb300.build.build()``); without it
+every call raises.
+
+Functions keep the C names (``pcx_setup``, ``pcx_apply``, ...).  Device
+buffers are torch tensors (complex64 for PCX_FP32, complex128 for PCX_FP64),
+contiguous, shaped (nvec, 3, N, N, N); streams default to torch's current
+stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PCX_OK, PCX_EINVAL, PCX_ENOMEM, PCX_ENOTHPD, PCX_ENOCONV, PCX_ENUMERIC, PCX_ECUDA = 0, -1, -2, -3, -4, -5, -6
+PCX_FP64, PCX_FP32 = 0, 1
+PCX_CT_SUMMED, PCX_CT_LITERAL = 0, 1
+STATUS_NAMES = {0: "PCX_OK", -1: "PCX_EINVAL", -2: "PCX_ENOMEM", -3: "PCX_ENOTHPD", -4: "PCX_ENOCONV",
+                -5: "PCX_ENUMERIC", -6: "PCX_ECUDA"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpcx.so")
+
+
+class PcxError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class pcx_shape(C.Structure):
+    _fields_ = [("kind", C.c_int), ("material", C.c_int), ("p", C.c_double * 9)]
+
+
+class pcx_setup_desc(C.Structure):
+    _fields_ = [("n", C.c_int), ("stencil_m", C.c_int), ("ct_reading", C.c_int), ("lattice", C.c_double * 9),
+                ("n_mat", C.c_int), ("eps", C.POINTER(C.c_double)), ("background", C.c_int),
+                ("n_shape", C.c_int), ("shapes", C.POINTER(pcx_shape)), ("cell_blocks", C.POINTER(C.c_double))]
+
+
+class pcx_solve_opts(C.Structure):
+    _fields_ = [("block", C.c_int), ("maxit", C.c_int), ("precision", C.c_int), ("switch_tol", C.c_double),
+                ("seed", C.c_uint64), ("verbose", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpcx.so is missing at {LIB_PATH}: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        try:   # make torch's CUDA runtime the one libpcx binds to
+            import torch  # noqa: F401
+        except ImportError:
+            pass
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip, st = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int
+        sig = {
+            "pcx_setup": (st, [C.POINTER(pcx_setup_desc), C.POINTER(vp)]),
+            "pcx_destroy": (None, [vp]),
+            "pcx_sample_host": (st, [C.POINTER(pcx_setup_desc), dp, C.POINTER(C.c_int32), C.POINTER(C.c_longlong)]),
+            "pcx_last_error": (C.c_char_p, [vp]),
+            "pcx_grid_n": (C.c_int, [vp]),
+            "pcx_vector_length": (C.c_size_t, [vp]),
+            "pcx_cell_blocks": (st, [vp, dp, dp]),
+            "pcx_symbols": (st, [vp, dp, C.c_double, dp, dp, dp, dp]),
+            "pcx_apply": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+            "pcx_apply_host": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+            "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+            "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
+            "pcx_combine": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_double, vp, C.c_size_t, C.c_int, vp]),
+            "pcx_residual": (st, [vp, vp, vp, vp, vp, vp, C.c_int, C.c_size_t, C.c_int, vp]),
+            "pcx_rr_eig": (st, [C.c_int, dp, dp, C.c_double, dp, dp, ip]),
+            "pcx_solve": (st, [vp, dp, C.c_int, C.c_int, C.c_double, C.POINTER(pcx_solve_opts), dp, dp, ip, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
+                        "pcx_cell_blocks", "pcx_symbols", "pcx_apply", "pcx_apply_host", "pcx_precond",
+                        "pcx_gram", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
+
+
+def _check(status, ctx=None):
+    if status != PCX_OK:
+        msg = lib().pcx_last_error(ctx)
+        raise PcxError(status, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _kvec(k):
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.float64).reshape(3))
+    return k, _dptr(k)
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.complex64:
+        return PCX_FP32
+    if t.dtype == torch.complex128:
+        return PCX_FP64
+    raise TypeError(f"expected complex64 or complex128, got {t.dtype}")
+
+
+def _devptr(t):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns a pcx_ctx (device M, symbol and twiddle tables)."""
+
+    def __init__(self, handle, n, keep=None):
+        self.handle = handle
+        self.n = n
+        self._keep = keep
+
+    @property
+    def vector_length(self):
+        return int(lib().pcx_vector_length(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().pcx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks):
+    d = pcx_setup_desc()
+    d.n = n
+    d.stencil_m = stencil_m
+    d.ct_reading = ct_reading
+    lat = np.eye(3) if lattice is None else np.asarray(lattice, dtype=np.float64)
+    for i, v in enumerate(lat.reshape(9)):
+        d.lattice[i] = v
+    keep = []
+    if cell_blocks is not None:
+        cb = np.ascontiguousarray(np.asarray(cell_blocks, dtype=np.float64).reshape(-1))
+        keep.append(cb)
+        d.cell_blocks = _dptr(cb)
+    else:
+        e = np.asarray(eps, dtype=np.complex128)
+        epsf = np.ascontiguousarray(np.stack([e.real, e.imag], axis=-1).reshape(-1))
+        keep.append(epsf)
+        d.n_mat = e.shape[0]
+        d.eps = _dptr(epsf)
+        d.background = background
+        arr = (pcx_shape * max(1, len(shapes)))()
+        for i, s in enumerate(shapes):
+            arr[i].kind = int(s.kind)
+            arr[i].material = int(s.material)
+            for j, v in enumerate(s.params):
+                arr[i].p[j] = float(v)
+        keep.append(arr)
+        d.n_shape = len(shapes)
+        d.shapes = C.cast(arr, C.POINTER(pcx_shape))
+    return d, keep
+
+
+def pcx_setup(n, lattice=None, eps=None, background=0, shapes=(), stencil_m=1, ct_reading=PCX_CT_SUMMED,
+              cell_blocks=None):
+    """Create a context.  ``eps``: (n_mat, 3, 3) complex permittivities;
+    ``shapes``: objects with .kind, .material, .params; ``cell_blocks``:
+    optional (N^3, 9) float64 packed blocks overriding the structure."""
+    d, keep = _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks)
+    h = C.c_void_p()
+    st = lib().pcx_setup(C.byref(d), C.byref(h))
+    if st != PCX_OK:
+        msg = lib().pcx_last_error(h if h.value else None)
+        if h.value:
+            lib().pcx_destroy(h)
+        raise PcxError(st, msg.decode() if msg else "")
+    return Context(h, n)
+
+
+def setup_structure(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED):
+    """pcx_setup from a ``workloads.Structure``."""
+    return pcx_setup(n, structure.lattice, structure.eps, structure.background, structure.shapes,
+                     stencil_m=stencil_m, ct_reading=ct_reading)
+
+
+def pcx_sample_host(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED):
+    """Host sampling (no GPU): (blocks (N^3, 9), ids (4, N^3) int32, first_bad)."""
+    d, keep = _desc(n, structure.lattice, structure.eps, structure.background, structure.shapes, stencil_m,
+                    ct_reading, None)
+    n3 = n ** 3
+    blocks = np.zeros((n3, 9))
+    ids = np.zeros((4, n3), dtype=np.int32)
+    bad = C.c_longlong()
+    _check(lib().pcx_sample_host(C.byref(d), _dptr(blocks), ids.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 C.byref(bad)))
+    return blocks, ids, bad.value
+
+
+def pcx_cell_blocks(ctx):
+    n3 = ctx.n ** 3
+    out = np.zeros((n3, 9), dtype=np.float64)
+    lmin = np.zeros(1)
+    _check(lib().pcx_cell_blocks(ctx.handle, _dptr(out), _dptr(lmin)), ctx.handle)
+    return out, float(lmin[0])
+
+
+def pcx_symbols(ctx, k, gamma=0.0):
+    n = ctx.n
+    s = np.zeros((3, n, 2))
+    q = np.zeros((3, n, 2))
+    b = np.zeros(9)
+    g = np.zeros(1)
+    kk, kp = _kvec(k)
+    _check(lib().pcx_symbols(ctx.handle, kp, float(gamma), _dptr(s), _dptr(q), _dptr(b), _dptr(g)), ctx.handle)
+    return s[..., 0] + 1j * s[..., 1], q[..., 0] + 1j * q[..., 1], b.reshape(3, 3), float(g[0])
+
+
+def pcx_apply(ctx, k, X, Y, gamma=0.0, stream=None):
+    kk, kp = _kvec(k)
+    prec = _prec_of(X)
+    if Y.dtype != X.dtype or Y.shape != X.shape:
+        raise ValueError("X and Y must have the same dtype and shape")
+    nvec = X.shape[0] if X.dim() == 5 else X.numel() // ctx.vector_length
+    _check(lib().pcx_apply(ctx.handle, kp, float(gamma), _devptr(X), _devptr(Y), nvec, prec, _stream(stream)),
+           ctx.handle)
+    return Y
+
+
+def pcx_apply_host(ctx, k, X, Y, gamma=0.0, stream=None):
+    """X, Y: host arrays (numpy or CPU torch; pinned memory copies fastest)."""
+    kk, kp = _kvec(k)
+    if isinstance(X, np.ndarray):
+        prec = PCX_FP32 if X.dtype == np.complex64 else PCX_FP64
+        xp, yp = X.ctypes.data, Y.ctypes.data
+        nvec = X.size // ctx.vector_length
+    else:
+        prec = _prec_of(X)
+        xp, yp = X.data_ptr(), Y.data_ptr()
+        nvec = X.numel() // ctx.vector_length
+    _check(lib().pcx_apply_host(ctx.handle, kp, float(gamma), C.c_void_p(xp), C.c_void_p(yp), nvec, prec,
+                                _stream(stream)), ctx.handle)
+    return Y
+
+
+def pcx_precond(ctx, k, R, W, gamma=0.0, stream=None):
+    kk, kp = _kvec(k)
+    nvec = R.numel() // ctx.vector_length
+    _check(lib().pcx_precond(ctx.handle, kp, float(gamma), _devptr(R), _devptr(W), nvec, _prec_of(R),
+                             _stream(stream)), ctx.handle)
+    return W
+
+
+def pcx_gram(A, B, G, L=None, ctx=None, stream=None):
+    """G (complex128 CUDA tensor, na x nb) = A^H B for column blocks A (na, L), B (nb, L)."""
+    na, nb = A.shape[0], B.shape[0]
+    L = A[0].numel() if L is None else L
+    _check(lib().pcx_gram(ctx.handle if ctx else None, _devptr(A), na, _devptr(B), nb, L, _prec_of(A), _devptr(G),
+                          _stream(stream)), ctx.handle if ctx else None)
+    return G
+
+
+def pcx_combine(S, Cm, Y, beta=0.0, ctx=None, stream=None):
+    """Y_j = sum_i S_i C[i, j] (+ beta Y_j); Cm: complex128 CUDA tensor (ns, ny)."""
+    ns, ny = S.shape[0], Y.shape[0]
+    L = S[0].numel()
+    _check(lib().pcx_combine(ctx.handle if ctx else None, _devptr(S), ns, _devptr(Cm), ny, float(beta), _devptr(Y),
+                             L, _prec_of(S), _stream(stream)), ctx.handle if ctx else None)
+    return Y
+
+
+def pcx_residual(X, AX, theta, R, norms, ctx=None, stream=None):
+    """R = AX - X diag(theta); norms (float64 CUDA, 2 nvec) = [|R_j|^2, |X_j|^2]."""
+    nvec = X.shape[0]
+    L = X[0].numel()
+    _check(lib().pcx_residual(ctx.handle if ctx else None, _devptr(X), _devptr(AX), _devptr(theta), _devptr(R),
+                              _devptr(norms), nvec, L, _prec_of(X), _stream(stream)), ctx.handle if ctx else None)
+    return R, norms
+
+
+def pcx_rr_eig(ga, gb, drop_tol=1e-13):
+    """Host Rayleigh-Ritz: returns (theta[r], C (m, r)) for ga c = theta gb c."""
+    ga = np.ascontiguousarray(ga, dtype=np.complex128)
+    gb = np.ascontiguousarray(gb, dtype=np.complex128)
+    m = ga.shape[0]
+    th = np.zeros(m)
+    cm = np.zeros((m, m), dtype=np.complex128)
+    rank = C.c_int()
+    st = lib().pcx_rr_eig(m, ga.ctypes.data_as(C.POINTER(C.c_double)), gb.ctypes.data_as(C.POINTER(C.c_double)),
+                          float(drop_tol), _dptr(th), cm.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rank))
+    _check(st)
+    r = rank.value
+    return th[:r], cm.reshape(-1)[: m * r].reshape(m, r)
+
+
+def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
+              vec_out=None, stream=None, raise_on_noconv=True):
+    """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status)."""
+    kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+    nk = kp.shape[0]
+    o = pcx_solve_opts(block, maxit, precision, switch_tol, seed, verbose)
+    eig = np.zeros((nk, nev))
+    res = np.zeros((nk, nev))
+    its = np.zeros(nk, dtype=np.int32)
+    vptr = _devptr(vec_out) if vec_out is not None else None
+    st = lib().pcx_solve(ctx.handle, _dptr(kp), nk, nev, float(tol), C.byref(o), _dptr(eig), _dptr(res),
+                         its.ctypes.data_as(C.POINTER(C.c_int)), vptr, _stream(stream))
+    if st != PCX_OK and not (st == PCX_ENOCONV and not raise_on_noconv):
+        _check(st, ctx.handle)
+    return eig, res, its, st

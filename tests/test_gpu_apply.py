@@ -1,0 +1,157 @@
+"""GPU parity of the operator apply, the preconditioner and the block
+kernels against the CPU oracle (element by element), through the C ABI.
+
+Tolerances (derived in DESIGN.md, "Parity tolerances"): every output is
+compared as |y_gpu - y_oracle| <= tol * max|y_oracle| with tol = 1e-12 for
+FP64 and 2e-5 for FP32 storage and arithmetic.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fourier, penalty, permittivity, yee
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {np.complex128: 1e-12, np.complex64: 2e-5}
+
+
+@pytest.fixture(scope="module")
+def pcx():
+    from paper_2511_17107_gb300 import build, pcx as binding
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return binding
+
+
+def _oracle_apply(structure, n, k, x, m=1, reading="summed"):
+    blocks = permittivity.cell_blocks(structure, n)
+    ops = yee.YeeOperators(n, structure.lattice, k, m, reading)
+    g = penalty.gamma_practical(k)
+    return fourier.apply_definition(x, ops, lambda e: permittivity.apply_m(blocks, e), g)
+
+
+def _close(got, want, dtype):
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err <= TOL[dtype], err
+    return err
+
+
+CASES = [
+    # name, structure maker, N, dtype, nvec, stencil m, reading
+    ("sc8-f64", wl.sc_gyro_sphere, 8, np.complex128, 3, 1, "summed"),
+    ("sc16-f64", wl.sc_gyro_sphere, 16, np.complex128, 2, 1, "summed"),
+    ("fcc16-f64", wl.fcc_air_spheres, 16, np.complex128, 2, 1, "summed"),
+    ("diamond32-f64", wl.diamond_rods, 32, np.complex128, 1, 1, "summed"),
+    ("sc32-f32", wl.sc_gyro_sphere, 32, np.complex64, 3, 1, "summed"),
+    ("fcc32-f32", wl.fcc_air_spheres, 32, np.complex64, 2, 1, "summed"),
+    ("woodpile16-m3-f64", wl.woodpile, 16, np.complex128, 2, 3, "summed"),
+    ("fcc16-literal-f64", wl.fcc_air_spheres, 16, np.complex128, 1, 1, "literal"),
+    ("random64-f32", lambda: wl.random_inclusions(3), 64, np.complex64, 1, 2, "summed"),
+]
+
+
+@pytest.mark.parametrize("name,maker,n,dtype,nvec,m,reading", CASES, ids=[c[0] for c in CASES])
+def test_apply_matches_oracle(pcx, name, maker, n, dtype, nvec, m, reading):
+    s = maker()
+    k = wl.config_k(s.name)[min(3, len(wl.config_k(s.name)) - 1)] if not s.name.startswith("random") else \
+        np.array([np.pi, np.pi, np.pi])
+    x = wl.random_block(nvec, n, seed=11).astype(dtype)
+    want = _oracle_apply(s, n, k, x.astype(np.complex128), m, reading)
+    ctx = pcx.setup_structure(s, n, stencil_m=m, ct_reading=pcx.PCX_CT_LITERAL if reading == "literal" else 0)
+    X = torch.from_numpy(x).cuda()
+    Y = torch.empty_like(X)
+    pcx.pcx_apply(ctx, k, X, Y)
+    torch.cuda.synchronize()
+    _close(Y.cpu().numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_apply_at_k_zero_and_host_entry(pcx, dtype):
+    """k = 0 (mode p = 0 maps to 0) and the host-buffer entry point."""
+    n = 16
+    s = wl.sc_gyro_sphere()
+    k = np.zeros(3)
+    x = wl.random_block(2, n, seed=5).astype(dtype)
+    want = _oracle_apply(s, n, k, x.astype(np.complex128))
+    ctx = pcx.setup_structure(s, n)
+    y = np.zeros_like(x)
+    pcx.pcx_apply_host(ctx, k, x, y)
+    _close(y, want, dtype)
+    assert np.abs(y[:, :, 0, 0, 0]).max() <= TOL[dtype] * np.abs(want).max()
+
+
+def test_apply_full_size_bench_workload(pcx):
+    """The benchmark's workload: 128^3 diamond rods, complex64, checked on a
+    full vector against the oracle (2 vectors of the timed launch shape)."""
+    n = 128
+    s = wl.diamond_rods()
+    k = wl.config_k(s.name)[5]
+    x = wl.random_block(2, n, seed=20251117).astype(np.complex64)
+    ctx = pcx.setup_structure(s, n)
+    X = torch.from_numpy(x).cuda()
+    Y = torch.empty_like(X)
+    pcx.pcx_apply(ctx, k, X, Y)
+    torch.cuda.synchronize()
+    got = Y.cpu().numpy()
+    want = _oracle_apply(s, n, k, x[1:2].astype(np.complex128))
+    _close(got[1:2], want, np.complex64)
+
+
+def test_apply_rejects_bad_arguments(pcx):
+    n = 8
+    ctx = pcx.setup_structure(wl.sc_gyro_sphere(), n)
+    X = torch.zeros((1, 3, n, n, n), dtype=torch.complex64, device="cuda")
+    with pytest.raises(pcx.PcxError) as e:
+        pcx.pcx_apply(ctx, [0.1, 0.2, 0.3], X, X)
+    assert e.value.status == pcx.PCX_EINVAL
+    with pytest.raises(pcx.PcxError):
+        pcx.pcx_setup(12, wl.SC, np.stack([wl.VACUUM]), 0, [])
+
+
+@pytest.mark.parametrize("dtype,lat,kvec", [(np.complex128, "SC", (0.3, -1.2, 2.0)), (np.complex64, "FCC", (1.0, 0.5, 3.0)),
+                                            (np.complex128, "SC", (0.0, 0.0, 0.0))])
+def test_precond_matches_oracle(pcx, dtype, lat, kvec):
+    n = 16
+    lattice = getattr(wl, lat)
+    s = wl.homogeneous(wl.VACUUM, lattice)
+    k = np.array(kvec)
+    g = penalty.gamma_practical(k)
+    r = wl.random_block(3, n, seed=9).astype(dtype)
+    want = fourier.precondition(r.astype(np.complex128), fourier.kappa(n, lattice, k), g)
+    ctx = pcx.setup_structure(s, n)
+    R = torch.from_numpy(r).cuda()
+    W = torch.empty_like(R)
+    pcx.pcx_precond(ctx, k, R, W)
+    _close(W.cpu().numpy(), want, dtype)
+    pcx.pcx_precond(ctx, k, R, R)          # in place
+    _close(R.cpu().numpy(), want, dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+@pytest.mark.parametrize("na,nb,L", [(5, 7, 1000), (48, 48, 3 * 16 ** 3), (33, 17, 12345)])
+def test_gram_combine_residual(pcx, dtype, na, nb, L):
+    rng = np.random.default_rng(na + nb)
+    a = (rng.standard_normal((na, L)) + 1j * rng.standard_normal((na, L))).astype(dtype)
+    b = (rng.standard_normal((nb, L)) + 1j * rng.standard_normal((nb, L))).astype(dtype)
+    A, B = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    G = torch.empty((na, nb), dtype=torch.complex128, device="cuda")
+    pcx.pcx_gram(A, B, G)
+    want = a.astype(np.complex128).conj() @ b.astype(np.complex128).T
+    tol = 1e-12 if dtype == np.complex128 else 1e-5
+    assert np.abs(G.cpu().numpy() - want).max() <= tol * np.abs(want).max() * 10
+    c = rng.standard_normal((na, nb)) + 1j * rng.standard_normal((na, nb))
+    Y = torch.from_numpy(b.copy()).cuda()
+    pcx.pcx_combine(A, torch.from_numpy(c).cuda(), Y, beta=0.5)
+    wantc = c.T @ a.astype(np.complex128) + 0.5 * b
+    assert np.abs(Y.cpu().numpy() - wantc).max() <= TOL[dtype] * 10 * np.abs(wantc).max()
+    th = rng.uniform(0, 5, size=nb)
+    R = torch.empty_like(B)
+    norms = torch.zeros(2 * nb, dtype=torch.float64, device="cuda")
+    pcx.pcx_residual(B, Y, torch.from_numpy(th).cuda(), R, norms)
+    wr = Y.cpu().numpy().astype(np.complex128) - th[:, None] * b
+    assert np.abs(R.cpu().numpy() - wr).max() <= TOL[dtype] * 10 * np.abs(wr).max()
+    nr = norms.cpu().numpy()
+    np.testing.assert_allclose(nr[:nb], np.sum(np.abs(R.cpu().numpy().astype(np.complex128)) ** 2, axis=1), rtol=1e-5)
+    np.testing.assert_allclose(nr[nb:], np.sum(np.abs(b.astype(np.complex128)) ** 2, axis=1), rtol=1e-5)

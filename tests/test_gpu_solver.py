@@ -1,0 +1,82 @@
+"""GPU eigenvalue parity of pcx_solve against the oracle: dense spectra at
+8^3, closed-form homogeneous spectra, and the oracle's textbook LOBPCG on
+configuration 1 (16^3 gyrotropic sphere, 10 eigenpairs).  Tolerances: the
+relative eigenvalue errors 1e-10 (FP64) and 1e-6 (mixed precision)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import eig, fourier, penalty, permittivity, yee
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pcx():
+    from paper_2511_17107_gb300 import build, pcx as binding
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return binding
+
+
+def _dense_lowest(structure, n, k, nev):
+    blocks = permittivity.cell_blocks(structure, n)
+    ops = yee.YeeOperators(n, structure.lattice, k)
+    g = penalty.gamma_practical(k)
+    am = lambda e: permittivity.apply_m(blocks, e)
+    mat = eig.dense_matrix(lambda c: ops.compensated(c.reshape(-1, 3, n, n, n), am, g).reshape(c.shape[0], -1),
+                           3 * n ** 3)
+    ev = np.linalg.eigvalsh(0.5 * (mat + mat.conj().T))
+    return ev[ev > 1e-9 * ev.max()][:nev]
+
+
+@pytest.mark.parametrize("prec,rtol", [(0, 1e-10), (1, 1e-6)])
+@pytest.mark.parametrize("kvec", [(0.6, 1.3, -0.5), (0.0, 0.0, 0.0)])
+def test_solve_matches_dense_8(pcx, prec, rtol, kvec):
+    n, nev = 8, 6
+    s = wl.sc_gyro_sphere()
+    k = np.array(kvec)
+    want = _dense_lowest(s, n, k, nev)
+    ctx = pcx.setup_structure(s, n)
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-10, block=nev + 4, precision=prec)
+    assert st == pcx.PCX_OK and np.all(res <= 1e-10)
+    np.testing.assert_allclose(ev[0], want, rtol=rtol)
+
+
+@pytest.mark.parametrize("lat,n", [("SC", 32), ("FCC", 16)])
+def test_solve_homogeneous_closed_form(pcx, lat, n):
+    rng = np.random.default_rng(4)
+    lattice = getattr(wl, lat)
+    eps = wl.hermitian_pd(rng, 2.0, 9.0)
+    s = wl.homogeneous(eps, lattice)
+    k = np.array([0.7, -0.2, 0.4])
+    g = penalty.gamma_practical(k)
+    spec = eig.homogeneous_spectrum(fourier.kappa(n, lattice, k), np.linalg.inv(eps), g)
+    nev = 8
+    ctx = pcx.setup_structure(s, n)
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-9, block=12, precision=0)
+    assert st == pcx.PCX_OK
+    np.testing.assert_allclose(ev[0], spec[:nev], rtol=1e-10)
+
+
+@pytest.mark.parametrize("prec,rtol", [(0, 1e-10), (1, 1e-6)])
+def test_solve_config1_matches_oracle_lobpcg(pcx, prec, rtol):
+    """Configuration 1: 16^3, sphere r = 1/4 with a gyrotropic rotated tensor,
+    k = 2 pi (0.1, 0.2, 0.3), 10 lowest eigenpairs, gamma by the paper's rule."""
+    n, nev = 16, 10
+    s = wl.sc_gyro_sphere()
+    k = wl.config_k(s.name)[0]
+    g = penalty.gamma_practical(k)
+    blocks = permittivity.cell_blocks(s, n)
+    ops = yee.YeeOperators(n, s.lattice, k)
+    am = lambda e: permittivity.apply_m(blocks, e)
+    kap = fourier.kappa(n, s.lattice, k)
+    want, _, ores, _ = eig.lobpcg(lambda x: fourier.apply_symbols(x, kap, am, g),
+                                  lambda r: fourier.precondition(r, kap, g),
+                                  wl.random_block(nev + 4, n, seed=1), nev, tol=1e-10, maxit=600)
+    assert np.all(ores <= 1e-10)
+    ctx = pcx.setup_structure(s, n)
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-10, block=nev + 4, precision=prec)
+    assert st == pcx.PCX_OK and np.all(res <= 1e-10)
+    np.testing.assert_allclose(ev[0], want, rtol=rtol)
