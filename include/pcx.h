@@ -172,6 +172,15 @@ pcx_status pcx_symbols(const pcx_ctx* ctx, const double k[3], double gamma,
                        double* s_tab, double* q_tab, double* b, double* gamma_out);
 
 /*
+ * pcx_set_apply_chunk -- tuning knob of pcx_apply: the number of vectors
+ * that run through all five FFT passes before the next ones start (their
+ * work space is meant to stay resident in L2).  chunk <= 0 restores the
+ * default (largest count whose vectors fill at most half of L2, >= 1).
+ * Host-only; affects calls issued afterwards.
+ */
+pcx_status pcx_set_apply_chunk(pcx_ctx* ctx, int chunk);
+
+/*
  * pcx_apply -- Y = Op_F X for a block of nvec vectors (device, stream-ordered).
  *
  * Sec. 2.4 eq. matrixfree_kcform with Prop. 2.8:
@@ -180,7 +189,10 @@ pcx_status pcx_symbols(const pcx_ctx* ctx, const double k[3], double gamma,
  *   y = K_A w + gamma K_B x = kappa x w + gamma conj(kappa) (kappa . x)
  * with F3 = F (x) F (x) F, F_ij = w^{(i-1)(j-1)}/sqrt(N), w = exp(2 pi i/N)
  * (Lemma 2.1).  X and Y: nvec vectors in `precision`; X and Y must not
- * overlap.  Y is also the work space: no other device memory is used.
+ * overlap.  Y is the work space of the transforms; the context owns a
+ * scratch array of chunk x N^3 complex entries (gamma kappa . x carried from
+ * the first pass to the last), allocated on first use and grown on demand
+ * (the growth synchronises the device).
  * Errors: PCX_EINVAL (NULL or misaligned pointers, nvec < 0, X == Y,
  * bad precision), PCX_ECUDA (launch failure).  nvec == 0 is a no-op.
  */

@@ -90,7 +90,8 @@ pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32
 
 void pcx_destroy(pcx_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64, c->dev.tw32, c->dev.m64, c->dev.m32, c->stage_x, c->stage_y};
+  void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64,  c->dev.tw32, c->dev.m64,  c->dev.m32,
+                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -154,6 +155,12 @@ static pcx_status check_block(pcx_ctx* c, const char* who, const void* X, const 
   if (nvec == 0) return PCX_OK;
   if (!X || !Y) return inval(c, std::string(who) + ": NULL buffer");
   if (!aligned16(X) || !aligned16(Y)) return inval(c, std::string(who) + ": buffers must be 16-byte aligned");
+  return PCX_OK;
+}
+
+pcx_status pcx_set_apply_chunk(pcx_ctx* c, int chunk) {
+  if (!c) return inval(nullptr, "pcx_set_apply_chunk: NULL context");
+  c->apply_chunk = chunk > 0 ? chunk : 0;
   return PCX_OK;
 }
 

@@ -19,7 +19,10 @@
 //   pass 3  z-axis: inverse FFT along z, M sandwich, forward FFT along z
 //   pass 4  y-axis: forward FFT along y
 //   pass 5  x-axis: forward FFT along x + C w + gamma K_B x
-// The output block Y is the only work space: passes 2-4 are in place.
+// The output block Y is the work space of passes 2-4 (in place); pass 1 also
+// stores gamma (kappa . x) per mode into a scratch array that pass 5 reads
+// instead of X.  The block is processed in chunks of vectors small enough
+// for the chunk's work space to stay resident in L2 across the five passes.
 //
 // A CTA holds T pencils x 3 components x N points in shared memory and runs
 // Stockham radix-R stages (Govindaraju et al., SC 2008 formulation) with the
@@ -64,10 +67,13 @@ struct Cfg {
 struct PassArgs {
   const void* in;
   void* out;
-  const void* xin;     // pass 5: the original X
+  void* sbuf;          // [chunk][N^3]: gamma (kappa . x), written by pass 1, read by pass 5
   const void* lam;     // [2][N] Lambda_1, Lambda_0
   const void* tw;      // [N] exp(-2 pi i m / N)
-  const void* M;       // [9][N^3] cell blocks
+  const void* M;       // [9][N^3] dense cell blocks (when mid == nullptr)
+  const void* mid;     // [N^3] uchar4 material ids (E1, E2, E3, V)
+  const void* mtab;    // [n_mat][9] block entries per material
+  int n_mat;
   KParams kp;
   int axis;
   int op;
@@ -183,11 +189,16 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* tw = s + 3 * C::CS;
   cx<T>* lam = tw + N;
+  T* mtab = reinterpret_cast<T*>(lam + 2 * N);
 
   const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
   const cx<T>* glam = static_cast<const cx<T>*>(a.lam);
   for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = gtw[i];
   for (int i = threadIdx.x; i < 2 * N; i += C::THREADS) lam[i] = glam[i];
+  if (a.op == OP_SANDWICH && a.mid) {
+    const T* gt = static_cast<const T*>(a.mtab);
+    for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) mtab[i] = gt[i];
+  }
 
   const size_t q0 = (size_t)blockIdx.x * TP;       // first pencil (global across vectors)
   const size_t v = q0 / N2;
@@ -196,12 +207,25 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
   const cx<T>* in = static_cast<const cx<T>*>(a.in) + v * 3 * N3;
   cx<T>* out = static_cast<cx<T>*>(a.out) + v * 3 * N3;
 
-  // load the tile: consecutive threads walk the memory-contiguous index
-  for (int w = threadIdx.x; w < 3 * TP * N; w += C::THREADS) {
-    const int c = w / (TP * N), rem = w % (TP * N);
-    const int t = axis == 0 ? rem / N : rem % TP;
-    const int n = axis == 0 ? rem % N : rem / TP;
-    s[TL::sidx(axis, c, t, n)] = in[c * N3 + TL::gidx(axis, qb + t, n)];
+  // load the tile: consecutive threads walk the memory-contiguous index, two
+  // complex numbers (16 bytes) per access for complex64
+  if constexpr (sizeof(T) == 4) {
+    for (int w2 = threadIdx.x; w2 < 3 * TP * N / 2; w2 += C::THREADS) {
+      const int w = 2 * w2;
+      const int c = w / (TP * N), rem = w % (TP * N);
+      const int t = axis == 0 ? rem / N : rem % TP;
+      const int n = axis == 0 ? rem % N : rem / TP;
+      const float4 v4 = *reinterpret_cast<const float4*>(in + c * N3 + TL::gidx(axis, qb + t, n));
+      s[TL::sidx(axis, c, t, n)] = mk((T)v4.x, (T)v4.y);
+      s[axis == 0 ? TL::sidx(axis, c, t, n + 1) : TL::sidx(axis, c, t + 1, n)] = mk((T)v4.z, (T)v4.w);
+    }
+  } else {
+    for (int w = threadIdx.x; w < 3 * TP * N; w += C::THREADS) {
+      const int c = w / (TP * N), rem = w % (TP * N);
+      const int t = axis == 0 ? rem / N : rem % TP;
+      const int n = axis == 0 ? rem % N : rem / TP;
+      s[TL::sidx(axis, c, t, n)] = in[c * N3 + TL::gidx(axis, qb + t, n)];
+    }
   }
   __syncthreads();
 
@@ -214,6 +238,8 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
       cx<T> kap[3];
       kappa_at<T>(lam, N, a.kp, p1, p2, p3, kap);
       cx<T> x0 = s[TL::sidx(axis, 0, t, n)], x1 = s[TL::sidx(axis, 1, t, n)], x2 = s[TL::sidx(axis, 2, t, n)];
+      const cx<T> sk = cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0));
+      static_cast<cx<T>*>(a.sbuf)[v * N3 + TL::gidx(axis, qb + t, n)] = scale(sk, (T)a.kp.gamma);
       // conj(kappa_2) x1 - ... written with conj-multiplies
       cx<T> u0 = cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, mk((T)0, (T)0)), (T)-1));
       cx<T> u1 = cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, mk((T)0, (T)0)), (T)-1));
@@ -230,14 +256,30 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
 
   if (a.op == OP_SANDWICH) {   // m = M e / N^3 per cell (axis == 2: q = y*N + x, n = z)
     const T* M = static_cast<const T*>(a.M);
+    const uchar4* mid = static_cast<const uchar4*>(a.mid);
     const T inv_n3 = (T)(1.0 / (double)N3);
     for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {
       const int t = w % TP, n = w / TP;
       const size_t cell = (size_t)n * N2 + (qb + t);
-      const T d1 = M[cell], d2 = M[N3 + cell], d3 = M[2 * N3 + cell];
-      const cx<T> o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
-      const cx<T> o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
-      const cx<T> o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
+      T d1, d2, d3;
+      cx<T> o12, o13, o23;
+      if (mid) {
+        const uchar4 id = mid[cell];
+        d1 = mtab[9 * id.x];
+        d2 = mtab[9 * id.y + 1];
+        d3 = mtab[9 * id.z + 2];
+        const T* o = mtab + 9 * id.w;
+        o12 = mk(o[3], o[4]);
+        o13 = mk(o[5], o[6]);
+        o23 = mk(o[7], o[8]);
+      } else {
+        d1 = M[cell];
+        d2 = M[N3 + cell];
+        d3 = M[2 * N3 + cell];
+        o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
+        o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
+        o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
+      }
       const int i0 = TL::sidx(2, 0, t, n), i1 = TL::sidx(2, 1, t, n), i2 = TL::sidx(2, 2, t, n);
       const cx<T> e0 = s[i0], e1 = s[i1], e2 = s[i2];
       cx<T> m0 = cfma(o13, e2, cfma(o12, e1, scale(e0, d1)));
@@ -252,8 +294,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
   }
 
   if (a.op == OP_POST) {   // y = kappa x w + gamma conj(kappa) (kappa . x)
-    const cx<T>* xin = static_cast<const cx<T>*>(a.xin) + v * 3 * N3;
-    const T gamma = (T)a.kp.gamma;
+    const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
     for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {
       const int t = axis == 0 ? w / N : w % TP;
       const int n = axis == 0 ? w % N : w / TP;
@@ -262,15 +303,11 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
       cx<T> kap[3];
       kappa_at<T>(lam, N, a.kp, p1, p2, p3, kap);
       const size_t g = TL::gidx(axis, qb + t, n);
-      const cx<T> x0 = xin[g], x1 = xin[N3 + g], x2 = xin[2 * N3 + g];
       const cx<T> w0 = s[TL::sidx(axis, 0, t, n)], w1 = s[TL::sidx(axis, 1, t, n)], w2 = s[TL::sidx(axis, 2, t, n)];
-      const cx<T> zero = mk((T)0, (T)0);
-      cx<T> sk = cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0));
-      sk = scale(sk, gamma);
+      const cx<T> sk = sb[g];
       cx<T> y0 = cfma_conj(kap[0], sk, cfma(kap[1], w2, scale(kap[2] * w1, (T)-1)));
       cx<T> y1 = cfma_conj(kap[1], sk, cfma(kap[2], w0, scale(kap[0] * w2, (T)-1)));
       cx<T> y2 = cfma_conj(kap[2], sk, cfma(kap[0], w1, scale(kap[1] * w0, (T)-1)));
-      (void)zero;
       out[g] = y0;
       out[N3 + g] = y1;
       out[2 * N3 + g] = y2;
@@ -319,56 +356,101 @@ __global__ void precond_kernel(const cx<T>* __restrict__ R, cx<T>* __restrict__ 
 }
 
 template <typename T, int N>
-cudaError_t run_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, cudaStream_t st) {
+cudaError_t run_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
+                      cudaStream_t st) {
   using C = Cfg<T, N>;
-  static bool attr_done = false;   // per instantiation; set once per process
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
   const bool dbl = sizeof(T) == 8;
+  const int n_mat = c->dev.mid ? c->dev.n_mat : 0;
+  const size_t smem = C::SMEM + (size_t)9 * n_mat * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(pass_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pass_kernel<T, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   PassArgs a;
   a.lam = dbl ? c->dev.lam64 : c->dev.lam32;
   a.tw = dbl ? c->dev.tw64 : c->dev.tw32;
   a.M = dbl ? c->dev.m64 : c->dev.m32;
+  a.mid = c->dev.mid;
+  a.mtab = dbl ? c->dev.mtab64 : c->dev.mtab32;
+  a.n_mat = n_mat;
   a.kp = kp;
-  a.xin = X;
-  const size_t tiles = (size_t)nvec * N * N / C::T_;
+  a.sbuf = sbuf;
+  const size_t vlen = (size_t)3 * N * N * N;
   const int axes[5] = {0, 1, 2, 1, 0};
   const int ops[5] = {OP_PRE, OP_INV, OP_SANDWICH, OP_FWD, OP_POST};
-  for (int p = 0; p < 5; ++p) {
-    a.axis = axes[p];
-    a.op = ops[p];
-    a.in = p == 0 ? X : Y;
-    a.out = Y;
-    pass_kernel<T, N><<<(unsigned)tiles, C::THREADS, C::SMEM, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+  for (int v0 = 0; v0 < nvec; v0 += chunk) {
+    const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
+    const size_t tiles = (size_t)nv * N * N / C::T_;
+    const cx<T>* x = static_cast<const cx<T>*>(X) + (size_t)v0 * vlen;
+    cx<T>* y = static_cast<cx<T>*>(Y) + (size_t)v0 * vlen;
+    for (int p = 0; p < 5; ++p) {
+      a.axis = axes[p];
+      a.op = ops[p];
+      a.in = p == 0 ? static_cast<const void*>(x) : static_cast<const void*>(y);
+      a.out = y;
+      pass_kernel<T, N><<<(unsigned)tiles, C::THREADS, smem, st>>>(a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
 
 template <typename T>
-cudaError_t dispatch_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, cudaStream_t st) {
+cudaError_t dispatch_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk,
+                           void* sbuf, cudaStream_t st) {
   switch (c->n) {
-    case 8: return run_apply<T, 8>(c, kp, X, Y, nvec, st);
-    case 16: return run_apply<T, 16>(c, kp, X, Y, nvec, st);
-    case 32: return run_apply<T, 32>(c, kp, X, Y, nvec, st);
-    case 64: return run_apply<T, 64>(c, kp, X, Y, nvec, st);
-    case 128: return run_apply<T, 128>(c, kp, X, Y, nvec, st);
-    case 256: return run_apply<T, 256>(c, kp, X, Y, nvec, st);
+    case 8: return run_apply<T, 8>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 16: return run_apply<T, 16>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 32: return run_apply<T, 32>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 64: return run_apply<T, 64>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 128: return run_apply<T, 128>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 256: return run_apply<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st);
   }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
+int apply_chunk(const pcx_ctx* c, int precision) {
+  if (c->apply_chunk > 0) return c->apply_chunk;
+  const size_t vbytes = (size_t)3 * c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  const size_t l2 = c->l2_bytes ? c->l2_bytes : ((size_t)126 << 20);
+  const size_t k = (l2 / 2) / vbytes;
+  return (int)(k < 1 ? 1 : (k > 64 ? 64 : k));
+}
+
+size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec) {
+  const int chunk = apply_chunk(c, precision);
+  const int nv = nvec < chunk ? nvec : chunk;
+  return (size_t)nv * c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+}
+
+cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
+                                 void* scratch, cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const int chunk = apply_chunk(c, precision);
+  return precision == PCX_FP64 ? dispatch_apply<double>(c, kp, X, Y, nvec, chunk, scratch, s)
+                               : dispatch_apply<float>(c, kp, X, Y, nvec, chunk, scratch, s);
+}
+
+cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
                          cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
-  return precision == PCX_FP64 ? dispatch_apply<double>(c, kp, X, Y, nvec, s)
-                               : dispatch_apply<float>(c, kp, X, Y, nvec, s);
+  const size_t need = apply_scratch_bytes(c, precision, nvec);
+  if (need > c->scratch_bytes) {
+    // the previous scratch may still be in use by work queued on another stream
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    e = cudaMalloc(&c->scratch, need);
+    if (e != cudaSuccess) return e;
+    c->scratch_bytes = need;
+  }
+  return launch_apply_scratch(c, kp, X, Y, nvec, precision, c->scratch, s);
 }
 
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,

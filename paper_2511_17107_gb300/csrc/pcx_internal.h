@@ -32,6 +32,13 @@ struct DeviceTables {
   void* lam32 = nullptr;   // [2][N] float2
   void* tw64 = nullptr;    // [N] double2: exp(-2 pi i m / N)
   void* tw32 = nullptr;    // [N] float2
+  // M as material ids: one uchar4 per cell (materials at E1, E2, E3 and the
+  // volume centre) plus a per-material table of the nine block entries.
+  void* mid = nullptr;     // [N^3] uchar4
+  void* mtab64 = nullptr;  // [n_mat][9] double: e11 e22 e33 re12 im12 re13 im13 re23 im23
+  void* mtab32 = nullptr;  // [n_mat][9] float
+  int n_mat = 0;
+  // M as dense blocks (caller-supplied cell blocks, or more than 255 materials)
   void* m64 = nullptr;     // [9][N^3] double: d1 d2 d3 re12 im12 re13 im13 re23 im23
   void* m32 = nullptr;     // [9][N^3] float
 };
@@ -49,6 +56,11 @@ struct pcx_ctx {
   std::vector<double> blocks;            // host N^3 x 9 packed cell blocks
   double lambda_min = 0.0;
   pcx::DeviceTables dev;
+  // apply tuning and scratch: vectors per L2-resident chunk (0 = from L2 size)
+  int apply_chunk = 0;
+  void* scratch = nullptr;     // gamma kappa.x carried from pass 1 to pass 5
+  size_t scratch_bytes = 0;
+  size_t l2_bytes = 0;
   // staging for pcx_apply_host
   void* stage_x = nullptr;
   void* stage_y = nullptr;
@@ -68,8 +80,14 @@ KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma);
 double gamma_rule(const double k[3]);
 
 // kernels (fft_apply.cu, blas.cu)
-cudaError_t launch_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
-                         int precision, cudaStream_t s);
+// apply with the context-owned scratch (allocated on first use / growth)
+cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
+                         cudaStream_t s);
+// apply with caller-provided scratch of apply_scratch_bytes(c, precision, nvec) bytes
+cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
+                                 int precision, void* scratch, cudaStream_t s);
+int apply_chunk(const pcx_ctx* c, int precision);
+size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec);
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec,
                            int precision, cudaStream_t s);
 cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision,

@@ -365,7 +365,9 @@ pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c) {
   std::memcpy(c->A, d->lattice, sizeof(c->A));
   invert3(c->A, c->b);
   const size_t n3 = (size_t)n * n * n;
-  st = sample_blocks(d, c->A, c->blocks, nullptr, c->err);
+  std::vector<int32_t> ids;
+  const bool use_ids = !d->cell_blocks && d->n_mat <= 255;
+  st = sample_blocks(d, c->A, c->blocks, use_ids ? &ids : nullptr, c->err);
   if (st != PCX_OK) return st;
   // HPD check of every cell block (Lemma 3.5: spectrum of M = union of blocks)
   const long long bad = first_non_hpd(c->blocks);
@@ -397,20 +399,52 @@ pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c) {
     tw32[2 * mm] = (float)std::cos(a);
     tw32[2 * mm + 1] = (float)(-std::sin(a));
   }
-  std::vector<double> m64(9 * n3);
-  for (size_t i = 0; i < n3; ++i)
-    for (int f = 0; f < 9; ++f) m64[f * n3 + i] = c->blocks[9 * i + f];
-  std::vector<float> m32(m64.begin(), m64.end());
-
   cudaError_t e;
   if ((e = cudaGetDevice(&c->device)) != cudaSuccess || (e = upload(&c->dev.lam64, lam64)) != cudaSuccess ||
       (e = upload(&c->dev.lam32, lam32)) != cudaSuccess || (e = upload(&c->dev.tw64, tw64)) != cudaSuccess ||
-      (e = upload(&c->dev.tw32, tw32)) != cudaSuccess || (e = upload(&c->dev.m64, m64)) != cudaSuccess ||
-      (e = upload(&c->dev.m32, m32)) != cudaSuccess) {
+      (e = upload(&c->dev.tw32, tw32)) != cudaSuccess)
+    goto cuda_error;
+  if (use_ids) {
+    // uchar4 per cell + per-material table of (epsilon_1)_11, _22, _33, _12, _13, _23
+    std::vector<uint8_t> mid(4 * n3);
+    for (int set = 0; set < 4; ++set)
+      for (size_t i = 0; i < n3; ++i) mid[4 * i + set] = (uint8_t)ids[set * n3 + i];
+    std::vector<cd> inv(9 * (size_t)d->n_mat);
+    for (int mt = 0; mt < d->n_mat; ++mt) {
+      cd a[9];
+      for (int i = 0; i < 9; ++i) a[i] = cd(d->eps[18 * mt + 2 * i], d->eps[18 * mt + 2 * i + 1]);
+      invert3c(a, &inv[9 * mt]);
+    }
+    std::vector<double> t64(9 * (size_t)d->n_mat);
+    for (int mt = 0; mt < d->n_mat; ++mt) {
+      const cd* v = &inv[9 * mt];
+      const double row[9] = {v[0].real(), v[4].real(), v[8].real(), v[1].real(), v[1].imag(),
+                             v[2].real(), v[2].imag(), v[5].real(), v[5].imag()};
+      for (int f = 0; f < 9; ++f) t64[9 * mt + f] = row[f];
+    }
+    std::vector<float> t32(t64.begin(), t64.end());
+    c->dev.n_mat = d->n_mat;
+    if ((e = upload(&c->dev.mid, mid)) != cudaSuccess || (e = upload(&c->dev.mtab64, t64)) != cudaSuccess ||
+        (e = upload(&c->dev.mtab32, t32)) != cudaSuccess)
+      goto cuda_error;
+  } else {
+    std::vector<double> m64(9 * n3);
+    for (size_t i = 0; i < n3; ++i)
+      for (int f = 0; f < 9; ++f) m64[f * n3 + i] = c->blocks[9 * i + f];
+    std::vector<float> m32(m64.begin(), m64.end());
+    if ((e = upload(&c->dev.m64, m64)) != cudaSuccess || (e = upload(&c->dev.m32, m32)) != cudaSuccess)
+      goto cuda_error;
+  }
+  {
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) == cudaSuccess) c->l2_bytes = (size_t)l2;
+  }
+  return PCX_OK;
+cuda_error:
+  {
     c->err = std::string("pcx_setup: CUDA error ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? PCX_ENOMEM : PCX_ECUDA;
   }
-  return PCX_OK;
 }
 
 }  // namespace pcx

@@ -70,6 +70,7 @@ def lib():
             "pcx_vector_length": (C.c_size_t, [vp]),
             "pcx_cell_blocks": (st, [vp, dp, dp]),
             "pcx_symbols": (st, [vp, dp, C.c_double, dp, dp, dp, dp]),
+            "pcx_set_apply_chunk": (st, [vp, C.c_int]),
             "pcx_apply": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_apply_host": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
@@ -89,7 +90,7 @@ def lib():
 
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
-                        "pcx_cell_blocks", "pcx_symbols", "pcx_apply", "pcx_apply_host", "pcx_precond",
+                        "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_apply", "pcx_apply_host", "pcx_precond",
                         "pcx_gram", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
 
@@ -238,6 +239,10 @@ def pcx_symbols(ctx, k, gamma=0.0):
     kk, kp = _kvec(k)
     _check(lib().pcx_symbols(ctx.handle, kp, float(gamma), _dptr(s), _dptr(q), _dptr(b), _dptr(g)), ctx.handle)
     return s[..., 0] + 1j * s[..., 1], q[..., 0] + 1j * q[..., 1], b.reshape(3, 3), float(g[0])
+
+
+def pcx_set_apply_chunk(ctx, chunk):
+    _check(lib().pcx_set_apply_chunk(ctx.handle, int(chunk)), ctx.handle)
 
 
 def pcx_apply(ctx, k, X, Y, gamma=0.0, stream=None):

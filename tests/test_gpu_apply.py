@@ -99,6 +99,29 @@ def test_apply_full_size_bench_workload(pcx):
     _close(got[1:2], want, np.complex64)
 
 
+@pytest.mark.parametrize("dtype", [np.complex64, np.complex128])
+def test_apply_dense_cell_blocks_and_chunking(pcx, dtype):
+    """Caller-supplied cell blocks (the dense M path) agree with the oracle
+    and with the material-id path, for several chunk sizes (1, 2, default)."""
+    n = 32
+    s = wl.fcc_air_spheres()
+    k = wl.config_k(s.name)[7]
+    ob = permittivity.cell_blocks(s, n).reshape(-1, 3, 3)
+    packed = np.stack([ob[:, 0, 0].real, ob[:, 1, 1].real, ob[:, 2, 2].real, ob[:, 0, 1].real, ob[:, 0, 1].imag,
+                       ob[:, 0, 2].real, ob[:, 0, 2].imag, ob[:, 1, 2].real, ob[:, 1, 2].imag], axis=1)
+    dense = pcx.pcx_setup(n, s.lattice, cell_blocks=packed)
+    ids = pcx.setup_structure(s, n)
+    x = wl.random_block(3, n, seed=2).astype(dtype)
+    want = _oracle_apply(s, n, k, x.astype(np.complex128))
+    X = torch.from_numpy(x).cuda()
+    for ctx in (dense, ids):
+        for chunk in (1, 2, 0):
+            pcx.pcx_set_apply_chunk(ctx, chunk)
+            Y = torch.empty_like(X)
+            pcx.pcx_apply(ctx, k, X, Y)
+            _close(Y.cpu().numpy(), want, dtype)
+
+
 def test_apply_rejects_bad_arguments(pcx):
     n = 8
     ctx = pcx.setup_structure(wl.sc_gyro_sphere(), n)
