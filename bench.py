@@ -172,6 +172,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--n", type=int, default=N, help="grid size (profiling runs use the default)")
+    ap.add_argument("--block", type=int, default=BLOCK, help="vectors per step (profiling runs)")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -197,10 +201,12 @@ def main():
         _build.build()
     if dist:
         td.barrier()
+    n, block = args.n, args.block
+    cdt, es = (np.complex64, 8) if args.precision == "f32" else (np.complex128, 16)
     s = wl.diamond_rods()
     k = wl.config_k(s.name)[K_INDEX]
-    ctx = pcx.setup_structure(s, N)
-    x = wl.random_block(BLOCK, N, seed=20251117 + rank).astype(np.complex64)
+    ctx = pcx.setup_structure(s, n)
+    x = wl.random_block(block, n, seed=20251117 + rank).astype(cdt)
     X = torch.from_numpy(x).cuda()
     Y = torch.empty_like(X)
     stream = torch.cuda.current_stream()
@@ -238,36 +244,39 @@ def main():
         td.all_reduce(t, op=td.ReduceOp.MAX)
         ms = float(t.item())
     per_launch_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps
-    value = world * BLOCK * args.steps / (ms / 1e3)
+    value = world * block * args.steps / (ms / 1e3)
 
-    # parity spot check of the timed output (vector 0, a few modes) is in tests
     # end-to-end: host buffers through pcx_apply_host (copies inside the timed region)
-    xh = torch.from_numpy(x).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    pcx.pcx_apply_host(ctx, k, xh, yh)
-    e2e_steps = max(3, min(args.steps, 10))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
         pcx.pcx_apply_host(ctx, k, xh, yh)
-    e2e_dt = time.perf_counter() - t0
-    e2e_value = world * BLOCK * e2e_steps / e2e_dt
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pcx.pcx_apply_host(ctx, k, xh, yh)
+        e2e_dt = time.perf_counter() - t0
+        e2e = {"value": world * block * e2e_steps / e2e_dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(xh.numel() * es), "d2h_bytes_per_step": int(yh.numel() * es)}
 
     peak, peak_kind = peaks()
-    abytes = algorithmic_bytes(N, BLOCK, 8, 4)
+    abytes = algorithmic_bytes(n, block, es, 4)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "block": BLOCK, "k_index": K_INDEX,
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD if (n, block, es) == (N, BLOCK, 8) else
+                   f"diamond-rods {n}^3 FCC, block of {block} vectors, {args.precision} apply (pcx_apply)",
+                   "N": n, "block": block, "k_index": K_INDEX,
                    "l2": "inputs larger than L2 (805 MB per block)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "pcx_apply pass chain (5 launches)", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": abytes},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 8),
-                "d2h_bytes_per_step": int(yh.numel() * 8)},
+        "e2e": e2e,
         "gpu_launches": 5 * args.steps,
         "clocks": ck,
     }
