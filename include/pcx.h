@@ -200,6 +200,40 @@ pcx_status pcx_apply(pcx_ctx* ctx, const double k[3], double gamma, const void* 
                      int nvec, int precision, void* stream);
 
 /*
+ * pcx_apply_noalloc -- pcx_apply for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this entry point exists for
+ * integration, not for the method.  Some callers must not call cudaMalloc or
+ * cudaFree during their steady state: a host thread that is capturing a CUDA
+ * stream into a graph (allocation calls are not capturable and break the
+ * capture), an application whose device memory is carved out up front by
+ * its own pool or framework allocator and must not be fragmented or
+ * oversubscribed by a library, or a real-time loop where an allocation's
+ * latency (and its implicit device synchronisation) is not acceptable.
+ * pcx_apply may allocate (its scratch grows on demand); this variant never
+ * does: no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * Its scratch (gamma kappa . x for one chunk of vectors) lives in a
+ * file-scope device array of PCX_NOALLOC_SCRATCH_BYTES (32 MiB) that every
+ * GPU loading the library holds until the process exits.  Limit: one
+ * vector's scratch, N^3 complex entries, must fit, i.e. N^3 * 8 bytes
+ * (PCX_FP32) or N^3 * 16 bytes (PCX_FP64) <= 32 MiB -- every N <= 128 in
+ * both precisions; larger grids are rejected with PCX_EINVAL before any
+ * launch.  Vectors are processed in chunks that fit the array.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The context's device must be current.
+ * The array is shared by every call and keeps the last call's contents;
+ * nothing in it needs to start at zero (the first FFT pass writes all of it
+ * before the last pass reads it).  Calls whose execution overlaps on the GPU
+ * (other streams, other threads) race on the array: serialise them.
+ * Arguments, results and errors otherwise as pcx_apply.
+ */
+#define PCX_NOALLOC_SCRATCH_BYTES (32u << 20)
+pcx_status pcx_apply_noalloc(pcx_ctx* ctx, const double k[3], double gamma, const void* X, void* Y, int nvec,
+                             int precision, void* stream);
+
+/*
  * pcx_apply_host -- pcx_apply on HOST buffers: copies X to the device, applies,
  * copies Y back, and synchronises `stream` before returning.  Pinned host
  * memory gives full copy bandwidth; pageable memory also works.  Staging

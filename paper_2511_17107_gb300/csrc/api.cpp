@@ -176,6 +176,22 @@ pcx_status pcx_apply(pcx_ctx* c, const double k[3], double gamma, const void* X,
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply", e);
 }
 
+pcx_status pcx_apply_noalloc(pcx_ctx* c, const double k[3], double gamma, const void* X, void* Y, int nvec,
+                             int precision, void* stream) {
+  pcx_status st = check_block(c, "pcx_apply_noalloc", X, Y, nvec, precision);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k) return inval(c, "pcx_apply_noalloc: NULL k");
+  const size_t per_vec = (size_t)c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  if (per_vec > (size_t)PCX_NOALLOC_SCRATCH_BYTES)
+    return inval(c, "pcx_apply_noalloc: N^3 scratch entries of one vector (" + std::to_string(per_vec) +
+                        " bytes) exceed the 32 MiB static scratch; use pcx_apply");
+  const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
+  if (ranges_overlap(X, bytes, Y, bytes)) return inval(c, "pcx_apply_noalloc: X and Y overlap");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  cudaError_t e = pcx::launch_apply_noalloc(c, kp, X, Y, nvec, precision, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply_noalloc", e);
+}
+
 pcx_status pcx_apply_host(pcx_ctx* c, const double k[3], double gamma, const void* Xh, void* Yh, int nvec,
                           int precision, void* stream) {
   pcx_status st = check_block(c, "pcx_apply_host", Xh, Yh, nvec, precision);

@@ -29,8 +29,16 @@
 // small DFTs in registers.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "cx.cuh"
 #include "pcx_internal.h"
+
+// Scratch of pcx_apply_noalloc: a file-scope device array, present on every
+// GPU that loads the library until the process exits.  Host code must not
+// use this name as an address: the device address comes from
+// cudaGetSymbolAddress (noalloc_scratch below).
+static __device__ __align__(256) unsigned char g_apply_noalloc_scratch[PCX_NOALLOC_SCRATCH_BYTES];
 
 namespace pcx {
 namespace {
@@ -431,6 +439,41 @@ cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void
                                  void* scratch, cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
   const int chunk = apply_chunk(c, precision);
+  return precision == PCX_FP64 ? dispatch_apply<double>(c, kp, X, Y, nvec, chunk, scratch, s)
+                               : dispatch_apply<float>(c, kp, X, Y, nvec, chunk, scratch, s);
+}
+
+// Device address of g_apply_noalloc_scratch on the current device, looked up
+// once per device (the first pcx_apply_noalloc call on that device).
+static cudaError_t noalloc_scratch(void** out) {
+  static std::mutex mu;
+  static void* ptr[256] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_apply_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    ptr[dev] = p;
+  }
+  *out = ptr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_apply_noalloc(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
+                                 cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const size_t per_vec = (size_t)c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  if (per_vec > (size_t)PCX_NOALLOC_SCRATCH_BYTES) return cudaErrorInvalidValue;
+  void* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return e;
+  int chunk = apply_chunk(c, precision);
+  const int fit = (int)((size_t)PCX_NOALLOC_SCRATCH_BYTES / per_vec);
+  if (chunk > fit) chunk = fit;
   return precision == PCX_FP64 ? dispatch_apply<double>(c, kp, X, Y, nvec, chunk, scratch, s)
                                : dispatch_apply<float>(c, kp, X, Y, nvec, chunk, scratch, s);
 }

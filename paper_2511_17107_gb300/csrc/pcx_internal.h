@@ -86,6 +86,10 @@ cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, 
 // apply with caller-provided scratch of apply_scratch_bytes(c, precision, nvec) bytes
 cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
                                  int precision, void* scratch, cudaStream_t s);
+// apply with the file-scope device scratch (pcx_apply_noalloc); returns
+// cudaErrorInvalidValue if one vector's scratch exceeds PCX_NOALLOC_SCRATCH_BYTES
+cudaError_t launch_apply_noalloc(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
+                                 int precision, cudaStream_t s);
 int apply_chunk(const pcx_ctx* c, int precision);
 size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec);
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec,

@@ -72,6 +72,7 @@ def lib():
             "pcx_symbols": (st, [vp, dp, C.c_double, dp, dp, dp, dp]),
             "pcx_set_apply_chunk": (st, [vp, C.c_int]),
             "pcx_apply": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+            "pcx_apply_noalloc": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_apply_host": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
@@ -90,7 +91,7 @@ def lib():
 
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
-                        "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_apply", "pcx_apply_host", "pcx_precond",
+                        "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
                         "pcx_gram", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
 
@@ -253,6 +254,18 @@ def pcx_apply(ctx, k, X, Y, gamma=0.0, stream=None):
     nvec = X.shape[0] if X.dim() == 5 else X.numel() // ctx.vector_length
     _check(lib().pcx_apply(ctx.handle, kp, float(gamma), _devptr(X), _devptr(Y), nvec, prec, _stream(stream)),
            ctx.handle)
+    return Y
+
+
+def pcx_apply_noalloc(ctx, k, X, Y, gamma=0.0, stream=None):
+    """pcx_apply without any device allocation (static 32 MiB scratch)."""
+    kk, kp = _kvec(k)
+    prec = _prec_of(X)
+    if Y.dtype != X.dtype or Y.shape != X.shape:
+        raise ValueError("X and Y must have the same dtype and shape")
+    nvec = X.shape[0] if X.dim() == 5 else X.numel() // ctx.vector_length
+    _check(lib().pcx_apply_noalloc(ctx.handle, kp, float(gamma), _devptr(X), _devptr(Y), nvec, prec,
+                                   _stream(stream)), ctx.handle)
     return Y
 
 
