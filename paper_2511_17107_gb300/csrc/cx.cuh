@@ -3,6 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace pcx {
 
 template <typename T>
@@ -53,15 +56,33 @@ __host__ __device__ constexpr double cos16(int m) {
 }
 __host__ __device__ constexpr double sin16(int m) { return cos16((m + 12) & 15); }
 
-// b * exp(DIR * 2 pi i m / 16) with the trivial factors done exactly.
-template <int DIR, typename T>
-__device__ __forceinline__ cx<T> rot16(cx<T> b, int m) {
-  if (m == 0) return b;
-  if (m == 4) return DIR > 0 ? mk(-b.y, b.x) : mk(b.y, -b.x);
-  if (m == 8) return mk(-b.x, -b.y);
-  if (m == 12) return DIR > 0 ? mk(b.y, -b.x) : mk(-b.y, b.x);
-  const T c = (T)cos16(m), s = (T)(DIR * sin16(m));
-  return mk(fma(b.x, c, -b.y * s), fma(b.x, s, b.y * c));
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0..COUNT-1.
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int COUNT, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, COUNT>{});
+}
+
+// b * exp(DIR * 2 pi i M / 16), M a compile-time constant; the factors 1,
+// +-i and -1 are applied exactly.
+template <int DIR, int M, typename T>
+__device__ __forceinline__ cx<T> rot16(cx<T> b) {
+  if constexpr (M == 0) {
+    return b;
+  } else if constexpr (M == 4) {
+    return DIR > 0 ? mk(-b.y, b.x) : mk(b.y, -b.x);
+  } else if constexpr (M == 8) {
+    return mk(-b.x, -b.y);
+  } else if constexpr (M == 12) {
+    return DIR > 0 ? mk(b.y, -b.x) : mk(-b.y, b.x);
+  } else {
+    constexpr double cd = cos16(M), sd = DIR * sin16(M);
+    const T c = (T)cd, s = (T)sd;
+    return mk(fma(b.x, c, -b.y * s), fma(b.x, s, b.y * c));
+  }
 }
 
 __host__ __device__ constexpr int bitrev(int i, int bits) {
@@ -73,28 +94,27 @@ __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n
 
 // In-register DFT of length R (power of two, <= 16):
 //   V[s] = sum_r v[r] exp(DIR * 2 pi i r s / R)
-// by radix-2 decimation in time (bit-reversed load, log2 R butterfly stages).
+// by radix-2 decimation in time (bit-reversed load, log2 R butterfly
+// stages); every index and twiddle is a compile-time constant.
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void dft(cx<T>* v) {
   constexpr int B = ilog2(R);
   cx<T> t[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) t[i] = v[bitrev(i, B)];
-#pragma unroll
-  for (int len = 2; len <= R; len <<= 1) {
-#pragma unroll
-    for (int i = 0; i < R; i += len) {
-#pragma unroll
-      for (int k = 0; k < len / 2; ++k) {
-        cx<T> a = t[i + k];
-        cx<T> b = rot16<DIR>(t[i + k + len / 2], k * (16 / len));
-        t[i + k] = a + b;
-        t[i + k + len / 2] = a - b;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < R; ++i) v[i] = t[i];
+  static_for<R>([&](auto i) { t[decltype(i)::value] = v[bitrev(decltype(i)::value, B)]; });
+  static_for<B>([&](auto lg) {
+    constexpr int LEN = 2 << decltype(lg)::value;
+    static_for<R / LEN>([&](auto blk) {
+      static_for<LEN / 2>([&](auto kk) {
+        constexpr int K = decltype(kk)::value;
+        constexpr int A = decltype(blk)::value * LEN + K;
+        const cx<T> a = t[A];
+        const cx<T> b = rot16<DIR, K * (16 / LEN)>(t[A + LEN / 2]);
+        t[A] = a + b;
+        t[A + LEN / 2] = a - b;
+      });
+    });
+  });
+  static_for<R>([&](auto i) { v[decltype(i)::value] = t[decltype(i)::value]; });
 }
 
 }  // namespace pcx

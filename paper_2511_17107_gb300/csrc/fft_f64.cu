@@ -1,0 +1,8 @@
+// complex128 instantiation of the apply and preconditioner kernels.
+#include "fft_kernels.cuh"
+
+namespace pcx {
+template cudaError_t run_apply_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
+                                         cudaStream_t);
+template cudaError_t run_precond_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, cudaStream_t);
+}  // namespace pcx

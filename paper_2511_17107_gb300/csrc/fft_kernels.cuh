@@ -1,0 +1,486 @@
+// Kernels of the matrix-free apply of the compensated operator in the
+// Fourier basis (Sec. 2.4 eq. matrixfree_kcform with the factorisation of
+// Prop. 2.8) and of the FFT-diagonal preconditioner (eqs. matrixfree_diagP,
+// matrixfree_finalform):
+//
+//   u = K_A^H x = -conj(kappa) x x          (per Fourier mode)
+//   e = F3 u                                 (inverse DFT, positive exponent)
+//   m = M e / N^3                            (per cell, Sec. 3.2.1 M_Trivial)
+//   w = DFT(m)                               (negative exponent)
+//   y = K_A w + gamma K_B x = kappa x w + gamma conj(kappa) (kappa . x)
+//
+// Five pencil passes, each a batch of 1D FFTs along one axis in shared
+// memory, with the pointwise stages fused where all three components of a
+// mode or a cell are at hand:
+//   pass 1  x: C^H on load (and gamma kappa.x to scratch), inverse FFT
+//   pass 2  y: inverse FFT
+//   pass 3  z: inverse FFT, M sandwich, forward FFT
+//   pass 4  y: forward FFT
+//   pass 5  x: forward FFT, C w + gamma conj(kappa) (kappa.x) on store
+// A CTA holds T pencils x 3 components x N points.  The 1D FFTs are Stockham
+// radix-R stages (Govindaraju et al., SC 2008 formulation) with the small
+// DFTs in registers.  Along y and z, where consecutive pencils are
+// consecutive in memory, the first stage reads straight from global memory
+// and the last stage writes straight to it; along x the tile is staged
+// through shared memory with 16-byte accesses.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "cx.cuh"
+#include "pcx_internal.h"
+
+namespace pcx {
+namespace fftk {
+
+enum { OP_PRE = 0, OP_INV = 1, OP_SANDWICH = 2, OP_FWD = 3, OP_POST = 4 };
+
+// Radix plans: elements held per thread per stage E (16 complex floats or 8
+// complex doubles), radices R0..R2 with N = R0 R1 R2 and every R <= E.
+template <int N, int E>
+struct Plan;
+template <> struct Plan<8, 16> { static constexpr int R0 = 8, R1 = 0, R2 = 0, NST = 1; };
+template <> struct Plan<16, 16> { static constexpr int R0 = 16, R1 = 0, R2 = 0, NST = 1; };
+template <> struct Plan<32, 16> { static constexpr int R0 = 8, R1 = 4, R2 = 0, NST = 2; };
+template <> struct Plan<64, 16> { static constexpr int R0 = 8, R1 = 8, R2 = 0, NST = 2; };
+template <> struct Plan<128, 16> { static constexpr int R0 = 16, R1 = 8, R2 = 0, NST = 2; };
+template <> struct Plan<256, 16> { static constexpr int R0 = 16, R1 = 16, R2 = 0, NST = 2; };
+template <> struct Plan<8, 8> { static constexpr int R0 = 8, R1 = 0, R2 = 0, NST = 1; };
+template <> struct Plan<16, 8> { static constexpr int R0 = 4, R1 = 4, R2 = 0, NST = 2; };
+template <> struct Plan<32, 8> { static constexpr int R0 = 8, R1 = 4, R2 = 0, NST = 2; };
+template <> struct Plan<64, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 0, NST = 2; };
+template <> struct Plan<128, 8> { static constexpr int R0 = 8, R1 = 4, R2 = 4, NST = 3; };
+template <> struct Plan<256, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 4, NST = 3; };
+
+template <typename T, int N>
+struct Cfg {
+  static constexpr int E = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int TN = sizeof(T) == 4 ? 2048 : 1024;        // pencils x points per component
+  static constexpr int TP = (TN / N < N * N) ? TN / N : N * N;   // pencils per CTA
+  static constexpr int THREADS = 3 * TP * N / E;
+  static constexpr int CS = N * (TP + 1);                          // padded component stride
+  // tile + twiddles + Lambda tables + kappa parts (3N per point, 3TP per pencil)
+  static constexpr size_t SMEM = (size_t)(3 * CS + 3 * N + 3 * N + 3 * TP) * sizeof(cx<T>);
+  using P = Plan<N, E>;
+  static constexpr int RL = P::NST == 1 ? P::R0 : (P::NST == 2 ? P::R1 : P::R2);   // last radix
+};
+
+struct PassArgs {
+  const void* in;
+  void* out;
+  void* sbuf;          // [chunk][N^3]: gamma (kappa . x), written by pass 1, read by pass 5
+  const void* lam;     // [2][N] Lambda_1, Lambda_0
+  const void* tw;      // [N] exp(-2 pi i m / N)
+  const void* M;       // [9][N^3] dense cell blocks (when mid == nullptr)
+  const void* mid;     // [N^3] uchar4 material ids (E1, E2, E3, V)
+  const void* mtab;    // [n_mat][9] block entries per material
+  int n_mat;
+  KParams kp;
+};
+
+template <typename T, int N, int AXIS>
+struct Tile {
+  static constexpr int TP = Cfg<T, N>::TP;
+  static constexpr int CS = Cfg<T, N>::CS;
+  static constexpr int SN = TP + 1;    // shared-memory stride between points of a pencil
+  // shared-memory index of (component c, local pencil t, point n): pencils
+  // fastest, odd row stride, so that both pencil-fastest and point-fastest
+  // walks are free of bank conflicts
+  static __device__ __forceinline__ int sidx(int c, int t, int n) { return c * CS + n * SN + t; }
+  // element offset (within one component block) of pencil q, point n
+  static __device__ __forceinline__ int gidx(int q, int n) {
+    if constexpr (AXIS == 0) return q * N + n;                           // q = z*N + y
+    else if constexpr (AXIS == 1) return (q / N) * N * N + n * N + (q % N);   // q = z*N + x
+    else return n * N * N + q;                                           // q = y*N + x
+  }
+  static constexpr int GSTRIDE = AXIS == 0 ? 1 : (AXIS == 1 ? N : N * N);   // offset step of n
+};
+
+// kappa_i(p) = sum_j b_ji (L1(p_j) + i kt_j L0(p_j)) + i kq_i L0(p_i)
+template <typename T>
+__device__ __forceinline__ void kappa_at(const cx<T>* lam, int n, const KParams& kp, int p1, int p2, int p3,
+                                         cx<T> kap[3]) {
+  const int p[3] = {p1, p2, p3};
+  cx<T> s[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const cx<T> l1 = lam[p[j]], l0 = lam[n + p[j]];
+    const T kt = (T)kp.kt[j];
+    s[j] = mk(fma(-kt, l0.y, l1.x), fma(kt, l0.x, l1.y));
+  }
+  if (kp.diag_b) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) kap[i] = scale(s[i], (T)kp.b[4 * i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      kap[i] = mk((T)0, (T)0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        kap[i] = mk(fma((T)kp.b[3 * j + i], s[j].x, kap[i].x), fma((T)kp.b[3 * j + i], s[j].y, kap[i].y));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (kp.kq[i] != 0.0) {
+      const cx<T> l0 = lam[n + p[i]];
+      const T kq = (T)kp.kq[i];
+      kap[i] = mk(fma(-kq, l0.y, kap[i].x), fma(kq, l0.x, kap[i].y));
+    }
+  }
+}
+
+// two consecutive complex numbers, one 16-byte access for complex64
+template <typename T>
+__device__ __forceinline__ void ld2(const cx<T>* p, cx<T>& a, cx<T>& b) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = mk(v.x, v.y);
+    b = mk(v.z, v.w);
+  } else {
+    a = p[0];
+    b = p[1];
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st2(cx<T>* p, cx<T> a, cx<T> b) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
+}
+
+// Stockham stage of radix R (Ns = product of the radices already done).
+// SRC: 0 = shared memory, 1 = global (first stage only, Ns = 1).
+// DST: 0 = shared memory, 1 = global (last stage only, Ns = N / R).
+// Threads walk butterflies with the pencil index fastest.
+template <typename T, int N, int AXIS, int R, int DIR, int SRC, int DST>
+__device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const cx<T>* gin, cx<T>* gout, int qb) {
+  using C = Cfg<T, N>;
+  using TL = Tile<T, N, AXIS>;
+  constexpr int TP = C::TP;
+  constexpr int NB = N / R;
+  constexpr int PER = C::E / R;
+  constexpr int N3 = N * N * N;
+  cx<T> v[PER][R];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int w = threadIdx.x + i * C::THREADS;
+    const int t = w % TP, j = (w / TP) % NB, c = w / (TP * NB);
+    if constexpr (SRC == 1) {
+      const cx<T>* g = gin + (c * N3 + TL::gidx(qb + t, j));
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = g[r * NB * TL::GSTRIDE];
+    } else {
+      const cx<T>* sp = s + TL::sidx(c, t, j);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = sp[r * NB * TL::SN];
+    }
+  }
+  if constexpr (SRC == 0 && DST == 0) __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int w = threadIdx.x + i * C::THREADS;
+    const int t = w % TP, j = (w / TP) % NB, c = w / (TP * NB);
+    const int k = j % Ns;
+    if (SRC == 0 && Ns > 1) {
+      const int step = N / (Ns * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cx<T> wt = tw[r * k * step];
+        if (DIR > 0) wt.y = -wt.y;
+        v[i][r] = v[i][r] * wt;
+      }
+    }
+    dft<R, DIR>(v[i]);
+    const int base = (j / Ns) * Ns * R + k;
+    if constexpr (DST == 1) {
+      cx<T>* g = gout + (c * N3 + TL::gidx(qb + t, base));
+#pragma unroll
+      for (int r = 0; r < R; ++r) g[r * Ns * TL::GSTRIDE] = v[i][r];
+    } else {
+      cx<T>* sp = s + TL::sidx(c, t, base);
+#pragma unroll
+      for (int r = 0; r < R; ++r) sp[r * Ns * TL::SN] = v[i][r];
+    }
+  }
+  if constexpr (DST == 0) __syncthreads();
+}
+
+// Full 1D transform of the tile.  FROM_G: the first stage reads global
+// memory; TO_G: the last stage writes global memory.
+template <typename T, int N, int AXIS, int DIR, int FROM_G, int TO_G>
+__device__ __forceinline__ void fft_tile(cx<T>* s, const cx<T>* tw, const cx<T>* gin, cx<T>* gout, int qb) {
+  using P = typename Cfg<T, N>::P;
+  if constexpr (P::NST == 1) {
+    stage<T, N, AXIS, P::R0, DIR, FROM_G, TO_G>(s, tw, 1, gin, gout, qb);
+  } else if constexpr (P::NST == 2) {
+    stage<T, N, AXIS, P::R0, DIR, FROM_G, 0>(s, tw, 1, gin, gout, qb);
+    stage<T, N, AXIS, P::R1, DIR, 0, TO_G>(s, tw, P::R0, gin, gout, qb);
+  } else {
+    stage<T, N, AXIS, P::R0, DIR, FROM_G, 0>(s, tw, 1, gin, gout, qb);
+    stage<T, N, AXIS, P::R1, DIR, 0, 0>(s, tw, P::R0, gin, gout, qb);
+    stage<T, N, AXIS, P::R2, DIR, 0, TO_G>(s, tw, P::R0 * P::R1, gin, gout, qb);
+  }
+}
+
+template <typename T, int N, int AXIS, int OP>
+__global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
+  using C = Cfg<T, N>;
+  using TL = Tile<T, N, AXIS>;
+  constexpr int TP = C::TP;
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = s + 3 * C::CS;
+  cx<T>* ka = tw + N;          // [3][N]  kappa_i part that depends on p1
+  cx<T>* kb = ka + 3 * N;      // [TP][3] kappa_i part that depends on the pencil (p2, p3)
+  T* mtab = reinterpret_cast<T*>(kb + 3 * TP);
+
+  const size_t q0 = (size_t)blockIdx.x * TP;       // first pencil (counted across the chunk's vectors)
+  const size_t v = q0 / N2;
+  const int qb = (int)(q0 % N2);
+  const cx<T>* in = static_cast<const cx<T>*>(a.in) + v * 3 * N3;
+  cx<T>* out = static_cast<cx<T>*>(a.out) + v * 3 * N3;
+
+  const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
+  for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = gtw[i];
+  if constexpr (AXIS == 0) {
+    // kappa_i(p) = sum_j b_ji S_j(p_j) + i kq_i L0(p_i),  S_j = L1 + i kt_j L0,
+    // split as ka_i(p1) + kb_i(p2, p3)
+    const cx<T>* glam = static_cast<const cx<T>*>(a.lam);
+    for (int e = threadIdx.x; e < 3 * N + 3 * TP; e += C::THREADS) {
+      if (e < 3 * N) {
+        const int i = e / N, p = e % N;
+        const cx<T> l1 = glam[p], l0 = glam[N + p];
+        const T b0 = (T)a.kp.b[i];   // b_1i (row j = 0)
+        const T kt = (T)a.kp.kt[0];
+        cx<T> r = mk(b0 * fma(-kt, l0.y, l1.x), b0 * fma(kt, l0.x, l1.y));
+        if (i == 0) r = mk(fma(-(T)a.kp.kq[0], l0.y, r.x), fma((T)a.kp.kq[0], l0.x, r.y));
+        ka[e] = r;
+      } else {
+        const int f = e - 3 * N, t = f / 3, i = f % 3;
+        const int q = qb + t, p[3] = {0, q % N, q / N};
+        cx<T> r = mk((T)0, (T)0);
+#pragma unroll
+        for (int j = 1; j < 3; ++j) {
+          const cx<T> l1 = glam[p[j]], l0 = glam[N + p[j]];
+          const T bj = (T)a.kp.b[3 * j + i], kt = (T)a.kp.kt[j];
+          r = mk(fma(bj, fma(-kt, l0.y, l1.x), r.x), fma(bj, fma(kt, l0.x, l1.y), r.y));
+          if (i == j) r = mk(fma(-(T)a.kp.kq[j], l0.y, r.x), fma((T)a.kp.kq[j], l0.x, r.y));
+        }
+        kb[3 * t + i] = r;
+      }
+    }
+  }
+  if constexpr (OP == OP_SANDWICH) {
+    if (a.mid) {
+      const T* gt = static_cast<const T*>(a.mtab);
+      for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) mtab[i] = gt[i];
+    }
+  }
+
+  if constexpr (AXIS == 0) {
+    // ---- x-axis passes: staged through shared memory, points fastest ----
+    __syncthreads();   // tables visible
+    if constexpr (OP == OP_PRE) {
+      // u = -conj(kappa) x x per mode, and gamma kappa.x to the scratch
+      cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
+      const T gam = (T)a.kp.gamma;
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        const int g = TL::gidx(qb + t, n);
+        const cx<T> x0 = in[g], x1 = in[N3 + g], x2 = in[2 * N3 + g];
+        cx<T> kap[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
+        sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), gam);
+        const cx<T> z = mk((T)0, (T)0);
+        s[TL::sidx(0, t, n)] = cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, z), (T)-1));
+        s[TL::sidx(1, t, n)] = cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, z), (T)-1));
+        s[TL::sidx(2, t, n)] = cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, z), (T)-1));
+      }
+      __syncthreads();
+      fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, qb);
+      for (int e = threadIdx.x; e < 3 * TP * N; e += C::THREADS) {
+        const int c = e / (TP * N), rem = e % (TP * N), t = rem / N, n = rem % N;
+        out[c * N3 + TL::gidx(qb + t, n)] = s[TL::sidx(c, t, n)];
+      }
+    } else {   // OP_POST
+      for (int e = threadIdx.x; e < 3 * TP * N; e += C::THREADS) {
+        const int c = e / (TP * N), rem = e % (TP * N), t = rem / N, n = rem % N;
+        s[TL::sidx(c, t, n)] = in[c * N3 + TL::gidx(qb + t, n)];
+      }
+      __syncthreads();
+      fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, qb);
+      const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        const int g = TL::gidx(qb + t, n);
+        const cx<T> sk = sb[g];
+        cx<T> kap[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
+        const cx<T> w0 = s[TL::sidx(0, t, n)], w1 = s[TL::sidx(1, t, n)], w2 = s[TL::sidx(2, t, n)];
+        out[g] = cfma_conj(kap[0], sk, cfma(kap[1], w2, scale(kap[2] * w1, (T)-1)));
+        out[N3 + g] = cfma_conj(kap[1], sk, cfma(kap[2], w0, scale(kap[0] * w2, (T)-1)));
+        out[2 * N3 + g] = cfma_conj(kap[2], sk, cfma(kap[0], w1, scale(kap[1] * w0, (T)-1)));
+      }
+    }
+  } else if constexpr (OP == OP_SANDWICH) {
+    // ---- z-axis: inverse FFT, per-cell M (Sec. 3.2.1), forward FFT ----
+    __syncthreads();
+    fft_tile<T, N, 2, +1, 1, 0>(s, tw, in, nullptr, qb);
+    const T* M = static_cast<const T*>(a.M);
+    const uchar4* mid = static_cast<const uchar4*>(a.mid);
+    const T inv_n3 = (T)(1.0 / (double)N3);
+    for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {   // pencils fastest
+      const int t = w % TP, n = w / TP;
+      const int cell = n * N2 + (qb + t);   // (x, y, z) = (q % N, q / N, n)
+      T d1, d2, d3;
+      cx<T> o12, o13, o23;
+      if (mid) {
+        const uchar4 id = mid[cell];
+        d1 = mtab[9 * id.x];
+        d2 = mtab[9 * id.y + 1];
+        d3 = mtab[9 * id.z + 2];
+        const T* o = mtab + 9 * id.w;
+        o12 = mk(o[3], o[4]);
+        o13 = mk(o[5], o[6]);
+        o23 = mk(o[7], o[8]);
+      } else {
+        d1 = M[cell];
+        d2 = M[N3 + cell];
+        d3 = M[2 * N3 + cell];
+        o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
+        o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
+        o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
+      }
+      const int i0 = TL::sidx(0, t, n), i1 = TL::sidx(1, t, n), i2 = TL::sidx(2, t, n);
+      const cx<T> e0 = s[i0], e1 = s[i1], e2 = s[i2];
+      const cx<T> m0 = cfma(o13, e2, cfma(o12, e1, scale(e0, d1)));
+      const cx<T> m1 = cfma(o23, e2, cfma_conj(o12, e0, scale(e1, d2)));
+      const cx<T> m2 = cfma_conj(o23, e1, cfma_conj(o13, e0, scale(e2, d3)));
+      s[i0] = scale(m0, inv_n3);
+      s[i1] = scale(m1, inv_n3);
+      s[i2] = scale(m2, inv_n3);
+    }
+    __syncthreads();
+    fft_tile<T, N, 2, -1, 0, 1>(s, tw, nullptr, out, qb);
+  } else {
+    // ---- y-axis passes: straight from global and back ----
+    __syncthreads();
+    constexpr int DIR = OP == OP_INV ? +1 : -1;
+    fft_tile<T, N, 1, DIR, 1, 1>(s, tw, in, out, qb);
+  }
+}
+
+// W = K_P^{-1} R per mode: r/|k|^2 + (1/gamma - 1) conj(k) (k . r) / |k|^4.
+template <typename T>
+__global__ void precond_kernel(const cx<T>* __restrict__ R, cx<T>* __restrict__ W, const cx<T>* __restrict__ lam,
+                               int n, int nvec, KParams kp) {
+  const size_t n3 = (size_t)n * n * n;
+  const size_t total = n3 * nvec;
+  const T cg = (T)(1.0 / kp.gamma - 1.0);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = e / n3, mode = e % n3;
+    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    cx<T> kap[3];
+    kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
+    const size_t base = v * 3 * n3 + mode;
+    const cx<T> r0 = R[base], r1 = R[base + n3], r2 = R[base + 2 * n3];
+    const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+    cx<T> w0, w1, w2;
+    if (k2 > (T)0) {
+      const T ik2 = (T)1 / k2;
+      cx<T> sk = cfma(kap[2], r2, cfma(kap[1], r1, kap[0] * r0));
+      sk = scale(sk, cg * ik2 * ik2);
+      w0 = cfma_conj(kap[0], sk, scale(r0, ik2));
+      w1 = cfma_conj(kap[1], sk, scale(r1, ik2));
+      w2 = cfma_conj(kap[2], sk, scale(r2, ik2));
+    } else {
+      w0 = w1 = w2 = mk((T)0, (T)0);
+    }
+    W[base] = w0;
+    W[base + n3] = w1;
+    W[base + 2 * n3] = w2;
+  }
+}
+
+template <typename T, int N, int AXIS, int OP>
+cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st) {
+  auto kern = pass_kernel<T, N, AXIS, OP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)tiles, Cfg<T, N>::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
+                        cudaStream_t st) {
+  using C = Cfg<T, N>;
+  const bool dbl = sizeof(T) == 8;
+  const int n_mat = c->dev.mid ? c->dev.n_mat : 0;
+  const size_t smem = C::SMEM + (size_t)9 * n_mat * sizeof(T);
+  PassArgs a;
+  a.lam = dbl ? c->dev.lam64 : c->dev.lam32;
+  a.tw = dbl ? c->dev.tw64 : c->dev.tw32;
+  a.M = dbl ? c->dev.m64 : c->dev.m32;
+  a.mid = c->dev.mid;
+  a.mtab = dbl ? c->dev.mtab64 : c->dev.mtab32;
+  a.n_mat = n_mat;
+  a.kp = kp;
+  a.sbuf = sbuf;
+  const size_t vlen = (size_t)3 * N * N * N;
+  for (int v0 = 0; v0 < nvec; v0 += chunk) {
+    const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
+    const size_t tiles = (size_t)nv * N * N / C::TP;
+    const cx<T>* x = static_cast<const cx<T>*>(X) + (size_t)v0 * vlen;
+    cx<T>* y = static_cast<cx<T>*>(Y) + (size_t)v0 * vlen;
+    cudaError_t e;
+    a.in = x;
+    a.out = y;
+    if ((e = launch_pass<T, N, 0, OP_PRE>(a, tiles, smem, st)) != cudaSuccess) return e;
+    a.in = y;
+    if ((e = launch_pass<T, N, 1, OP_INV>(a, tiles, smem, st)) != cudaSuccess) return e;
+    if ((e = launch_pass<T, N, 2, OP_SANDWICH>(a, tiles, smem, st)) != cudaSuccess) return e;
+    if ((e = launch_pass<T, N, 1, OP_FWD>(a, tiles, smem, st)) != cudaSuccess) return e;
+    if ((e = launch_pass<T, N, 0, OP_POST>(a, tiles, smem, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace fftk
+
+template <typename T>
+cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
+                        cudaStream_t st) {
+  switch (c->n) {
+    case 8: return fftk::run_apply_n<T, 8>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 16: return fftk::run_apply_n<T, 16>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 32: return fftk::run_apply_n<T, 32>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 64: return fftk::run_apply_n<T, 64>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 128: return fftk::run_apply_n<T, 128>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 256: return fftk::run_apply_n<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t run_precond_t(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, cudaStream_t s) {
+  const size_t total = (size_t)c->n * c->n * c->n * nvec;
+  const int threads = 256;
+  size_t blocks = (total + threads - 1) / threads;
+  if (blocks > 152u * 16u) blocks = 152u * 16u;
+  const void* lam = sizeof(T) == 8 ? c->dev.lam64 : c->dev.lam32;
+  fftk::precond_kernel<T><<<(unsigned)blocks, threads, 0, s>>>(static_cast<const cx<T>*>(R), static_cast<cx<T>*>(W),
+                                                               static_cast<const cx<T>*>(lam), c->n, nvec, kp);
+  return cudaGetLastError();
+}
+
+}  // namespace pcx
