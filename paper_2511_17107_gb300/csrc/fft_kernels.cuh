@@ -58,7 +58,9 @@ struct Cfg {
   static constexpr int TN = sizeof(T) == 4 ? 2048 : 1024;        // pencils x points per component
   static constexpr int TP = (TN / N < N * N) ? TN / N : N * N;   // pencils per CTA
   static constexpr int THREADS = 3 * TP * N / E;
-  static constexpr int CS = N * (TP + 1);                          // padded component stride
+  // padded component stride: y/z tiles use N rows of TP + 1, x tiles TP
+  // pencils of N + 8 (see Tile)
+  static constexpr int CS = N * TP + (N > 8 * TP ? N : 8 * TP);
   // tile + twiddles + Lambda tables + kappa parts (3N per point, 3TP per pencil)
   static constexpr size_t SMEM = (size_t)(3 * CS + 3 * N + 3 * N + 3 * TP) * sizeof(cx<T>);
   using P = Plan<N, E>;
@@ -82,11 +84,19 @@ template <typename T, int N, int AXIS>
 struct Tile {
   static constexpr int TP = Cfg<T, N>::TP;
   static constexpr int CS = Cfg<T, N>::CS;
-  static constexpr int SN = TP + 1;    // shared-memory stride between points of a pencil
-  // shared-memory index of (component c, local pencil t, point n): pencils
-  // fastest, odd row stride, so that both pencil-fastest and point-fastest
-  // walks are free of bank conflicts
-  static __device__ __forceinline__ int sidx(int c, int t, int n) { return c * CS + n * SN + t; }
+  // y/z tiles: pencils fastest, odd row stride TP + 1 (conflict-free for
+  // pencil-fastest and point-fastest walks).
+  static constexpr int SN = TP + 1;
+  // x tiles: points fastest within a pencil, pencil stride N + 8 (= 8 mod 16)
+  // and the point index XOR-swizzled inside each group of 16, n ^ (n>>4 & 15),
+  // so that radix-R writes at stride R, reads at stride N/R and point-fastest
+  // walks all hit distinct banks.
+  static constexpr int SP = N + 8;
+  static __device__ __forceinline__ int swz(int n) { return N >= 32 ? (n ^ ((n >> 4) & 15)) : n; }
+  static __device__ __forceinline__ int sidx(int c, int t, int n) {
+    if constexpr (AXIS == 0) return c * CS + t * SP + swz(n);
+    else return c * CS + n * SN + t;
+  }
   // element offset (within one component block) of pencil q, point n
   static __device__ __forceinline__ int gidx(int q, int n) {
     if constexpr (AXIS == 0) return q * N + n;                           // q = z*N + y
@@ -94,6 +104,19 @@ struct Tile {
     else return n * N * N + q;                                           // q = y*N + x
   }
   static constexpr int GSTRIDE = AXIS == 0 ? 1 : (AXIS == 1 ? N : N * N);   // offset step of n
+  // butterfly walk: x tiles points fastest (coalesced global access along
+  // x), y/z tiles pencils fastest
+  static __device__ __forceinline__ void item(int w, int nb, int& t, int& j, int& c) {
+    if constexpr (AXIS == 0) {
+      j = w % nb;
+      t = (w / nb) % TP;
+      c = w / (nb * TP);
+    } else {
+      t = w % TP;
+      j = (w / TP) % nb;
+      c = w / (TP * nb);
+    }
+  }
 };
 
 // kappa_i(p) = sum_j b_ji (L1(p_j) + i kt_j L0(p_j)) + i kq_i L0(p_i)
@@ -160,19 +183,21 @@ template <typename T, int N, int AXIS, int R, int DIR, int SRC, int DST>
 __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const cx<T>* gin, cx<T>* gout, int qb) {
   using C = Cfg<T, N>;
   using TL = Tile<T, N, AXIS>;
-  constexpr int TP = C::TP;
   constexpr int NB = N / R;
   constexpr int PER = C::E / R;
   constexpr int N3 = N * N * N;
   cx<T> v[PER][R];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    const int w = threadIdx.x + i * C::THREADS;
-    const int t = w % TP, j = (w / TP) % NB, c = w / (TP * NB);
+    int t, j, c;
+    TL::item(threadIdx.x + i * C::THREADS, NB, t, j, c);
     if constexpr (SRC == 1) {
       const cx<T>* g = gin + (c * N3 + TL::gidx(qb + t, j));
 #pragma unroll
       for (int r = 0; r < R; ++r) v[i][r] = g[r * NB * TL::GSTRIDE];
+    } else if constexpr (AXIS == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = s[TL::sidx(c, t, j + r * NB)];
     } else {
       const cx<T>* sp = s + TL::sidx(c, t, j);
 #pragma unroll
@@ -182,8 +207,8 @@ __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const c
   if constexpr (SRC == 0 && DST == 0) __syncthreads();
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    const int w = threadIdx.x + i * C::THREADS;
-    const int t = w % TP, j = (w / TP) % NB, c = w / (TP * NB);
+    int t, j, c;
+    TL::item(threadIdx.x + i * C::THREADS, NB, t, j, c);
     const int k = j % Ns;
     if (SRC == 0 && Ns > 1) {
       const int step = N / (Ns * R);
@@ -200,6 +225,9 @@ __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const c
       cx<T>* g = gout + (c * N3 + TL::gidx(qb + t, base));
 #pragma unroll
       for (int r = 0; r < R; ++r) g[r * Ns * TL::GSTRIDE] = v[i][r];
+    } else if constexpr (AXIS == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) s[TL::sidx(c, t, base + r * Ns)] = v[i][r];
     } else {
       cx<T>* sp = s + TL::sidx(c, t, base);
 #pragma unroll
@@ -303,18 +331,9 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
         s[TL::sidx(2, t, n)] = cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, z), (T)-1));
       }
       __syncthreads();
-      fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, qb);
-      for (int e = threadIdx.x; e < 3 * TP * N; e += C::THREADS) {
-        const int c = e / (TP * N), rem = e % (TP * N), t = rem / N, n = rem % N;
-        out[c * N3 + TL::gidx(qb + t, n)] = s[TL::sidx(c, t, n)];
-      }
+      fft_tile<T, N, 0, +1, 0, 1>(s, tw, nullptr, out, qb);
     } else {   // OP_POST
-      for (int e = threadIdx.x; e < 3 * TP * N; e += C::THREADS) {
-        const int c = e / (TP * N), rem = e % (TP * N), t = rem / N, n = rem % N;
-        s[TL::sidx(c, t, n)] = in[c * N3 + TL::gidx(qb + t, n)];
-      }
-      __syncthreads();
-      fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, qb);
+      fft_tile<T, N, 0, -1, 1, 0>(s, tw, in, nullptr, qb);
       const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
       for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
         const int t = e / N, n = e % N;
