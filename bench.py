@@ -31,6 +31,10 @@ BLOCK = 16
 K_INDEX = 5
 WORKLOAD = "diamond-rods 128^3 FCC, block of 16 vectors, complex64 apply (pcx_apply)"
 METRIC = "compensated-operator applies/s at 128^3"
+# DRAM bytes of one vector through the five pass kernels (sum over the five
+# launches of one chunk), from the ncu capture summarised in
+# profiles/apply_pass_kernels_diamond128_c64.md; None once the kernels change.
+TRAFFIC_BYTES_PER_VECTOR_128_C64 = 292.67e6
 UNIT = "vector-applies/s"
 
 
@@ -273,11 +277,15 @@ def main():
                    "N": n, "block": block, "k_index": K_INDEX,
                    "l2": "inputs larger than L2 (805 MB per block)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "pcx_apply pass chain (5 launches)", "peak_kind": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": (TRAFFIC_BYTES_PER_VECTOR_128_C64 * block
+                                 if (n, es) == (N, 8) and TRAFFIC_BYTES_PER_VECTOR_128_C64 else None),
+                     "kernel": "pcx_apply pass chain (5 pass kernels per chunk of vectors)",
+                     "peak_kind": peak_kind + " (burst HBM copy)",
                      "algorithmic_bytes_per_launch": abytes},
         "e2e": e2e,
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 5 * -(-block // pcx.pcx_get_apply_chunk(ctx, pcx.PCX_FP32 if es == 8 else pcx.PCX_FP64))
+                        * args.steps,
         "clocks": ck,
     }
     if rank == 0 and not args.no_cpu_baseline:

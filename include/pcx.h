@@ -180,6 +180,10 @@ pcx_status pcx_symbols(const pcx_ctx* ctx, const double k[3], double gamma,
  */
 pcx_status pcx_set_apply_chunk(pcx_ctx* ctx, int chunk);
 
+/* The chunk pcx_apply uses for `precision` (vectors per five-pass sweep);
+ * one call launches 5 * ceil(nvec / chunk) kernels.  0 if ctx is NULL. */
+int pcx_get_apply_chunk(const pcx_ctx* ctx, int precision);
+
 /*
  * pcx_apply -- Y = Op_F X for a block of nvec vectors (device, stream-ordered).
  *

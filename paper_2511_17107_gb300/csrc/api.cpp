@@ -164,6 +164,8 @@ pcx_status pcx_set_apply_chunk(pcx_ctx* c, int chunk) {
   return PCX_OK;
 }
 
+int pcx_get_apply_chunk(const pcx_ctx* c, int precision) { return c ? pcx::apply_chunk(c, precision) : 0; }
+
 pcx_status pcx_apply(pcx_ctx* c, const double k[3], double gamma, const void* X, void* Y, int nvec, int precision,
                      void* stream) {
   pcx_status st = check_block(c, "pcx_apply", X, Y, nvec, precision);

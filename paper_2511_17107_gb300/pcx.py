@@ -71,6 +71,7 @@ def lib():
             "pcx_cell_blocks": (st, [vp, dp, dp]),
             "pcx_symbols": (st, [vp, dp, C.c_double, dp, dp, dp, dp]),
             "pcx_set_apply_chunk": (st, [vp, C.c_int]),
+            "pcx_get_apply_chunk": (C.c_int, [vp, C.c_int]),
             "pcx_apply": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_apply_noalloc": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_apply_host": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
@@ -91,7 +92,7 @@ def lib():
 
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
-                        "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
+                        "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
                         "pcx_gram", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
 
@@ -244,6 +245,10 @@ def pcx_symbols(ctx, k, gamma=0.0):
 
 def pcx_set_apply_chunk(ctx, chunk):
     _check(lib().pcx_set_apply_chunk(ctx.handle, int(chunk)), ctx.handle)
+
+
+def pcx_get_apply_chunk(ctx, precision):
+    return int(lib().pcx_get_apply_chunk(ctx.handle, int(precision)))
 
 
 def pcx_apply(ctx, k, X, Y, gamma=0.0, stream=None):
