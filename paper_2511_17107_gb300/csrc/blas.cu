@@ -206,6 +206,12 @@ unsigned grid_for(size_t work, int threads, unsigned cap = 152u * 32u) {
 
 cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision, double* G,
                         cudaStream_t s) {
+  if (precision == PCX_FP32 && L > 0 && gram_tc_supported(na, nb, L)) return launch_gram_tc(A, na, B, nb, L, G, s);
+  return launch_gram_cuda_cores(A, na, B, nb, L, precision, G, s);
+}
+
+cudaError_t launch_gram_cuda_cores(const void* A, int na, const void* B, int nb, size_t L, int precision, double* G,
+                                   cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * 2 * (size_t)na * nb, s);
   if (e != cudaSuccess) return e;
   if (L == 0) return cudaSuccess;

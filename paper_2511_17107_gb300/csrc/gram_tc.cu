@@ -1,0 +1,281 @@
+// Gram products of complex64 column blocks on the tensor cores:
+//   G = A^H B,  G_ij = sum_l conj(A_i[l]) B_j[l]
+// (the Rayleigh-Ritz Gram matrices of the block eigensolver, Sec. 4).
+//
+// The complex product is a real one over stacked rows:
+//   D = [Ar; Ai] [Br; Bi]^T  (contracted over l),
+//   Re G = D[i][j] + D[na+i][nb+j],  Im G = D[i][nb+j] - D[na+i][j].
+// D (M = 128 rows >= 2 na, N = NP columns >= 2 nb) accumulates in TMEM with
+// tcgen05.mma kind::tf32.  FP32 inputs are split into TF32 hi + lo parts
+// (round to nearest) and D += hi*hi + hi*lo + lo*hi, which keeps about the
+// precision of FP32 products.  Every CTA contracts a contiguous range of l in
+// chunks of KC rows staged in shared memory (double-buffered, tracked by two
+// mbarriers); raw FP32 chunks arrive through cp.async two chunks ahead of
+// their conversion.  Each CTA's FP32 partial D goes to global memory and a
+// second kernel sums the partials of all CTAs in FP64.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "cx.cuh"
+#include "pcx_internal.h"
+#include "tc.cuh"
+
+namespace pcx {
+namespace {
+
+constexpr int KC = 32;        // rows of l per stage (4 MMAs of K = 8)
+constexpr int MT = 128;       // M of the MMA: rows [Ar; Ai] padded
+constexpr int TMEM_COLS = 128;
+constexpr int NRAW = 3;       // raw FP32 chunk buffers (prefetch distance 2)
+constexpr int THREADS = 256;
+constexpr long WAIT_LIMIT = 1L << 22;   // mbarrier polls before giving up
+
+// Operand tile of R rows x KC tf32: core matrix (row group g, K group kk) at
+// kk * LBO + g * 128 bytes, rows 16 bytes apart inside it.  LBO = 16 R + 16
+// makes stores that walk K (one row, 32 consecutive k) hit 32 banks.
+__host__ __device__ constexpr int tile_lbo(int rows) { return 16 * rows + 16; }
+__host__ __device__ constexpr int tile_bytes(int rows) { return (KC / 4) * tile_lbo(rows); }
+__device__ __forceinline__ int tile_off(int rows, int row, int k) {
+  return (k >> 2) * tile_lbo(rows) + (row >> 3) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+struct GramArgs {
+  const float2* A;
+  const float2* B;
+  int na, nb, np;       // np = N of the MMA (multiple of 16, >= 2 nb)
+  int same;             // A == B and na == nb: one set of tiles serves both operands
+  size_t L;
+  long chunks_per_cta;
+  long nchunks;
+  float* partial;       // [gridDim.x][MT][np]
+  int* err;
+};
+
+// write hi/lo TF32 parts of one complex entry of column `col` at k
+__device__ __forceinline__ void put(unsigned char* hi, unsigned char* lo, int rows, int col, int ncol, int k,
+                                    float2 v) {
+  const float hr = tc::to_tf32(v.x), hm = tc::to_tf32(v.y);
+  const float lr = tc::to_tf32(v.x - hr), lm = tc::to_tf32(v.y - hm);
+  const int o0 = tile_off(rows, col, k), o1 = tile_off(rows, ncol + col, k);
+  *reinterpret_cast<float*>(hi + o0) = hr;
+  *reinterpret_cast<float*>(hi + o1) = hm;
+  *reinterpret_cast<float*>(lo + o0) = lr;
+  *reinterpret_cast<float*>(lo + o1) = lm;
+}
+
+__global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(GramArgs g) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int abytes = tile_bytes(MT);
+  const int bbytes = g.same ? 0 : tile_bytes(g.np);
+  const int stage_bytes = 2 * abytes + 2 * bbytes;
+  const int ncol = g.same ? g.na : g.na + g.nb;       // raw columns per chunk
+  const int raw_bytes = ncol * KC * 8;
+  unsigned char* raw0 = sm + 2 * stage_bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(raw0 + NRAW * raw_bytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid / 32;
+
+  // zero the tiles once (padding rows stay zero), allocate TMEM, init barriers
+  for (int i = tid; i < stage_bytes * 2 / 16; i += THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  if (warp == 0) tc::tmem_alloc<TMEM_COLS>(tslot);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::mbar_fence_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  const long c0 = (long)blockIdx.x * g.chunks_per_cta;
+  const long c1 = c0 + g.chunks_per_cta < g.nchunks ? c0 + g.chunks_per_cta : g.nchunks;
+  const long nfill = c1 > c0 ? c1 - c0 : 0;
+  const uint32_t idesc = tc::idesc_tf32(MT, g.np);
+
+  // raw chunk f -> buffer f % NRAW: column c (A columns, then B columns), KC
+  // complex numbers contiguous per column, 16-byte pieces
+  auto prefetch = [&](long f) {
+    if (f >= nfill) return;
+    unsigned char* rb = raw0 + (f % NRAW) * raw_bytes;
+    const size_t l0 = (size_t)(c0 + f) * KC;
+    for (int e = tid; e < ncol * (KC / 2); e += THREADS) {
+      const int col = e / (KC / 2), piece = e % (KC / 2);
+      const size_t l = l0 + 2 * piece;
+      const float2* base = col < g.na ? g.A + (size_t)col * g.L : g.B + (size_t)(col - g.na) * g.L;
+      const uint32_t bytes = l + 2 <= g.L ? 16u : (l < g.L ? 8u : 0u);
+      tc::cp_async16(rb + (size_t)(col * KC + 2 * piece) * 8, base + (l < g.L ? l : 0), bytes);
+    }
+  };
+  prefetch(0);
+  tc::cp_async_commit();
+  prefetch(1);
+  tc::cp_async_commit();
+
+  bool ok = true;
+  long issued = 0;
+  for (long f = 0; f < nfill && ok; ++f) {
+    prefetch(f + 2);
+    tc::cp_async_commit();
+    tc::cp_async_wait<2>();                      // this thread's copies of chunk f are done
+    const int s = (int)(f & 1);
+    const long use = f >> 1;                     // earlier fills of tile buffer s
+    const bool w_ok = use < 1 || tc::mbar_wait(&mbar[s], (uint32_t)((use - 1) & 1), WAIT_LIMIT);
+    if (!__syncthreads_and(w_ok)) {              // block-uniform; also publishes the raw chunk
+      ok = false;
+      break;
+    }
+    unsigned char* ahi = sm + s * stage_bytes;
+    unsigned char* alo = ahi + abytes;
+    unsigned char* bhi = alo + abytes;
+    unsigned char* blo = bhi + bbytes;
+    const float2* rb = reinterpret_cast<const float2*>(raw0 + (f % NRAW) * raw_bytes);
+    for (int e = tid; e < ncol * KC; e += THREADS) {
+      const int col = e / KC, k = e % KC;
+      const float2 v = rb[e];
+      if (col < g.na) put(ahi, alo, MT, col, g.na, k, v);
+      else put(bhi, blo, g.np, col - g.na, g.nb, k, v);
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a_hi = tc::smem_addr(ahi), a_lo = tc::smem_addr(alo);
+      const uint32_t b_hi = g.same ? a_hi : tc::smem_addr(bhi), b_lo = g.same ? a_lo : tc::smem_addr(blo);
+      const uint32_t alb = tile_lbo(MT), blb = g.same ? tile_lbo(MT) : tile_lbo(g.np);
+#pragma unroll
+      for (int ks = 0; ks < KC / 8; ++ks) {
+        const uint32_t ao = 2 * ks * alb, bo = 2 * ks * blb;
+        const uint64_t dah = tc::smem_desc(a_hi + ao, alb, 128), dal = tc::smem_desc(a_lo + ao, alb, 128);
+        const uint64_t dbh = tc::smem_desc(b_hi + bo, blb, 128), dbl = tc::smem_desc(b_lo + bo, blb, 128);
+        tc::mma_tf32(tmem, dah, dbh, idesc, issued > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
+        tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
+        ++issued;
+      }
+      tc::mma_commit(&mbar[s]);
+    }
+  }
+  tc::cp_async_wait<0>();
+  // the last commit covers every MMA issued by thread 0
+  bool last_ok = true;
+  if (nfill > 0) {
+    const int s_last = (int)((nfill - 1) & 1);
+    const long use_last = (nfill - 1) >> 1;
+    last_ok = tc::mbar_wait(&mbar[s_last], (uint32_t)(use_last & 1), ok ? WAIT_LIMIT : WAIT_LIMIT / 16);
+  }
+  ok = __syncthreads_and(ok && last_ok);
+  tc::fence_after_sync();
+  if (!ok) {
+    if (tid == 0) atomicExch(g.err, 1);
+  } else if (warp < 4) {
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of D)
+    const int row = warp * 32 + (tid & 31);
+    float* out = g.partial + ((size_t)blockIdx.x * MT + row) * g.np;
+    for (int cb = 0; cb < g.np; cb += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+      if (nfill == 0) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) out[cb + i] = v[i];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc<TMEM_COLS>(tmem);
+}
+
+// G[i][j] = sum over CTAs of the stacked-real products (FP64).
+__global__ void gram_reduce_kernel(const float* __restrict__ partial, int nctas, int na, int nb, int np,
+                                   const int* __restrict__ err, double* __restrict__ G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= na * nb) return;
+  const int i = idx / nb, j = idx % nb;
+  double re = 0.0, im = 0.0;
+  for (int c = 0; c < nctas; ++c) {
+    const float* p = partial + (size_t)c * MT * np;
+    re += (double)p[i * np + j] + (double)p[(na + i) * np + nb + j];
+    im += (double)p[i * np + nb + j] - (double)p[(na + i) * np + j];
+  }
+  if (*err) re = im = __longlong_as_double(0x7ff8000000000000LL);   // NaN: the kernel gave up
+  G[2 * idx] = re;
+  G[2 * idx + 1] = im;
+}
+
+struct Scratch {
+  std::mutex mu;
+  void* partial[64] = {nullptr};
+  size_t bytes[64] = {0};
+  int* err[64] = {nullptr};
+};
+Scratch& scratch() {
+  static Scratch s;
+  return s;
+}
+
+}  // namespace
+
+// 16-byte cp.async pieces need even column lengths (16-byte aligned columns)
+bool gram_tc_supported(int na, int nb, size_t L) {
+  return na >= 1 && nb >= 1 && 2 * na <= MT && 2 * nb <= TMEM_COLS && L % 2 == 0;
+}
+
+cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s) {
+  if (!gram_tc_supported(na, nb, L)) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  GramArgs g;
+  g.A = static_cast<const float2*>(A);
+  g.B = static_cast<const float2*>(B);
+  g.na = na;
+  g.nb = nb;
+  g.same = (A == B && na == nb) ? 1 : 0;
+  g.np = g.same ? MT : ((2 * nb + 15) / 16) * 16;
+  g.L = L;
+  g.nchunks = (long)((L + KC - 1) / KC);
+  long nctas = 8L * sms;   // short FP32 accumulation chains; partials are summed in FP64
+  if (nctas > g.nchunks) nctas = g.nchunks > 0 ? g.nchunks : 1;
+  g.chunks_per_cta = (g.nchunks + nctas - 1) / nctas;
+  nctas = g.nchunks > 0 ? (g.nchunks + g.chunks_per_cta - 1) / g.chunks_per_cta : 1;
+  const size_t pbytes = (size_t)nctas * MT * g.np * sizeof(float);
+  Scratch& sc = scratch();
+  {
+    std::lock_guard<std::mutex> lock(sc.mu);
+    if (!sc.err[dev]) {
+      if ((e = cudaMalloc(&sc.err[dev], sizeof(int))) != cudaSuccess) return e;
+    }
+    if (pbytes > sc.bytes[dev]) {
+      if (sc.partial[dev]) {
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+        cudaFree(sc.partial[dev]);
+      }
+      sc.partial[dev] = nullptr;
+      sc.bytes[dev] = 0;
+      if ((e = cudaMalloc(&sc.partial[dev], pbytes)) != cudaSuccess) return e;
+      sc.bytes[dev] = pbytes;
+    }
+    g.partial = static_cast<float*>(sc.partial[dev]);
+    g.err = sc.err[dev];
+  }
+  const int stage_bytes = 2 * tile_bytes(MT) + (g.same ? 0 : 2 * tile_bytes(g.np));
+  const int ncol = g.same ? na : na + nb;
+  const size_t smem = 2 * (size_t)stage_bytes + (size_t)NRAW * ncol * KC * 8 + 64;
+  if ((e = cudaMemsetAsync(g.err, 0, sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  gram_tc_kernel<<<(unsigned)nctas, THREADS, smem, s>>>(g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int total = na * nb;
+  gram_reduce_kernel<<<(total + 127) / 128, 128, 0, s>>>(g.partial, (int)nctas, na, nb, g.np, g.err, G);
+  return cudaGetLastError();
+}
+
+}  // namespace pcx

@@ -94,8 +94,14 @@ int apply_chunk(const pcx_ctx* c, int precision);
 size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec);
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec,
                            int precision, cudaStream_t s);
+// Gram G = A^H B: tensor cores (gram_tc.cu) for complex64 with na, nb <= 64 and even L,
+// CUDA cores (blas.cu) otherwise
 cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision,
                         double* G, cudaStream_t s);
+cudaError_t launch_gram_cuda_cores(const void* A, int na, const void* B, int nb, size_t L, int precision,
+                                   double* G, cudaStream_t s);
+bool gram_tc_supported(int na, int nb, size_t L);
+cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s);
 cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, double beta, void* Y,
                            size_t L, int precision, cudaStream_t s);
 cudaError_t launch_residual(const void* X, const void* AX, const double* theta, void* R,

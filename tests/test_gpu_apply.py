@@ -178,3 +178,24 @@ def test_gram_combine_residual(pcx, dtype, na, nb, L):
     nr = norms.cpu().numpy()
     np.testing.assert_allclose(nr[:nb], np.sum(np.abs(R.cpu().numpy().astype(np.complex128)) ** 2, axis=1), rtol=1e-5)
     np.testing.assert_allclose(nr[nb:], np.sum(np.abs(b.astype(np.complex128)) ** 2, axis=1), rtol=1e-5)
+
+
+@pytest.mark.parametrize("same", [True, False])
+@pytest.mark.parametrize("na,nb", [(48, 48), (64, 16), (1, 1)])
+def test_gram_tensor_cores_long_blocks(pcx, same, na, nb):
+    """complex64 Gram products run on the tensor cores (TF32 with error
+    compensation, FP64 sums across CTAs); checked against FP64 products of
+    the same FP32 data over L = 3 * 64^3 rows."""
+    if same:
+        nb = na
+    L = 3 * 64 ** 3
+    rng = np.random.default_rng(na * 7 + nb)
+    a = (rng.standard_normal((na, L)) + 1j * rng.standard_normal((na, L))).astype(np.complex64)
+    b = a if same else (rng.standard_normal((nb, L)) + 1j * rng.standard_normal((nb, L))).astype(np.complex64)
+    A = torch.from_numpy(a).cuda()
+    B = A if same else torch.from_numpy(b).cuda()
+    G = torch.empty((na, nb), dtype=torch.complex128, device="cuda")
+    pcx.pcx_gram(A, B, G)
+    want = a.astype(np.complex128).conj() @ b.astype(np.complex128).T
+    err = np.abs(G.cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= 1e-5, err
