@@ -199,3 +199,21 @@ def test_gram_tensor_cores_long_blocks(pcx, same, na, nb):
     want = a.astype(np.complex128).conj() @ b.astype(np.complex128).T
     err = np.abs(G.cpu().numpy() - want).max() / np.abs(want).max()
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("same", [True, False])
+def test_gram_fp64_on_fp32_pipes(pcx, same):
+    """complex128 Gram products by split FP32 hi/lo products and double-float
+    accumulation, against numpy FP64 products (relative 1e-12 of max|G|)."""
+    na = nb = 48
+    L = 3 * 64 ** 3
+    rng = np.random.default_rng(5 + same)
+    a = rng.standard_normal((na, L)) + 1j * rng.standard_normal((na, L))
+    b = a if same else rng.standard_normal((nb, L)) + 1j * rng.standard_normal((nb, L))
+    A = torch.from_numpy(a).cuda()
+    B = A if same else torch.from_numpy(b).cuda()
+    G = torch.empty((na, nb), dtype=torch.complex128, device="cuda")
+    pcx.pcx_gram(A, B, G)
+    want = a.conj() @ b.T
+    err = np.abs(G.cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= 1e-12, err
