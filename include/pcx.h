@@ -263,8 +263,11 @@ pcx_status pcx_precond(pcx_ctx* ctx, const double k[3], double gamma, const void
  * (interleaved doubles) to the DEVICE buffer G.  The Gram products of the
  * Rayleigh-Ritz step (Sec. 4: LOBPCG).  Column i of A starts at
  * A + i * L elements.  precision PCX_FP32: FP32 products on tensor cores
- * (TF32 with error compensation) accumulated per chunk and summed in FP64;
- * PCX_FP64: FP64 FMA.  1 <= na, nb <= 128.
+ * (tcgen05 TF32 with hi/lo error compensation; na, nb <= 64 and even L,
+ * else CUDA-core FP32) accumulated per chunk and summed in FP64;
+ * PCX_FP64: double-float products and sums on the FP32 pipes (error-free
+ * product and sum transformations, about 2^-44 relative per term) with the
+ * per-block partials summed in FP64.  1 <= na, nb <= 128.
  */
 pcx_status pcx_gram(pcx_ctx* ctx, const void* A, int na, const void* B, int nb, size_t L,
                     int precision, void* G, void* stream);
@@ -303,6 +306,21 @@ pcx_status pcx_residual(pcx_ctx* ctx, const void* X, const void* AX, const doubl
 pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol, double* theta, double* cvec,
                       int* rank);
 
+/* Counters and wall-clock split of one pcx_solve call (summed over k).
+ * Phase times are measured with a stream synchronisation after each phase
+ * when this struct is requested, so they add up to the total. */
+typedef struct {
+  int iters_fp32;        /* LOBPCG iterations with FP32 storage and apply          */
+  int iters_fp64;        /* LOBPCG iterations with FP64 storage and apply          */
+  long long applies_fp32;  /* vectors applied in FP32                                */
+  long long applies_fp64;  /* vectors applied in FP64                                */
+  double ms_total;
+  double ms_apply;       /* pcx_apply work                                          */
+  double ms_gram;        /* Gram products (device) and their transfer to the host  */
+  double ms_rr;          /* host Rayleigh-Ritz and Cholesky                         */
+  double ms_other;       /* preconditioner, combinations, residuals, conversions   */
+} pcx_solve_stats;
+
 /* Eigensolver options (pcx_solve).  Zero-initialised fields take defaults. */
 typedef struct {
   int block;          /* vectors per block (>= nev; default nev + 4)               */
@@ -312,6 +330,7 @@ typedef struct {
   double switch_tol;  /* mixed: switch to FP64 when all Res_j <= this (default 1e-4) */
   uint64_t seed;      /* initial block seed (default 20251117)                     */
   int verbose;        /* print per-iteration residuals to stderr                   */
+  pcx_solve_stats* stats;  /* optional output (host), zeroed and filled by pcx_solve */
 } pcx_solve_opts;
 
 /*

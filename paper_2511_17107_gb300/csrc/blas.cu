@@ -211,6 +211,102 @@ __global__ void __launch_bounds__(256) combine_kernel(const cx<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Combine for complex128 on the FP32 pipes with FP64-level accuracy: the
+// same split / TwoProd / TwoSum scheme as gram_ff_kernel.  Each row's inputs
+// are split once and reused for the CY outputs of the sweep; C is split once
+// per CTA into shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) combine_ff_kernel(const double2* __restrict__ S, int ns,
+                                                         const double* __restrict__ Cm, int ny, int j0, double beta,
+                                                         double2* __restrict__ Y, size_t L) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  float4* c = reinterpret_cast<float4*>(csm);   // [ns][CY]: (re hi, re lo, im hi, im lo)
+  const int nyl = (ny - j0 < CY) ? ny - j0 : CY;
+  for (int e = threadIdx.x; e < ns * CY; e += blockDim.x) {
+    const int i = e / CY, j = e % CY;
+    float4 v = make_float4(0, 0, 0, 0);
+    if (j < nyl) {
+      const double re = Cm[2 * ((size_t)i * ny + j0 + j)], im = Cm[2 * ((size_t)i * ny + j0 + j) + 1];
+      const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+      v = make_float4(rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih));
+    }
+    c[e] = v;
+  }
+  __syncthreads();
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (size_t)gridDim.x * blockDim.x) {
+    DF re[CY], im[CY];
+#pragma unroll
+    for (int j = 0; j < CY; ++j) re[j] = im[j] = DF{0.f, 0.f};
+    for (int i = 0; i < ns; ++i) {
+      const double2 sv = S[(size_t)i * L + l];
+      const float sr = __double2float_rn(sv.x), si = __double2float_rn(sv.y);
+      const float srl = __double2float_rn(sv.x - (double)sr), sil = __double2float_rn(sv.y - (double)si);
+#pragma unroll
+      for (int j = 0; j < CY; ++j) {
+        const float4 cv = c[i * CY + j];
+        // s c: re = sr cr - si ci, im = sr ci + si cr
+        df_add_prod(re[j], sr, srl, cv.x, cv.y, false);
+        df_add_prod(re[j], si, sil, cv.z, cv.w, true);
+        df_add_prod(im[j], sr, srl, cv.z, cv.w, false);
+        df_add_prod(im[j], si, sil, cv.x, cv.y, false);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CY; ++j) {
+      if (j < nyl) {
+        double2* yp = Y + (size_t)(j0 + j) * L + l;
+        double2 r = make_double2((double)re[j].s + (double)re[j].c, (double)im[j].s + (double)im[j].c);
+        if (beta != 0.0) {
+          const double2 y0 = *yp;
+          r.x += beta * y0.x;
+          r.y += beta * y0.y;
+        }
+        *yp = r;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Y64_j += sum_i S32_i C[i][j]: a combination of complex64 columns evaluated
+// in FP32 and added into complex128 columns (the small correction part of a
+// mixed-precision update).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) combine_add32_kernel(const cx<float>* __restrict__ S, int ns,
+                                                            const double* __restrict__ Cm, int ny, int j0,
+                                                            double2* __restrict__ Y, size_t L) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  cx<float>* c = reinterpret_cast<cx<float>*>(csm);
+  const int nyl = (ny - j0 < CY) ? ny - j0 : CY;
+  for (int e = threadIdx.x; e < ns * CY; e += blockDim.x) {
+    const int i = e / CY, j = e % CY;
+    c[e] = (j < nyl) ? mk((float)Cm[2 * ((size_t)i * ny + j0 + j)], (float)Cm[2 * ((size_t)i * ny + j0 + j) + 1])
+                     : mk(0.f, 0.f);
+  }
+  __syncthreads();
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (size_t)gridDim.x * blockDim.x) {
+    cx<float> acc[CY];
+#pragma unroll
+    for (int j = 0; j < CY; ++j) acc[j] = mk(0.f, 0.f);
+    for (int i = 0; i < ns; ++i) {
+      const cx<float> sv = S[(size_t)i * L + l];
+#pragma unroll
+      for (int j = 0; j < CY; ++j) acc[j] = cfma(sv, c[i * CY + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < CY; ++j) {
+      if (j < nyl) {
+        double2* yp = Y + (size_t)(j0 + j) * L + l;
+        double2 y = *yp;
+        y.x += (double)acc[j].x;
+        y.y += (double)acc[j].y;
+        *yp = y;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Residual R_j = AX_j - theta_j X_j with ||R_j||^2 and ||X_j||^2 (FP64).
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -333,14 +429,32 @@ cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, doubl
   const unsigned blocks = grid_for(L, threads, 152u * 8u);
   for (int j0 = 0; j0 < ny; j0 += CY) {
     if (precision == PCX_FP64) {
-      const size_t smem = (size_t)ns * CY * sizeof(cx<double>);
-      combine_kernel<double><<<blocks, threads, smem, s>>>(static_cast<const cx<double>*>(S), ns, C, ny, j0, beta,
-                                                           static_cast<cx<double>*>(Y), L);
+      const size_t smem = (size_t)ns * CY * sizeof(float4);
+      if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(combine_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      combine_ff_kernel<<<grid_for(L, 128, 152u * 16u), 128, smem, s>>>(static_cast<const double2*>(S), ns, C, ny,
+                                                                         j0, beta, static_cast<double2*>(Y), L);
     } else {
       const size_t smem = (size_t)ns * CY * sizeof(cx<float>);
       combine_kernel<float><<<blocks, threads, smem, s>>>(static_cast<const cx<float>*>(S), ns, C, ny, j0, beta,
                                                           static_cast<cx<float>*>(Y), L);
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_combine_add32(const void* S32, int ns, const double* C, int ny, void* Y64, size_t L,
+                                cudaStream_t s) {
+  if (L == 0) return cudaSuccess;
+  const unsigned blocks = grid_for(L, 256, 152u * 8u);
+  for (int j0 = 0; j0 < ny; j0 += CY) {
+    const size_t smem = (size_t)ns * CY * sizeof(cx<float>);
+    combine_add32_kernel<<<blocks, 256, smem, s>>>(static_cast<const cx<float>*>(S32), ns, C, ny, j0,
+                                                   static_cast<double2*>(Y64), L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -104,6 +104,9 @@ bool gram_tc_supported(int na, int nb, size_t L);
 cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s);
 cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, double beta, void* Y,
                            size_t L, int precision, cudaStream_t s);
+// Y64 += S32 C (complex64 combination evaluated in FP32, added into complex128)
+cudaError_t launch_combine_add32(const void* S32, int ns, const double* C, int ny, void* Y64, size_t L,
+                                cudaStream_t s);
 cudaError_t launch_residual(const void* X, const void* AX, const double* theta, void* R,
                             double* norms, int nvec, size_t L, int precision, cudaStream_t s);
 cudaError_t launch_fill_random(void* X, int nvec, size_t L, uint64_t seed, int precision,

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -52,7 +53,24 @@ struct DevBuf {
     if (_e != cudaSuccess) return fail_cuda(_e); \
   } while (0)
 
+// Wall-clock attribution of solver phases (only when statistics are asked
+// for: each tick synchronises the stream and charges the elapsed time).
+struct Times {
+  double apply = 0, gram = 0, rr = 0, other = 0;
+  long long applies = 0;
+};
+
 struct Run {
+  Times* tm = nullptr;
+  std::chrono::steady_clock::time_point own_clock = std::chrono::steady_clock::now();
+  std::chrono::steady_clock::time_point* t0 = &own_clock;   // may be shared between runs
+  void tick(double Times::*bucket) {
+    if (!tm) return;
+    cudaStreamSynchronize(s);
+    const auto t1 = std::chrono::steady_clock::now();
+    tm->*bucket += std::chrono::duration<double, std::milli>(t1 - *t0).count();
+    *t0 = t1;
+  }
   pcx_ctx* c;
   cudaStream_t s;
   int prec;          // PCX_FP32 or PCX_FP64
@@ -62,6 +80,7 @@ struct Run {
   KParams kp;
   bool k_zero;
   int verbose;
+  int np = 0;        // P columns at S[n : n+np] (valid when lobpcg returns)
   // device buffers
   DevBuf S, AS, S2, AS2, R, G, C, theta, norms;
   std::string err;
@@ -88,11 +107,21 @@ struct Run {
 
   // host copy of an m x m Gram matrix computed on the device
   pcx_status gram(const void* A, int na, const void* B, int nb, std::vector<cd>& out) {
+    tick(&Times::other);
     CK(launch_gram(A, na, B, nb, L, prec, static_cast<double*>(G.p), s));
     out.resize((size_t)na * nb);
     CK(cudaMemcpyAsync(out.data(), G.p, sizeof(cd) * na * nb, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    tick(&Times::gram);
     return PCX_OK;
+  }
+
+  cudaError_t apply(const void* X, void* Y, int nvec) {
+    tick(&Times::other);
+    cudaError_t e = launch_apply(c, kp, X, Y, nvec, prec, s);
+    if (tm) tm->applies += nvec;
+    tick(&Times::apply);
+    return e;
   }
 
   pcx_status upload_c(const std::vector<cd>& cm) {
@@ -107,8 +136,9 @@ struct Run {
     pcx_status st = gram(cols, nw, cols, nw, g);
     if (st != PCX_OK) return st;
     ok = cholesky_upper(nw, g, r);
+    if (ok) upper_inverse(nw, r, ri);
+    tick(&Times::rr);
     if (!ok) return PCX_OK;
-    upper_inverse(nw, r, ri);
     if ((st = upload_c(ri)) != PCX_OK) return st;
     CK(launch_combine(cols, nw, static_cast<double*>(C.p), nw, 0.0, tmp, L, prec, s));
     CK(cudaMemcpyAsync(cols, tmp, (size_t)nw * L * es, cudaMemcpyDeviceToDevice, s));
@@ -139,7 +169,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
     run.err = "pcx_solve: initial block is rank deficient";
     return PCX_ENUMERIC;
   }
-  CK(launch_apply(run.c, run.kp, run.S.p, run.AS.p, n, run.prec, run.s));
+  CK(run.apply(run.S.p, run.AS.p, n));
   {
     std::vector<cd> ga, gb;
     if ((st = run.gram(run.S.p, n, run.AS.p, n, ga)) != PCX_OK) return st;
@@ -147,6 +177,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
     std::vector<double> th;
     std::vector<cd> cm;
     int r = gen_eig(n, ga, gb, 1e-14, th, cm);
+    run.tick(&Times::rr);
     if (r < n) {
       run.err = "pcx_solve: initial Rayleigh-Ritz breakdown";
       return PCX_ENUMERIC;
@@ -158,7 +189,8 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
     std::swap(run.S.p, run.S2.p);
     std::swap(run.AS.p, run.AS2.p);
   }
-  int np = 0;   // P columns at S[n : n+np]
+  int& np = run.np;   // P columns at S[n : n+np]
+  np = 0;
   std::vector<double> best_hist;
   double best = INFINITY;
   int since_best = 0;
@@ -219,7 +251,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
         ok = true;
       }
     }
-    CK(launch_apply(run.c, run.kp, run.col(run.S, w0), run.col(run.AS, w0), na, run.prec, run.s));
+    CK(run.apply(run.col(run.S, w0), run.col(run.AS, w0), na));
     // Rayleigh-Ritz on S = [X P W]
     int m = n + np + na;
     std::vector<double> th;
@@ -231,6 +263,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       if ((st = run.gram(run.S.p, m, run.S.p, m, gb)) != PCX_OK) return st;
       const double drop = run.prec == PCX_FP64 ? 1e-13 : 1e-7;
       r = gen_eig(m, ga, gb, drop, th, cm);
+      run.tick(&Times::rr);
       if (r >= n) break;
       if (np == 0) break;
       // drop P and retry: move W down to S[n : n+na]
@@ -276,6 +309,207 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
   }
 }
 
+// Mixed-precision refinement (PCX_FP32 mode, after the FP32 phase): X and
+// AX = Op X are held and updated in FP64, so the residual R = AX - X Theta
+// and the X-X blocks of the Rayleigh-Ritz matrices are FP64-accurate; the
+// search directions W = K_P^{-1} R, P and their images are FP32 with FP32
+// applies and tensor-core Gram products.  An error in a direction block
+// enters the new X scaled by that block's coefficient, which shrinks with
+// the residual, so the FP64 residual keeps converging.  AX is recomputed
+// with an FP64 apply every `refresh` iterations and before convergence is
+// accepted.  r64.S/AS hold [X64 | FP64 copies of P, W]; r32.S/AS hold
+// [X32 | P32 | W32] with X32, AX32 rounded from the FP64 columns.
+pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int& iters, std::vector<double>& theta,
+                         std::vector<double>& res) {
+  Run& run = r64;   // for CK
+  const int n = r64.n;
+  const size_t L = r64.L;
+  pcx_status st;
+  bool ok = true;
+  // X64 from the FP32 block: orthonormalise in FP64, AX64 = Op X64, Rayleigh-Ritz
+  CK(launch_convert(r32.S.p, PCX_FP32, r64.S.p, PCX_FP64, (size_t)n * L, r64.s));
+  if ((st = r64.cholqr(r64.S.p, n, r64.S2.p, ok)) != PCX_OK) return st;
+  if (!ok) {
+    r64.err = "pcx_solve: refinement block is rank deficient";
+    return PCX_ENUMERIC;
+  }
+  auto fresh_ax = [&]() -> pcx_status {
+    CK(r64.apply(r64.S.p, r64.AS.p, n));
+    return PCX_OK;
+  };
+  auto rr_x = [&]() -> pcx_status {   // Rayleigh-Ritz on span(X64), FP64
+    std::vector<cd> ga, gb, cm;
+    std::vector<double> th;
+    pcx_status s2;
+    if ((s2 = r64.gram(r64.S.p, n, r64.AS.p, n, ga)) != PCX_OK) return s2;
+    if ((s2 = r64.gram(r64.S.p, n, r64.S.p, n, gb)) != PCX_OK) return s2;
+    const int r = gen_eig(n, ga, gb, 1e-14, th, cm);
+    r64.tick(&Times::rr);
+    if (r < n) {
+      r64.err = "pcx_solve: refinement Rayleigh-Ritz breakdown";
+      return PCX_ENUMERIC;
+    }
+    theta.assign(th.begin(), th.begin() + n);
+    if ((s2 = r64.upload_c(cm)) != PCX_OK) return s2;
+    CK(launch_combine(r64.S.p, n, static_cast<double*>(r64.C.p), n, 0.0, r64.S2.p, L, PCX_FP64, r64.s));
+    CK(launch_combine(r64.AS.p, n, static_cast<double*>(r64.C.p), n, 0.0, r64.AS2.p, L, PCX_FP64, r64.s));
+    CK(cudaMemcpyAsync(r64.S.p, r64.S2.p, (size_t)n * L * 16, cudaMemcpyDeviceToDevice, r64.s));
+    CK(cudaMemcpyAsync(r64.AS.p, r64.AS2.p, (size_t)n * L * 16, cudaMemcpyDeviceToDevice, r64.s));
+    return PCX_OK;
+  };
+  if ((st = fresh_ax()) != PCX_OK) return st;
+  if ((st = rr_x()) != PCX_OK) return st;
+  int np = r32.np;          // P32 / AP32 from the FP32 phase stay valid directions
+  const int refresh = 20;
+  int since_fresh = 0;
+  res.assign(n, INFINITY);
+  for (iters = 0;; ++iters) {
+    // FP64 residual
+    CK(cudaMemcpyAsync(r64.theta.p, theta.data(), sizeof(double) * n, cudaMemcpyHostToDevice, r64.s));
+    CK(launch_residual(r64.S.p, r64.AS.p, static_cast<double*>(r64.theta.p), r64.R.p,
+                       static_cast<double*>(r64.norms.p), n, L, PCX_FP64, r64.s));
+    std::vector<double> nrm(2 * n);
+    CK(cudaMemcpyAsync(nrm.data(), r64.norms.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, r64.s));
+    CK(cudaStreamSynchronize(r64.s));
+    double worst = 0;
+    for (int j = 0; j < n; ++j) {
+      res[j] = std::sqrt(nrm[j]) / std::sqrt(nrm[n + j]);
+      if (!std::isfinite(res[j]) || !std::isfinite(theta[j])) {
+        r64.err = "pcx_solve: NaN or Inf in the refinement residual";
+        return PCX_ENUMERIC;
+      }
+      if (j < nev) worst = std::max(worst, res[j]);
+    }
+    if (r64.verbose)
+      std::fprintf(stderr, "[pcx] refine it %d worst %.3e theta0 %.12g%s\n", iters, worst, theta[0],
+                   since_fresh == 0 ? " (fresh AX)" : "");
+    if (worst <= tol) {
+      if (since_fresh == 0) return PCX_OK;   // accepted on an exactly recomputed AX
+      if ((st = fresh_ax()) != PCX_OK) return st;
+      since_fresh = 0;
+      --iters;
+      continue;
+    }
+    if (iters >= maxit) return PCX_ENOCONV;
+    if (++since_fresh >= refresh) {   // exact image of the unchanged X; P is kept
+      if ((st = fresh_ax()) != PCX_OK) return st;
+      since_fresh = 0;
+      --iters;
+      continue;
+    }
+    std::vector<int> act;
+    for (int j = 0; j < n; ++j)
+      if (res[j] > tol) act.push_back(j);
+    const int na = (int)act.size();
+    const int w0 = n + np;
+    // X32 rounded from the FP64 columns; W32 = K_P^{-1} R (FP32)
+    CK(launch_convert(r64.S.p, PCX_FP64, r32.S.p, PCX_FP32, (size_t)n * L, r64.s));
+    for (int a = 0; a < na; ++a) {
+      CK(launch_convert(r64.col(r64.R, act[a]), PCX_FP64, r32.col(r32.R, a), PCX_FP32, L, r64.s));
+      CK(launch_precond(r32.c, r32.kp, r32.col(r32.R, a), r32.col(r32.S, w0 + a), 1, PCX_FP32, r64.s));
+    }
+    // [P W] is orthogonalised against X and orthonormalised (Cholesky QR,
+    // two passes) in FP32, so the FP32 part of the Gram matrices is close to
+    // the identity; P is dropped when [P W] is numerically rank deficient.
+    auto orth_block = [&](int c0, int cnt, bool& okb) -> pcx_status {
+      okb = true;
+      for (int pass = 0; pass < 2 && okb; ++pass) {
+        std::vector<cd> xw;
+        pcx_status s2;
+        if ((s2 = r32.gram(r32.S.p, n, r32.col(r32.S, c0), cnt, xw)) != PCX_OK) return s2;
+        for (auto& v : xw) v = -v;
+        if ((s2 = r32.upload_c(xw)) != PCX_OK) return s2;
+        CK(launch_combine(r32.S.p, n, static_cast<double*>(r32.C.p), cnt, 1.0, r32.col(r32.S, c0), L, PCX_FP32,
+                          r64.s));
+        if ((s2 = r32.cholqr(r32.col(r32.S, c0), cnt, r32.col(r32.S2, c0), okb)) != PCX_OK) return s2;
+      }
+      return PCX_OK;
+    };
+    bool okb = true;
+    if ((st = orth_block(n, np + na, okb)) != PCX_OK) return st;
+    if (!okb && np > 0) {
+      CK(cudaMemcpyAsync(r32.col(r32.S, n), r32.col(r32.S, w0), (size_t)na * L * 8, cudaMemcpyDeviceToDevice,
+                         r64.s));
+      np = 0;
+      if ((st = orth_block(n, na, okb)) != PCX_OK) return st;
+    }
+    // (a W block that stays rank deficient is left to the drop tolerance of
+    // the Rayleigh-Ritz step)
+    CK(r32.apply(r32.col(r32.S, n), r32.col(r32.AS, n), np + na));
+    const int m = n + np + na;
+    const int mp = m - n;
+    // Rows of X in FP64: (AX)^H [X P W] and X^H [X P W] with P, W converted
+    // exactly to FP64 (the couplings x^H A w are of the size of the residual,
+    // far below the FP32 error of A w).  The P/W-P/W blocks come from FP32
+    // products on the tensor cores.
+    CK(launch_convert(r32.col(r32.S, n), PCX_FP32, r64.col(r64.S, n), PCX_FP64, (size_t)mp * L, r64.s));
+    std::vector<cd> gxa, gxb, gpa, gpb;
+    if ((st = r64.gram(r64.AS.p, n, r64.S.p, m, gxa)) != PCX_OK) return st;
+    if ((st = r64.gram(r64.S.p, n, r64.S.p, m, gxb)) != PCX_OK) return st;
+    if ((st = r32.gram(r32.col(r32.S, n), mp, r32.col(r32.AS, n), mp, gpa)) != PCX_OK) return st;
+    if ((st = r32.gram(r32.col(r32.S, n), mp, r32.col(r32.S, n), mp, gpb)) != PCX_OK) return st;
+    std::vector<cd> ga((size_t)m * m), gb((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        cd a, b;
+        if (i < n) {
+          a = gxa[(size_t)i * m + j];
+          b = gxb[(size_t)i * m + j];
+        } else if (j < n) {
+          a = std::conj(gxa[(size_t)j * m + i]);
+          b = std::conj(gxb[(size_t)j * m + i]);
+        } else {
+          a = gpa[(size_t)(i - n) * mp + (j - n)];
+          b = gpb[(size_t)(i - n) * mp + (j - n)];
+        }
+        ga[(size_t)i * m + j] = a;
+        gb[(size_t)i * m + j] = b;
+      }
+    std::vector<double> th;
+    std::vector<cd> cm;
+    const int r = gen_eig(m, ga, gb, 1e-7, th, cm);
+    r64.tick(&Times::rr);
+    if (r < n) {
+      // drop P and restart the directions from a fresh FP64 image
+      if ((st = fresh_ax()) != PCX_OK) return st;
+      if ((st = rr_x()) != PCX_OK) return st;
+      since_fresh = 0;
+      np = 0;
+      continue;
+    }
+    // X64' = X64 C_XX + [P32 W32] C_PX ;  AX64' likewise
+    std::vector<cd> cxx((size_t)n * n), cpx((size_t)mp * n);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < n; ++j) {
+        if (i < n) cxx[(size_t)i * n + j] = cm[(size_t)i * r + j];
+        else cpx[(size_t)(i - n) * n + j] = cm[(size_t)i * r + j];
+      }
+    if ((st = r64.upload_c(cxx)) != PCX_OK) return st;
+    CK(launch_combine(r64.S.p, n, static_cast<double*>(r64.C.p), n, 0.0, r64.S2.p, L, PCX_FP64, r64.s));
+    CK(launch_combine(r64.AS.p, n, static_cast<double*>(r64.C.p), n, 0.0, r64.AS2.p, L, PCX_FP64, r64.s));
+    if ((st = r32.upload_c(cpx)) != PCX_OK) return st;
+    CK(launch_combine_add32(r32.col(r32.S, n), m - n, static_cast<double*>(r32.C.p), n, r64.S2.p, L, r64.s));
+    CK(launch_combine_add32(r32.col(r32.AS, n), m - n, static_cast<double*>(r32.C.p), n, r64.AS2.p, L, r64.s));
+    // P32' = [P32 W32] C_P,act (FP32), the part of the new Ritz vectors outside span(X)
+    const int npn = na;
+    {
+      std::vector<cd> cp((size_t)(m - n) * npn);
+      for (int i = n; i < m; ++i)
+        for (int a = 0; a < npn; ++a) cp[(size_t)(i - n) * npn + a] = cm[(size_t)i * r + act[a]];
+      CK(cudaStreamSynchronize(r64.s));
+      if ((st = r32.upload_c(cp)) != PCX_OK) return st;
+      CK(launch_combine(r32.col(r32.S, n), m - n, static_cast<double*>(r32.C.p), npn, 0.0, r32.col(r32.S2, n), L,
+                        PCX_FP32, r64.s));
+    }
+    np = npn;
+    theta.assign(th.begin(), th.begin() + n);
+    std::swap(r64.S.p, r64.S2.p);
+    std::swap(r64.AS.p, r64.AS2.p);
+    std::swap(r32.S.p, r32.S2.p);
+    std::swap(r32.AS.p, r32.AS2.p);
+  }
+}
+
 }  // namespace
 
 pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, const pcx_solve_opts* opts,
@@ -297,13 +531,23 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
   }
   const size_t L = (size_t)3 * c->n * c->n * c->n;
   pcx_status result = PCX_OK;
+  Times t32, t64;
+  int iters32 = 0, iters64 = 0;
+  const auto t_start = std::chrono::steady_clock::now();
+  if (o.stats) std::memset(o.stats, 0, sizeof(*o.stats));
   for (int ik = 0; ik < nk; ++ik) {
     const double* k = kpts + 3 * ik;
     const bool kz = k[0] == 0 && k[1] == 0 && k[2] == 0;
     std::vector<double> theta, res;
     int iters_total = 0;
     pcx_status st;
+    bool refined = false;
+    pcx_status refine_status = PCX_OK;
+    Run r32;
     Run r64;
+    std::chrono::steady_clock::time_point clock = std::chrono::steady_clock::now();
+    r32.t0 = &clock;
+    r64.t0 = &clock;
     r64.c = c;
     r64.s = s;
     r64.prec = PCX_FP64;
@@ -313,12 +557,12 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
     r64.kp = make_kparams(c, k, 0.0);
     r64.k_zero = kz;
     r64.verbose = o.verbose;
+    if (o.stats) r64.tm = &t64;
     if ((st = r64.alloc_all()) != PCX_OK) {
       c->err = r64.err;
       return st;
     }
     if (o.precision == PCX_FP32) {
-      Run r32;
       r32.c = c;
       r32.s = s;
       r32.prec = PCX_FP32;
@@ -328,6 +572,7 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
       r32.kp = r64.kp;
       r32.k_zero = kz;
       r32.verbose = o.verbose;
+      if (o.stats) r32.tm = &t32;
       if ((st = r32.alloc_all()) != PCX_OK) {
         c->err = r32.err;
         return st;
@@ -340,18 +585,28 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
       }
       int it32 = 0;
       bool early = false;
+      *r32.t0 = std::chrono::steady_clock::now();
       st = lobpcg(r32, nev, tol, maxit, switch_tol, it32, theta, res, early);
+      r32.tick(&Times::other);
       iters_total += it32;
+      iters32 += it32;
       if (st != PCX_OK && st != PCX_ENOCONV) {
         c->err = r32.err;
         return st;
       }
-      // refine in FP64 from the FP32 block
-      e = launch_convert(r32.S.p, PCX_FP32, r64.S.p, PCX_FP64, (size_t)n * L, s);
-      if (e != cudaSuccess) {
-        c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
-        return PCX_ECUDA;
+      // refine: X, AX in FP64, directions in FP32
+      int itr = 0;
+      *r64.t0 = std::chrono::steady_clock::now();
+      st = lobpcg_refine(r64, r32, nev, tol, std::max(1, maxit - iters_total), itr, theta, res);
+      r64.tick(&Times::other);
+      iters_total += itr;
+      iters64 += itr;
+      if (st != PCX_OK && st != PCX_ENOCONV) {
+        c->err = r64.err.empty() ? r32.err : r64.err;
+        return st;
       }
+      refined = true;
+      refine_status = st;
     } else {
       cudaError_t e = launch_fill_random(r64.S.p, n, L, seed + ik, PCX_FP64, s);
       if (e == cudaSuccess && kz) e = launch_deflate_p0(r64.S.p, n, c->n, PCX_FP64, s);
@@ -360,10 +615,17 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
         return PCX_ECUDA;
       }
     }
-    int it64 = 0;
-    bool early = false;
-    st = lobpcg(r64, nev, tol, std::max(1, maxit - iters_total), 0.0, it64, theta, res, early);
-    iters_total += it64;
+    if (!refined) {
+      int it64 = 0;
+      bool early = false;
+      *r64.t0 = std::chrono::steady_clock::now();
+      st = lobpcg(r64, nev, tol, std::max(1, maxit - iters_total), 0.0, it64, theta, res, early);
+      r64.tick(&Times::other);
+      iters_total += it64;
+      iters64 += it64;
+    } else {
+      st = refine_status;
+    }
     if (st != PCX_OK && st != PCX_ENOCONV) {
       c->err = r64.err;
       return st;
@@ -390,6 +652,18 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
       c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
       return PCX_ECUDA;
     }
+  }
+  if (o.stats) {
+    pcx_solve_stats& st = *o.stats;
+    st.iters_fp32 = iters32;
+    st.iters_fp64 = iters64;
+    st.applies_fp32 = t32.applies;
+    st.applies_fp64 = t64.applies;
+    st.ms_apply = t32.apply + t64.apply;
+    st.ms_gram = t32.gram + t64.gram;
+    st.ms_rr = t32.rr + t64.rr;
+    st.ms_other = t32.other + t64.other;
+    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   }
   return result;
 }

@@ -40,9 +40,18 @@ class pcx_setup_desc(C.Structure):
                 ("n_shape", C.c_int), ("shapes", C.POINTER(pcx_shape)), ("cell_blocks", C.POINTER(C.c_double))]
 
 
+class pcx_solve_stats(C.Structure):
+    _fields_ = [("iters_fp32", C.c_int), ("iters_fp64", C.c_int), ("applies_fp32", C.c_longlong),
+                ("applies_fp64", C.c_longlong), ("ms_total", C.c_double), ("ms_apply", C.c_double),
+                ("ms_gram", C.c_double), ("ms_rr", C.c_double), ("ms_other", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class pcx_solve_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("maxit", C.c_int), ("precision", C.c_int), ("switch_tol", C.c_double),
-                ("seed", C.c_uint64), ("verbose", C.c_int)]
+                ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats))]
 
 
 _lib = None
@@ -341,11 +350,13 @@ def pcx_rr_eig(ga, gb, drop_tol=1e-13):
 
 
 def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
-              vec_out=None, stream=None, raise_on_noconv=True):
-    """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status)."""
+              vec_out=None, stream=None, raise_on_noconv=True, stats=None):
+    """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status).  Pass a
+    pcx_solve_stats instance as ``stats`` to receive counters and timings."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
     nk = kp.shape[0]
-    o = pcx_solve_opts(block, maxit, precision, switch_tol, seed, verbose)
+    o = pcx_solve_opts(block, maxit, precision, switch_tol, seed, verbose,
+                       C.pointer(stats) if stats is not None else None)
     eig = np.zeros((nk, nev))
     res = np.zeros((nk, nev))
     its = np.zeros(nk, dtype=np.int32)
