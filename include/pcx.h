@@ -273,6 +273,22 @@ pcx_status pcx_gram(pcx_ctx* ctx, const void* A, int na, const void* B, int nb, 
                     int precision, void* G, void* stream);
 
 /*
+ * pcx_gram_mixed -- G = A^H B with A complex128 (na columns) and B complex64
+ * (nb columns), both of length L, written as na x nb complex128 to the
+ * DEVICE buffer G (G[i*nb + j], interleaved doubles).  The X rows of the
+ * Rayleigh-Ritz matrices in the mixed-precision refinement (Sec. 4: LOBPCG
+ * with the block X held in FP64 and the search directions in FP32).
+ * Accuracy: about 2^-44 relative to ||A_i|| ||B_j|| (double-float sums on
+ * the FP32 pipes).  Entries of A must lie inside the FP32 range: magnitudes
+ * below 2^-126 count as 0, magnitudes at or above 2^128 give NaN.  A, B, G
+ * 16-byte aligned device pointers; 1 <= na, nb <= 128.  Uses a per-device
+ * scratch buffer owned by the library: concurrent calls on different streams
+ * of one device must be serialised by the caller.
+ */
+pcx_status pcx_gram_mixed(pcx_ctx* ctx, const void* A, int na, const void* B, int nb, size_t L, void* G,
+                          void* stream);
+
+/*
  * pcx_combine -- Y_j = sum_i S_i C[i*ny + j]  (+ beta * Y_j if beta != 0):
  * tall x small product of the Rayleigh-Ritz update (Sec. 4: LOBPCG).
  * S: ns columns of length L; C: DEVICE ns x ny complex128; Y: ny columns;

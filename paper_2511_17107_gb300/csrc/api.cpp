@@ -243,6 +243,15 @@ pcx_status pcx_gram(pcx_ctx* c, const void* A, int na, const void* B, int nb, si
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_gram", e);
 }
 
+pcx_status pcx_gram_mixed(pcx_ctx* c, const void* A, int na, const void* B, int nb, size_t L, void* G, void* stream) {
+  if (na < 1 || nb < 1 || na > 128 || nb > 128) return inval(c, "pcx_gram_mixed: need 1 <= na, nb <= 128");
+  if (!A || !B || !G || !aligned16(A) || !aligned16(B) || !aligned16(G))
+    return inval(c, "pcx_gram_mixed: NULL or misaligned buffer");
+  cudaError_t e = pcx::launch_gram_x(A, na, nullptr, 0, B, nb, L, static_cast<double*>(G),
+                                     static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_gram_mixed", e);
+}
+
 pcx_status pcx_combine(pcx_ctx* c, const void* S, int ns, const void* C, int ny, double beta, void* Y, size_t L,
                        int precision, void* stream) {
   if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, "pcx_combine: bad precision");

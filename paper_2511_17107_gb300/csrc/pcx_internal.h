@@ -101,6 +101,10 @@ cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, 
 cudaError_t launch_gram_cuda_cores(const void* A, int na, const void* B, int nb, size_t L, int precision,
                                    double* G, cudaStream_t s);
 bool gram_tc_supported(int na, int nb, size_t L);
+// G = [A1 | A2]^H B: A1 (na1 columns) and A2 (na2 columns) complex128, B
+// complex64; double-float accumulation on the FP32 pipes.
+cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, const void* B, int nb, size_t L,
+                          double* G, cudaStream_t s);
 cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s);
 cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, double beta, void* Y,
                            size_t L, int precision, cudaStream_t s);

@@ -311,14 +311,17 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
 
 // Mixed-precision refinement (PCX_FP32 mode, after the FP32 phase): X and
 // AX = Op X are held and updated in FP64, so the residual R = AX - X Theta
-// and the X-X blocks of the Rayleigh-Ritz matrices are FP64-accurate; the
-// search directions W = K_P^{-1} R, P and their images are FP32 with FP32
-// applies and tensor-core Gram products.  An error in a direction block
-// enters the new X scaled by that block's coefficient, which shrinks with
-// the residual, so the FP64 residual keeps converging.  AX is recomputed
-// with an FP64 apply every `refresh` iterations and before convergence is
-// accepted.  r64.S/AS hold [X64 | FP64 copies of P, W]; r32.S/AS hold
-// [X32 | P32 | W32] with X32, AX32 rounded from the FP64 columns.
+// is FP64-accurate; the search directions W = K_P^{-1} R, P and their images
+// are FP32 with FP32 applies.  The Rayleigh-Ritz matrices take their X rows
+// from double-float products of the FP64 X, AX with the FP32 directions
+// (launch_gram_x), their P/W blocks from tensor-core FP32 products, and their
+// X-X blocks from the previous step (Theta, I).  [P W] is orthonormalised
+// against X in FP32 each step.  An error in a direction block enters the new
+// X scaled by that block's coefficient, which shrinks with the residual, so
+// the FP64 residual keeps converging.  AX is recomputed with an FP64 apply,
+// followed by a Rayleigh-Ritz step on X, every `refresh` iterations and
+// before convergence is accepted.  r64.S/AS hold X64/AX64; r32.S/AS hold
+// [X32 | P32 | W32] and their images, X32 rounded from X64.
 pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int& iters, std::vector<double>& theta,
                          std::vector<double>& res) {
   Run& run = r64;   // for CK
@@ -386,13 +389,15 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     if (worst <= tol) {
       if (since_fresh == 0) return PCX_OK;   // accepted on an exactly recomputed AX
       if ((st = fresh_ax()) != PCX_OK) return st;
+      if ((st = rr_x()) != PCX_OK) return st;
       since_fresh = 0;
       --iters;
       continue;
     }
     if (iters >= maxit) return PCX_ENOCONV;
-    if (++since_fresh >= refresh) {   // exact image of the unchanged X; P is kept
+    if (++since_fresh >= refresh) {   // exact image of X and Rayleigh-Ritz on X; P is kept
       if ((st = fresh_ax()) != PCX_OK) return st;
+      if ((st = rr_x()) != PCX_OK) return st;
       since_fresh = 0;
       --iters;
       continue;
@@ -438,26 +443,36 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     CK(r32.apply(r32.col(r32.S, n), r32.col(r32.AS, n), np + na));
     const int m = n + np + na;
     const int mp = m - n;
-    // Rows of X in FP64: (AX)^H [X P W] and X^H [X P W] with P, W converted
-    // exactly to FP64 (the couplings x^H A w are of the size of the residual,
-    // far below the FP32 error of A w).  The P/W-P/W blocks come from FP32
-    // products on the tensor cores.
-    CK(launch_convert(r32.col(r32.S, n), PCX_FP32, r64.col(r64.S, n), PCX_FP64, (size_t)mp * L, r64.s));
-    std::vector<cd> gxa, gxb, gpa, gpb;
-    if ((st = r64.gram(r64.AS.p, n, r64.S.p, m, gxa)) != PCX_OK) return st;
-    if ((st = r64.gram(r64.S.p, n, r64.S.p, m, gxb)) != PCX_OK) return st;
+    // Rows of X: X^H [P W] and (AX)^H [P W] from FP64 X, AX against the FP32
+    // directions with double-float sums (these couplings are of the size of
+    // the residual, far below the FP32 rounding of the products).  The X-X
+    // blocks are Theta and I: X and AX are the Ritz vectors and images of the
+    // previous Rayleigh-Ritz step (or of rr_x after an exact refresh).  The
+    // P/W-P/W blocks come from FP32 products on the tensor cores.
+    std::vector<cd> gx, gpa, gpb;
+    {
+      r64.tick(&Times::other);
+      CK(launch_gram_x(r64.S.p, n, r64.AS.p, n, r32.col(r32.S, n), mp, L, static_cast<double*>(r64.G.p), r64.s));
+      gx.resize((size_t)2 * n * mp);
+      CK(cudaMemcpyAsync(gx.data(), r64.G.p, sizeof(cd) * gx.size(), cudaMemcpyDeviceToHost, r64.s));
+      CK(cudaStreamSynchronize(r64.s));
+      r64.tick(&Times::gram);
+    }
     if ((st = r32.gram(r32.col(r32.S, n), mp, r32.col(r32.AS, n), mp, gpa)) != PCX_OK) return st;
     if ((st = r32.gram(r32.col(r32.S, n), mp, r32.col(r32.S, n), mp, gpb)) != PCX_OK) return st;
     std::vector<cd> ga((size_t)m * m), gb((size_t)m * m);
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) {
         cd a, b;
-        if (i < n) {
-          a = gxa[(size_t)i * m + j];
-          b = gxb[(size_t)i * m + j];
+        if (i < n && j < n) {
+          a = i == j ? cd(theta[i], 0.0) : cd(0.0, 0.0);
+          b = i == j ? cd(1.0, 0.0) : cd(0.0, 0.0);
+        } else if (i < n) {
+          a = gx[(size_t)(n + i) * mp + (j - n)];
+          b = gx[(size_t)i * mp + (j - n)];
         } else if (j < n) {
-          a = std::conj(gxa[(size_t)j * m + i]);
-          b = std::conj(gxb[(size_t)j * m + i]);
+          a = std::conj(gx[(size_t)(n + j) * mp + (i - n)]);
+          b = std::conj(gx[(size_t)j * mp + (i - n)]);
         } else {
           a = gpa[(size_t)(i - n) * mp + (j - n)];
           b = gpb[(size_t)(i - n) * mp + (j - n)];

@@ -86,6 +86,7 @@ def lib():
             "pcx_apply_host": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
+            "pcx_gram_mixed": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, vp, vp]),
             "pcx_combine": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_double, vp, C.c_size_t, C.c_int, vp]),
             "pcx_residual": (st, [vp, vp, vp, vp, vp, vp, C.c_int, C.c_size_t, C.c_int, vp]),
             "pcx_rr_eig": (st, [C.c_int, dp, dp, C.c_double, dp, dp, ip]),
@@ -102,7 +103,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_gram", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
+                        "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
 
 def _check(status, ctx=None):
@@ -313,6 +314,18 @@ def pcx_gram(A, B, G, L=None, ctx=None, stream=None):
     L = A[0].numel() if L is None else L
     _check(lib().pcx_gram(ctx.handle if ctx else None, _devptr(A), na, _devptr(B), nb, L, _prec_of(A), _devptr(G),
                           _stream(stream)), ctx.handle if ctx else None)
+    return G
+
+
+def pcx_gram_mixed(A, B, G, ctx=None, stream=None):
+    """G (complex128 CUDA tensor, na x nb) = A^H B with A complex128 (na, L) and B complex64 (nb, L)."""
+    import torch
+    na, nb = A.shape[0], B.shape[0]
+    L = A[0].numel()
+    if A.dtype != torch.complex128 or B.dtype != torch.complex64 or B[0].numel() != L:
+        raise ValueError("pcx_gram_mixed: A complex128 and B complex64 with equal column lengths")
+    _check(lib().pcx_gram_mixed(ctx.handle if ctx else None, _devptr(A), na, _devptr(B), nb, L, _devptr(G),
+                                _stream(stream)), ctx.handle if ctx else None)
     return G
 
 

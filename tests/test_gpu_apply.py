@@ -217,3 +217,29 @@ def test_gram_fp64_on_fp32_pipes(pcx, same):
     want = a.conj() @ b.T
     err = np.abs(G.cpu().numpy() - want).max() / np.abs(want).max()
     assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("na,nb,L", [(33, 5, 3 * 17 ** 3), (32, 32, 3 * 64 ** 3), (1, 40, 1), (7, 1, 31)])
+def test_gram_mixed_fp64_fp32(pcx, na, nb, L):
+    """pcx_gram_mixed: complex128 rows against complex64 columns, with the
+    columns of B orthogonalised against A before rounding to FP32 so that
+    G is ~1e-7 of the norms (the cancelling case of the mixed Rayleigh-Ritz
+    rows).  Entries of A span twelve decades and include exact zeros.
+    Absolute error <= 1e-13 of max ||a_i|| ||b_j|| against numpy FP64."""
+    rng = np.random.default_rng(na * 131 + nb + L)
+    scale = 10.0 ** rng.uniform(-8, 4, size=(na, L))
+    a = (rng.standard_normal((na, L)) + 1j * rng.standard_normal((na, L))) * scale
+    a[:, 1::97] = 0.0
+    b = rng.standard_normal((nb, L)) + 1j * rng.standard_normal((nb, L))
+    if na < L:
+        q, _ = np.linalg.qr(a.T)
+        b = b - (b @ q.conj()) @ q.T
+    b32 = b.astype(np.complex64)
+    A = torch.from_numpy(a).cuda()
+    B = torch.from_numpy(b32).cuda()
+    G = torch.empty((na, nb), dtype=torch.complex128, device="cuda")
+    pcx.pcx_gram_mixed(A, B, G)
+    want = a.conj() @ b32.astype(np.complex128).T
+    norm = np.linalg.norm(a, axis=1).max() * np.linalg.norm(b32.astype(np.complex128), axis=1).max()
+    err = np.abs(G.cpu().numpy() - want).max() / norm
+    assert err <= 1e-13, err
