@@ -322,6 +322,18 @@ pcx_status pcx_residual(pcx_ctx* ctx, const void* X, const void* AX, const doubl
 pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol, double* theta, double* cvec,
                       int* rank);
 
+/*
+ * pcx_div_norms -- per column of X (Fourier basis, nvec vectors):
+ *   out[j] = x_j^H K_B x_j = sum over modes |kappa(p) . x_j(p)|^2,
+ *   out[nvec + j] = ||x_j||^2   (DEVICE doubles).
+ * K_B = [K_1^H; K_2^H; K_3^H][K_1 K_2 K_3] is the Fourier form of B^H B
+ * (Prop. 2.8), so out[j] = ||B h_j||^2 for the real-space field h_j = F3_3 x_j:
+ * the penalty share of a Rayleigh quotient is gamma out[j] / (theta out[nvec+j]).
+ * Stream-ordered; X as in pcx_apply.
+ */
+pcx_status pcx_div_norms(pcx_ctx* ctx, const double k[3], const void* X, int nvec, int precision, double* out,
+                         void* stream);
+
 /* Counters and wall-clock split of one pcx_solve call (summed over k).
  * Phase times are measured with a stream synchronisation after each phase
  * when this struct is requested, so they add up to the total. */
@@ -335,6 +347,8 @@ typedef struct {
   double ms_gram;        /* Gram products (device) and their transfer to the host  */
   double ms_rr;          /* host Rayleigh-Ritz and Cholesky                         */
   double ms_other;       /* preconditioner, combinations, residuals, conversions   */
+  int gamma_raises;      /* times the spurious-mode guard raised gamma (all k)     */
+  double gamma_last;     /* penalty coefficient used at the last k                 */
 } pcx_solve_stats;
 
 /* Eigensolver options (pcx_solve).  Zero-initialised fields take defaults. */
@@ -347,6 +361,14 @@ typedef struct {
   uint64_t seed;      /* initial block seed (default 20251117)                     */
   int verbose;        /* print per-iteration residuals to stderr                   */
   pcx_solve_stats* stats;  /* optional output (host), zeroed and filled by pcx_solve */
+  double gamma;       /* penalty coefficient; 0: the rule of Sec. 2 per k
+                         (4 pi^2 if k = 0 or |k| >= 1, else 4 pi^2 / |k|^2)        */
+  double penalty_tol; /* spurious-mode guard: after convergence, a wanted pair
+                         with gamma x^H K_B x / (theta ||x||^2) above this is a
+                         penalty mode (Prop. 2.5: eigenvalue gamma * lambda^B);
+                         gamma is then multiplied by 4 and k re-solved, at most
+                         4 times (then PCX_ENUMERIC).  0: default 1e-6;
+                         negative: guard off                                      */
 } pcx_solve_opts;
 
 /*

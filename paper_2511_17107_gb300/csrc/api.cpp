@@ -233,6 +233,17 @@ pcx_status pcx_precond(pcx_ctx* c, const double k[3], double gamma, const void* 
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_precond", e);
 }
 
+pcx_status pcx_div_norms(pcx_ctx* c, const double k[3], const void* X, int nvec, int precision, double* out,
+                         void* stream) {
+  pcx_status st = check_block(c, "pcx_div_norms", X, X, nvec, precision);
+  if (st != PCX_OK) return st;
+  if (!k || !out) return inval(c, "pcx_div_norms: NULL k or out");
+  if (nvec > 65535) return inval(c, "pcx_div_norms: nvec > 65535");
+  pcx::KParams kp = pcx::make_kparams(c, k, 0.0);
+  cudaError_t e = pcx::launch_div_norms(c, kp, X, nvec, precision, out, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_div_norms", e);
+}
+
 pcx_status pcx_gram(pcx_ctx* c, const void* A, int na, const void* B, int nb, size_t L, int precision, void* G,
                     void* stream) {
   if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, "pcx_gram: bad precision");

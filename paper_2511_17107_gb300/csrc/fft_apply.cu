@@ -21,6 +21,8 @@ cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void
                         cudaStream_t st);
 template <typename T>
 cudaError_t run_precond_t(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, cudaStream_t s);
+template <typename T>
+cudaError_t run_div_norms_t(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, double* out, cudaStream_t s);
 extern template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
                                                cudaStream_t);
 extern template cudaError_t run_apply_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
@@ -113,6 +115,12 @@ cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, v
                            cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
   return precision == PCX_FP64 ? run_precond_t<double>(c, kp, R, W, nvec, s) : run_precond_t<float>(c, kp, R, W, nvec, s);
+}
+
+cudaError_t launch_div_norms(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, int precision, double* out,
+                             cudaStream_t s) {
+  return precision == PCX_FP64 ? run_div_norms_t<double>(c, kp, X, nvec, out, s)
+                               : run_div_norms_t<float>(c, kp, X, nvec, out, s);
 }
 
 }  // namespace pcx

@@ -5,4 +5,6 @@ namespace pcx {
 template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
                                         cudaStream_t);
 template cudaError_t run_precond_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, cudaStream_t);
+template cudaError_t run_div_norms_t<float>(const pcx_ctx*, const KParams&, const void*, int, double*,
+                                            cudaStream_t);
 }  // namespace pcx

@@ -428,6 +428,49 @@ __global__ void precond_kernel(const cx<T>* __restrict__ R, cx<T>* __restrict__ 
   }
 }
 
+// Quadratic form of the penalty term per column: out[v] += sum over modes
+// |kappa(p) . x_v(p)|^2 = x_v^H K_B x_v (= ||B x||^2 for the real-space
+// field, Prop. 2.8), and out[nvec + v] += ||x_v||^2.  One block row per
+// column (blockIdx.y); block sums are added with FP64 atomics.
+template <typename T>
+__global__ void __launch_bounds__(256) div_norm_kernel(const cx<T>* __restrict__ X, const cx<T>* __restrict__ lam,
+                                                      int n, int nvec, KParams kp, double* __restrict__ out) {
+  const size_t n3 = (size_t)n * n * n;
+  const int v = blockIdx.y;
+  const cx<T>* x = X + (size_t)v * 3 * n3;
+  double sb = 0.0, sx = 0.0;
+  for (size_t mode = (size_t)blockIdx.x * blockDim.x + threadIdx.x; mode < n3; mode += (size_t)gridDim.x * blockDim.x) {
+    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    cx<T> kap[3];
+    kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
+    const cx<T> x0 = x[mode], x1 = x[mode + n3], x2 = x[mode + 2 * n3];
+    const cx<T> d = cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0));
+    sb += (double)norm2(d);
+    sx += (double)norm2(x0) + (double)norm2(x1) + (double)norm2(x2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+  }
+  __shared__ double red[2][8];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    red[0][warp] = sb;
+    red[1][warp] = sx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tb = 0.0, tx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      tb += red[0][w];
+      tx += red[1][w];
+    }
+    atomicAdd(out + v, tb);
+    atomicAdd(out + nvec + v, tx);
+  }
+}
+
 template <typename T, int N, int AXIS, int OP>
 cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st) {
   auto kern = pass_kernel<T, N, AXIS, OP>;
@@ -488,6 +531,20 @@ cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void
     case 256: return fftk::run_apply_n<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st);
   }
   return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t run_div_norms_t(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)nvec, s);
+  if (e != cudaSuccess || nvec == 0) return e;
+  const size_t n3 = (size_t)c->n * c->n * c->n;
+  size_t bx = (n3 + 255) / 256;
+  const size_t cap = (size_t)152 * 8 / (size_t)nvec;
+  if (bx > cap) bx = cap > 0 ? cap : 1;
+  const void* lam = sizeof(T) == 8 ? c->dev.lam64 : c->dev.lam32;
+  fftk::div_norm_kernel<T><<<dim3((unsigned)bx, (unsigned)nvec), 256, 0, s>>>(
+      static_cast<const cx<T>*>(X), static_cast<const cx<T>*>(lam), c->n, nvec, kp, out);
+  return cudaGetLastError();
 }
 
 template <typename T>

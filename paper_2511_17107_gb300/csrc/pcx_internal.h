@@ -94,6 +94,9 @@ int apply_chunk(const pcx_ctx* c, int precision);
 size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec);
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec,
                            int precision, cudaStream_t s);
+// out[v] = x_v^H K_B x_v, out[nvec + v] = ||x_v||^2 (device doubles, zeroed here)
+cudaError_t launch_div_norms(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, int precision, double* out,
+                             cudaStream_t s);
 // Gram G = A^H B: tensor cores (gram_tc.cu) for complex64 with na, nb <= 64 and even L,
 // CUDA cores (blas.cu) otherwise
 cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision,

@@ -527,15 +527,130 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
 
 }  // namespace
 
+// Everything one Bloch vector needs: the runs (device buffers) of both
+// precisions and the counters of the call.
+struct KSolve {
+  pcx_ctx* c;
+  cudaStream_t s;
+  const pcx_solve_opts* o;
+  int n, nev, maxit;
+  double tol, switch_tol;
+  uint64_t seed;
+  Times *t32, *t64;
+  int iters32 = 0, iters64 = 0;
+};
+
+// LOBPCG for one k with penalty coefficient gamma (<= 0: the rule of Sec. 2).
+// On return r64.S[0:nev] holds the FP64 eigenvectors.
+pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run& r64, Run& r32,
+                       std::vector<double>& theta, std::vector<double>& res, int& iters_total) {
+  pcx_ctx* c = ks.c;
+  const cudaStream_t s = ks.s;
+  const int n = ks.n, nev = ks.nev, maxit = ks.maxit;
+  const size_t L = (size_t)3 * c->n * c->n * c->n;
+  const bool kz = k[0] == 0 && k[1] == 0 && k[2] == 0;
+  iters_total = 0;
+  pcx_status st;
+  r64.c = c;
+  r64.s = s;
+  r64.prec = PCX_FP64;
+  r64.L = L;
+  r64.es = 16;
+  r64.n = n;
+  r64.kp = make_kparams(c, k, gamma);
+  r64.k_zero = kz;
+  r64.verbose = ks.o->verbose;
+  if (ks.o->stats) r64.tm = ks.t64;
+  if ((st = r64.alloc_all()) != PCX_OK) {
+    c->err = r64.err;
+    return st;
+  }
+  if (ks.o->precision == PCX_FP32) {
+    r32.c = c;
+    r32.s = s;
+    r32.prec = PCX_FP32;
+    r32.L = L;
+    r32.es = 8;
+    r32.n = n;
+    r32.kp = r64.kp;
+    r32.k_zero = kz;
+    r32.verbose = ks.o->verbose;
+    r32.t0 = r64.t0;
+    if (ks.o->stats) r32.tm = ks.t32;
+    if ((st = r32.alloc_all()) != PCX_OK) {
+      c->err = r32.err;
+      return st;
+    }
+    cudaError_t e = launch_fill_random(r32.S.p, n, L, ks.seed + ik, PCX_FP32, s);
+    if (e == cudaSuccess && kz) e = launch_deflate_p0(r32.S.p, n, c->n, PCX_FP32, s);
+    if (e != cudaSuccess) {
+      c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+      return PCX_ECUDA;
+    }
+    int it32 = 0;
+    bool early = false;
+    *r32.t0 = std::chrono::steady_clock::now();
+    st = lobpcg(r32, nev, ks.tol, maxit, ks.switch_tol, it32, theta, res, early);
+    r32.tick(&Times::other);
+    iters_total += it32;
+    ks.iters32 += it32;
+    if (st != PCX_OK && st != PCX_ENOCONV) {
+      c->err = r32.err;
+      return st;
+    }
+    // refine: X, AX in FP64, directions in FP32
+    int itr = 0;
+    *r64.t0 = std::chrono::steady_clock::now();
+    st = lobpcg_refine(r64, r32, nev, ks.tol, std::max(1, maxit - iters_total), itr, theta, res);
+    r64.tick(&Times::other);
+    iters_total += itr;
+    ks.iters64 += itr;
+    if (st != PCX_OK && st != PCX_ENOCONV) c->err = r64.err.empty() ? r32.err : r64.err;
+    return st;
+  }
+  cudaError_t e = launch_fill_random(r64.S.p, n, L, ks.seed + ik, PCX_FP64, s);
+  if (e == cudaSuccess && kz) e = launch_deflate_p0(r64.S.p, n, c->n, PCX_FP64, s);
+  if (e != cudaSuccess) {
+    c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+    return PCX_ECUDA;
+  }
+  int it64 = 0;
+  bool early = false;
+  *r64.t0 = std::chrono::steady_clock::now();
+  st = lobpcg(r64, nev, ks.tol, std::max(1, maxit - iters_total), 0.0, it64, theta, res, early);
+  r64.tick(&Times::other);
+  iters_total += it64;
+  ks.iters64 += it64;
+  if (st != PCX_OK && st != PCX_ENOCONV) c->err = r64.err;
+  return st;
+}
+
+// Spurious-mode guard: the largest share of the penalty term in a wanted
+// Rayleigh quotient, max_j gamma x_j^H K_B x_j / (theta_j ||x_j||^2).  A
+// physical eigenvector lies in ker B (Prop. 2.5: the spectrum splits into
+// that of A M A^H and gamma times that of B^H B), so its share is at the
+// rounding level; a penalty eigenvector has share ~1.
+pcx_status penalty_share(Run& r64, int nev, const std::vector<double>& theta, double& worst) {
+  Run& run = r64;
+  CK(launch_div_norms(r64.c, r64.kp, r64.S.p, nev, PCX_FP64, static_cast<double*>(r64.norms.p), r64.s));
+  std::vector<double> q(2 * (size_t)nev);
+  CK(cudaMemcpyAsync(q.data(), r64.norms.p, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, r64.s));
+  CK(cudaStreamSynchronize(r64.s));
+  worst = 0.0;
+  for (int j = 0; j < nev; ++j) {
+    const double den = std::fabs(theta[j]) * q[nev + j];
+    const double share = den > 0 ? r64.kp.gamma * q[j] / den : INFINITY;
+    worst = std::max(worst, share);
+  }
+  return PCX_OK;
+}
+
 pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, const pcx_solve_opts* opts,
                  double* eig_out, double* res_out, int* iters_out, void* vec_out, cudaStream_t s) {
   pcx_solve_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   const int n = o.block > 0 ? o.block : nev + 4;
-  const int maxit = o.maxit > 0 ? o.maxit : 1000;
-  const uint64_t seed = o.seed ? o.seed : 20251117ull;
-  const double switch_tol = o.switch_tol > 0 ? o.switch_tol : 1e-4;
   if (nev < 1 || n < nev || n > 42 || nk < 0 || (nk > 0 && !kpts) || !(tol > 0)) {
     c->err = "pcx_solve: need 1 <= nev <= block <= 42, tol > 0, kpts";
     return PCX_EINVAL;
@@ -544,107 +659,60 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
     c->err = "pcx_solve: bad precision";
     return PCX_EINVAL;
   }
+  if (!(o.gamma >= 0) || !std::isfinite(o.gamma)) {
+    c->err = "pcx_solve: gamma must be finite and >= 0";
+    return PCX_EINVAL;
+  }
+  const double penalty_tol = o.penalty_tol == 0 ? 1e-6 : o.penalty_tol;
+  const int max_raises = 4;
   const size_t L = (size_t)3 * c->n * c->n * c->n;
   pcx_status result = PCX_OK;
   Times t32, t64;
-  int iters32 = 0, iters64 = 0;
+  KSolve ks;
+  ks.c = c;
+  ks.s = s;
+  ks.o = &o;
+  ks.n = n;
+  ks.nev = nev;
+  ks.maxit = o.maxit > 0 ? o.maxit : 1000;
+  ks.tol = tol;
+  ks.switch_tol = o.switch_tol > 0 ? o.switch_tol : 1e-4;
+  ks.seed = o.seed ? o.seed : 20251117ull;
+  ks.t32 = &t32;
+  ks.t64 = &t64;
+  int raises = 0;
+  double gamma_last = 0.0;
   const auto t_start = std::chrono::steady_clock::now();
   if (o.stats) std::memset(o.stats, 0, sizeof(*o.stats));
   for (int ik = 0; ik < nk; ++ik) {
     const double* k = kpts + 3 * ik;
-    const bool kz = k[0] == 0 && k[1] == 0 && k[2] == 0;
+    double gamma = o.gamma > 0 ? o.gamma : make_kparams(c, k, 0.0).gamma;
     std::vector<double> theta, res;
     int iters_total = 0;
+    Run r64, r32;
     pcx_status st;
-    bool refined = false;
-    pcx_status refine_status = PCX_OK;
-    Run r32;
-    Run r64;
-    std::chrono::steady_clock::time_point clock = std::chrono::steady_clock::now();
-    r32.t0 = &clock;
-    r64.t0 = &clock;
-    r64.c = c;
-    r64.s = s;
-    r64.prec = PCX_FP64;
-    r64.L = L;
-    r64.es = 16;
-    r64.n = n;
-    r64.kp = make_kparams(c, k, 0.0);
-    r64.k_zero = kz;
-    r64.verbose = o.verbose;
-    if (o.stats) r64.tm = &t64;
-    if ((st = r64.alloc_all()) != PCX_OK) {
-      c->err = r64.err;
-      return st;
+    for (int attempt = 0;; ++attempt) {
+      iters_total = 0;
+      st = solve_one_k(ks, k, gamma, ik, r64, r32, theta, res, iters_total);
+      if (st != PCX_OK && st != PCX_ENOCONV) return st;
+      if (st != PCX_OK || penalty_tol < 0) break;
+      double share = 0.0;
+      pcx_status sg = penalty_share(r64, nev, theta, share);
+      if (sg != PCX_OK) {
+        c->err = r64.err;
+        return sg;
+      }
+      if (r64.verbose) std::fprintf(stderr, "[pcx] k %d gamma %.6g penalty share %.3e\n", ik, gamma, share);
+      if (share <= penalty_tol) break;
+      if (attempt >= max_raises) {
+        c->err = "pcx_solve: penalty modes among the wanted eigenpairs after raising gamma " +
+                 std::to_string(max_raises) + " times";
+        return PCX_ENUMERIC;
+      }
+      gamma *= 4.0;   // lift gamma * lambda_1^B above the wanted part of the spectrum
+      ++raises;
     }
-    if (o.precision == PCX_FP32) {
-      r32.c = c;
-      r32.s = s;
-      r32.prec = PCX_FP32;
-      r32.L = L;
-      r32.es = 8;
-      r32.n = n;
-      r32.kp = r64.kp;
-      r32.k_zero = kz;
-      r32.verbose = o.verbose;
-      if (o.stats) r32.tm = &t32;
-      if ((st = r32.alloc_all()) != PCX_OK) {
-        c->err = r32.err;
-        return st;
-      }
-      cudaError_t e = launch_fill_random(r32.S.p, n, L, seed + ik, PCX_FP32, s);
-      if (e == cudaSuccess && kz) e = launch_deflate_p0(r32.S.p, n, c->n, PCX_FP32, s);
-      if (e != cudaSuccess) {
-        c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
-        return PCX_ECUDA;
-      }
-      int it32 = 0;
-      bool early = false;
-      *r32.t0 = std::chrono::steady_clock::now();
-      st = lobpcg(r32, nev, tol, maxit, switch_tol, it32, theta, res, early);
-      r32.tick(&Times::other);
-      iters_total += it32;
-      iters32 += it32;
-      if (st != PCX_OK && st != PCX_ENOCONV) {
-        c->err = r32.err;
-        return st;
-      }
-      // refine: X, AX in FP64, directions in FP32
-      int itr = 0;
-      *r64.t0 = std::chrono::steady_clock::now();
-      st = lobpcg_refine(r64, r32, nev, tol, std::max(1, maxit - iters_total), itr, theta, res);
-      r64.tick(&Times::other);
-      iters_total += itr;
-      iters64 += itr;
-      if (st != PCX_OK && st != PCX_ENOCONV) {
-        c->err = r64.err.empty() ? r32.err : r64.err;
-        return st;
-      }
-      refined = true;
-      refine_status = st;
-    } else {
-      cudaError_t e = launch_fill_random(r64.S.p, n, L, seed + ik, PCX_FP64, s);
-      if (e == cudaSuccess && kz) e = launch_deflate_p0(r64.S.p, n, c->n, PCX_FP64, s);
-      if (e != cudaSuccess) {
-        c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
-        return PCX_ECUDA;
-      }
-    }
-    if (!refined) {
-      int it64 = 0;
-      bool early = false;
-      *r64.t0 = std::chrono::steady_clock::now();
-      st = lobpcg(r64, nev, tol, std::max(1, maxit - iters_total), 0.0, it64, theta, res, early);
-      r64.tick(&Times::other);
-      iters_total += it64;
-      iters64 += it64;
-    } else {
-      st = refine_status;
-    }
-    if (st != PCX_OK && st != PCX_ENOCONV) {
-      c->err = r64.err;
-      return st;
-    }
+    gamma_last = gamma;
     if (st == PCX_ENOCONV) {
       result = PCX_ENOCONV;
       c->err = "pcx_solve: iteration cap reached";
@@ -670,8 +738,8 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
   }
   if (o.stats) {
     pcx_solve_stats& st = *o.stats;
-    st.iters_fp32 = iters32;
-    st.iters_fp64 = iters64;
+    st.iters_fp32 = ks.iters32;
+    st.iters_fp64 = ks.iters64;
     st.applies_fp32 = t32.applies;
     st.applies_fp64 = t64.applies;
     st.ms_apply = t32.apply + t64.apply;
@@ -679,6 +747,8 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
     st.ms_rr = t32.rr + t64.rr;
     st.ms_other = t32.other + t64.other;
     st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    st.gamma_raises = raises;
+    st.gamma_last = gamma_last;
   }
   return result;
 }

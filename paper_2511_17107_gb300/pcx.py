@@ -43,7 +43,8 @@ class pcx_setup_desc(C.Structure):
 class pcx_solve_stats(C.Structure):
     _fields_ = [("iters_fp32", C.c_int), ("iters_fp64", C.c_int), ("applies_fp32", C.c_longlong),
                 ("applies_fp64", C.c_longlong), ("ms_total", C.c_double), ("ms_apply", C.c_double),
-                ("ms_gram", C.c_double), ("ms_rr", C.c_double), ("ms_other", C.c_double)]
+                ("ms_gram", C.c_double), ("ms_rr", C.c_double), ("ms_other", C.c_double),
+                ("gamma_raises", C.c_int), ("gamma_last", C.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -51,7 +52,8 @@ class pcx_solve_stats(C.Structure):
 
 class pcx_solve_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("maxit", C.c_int), ("precision", C.c_int), ("switch_tol", C.c_double),
-                ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats))]
+                ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats)),
+                ("gamma", C.c_double), ("penalty_tol", C.c_double)]
 
 
 _lib = None
@@ -86,6 +88,7 @@ def lib():
             "pcx_apply_host": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
+            "pcx_div_norms": (st, [vp, dp, vp, C.c_int, C.c_int, vp, vp]),
             "pcx_gram_mixed": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, vp, vp]),
             "pcx_combine": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_double, vp, C.c_size_t, C.c_int, vp]),
             "pcx_residual": (st, [vp, vp, vp, vp, vp, vp, C.c_int, C.c_size_t, C.c_int, vp]),
@@ -103,7 +106,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
+                        "pcx_div_norms", "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
 
 def _check(status, ctx=None):
@@ -317,6 +320,14 @@ def pcx_gram(A, B, G, L=None, ctx=None, stream=None):
     return G
 
 
+def pcx_div_norms(ctx, k, X, out, stream=None):
+    """out (float64 CUDA, 2 nvec) = [x_j^H K_B x_j, ||x_j||^2] per column of X."""
+    kk = np.ascontiguousarray(np.asarray(k, dtype=np.float64).reshape(3))
+    _check(lib().pcx_div_norms(ctx.handle, _dptr(kk), _devptr(X), X.shape[0], _prec_of(X), _devptr(out),
+                               _stream(stream)), ctx.handle)
+    return out
+
+
 def pcx_gram_mixed(A, B, G, ctx=None, stream=None):
     """G (complex128 CUDA tensor, na x nb) = A^H B with A complex128 (na, L) and B complex64 (nb, L)."""
     import torch
@@ -363,13 +374,13 @@ def pcx_rr_eig(ga, gb, drop_tol=1e-13):
 
 
 def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
-              vec_out=None, stream=None, raise_on_noconv=True, stats=None):
+              vec_out=None, stream=None, raise_on_noconv=True, stats=None, gamma=0.0, penalty_tol=0.0):
     """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status).  Pass a
     pcx_solve_stats instance as ``stats`` to receive counters and timings."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
     nk = kp.shape[0]
     o = pcx_solve_opts(block, maxit, precision, switch_tol, seed, verbose,
-                       C.pointer(stats) if stats is not None else None)
+                       C.pointer(stats) if stats is not None else None, float(gamma), float(penalty_tol))
     eig = np.zeros((nk, nev))
     res = np.zeros((nk, nev))
     its = np.zeros(nk, dtype=np.int32)

@@ -243,3 +243,32 @@ def test_gram_mixed_fp64_fp32(pcx, na, nb, L):
     norm = np.linalg.norm(a, axis=1).max() * np.linalg.norm(b32.astype(np.complex128), axis=1).max()
     err = np.abs(G.cpu().numpy() - want).max() / norm
     assert err <= 1e-13, err
+
+
+DIV_CASES = [
+    ("fcc16-f64", wl.fcc_air_spheres, 16, np.complex128, 1, "summed"),
+    ("woodpile16-m3-f64", wl.woodpile, 16, np.complex128, 3, "summed"),
+    ("fcc8-literal-f64", wl.fcc_air_spheres, 8, np.complex128, 1, "literal"),
+    ("sc32-f32", wl.sc_gyro_sphere, 32, np.complex64, 2, "summed"),
+]
+
+
+@pytest.mark.parametrize("name,maker,n,dtype,m,reading", DIV_CASES, ids=[c[0] for c in DIV_CASES])
+def test_div_norms_match_real_space_divergence(pcx, name, maker, n, dtype, m, reading):
+    """pcx_div_norms: x^H K_B x equals ||B h||^2 of the real-space field
+    h = F3_3 x, with B built from the oracle's stencils (Sec. 2.2) rather than
+    from the Fourier symbols; also ||x||^2."""
+    s = maker()
+    k = np.array([0.9, -1.7, 2.3])
+    x = wl.random_block(3, n, seed=21).astype(dtype)
+    ops = yee.YeeOperators(n, s.lattice, k, m, reading)
+    h = fourier.f3(x.astype(np.complex128))
+    want_b = np.array([np.sum(np.abs(ops.div(h[j])) ** 2) for j in range(3)])
+    want_x = np.sum(np.abs(x.astype(np.complex128)) ** 2, axis=(1, 2, 3, 4))
+    ctx = pcx.setup_structure(s, n, stencil_m=m, ct_reading=pcx.PCX_CT_LITERAL if reading == "literal" else 0)
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    pcx.pcx_div_norms(ctx, k, torch.from_numpy(x).cuda(), out)
+    got = out.cpu().numpy()
+    rtol = 1e-12 if dtype == np.complex128 else 1e-5
+    np.testing.assert_allclose(got[:3], want_b, rtol=rtol)
+    np.testing.assert_allclose(got[3:], want_x, rtol=rtol)

@@ -80,3 +80,31 @@ def test_solve_config1_matches_oracle_lobpcg(pcx, prec, rtol):
     ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-10, block=nev + 4, precision=prec)
     assert st == pcx.PCX_OK and np.all(res <= 1e-10)
     np.testing.assert_allclose(ev[0], want, rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [(0, 1e-10), (1, 1e-6)])
+def test_penalty_guard_raises_gamma(pcx, prec, rtol):
+    """Spurious-mode guard.  Homogeneous SC medium eps = 2 I at k = (0.5, 0, 0):
+    the physical branch (Prop. 2.5) starts at |kappa|^2 / 2 = 0.125 (twice),
+    the penalty branch at gamma |kappa|^2 = gamma / 4.  With gamma = 0.05 the
+    penalty eigenvalue 0.0125 is the lowest: the guard off returns it, the
+    guard on raises gamma x4 (0.05 -> 0.2 -> 0.8) until both wanted pairs are
+    physical."""
+    n, nev = 16, 2
+    eps = 2.0 * np.eye(3)
+    s = wl.homogeneous(eps, wl.SC)
+    k = np.array([0.5, 0.0, 0.0])
+    kap = fourier.kappa(n, wl.SC, k)
+    ctx = pcx.setup_structure(s, n)
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-9, block=6, precision=prec, gamma=0.05, penalty_tol=-1)
+    assert st == pcx.PCX_OK
+    np.testing.assert_allclose(ev[0], eig.homogeneous_spectrum(kap, np.linalg.inv(eps), 0.05)[:nev], rtol=rtol)
+    assert abs(ev[0][0] - 0.0125) < 1e-6
+    stats = pcx.pcx_solve_stats()
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-9, block=6, precision=prec, gamma=0.05, stats=stats)
+    assert st == pcx.PCX_OK
+    assert stats.gamma_raises == 2 and abs(stats.gamma_last - 0.8) < 1e-15
+    phys = eig.homogeneous_spectrum(kap, np.linalg.inv(eps), 0.0)
+    phys = phys[phys > 1e-9 * phys.max()]
+    np.testing.assert_allclose(ev[0], phys[:nev], rtol=rtol)
+    np.testing.assert_allclose(ev[0], [0.125, 0.125], rtol=1e-3)
