@@ -48,6 +48,9 @@ def _compile(src: str, verbose: bool) -> str:
     flags = list(COMMON)
     if src == "setup.cpp":
         flags += ["-Xcompiler", "-ffp-contract=off"]
+    if src in ("linalg.cpp", "solver.cpp"):
+        # plain complex products and quotients (no Inf/NaN recovery calls)
+        flags += ["-Xcompiler", "-fcx-limited-range"]
     cmd = [nvcc()] + ARCH + flags + ["-c", path, "-o", obj]
     if src.endswith(".cu"):
         cmd += ["-Xptxas", "-v"] if verbose else []
