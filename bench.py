@@ -9,6 +9,11 @@ no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The line also carries "solve": the per-k solve time to Res_j <= 1e-8
+(12 bands, block 16, pcx_solve) on the same structure and k, mixed precision
+(FP32 apply and directions, FP64 X and Rayleigh-Ritz) against the plain FP64
+solve, wall-clock around the synchronising call (--no-solve skips it).
+
 --impl reference times the CPU oracle (the FP64 numpy definition
 F3^H (A M A^H + gamma B^H B) F3 x) on the same workload, one vector per step.
 """
@@ -169,6 +174,31 @@ def run_reference(args):
     return 0
 
 
+def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8):
+    """Per-k time to Res_j <= tol, mixed precision vs plain FP64 (pcx_solve)."""
+    import numpy as np
+    ks = [kpath[(K_INDEX + i) % len(kpath)] for i in range(nk)]
+    out = {"tol": tol, "nev": nev, "block": block, "k_points": nk, "k_first_index": K_INDEX,
+           "timer": "host wall-clock around pcx_solve (synchronises its stream)"}
+    eigs = {}
+    for name, prec in (("mixed", pcx.PCX_FP32), ("fp64", pcx.PCX_FP64)):
+        stats = pcx.pcx_solve_stats()
+        t0 = time.perf_counter()
+        ev, res, its, st = pcx.pcx_solve(ctx, ks, nev, tol, block=block, precision=prec, stats=stats,
+                                         raise_on_noconv=False)
+        dt = time.perf_counter() - t0
+        eigs[name] = ev
+        d = stats.as_dict()
+        out[name] = {"s_per_k": dt / nk, "status": int(st), "max_res": float(np.max(res)),
+                     "iters_per_k": float(np.mean(its)), "iters_fp32": d["iters_fp32"], "iters_fp64": d["iters_fp64"],
+                     "applies_fp32": d["applies_fp32"], "applies_fp64": d["applies_fp64"],
+                     "ms_apply": d["ms_apply"], "ms_gram": d["ms_gram"], "ms_rr": d["ms_rr"],
+                     "ms_other": d["ms_other"], "gamma_raises": d["gamma_raises"]}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["s_per_k"] / out["mixed"]["s_per_k"]
+    out["max_rel_eig_diff"] = float(np.max(np.abs(eigs["mixed"] - eigs["fp64"]) / np.abs(eigs["fp64"])))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +210,8 @@ def main():
     ap.add_argument("--n", type=int, default=N, help="grid size (profiling runs use the default)")
     ap.add_argument("--block", type=int, default=BLOCK, help="vectors per step (profiling runs)")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the per-k solve-time legs")
+    ap.add_argument("--solve-nk", type=int, default=1, help="k-points of the solve legs (from index k_index)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -288,6 +320,8 @@ def main():
                         * args.steps,
         "clocks": ck,
     }
+    if rank == 0 and not args.no_solve:
+        line["solve"] = solve_legs(pcx, ctx, wl.config_k(s.name), args.solve_nk, n)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess()
     if rank == 0:

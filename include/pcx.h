@@ -365,7 +365,7 @@ typedef struct {
                          (4 pi^2 if k = 0 or |k| >= 1, else 4 pi^2 / |k|^2)        */
   double penalty_tol; /* spurious-mode guard: after convergence, a wanted pair
                          with gamma x^H K_B x / (theta ||x||^2) above this is a
-                         penalty mode (Prop. 2.5: eigenvalue gamma * lambda^B);
+                         penalty mode (Prop. 2.3: eigenvalue gamma * lambda^B);
                          gamma is then multiplied by 4 and k re-solved, at most
                          4 times (then PCX_ENUMERIC).  0: default 1e-6;
                          negative: guard off                                      */

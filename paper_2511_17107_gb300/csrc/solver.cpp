@@ -627,7 +627,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
 
 // Spurious-mode guard: the largest share of the penalty term in a wanted
 // Rayleigh quotient, max_j gamma x_j^H K_B x_j / (theta_j ||x_j||^2).  A
-// physical eigenvector lies in ker B (Prop. 2.5: the spectrum splits into
+// physical eigenvector lies in ker B (Prop. 2.3: the spectrum splits into
 // that of A M A^H and gamma times that of B^H B), so its share is at the
 // rounding level; a penalty eigenvector has share ~1.
 pcx_status penalty_share(Run& r64, int nev, const std::vector<double>& theta, double& worst) {

@@ -85,7 +85,7 @@ def test_solve_config1_matches_oracle_lobpcg(pcx, prec, rtol):
 @pytest.mark.parametrize("prec,rtol", [(0, 1e-10), (1, 1e-6)])
 def test_penalty_guard_raises_gamma(pcx, prec, rtol):
     """Spurious-mode guard.  Homogeneous SC medium eps = 2 I at k = (0.5, 0, 0):
-    the physical branch (Prop. 2.5) starts at |kappa|^2 / 2 = 0.125 (twice),
+    the physical branch (Prop. 2.3) starts at |kappa|^2 / 2 = 0.125 (twice),
     the penalty branch at gamma |kappa|^2 = gamma / 4.  With gamma = 0.05 the
     penalty eigenvalue 0.0125 is the lowest: the guard off returns it, the
     guard on raises gamma x4 (0.05 -> 0.2 -> 0.8) until both wanted pairs are
