@@ -22,6 +22,9 @@ fourier       DFT matrix, circulant symbols, Fourier-basis operator and the
 penalty       the penalty-coefficient rules (Prop. 2.5, Remark 2.6)
 eig           dense spectra, homogeneous-medium spectra, textbook LOBPCG
               (Sec. 4)
+learned       the gated 3D convolution correction of K_P^{-1} (no counterpart
+              in the paper): forward pass, loss gradient by the chain rule,
+              the corrected preconditioner T(r) and its training pairs
 
 Every function that has no independent pin says "parity unpinned" in its
 docstring; at present every function is pinned by a test in

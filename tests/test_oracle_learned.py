@@ -1,0 +1,143 @@
+"""Pins of the learned-correction oracle (oracle/learned.py) against
+definitions outside it: scipy's periodic correlation, the circular
+correlation theorem through numpy FFTs, the adjoint identity, central finite
+differences of the loss, and the limits in which T reduces to K_P^{-1}."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fourier, learned, permittivity
+
+ndimage = pytest.importorskip("scipy.ndimage")
+
+
+def _rand_params(rng, c, scale=0.3):
+    p = {name: rng.standard_normal(shape) * scale for name, shape in learned.param_shapes(c)}
+    return p
+
+
+def test_conv_matches_scipy_periodic_correlation():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 5, 6, 7))
+    w = rng.standard_normal((3, 2, 3, 3, 3))
+    got = learned.conv(x, w)
+    want = np.zeros_like(got)
+    for o in range(3):
+        for i in range(2):
+            want[o] += ndimage.correlate(x[i], w[o, i], mode="wrap")
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_conv_matches_correlation_theorem():
+    """conv(x, w)[o] = sum_i IFFT(FFT(x_i) * conj(FFT(k_oi))) with k the taps
+    placed at the periodic offsets: an evaluation that shares nothing with
+    the shifted sums of the oracle."""
+    rng = np.random.default_rng(1)
+    n = 6
+    x = rng.standard_normal((2, n, n, n))
+    w = rng.standard_normal((4, 2, 3, 3, 3))
+    want = np.zeros((4, n, n, n))
+    for o in range(4):
+        for i in range(2):
+            k = np.zeros((n, n, n))
+            for dz, dy, dx in learned.OFFSETS:
+                k[dz % n, dy % n, dx % n] = w[o, i, dz + 1, dy + 1, dx + 1]
+            want[o] += np.real(np.fft.ifftn(np.fft.fftn(x[i]) * np.conj(np.fft.fftn(k))))
+    np.testing.assert_allclose(learned.conv(x, w), want, rtol=1e-11, atol=1e-11)
+
+
+def test_conv_adjoint_and_weight_gradient_identities():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((3, 4, 5, 6))
+    w = rng.standard_normal((2, 3, 3, 3, 3))
+    dy = rng.standard_normal((2, 4, 5, 6))
+    lhs = np.sum(dy * learned.conv(x, w))
+    np.testing.assert_allclose(np.sum(learned.conv_adjoint(dy, w) * x), lhs, rtol=1e-12)
+    np.testing.assert_allclose(np.sum(learned.conv_weight_grad(dy, x) * w), lhs, rtol=1e-12)
+
+
+def test_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    c, n, nv = 2, 4, 2
+    p = _rand_params(rng, c)
+    f = rng.uniform(0.05, 1.0, size=(9, n, n, n))
+    U = rng.standard_normal((nv, 3, n, n, n)) + 1j * rng.standard_normal((nv, 3, n, n, n))
+    T = rng.standard_normal((nv, 3, n, n, n)) + 1j * rng.standard_normal((nv, 3, n, n, n))
+    w = np.array([0.7, 1.3])
+    _, grads = learned.loss_and_grad(p, f, U, T, w)
+    flat = learned.pack(p, c)
+    gflat = learned.pack(grads, c)
+    idx = rng.choice(flat.size, size=60, replace=False)
+    h = 1e-6
+    for j in idx:
+        fp = flat.copy()
+        fm = flat.copy()
+        fp[j] += h
+        fm[j] -= h
+        lp, _ = learned.loss_and_grad(learned.unpack(fp, c), f, U, T, w)
+        lm, _ = learned.loss_and_grad(learned.unpack(fm, c), f, U, T, w)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (j, fd, gflat[j])
+
+
+def _small_case(n=8):
+    s = wl.random_inclusions(5)
+    blocks = permittivity.cell_blocks(s, n)
+    k = np.array([0.4, -0.9, 1.7])
+    kap = fourier.kappa(n, s.lattice, k)
+    return learned.features(blocks), kap, 4 * np.pi ** 2
+
+
+def test_preconditioner_is_complex_linear_and_reduces_to_kp():
+    rng = np.random.default_rng(4)
+    f, kap, gam = _small_case()
+    n = f.shape[-1]
+    p = _rand_params(rng, learned.HIDDEN, 0.2)
+    r1 = wl.random_block(1, n, seed=8)[0]
+    r2 = wl.random_block(1, n, seed=9)[0]
+    a, b = 0.3 - 1.1j, -2.0 + 0.5j
+    lhs = learned.precondition(p, f, a * r1 + b * r2, kap, gam)
+    rhs = a * learned.precondition(p, f, r1, kap, gam) + b * learned.precondition(p, f, r2, kap, gam)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-11, atol=1e-11 * np.abs(rhs).max())
+    p["W3"][:] = 0.0
+    np.testing.assert_allclose(learned.precondition(p, f, r1, kap, gam), fourier.precondition(r1, kap, gam),
+                               rtol=1e-13, atol=0)
+
+
+def test_open_gates_reduce_to_plain_convolutions():
+    """With V = 0 and large biases the gates are 1 and g is three plain
+    convolutions, evaluated here through the correlation theorem."""
+    rng = np.random.default_rng(6)
+    c, n = 3, 5
+    p = _rand_params(rng, c)
+    p["V1"][:] = 0
+    p["V2"][:] = 0
+    p["c1"][:] = 60.0
+    p["c2"][:] = 60.0
+    f = rng.uniform(0, 1, size=(9, n, n, n))
+    u = rng.standard_normal((3, n, n, n))
+
+    def fftconv(x, w):
+        out = np.zeros((w.shape[0], n, n, n))
+        for o in range(w.shape[0]):
+            for i in range(w.shape[1]):
+                k = np.zeros((n, n, n))
+                for dz, dy, dx in learned.OFFSETS:
+                    k[dz % n, dy % n, dx % n] = w[o, i, dz + 1, dy + 1, dx + 1]
+                out[o] += np.real(np.fft.ifftn(np.fft.fftn(x[i]) * np.conj(np.fft.fftn(k))))
+        return out
+
+    want = fftconv(fftconv(fftconv(u, p["W1"]), p["W2"]), p["W3"])
+    got, _ = learned.forward_real(p, f, u)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+
+
+def test_features_layout():
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal((2, 3, 4, 3, 3)) + 1j * rng.standard_normal((2, 3, 4, 3, 3))
+    f = learned.features(b)
+    assert f.shape == (9, 2, 3, 4)
+    np.testing.assert_array_equal(f[0], b[..., 0, 0].real)
+    np.testing.assert_array_equal(f[4], b[..., 0, 1].imag)
+    np.testing.assert_array_equal(f[8], b[..., 1, 2].imag)
+    assert learned.param_count(8) == 8 * 3 * 27 + 64 * 27 + 3 * 8 * 27 + 2 * (8 * 9 * 27 + 8)
