@@ -334,6 +334,74 @@ pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol
 pcx_status pcx_div_norms(pcx_ctx* ctx, const double k[3], const void* X, int nvec, int precision, double* out,
                          void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned correction of the preconditioner.  The paper has no learned
+ * component; this corrects its FFT-diagonal K_P^{-1} (eqs. matrixfree_diagP,
+ * matrixfree_finalform) as
+ *
+ *   T(r) = K_P^{-1} r + F3_3^H g(F3_3 K_P^{-1} r)
+ *
+ * with F3_3 the unitary 3D DFT of each component (Sec. 2.4: x = F3_3^H H) and
+ * g a three-layer circular 3D convolution net (3x3x3 taps) on the real-space
+ * field, applied with the same weights to its real and imaginary parts:
+ *   g1 = sigmoid(conv(f, V1) + c1),  g2 = sigmoid(conv(f, V2) + c2)
+ *   y  = conv(g2 * conv(g1 * conv(u, W1), W2), W3)
+ * where f are the 9 reals of the cell blocks of M (Sec. 3.2.1: d1, d2, d3,
+ * Re/Im M12, M13, M23).  g is linear in u, so T is a complex-linear map.
+ * conv(x, w)[o][z][y][x] = sum_{i,dz,dy,dx} w[o][i][t] x[i][z+dz][y+dy][x+dx]
+ * with tap t = (dz+1)*9 + (dy+1)*3 + (dx+1) and periodic wrap-around.
+ * Parameters: one DEVICE float array of PCX_CNN_NPARAMS entries laid out as
+ * W1[8][3][27], W2[8][8][27], W3[3][8][27], V1[8][9][27], c1[8],
+ * V2[8][9][27], c2[8].  Fields are complex64 [nvec][3][N][N][N], grid sizes
+ * 8 <= N (powers of two), FP32 arithmetic.  Device pointers, stream-ordered;
+ * workspace is owned by the context and grows on demand.
+ * ------------------------------------------------------------------------- */
+#define PCX_CNN_HIDDEN 8
+#define PCX_CNN_NPARAMS (PCX_CNN_HIDDEN * 3 * 27 + PCX_CNN_HIDDEN * PCX_CNN_HIDDEN * 27 + 3 * PCX_CNN_HIDDEN * 27 + \
+                         2 * (PCX_CNN_HIDDEN * 9 * 27 + PCX_CNN_HIDDEN))
+
+/* Random initial parameters (seeded): W1, W2, V1, V2 normal with variance
+ * 1/fan-in, W3 = 0 and c = 0 (so T starts as K_P^{-1}). */
+pcx_status pcx_cnn_init(uint64_t seed, float* params, void* stream);
+
+/* The two gate fields g1, g2 of this context's structure: gates = DEVICE
+ * 2 * 8 * N^3 floats, g1 then g2, each [8][N^3]. */
+pcx_status pcx_cnn_gates(pcx_ctx* ctx, const float* params, float* gates, void* stream);
+
+/* Y = g(Re U) + i g(Im U) for nvec real-space fields U (Y may not alias U). */
+pcx_status pcx_cnn_forward(pcx_ctx* ctx, const float* params, const float* gates, const void* U, void* Y, int nvec,
+                           void* stream);
+
+/* Loss L = sum_v w[v] ||g(U_v) - T_v||^2 (w: HOST doubles, nvec) and its
+ * gradient with respect to every parameter, written (accumulate = 0) or
+ * added (accumulate = 1) to the DEVICE float array grad (PCX_CNN_NPARAMS).
+ * *loss (HOST) receives L; synchronises `stream` when loss is not NULL. */
+pcx_status pcx_cnn_grad(pcx_ctx* ctx, const float* params, const void* U, const void* T, const double* w, int nvec,
+                        float* grad, int accumulate, double* loss, void* stream);
+
+/* One Adam step (Kingma and Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) on
+ * DEVICE arrays of PCX_CNN_NPARAMS floats; step counts from 1. */
+pcx_status pcx_cnn_adam(float* params, const float* grad, float* m, float* v, int step, float lr, void* stream);
+
+/* W = T(R) for nvec Fourier-basis vectors (complex64), gates from
+ * pcx_cnn_gates.  gamma <= 0: the rule of Remark 2.6. */
+pcx_status pcx_cnn_precond(pcx_ctx* ctx, const double k[3], double gamma, const float* params, const float* gates,
+                           const void* R, void* W, int nvec, void* stream);
+
+/* Training pairs from residuals R and targets E = Op^{-1} R (Fourier basis,
+ * complex64): U = F3_3 K_P^{-1} R and T = F3_3 (E - K_P^{-1} R) (real space),
+ * and enorm2[v] = ||E_v||^2 (HOST doubles; synchronises when not NULL). */
+pcx_status pcx_cnn_pairs(pcx_ctx* ctx, const double k[3], double gamma, const void* R, const void* E, void* U,
+                         void* T, double* enorm2, int nvec, void* stream);
+
+/* E = Op^{-1} R for nvec complex64 vectors by preconditioned conjugate
+ * gradients (K_P^{-1}; FP32 vectors, FP64 scalars), one recursion per column,
+ * until every ||R - Op E|| / ||R|| <= tol or maxit iterations.  *iters and
+ * relres[nvec] (HOST, optional) report the iterations and the recursion's
+ * relative residuals.  At k = 0 the p = 0 mode of R must be zero (Prop. 2.5). */
+pcx_status pcx_cg_solve(pcx_ctx* ctx, const double k[3], double gamma, const void* R, void* E, int nvec, double tol,
+                        int maxit, int* iters, double* relres, void* stream);
+
 /* Counters and wall-clock split of one pcx_solve call (summed over k).
  * Phase times are measured with a stream synchronisation after each phase
  * when this struct is requested, so they add up to the total. */

@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 
+#include "cnn.h"
 #include "linalg.h"
 #include "pcx_internal.h"
 
@@ -91,7 +92,7 @@ pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32
 void pcx_destroy(pcx_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64,  c->dev.tw32, c->dev.m64,  c->dev.m32,
-                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y};
+                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->cnn_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -242,6 +243,93 @@ pcx_status pcx_div_norms(pcx_ctx* c, const double k[3], const void* X, int nvec,
   pcx::KParams kp = pcx::make_kparams(c, k, 0.0);
   cudaError_t e = pcx::launch_div_norms(c, kp, X, nvec, precision, out, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_div_norms", e);
+}
+
+static pcx_status check_cnn(pcx_ctx* c, const char* who, int nvec) {
+  if (!c) return inval(nullptr, std::string(who) + ": NULL context");
+  if (c->n < 8) return inval(c, std::string(who) + ": needs N >= 8");
+  if (nvec < 0 || nvec > 32767) return inval(c, std::string(who) + ": need 0 <= nvec <= 32767");
+  return PCX_OK;
+}
+
+pcx_status pcx_cnn_init(uint64_t seed, float* params, void* stream) {
+  if (!params) return inval(nullptr, "pcx_cnn_init: NULL params");
+  cudaError_t e = pcx::cnn::init_params(params, seed, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(nullptr, "pcx_cnn_init", e);
+}
+
+pcx_status pcx_cnn_gates(pcx_ctx* c, const float* params, float* gates, void* stream) {
+  pcx_status st = check_cnn(c, "pcx_cnn_gates", 1);
+  if (st != PCX_OK) return st;
+  if (!params || !gates || !aligned16(gates)) return inval(c, "pcx_cnn_gates: NULL or misaligned buffer");
+  cudaError_t e = pcx::cnn_gates(c, params, gates, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_cnn_gates", e);
+}
+
+pcx_status pcx_cnn_forward(pcx_ctx* c, const float* params, const float* gates, const void* U, void* Y, int nvec,
+                           void* stream) {
+  pcx_status st = check_cnn(c, "pcx_cnn_forward", nvec);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!params || !gates || !U || !Y || !aligned16(U) || !aligned16(Y))
+    return inval(c, "pcx_cnn_forward: NULL or misaligned buffer");
+  const size_t bytes = pcx_vector_length(c) * nvec * 8;
+  if (ranges_overlap(U, bytes, Y, bytes)) return inval(c, "pcx_cnn_forward: U and Y overlap");
+  cudaError_t e = pcx::cnn_forward(c, params, gates, U, Y, nvec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_cnn_forward", e);
+}
+
+pcx_status pcx_cnn_grad(pcx_ctx* c, const float* params, const void* U, const void* T, const double* w, int nvec,
+                        float* grad, int accumulate, double* loss, void* stream) {
+  pcx_status st = check_cnn(c, "pcx_cnn_grad", nvec);
+  if (st != PCX_OK) return st;
+  if (nvec < 1) return inval(c, "pcx_cnn_grad: nvec < 1");
+  if (!params || !U || !T || !w || !grad || !aligned16(U) || !aligned16(T))
+    return inval(c, "pcx_cnn_grad: NULL or misaligned buffer");
+  cudaError_t e = pcx::cnn_grad(c, params, U, T, w, nvec, grad, accumulate ? 1 : 0, loss,
+                                static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_cnn_grad", e);
+}
+
+pcx_status pcx_cnn_adam(float* params, const float* grad, float* m, float* v, int step, float lr, void* stream) {
+  if (!params || !grad || !m || !v || step < 1 || !(lr > 0)) return inval(nullptr, "pcx_cnn_adam: bad argument");
+  cudaError_t e = pcx::cnn::adam(params, grad, m, v, pcx::cnn::NPARAMS, step, lr, 0.9f, 0.999f, 1e-8f,
+                                 static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(nullptr, "pcx_cnn_adam", e);
+}
+
+pcx_status pcx_cnn_precond(pcx_ctx* c, const double k[3], double gamma, const float* params, const float* gates,
+                           const void* R, void* W, int nvec, void* stream) {
+  pcx_status st = check_cnn(c, "pcx_cnn_precond", nvec);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k || !params || !gates || !R || !W || !aligned16(R) || !aligned16(W))
+    return inval(c, "pcx_cnn_precond: NULL or misaligned buffer");
+  const size_t bytes = pcx_vector_length(c) * nvec * 8;
+  if (R != W && ranges_overlap(R, bytes, W, bytes)) return inval(c, "pcx_cnn_precond: R and W partially overlap");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  cudaError_t e = pcx::cnn_precond(c, kp, params, gates, R, W, nvec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_cnn_precond", e);
+}
+
+pcx_status pcx_cnn_pairs(pcx_ctx* c, const double k[3], double gamma, const void* R, const void* E, void* U, void* T,
+                         double* enorm2, int nvec, void* stream) {
+  pcx_status st = check_cnn(c, "pcx_cnn_pairs", nvec);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k || !R || !E || !U || !T || !aligned16(R) || !aligned16(E) || !aligned16(U) || !aligned16(T))
+    return inval(c, "pcx_cnn_pairs: NULL or misaligned buffer");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  cudaError_t e = pcx::cnn_pairs(c, kp, R, E, U, T, enorm2, nvec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_cnn_pairs", e);
+}
+
+pcx_status pcx_cg_solve(pcx_ctx* c, const double k[3], double gamma, const void* R, void* E, int nvec, double tol,
+                        int maxit, int* iters, double* relres, void* stream) {
+  pcx_status st = check_cnn(c, "pcx_cg_solve", nvec);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k || !R || !E || !aligned16(R) || !aligned16(E) || !(tol > 0) || maxit < 1)
+    return inval(c, "pcx_cg_solve: bad argument");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  cudaError_t e = pcx::cg_solve(c, kp, R, E, nvec, tol, maxit, iters, relres, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_cg_solve", e);
 }
 
 pcx_status pcx_gram(pcx_ctx* c, const void* A, int na, const void* B, int nb, size_t L, int precision, void* G,

@@ -23,6 +23,8 @@ template <typename T>
 cudaError_t run_precond_t(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, cudaStream_t s);
 template <typename T>
 cudaError_t run_div_norms_t(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, double* out, cudaStream_t s);
+template <typename T>
+cudaError_t run_fft_t(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, cudaStream_t st);
 extern template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
                                                cudaStream_t);
 extern template cudaError_t run_apply_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
@@ -115,6 +117,10 @@ cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, v
                            cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
   return precision == PCX_FP64 ? run_precond_t<double>(c, kp, R, W, nvec, s) : run_precond_t<float>(c, kp, R, W, nvec, s);
+}
+
+cudaError_t launch_fft(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, int precision, cudaStream_t s) {
+  return precision == PCX_FP64 ? run_fft_t<double>(c, X, Y, nvec, dir, s) : run_fft_t<float>(c, X, Y, nvec, dir, s);
 }
 
 cudaError_t launch_div_norms(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, int precision, double* out,

@@ -7,4 +7,5 @@ template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const vo
 template cudaError_t run_precond_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, cudaStream_t);
 template cudaError_t run_div_norms_t<float>(const pcx_ctx*, const KParams&, const void*, int, double*,
                                             cudaStream_t);
+template cudaError_t run_fft_t<float>(const pcx_ctx*, const void*, void*, int, int, cudaStream_t);
 }  // namespace pcx

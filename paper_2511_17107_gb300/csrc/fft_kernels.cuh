@@ -33,7 +33,9 @@
 namespace pcx {
 namespace fftk {
 
-enum { OP_PRE = 0, OP_INV = 1, OP_SANDWICH = 2, OP_FWD = 3, OP_POST = 4 };
+// OP_PLAIN_INV / OP_PLAIN_FWD: a bare unnormalised 1D DFT along the pass axis
+// (positive / negative exponent), used for F3_3 and F3_3^H of whole vectors.
+enum { OP_PRE = 0, OP_INV = 1, OP_SANDWICH = 2, OP_FWD = 3, OP_POST = 4, OP_PLAIN_INV = 5, OP_PLAIN_FWD = 6 };
 
 // Radix plans: elements held per thread per stage E (16 complex floats or 8
 // complex doubles), radices R0..R2 with N = R0 R1 R2 and every R <= E.
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
 
   const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
   for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = gtw[i];
-  if constexpr (AXIS == 0) {
+  if constexpr (AXIS == 0 && OP < OP_PLAIN_INV) {
     // kappa_i(p) = sum_j b_ji S_j(p_j) + i kq_i L0(p_i),  S_j = L1 + i kt_j L0,
     // split as ka_i(p1) + kb_i(p2, p3)
     const cx<T>* glam = static_cast<const cx<T>*>(a.lam);
@@ -310,7 +312,10 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
     }
   }
 
-  if constexpr (AXIS == 0) {
+  if constexpr (OP == OP_PLAIN_INV || OP == OP_PLAIN_FWD) {
+    __syncthreads();
+    fft_tile<T, N, AXIS, OP == OP_PLAIN_INV ? +1 : -1, 1, 1>(s, tw, in, out, qb);
+  } else if constexpr (AXIS == 0) {
     // ---- x-axis passes: staged through shared memory, points fastest ----
     __syncthreads();   // tables visible
     if constexpr (OP == OP_PRE) {
@@ -529,6 +534,49 @@ cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void
     case 64: return fftk::run_apply_n<T, 64>(c, kp, X, Y, nvec, chunk, sbuf, st);
     case 128: return fftk::run_apply_n<T, 128>(c, kp, X, Y, nvec, chunk, sbuf, st);
     case 256: return fftk::run_apply_n<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Unnormalised 3D DFT of every component of nvec vectors, X -> Y (Y may be
+// X): dir > 0 positive exponent (N^{3/2} F3_3), dir < 0 negative exponent
+// (N^{3/2} F3_3^H).  Three passes, x then y then z, the last two in place.
+namespace fftk {
+template <typename T, int N>
+cudaError_t run_fft_n(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, cudaStream_t st) {
+  using C = Cfg<T, N>;
+  const bool dbl = sizeof(T) == 8;
+  PassArgs a{};
+  a.lam = dbl ? c->dev.lam64 : c->dev.lam32;
+  a.tw = dbl ? c->dev.tw64 : c->dev.tw32;
+  a.kp = KParams{};
+  const size_t tiles = (size_t)nvec * N * N / C::TP;
+  cudaError_t e;
+  a.in = X;
+  a.out = Y;
+  if (dir > 0) {
+    if ((e = launch_pass<T, N, 0, OP_PLAIN_INV>(a, tiles, C::SMEM, st)) != cudaSuccess) return e;
+    a.in = Y;
+    if ((e = launch_pass<T, N, 1, OP_PLAIN_INV>(a, tiles, C::SMEM, st)) != cudaSuccess) return e;
+    return launch_pass<T, N, 2, OP_PLAIN_INV>(a, tiles, C::SMEM, st);
+  }
+  if ((e = launch_pass<T, N, 0, OP_PLAIN_FWD>(a, tiles, C::SMEM, st)) != cudaSuccess) return e;
+  a.in = Y;
+  if ((e = launch_pass<T, N, 1, OP_PLAIN_FWD>(a, tiles, C::SMEM, st)) != cudaSuccess) return e;
+  return launch_pass<T, N, 2, OP_PLAIN_FWD>(a, tiles, C::SMEM, st);
+}
+}  // namespace fftk
+
+template <typename T>
+cudaError_t run_fft_t(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, cudaStream_t st) {
+  if (nvec == 0) return cudaSuccess;
+  switch (c->n) {
+    case 8: return fftk::run_fft_n<T, 8>(c, X, Y, nvec, dir, st);
+    case 16: return fftk::run_fft_n<T, 16>(c, X, Y, nvec, dir, st);
+    case 32: return fftk::run_fft_n<T, 32>(c, X, Y, nvec, dir, st);
+    case 64: return fftk::run_fft_n<T, 64>(c, X, Y, nvec, dir, st);
+    case 128: return fftk::run_fft_n<T, 128>(c, X, Y, nvec, dir, st);
+    case 256: return fftk::run_fft_n<T, 256>(c, X, Y, nvec, dir, st);
   }
   return cudaErrorInvalidValue;
 }

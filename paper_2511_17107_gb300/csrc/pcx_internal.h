@@ -61,6 +61,9 @@ struct pcx_ctx {
   void* scratch = nullptr;     // gamma kappa.x carried from pass 1 to pass 5
   size_t scratch_bytes = 0;
   size_t l2_bytes = 0;
+  // workspace of the learned-correction kernels (learned.cpp)
+  void* cnn_ws = nullptr;
+  size_t cnn_ws_bytes = 0;
   // staging for pcx_apply_host
   void* stage_x = nullptr;
   void* stage_y = nullptr;
@@ -94,6 +97,20 @@ int apply_chunk(const pcx_ctx* c, int precision);
 size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec);
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec,
                            int precision, cudaStream_t s);
+// learned correction of K_P^{-1} (learned.cpp; parameters: cnn::NPARAMS floats)
+cudaError_t cnn_gates(pcx_ctx* c, const float* params, float* gates, cudaStream_t s);
+cudaError_t cnn_forward(pcx_ctx* c, const float* params, const float* gates, const void* U, void* Y, int nvec,
+                        cudaStream_t s);
+cudaError_t cnn_grad(pcx_ctx* c, const float* params, const void* U, const void* T, const double* wv_host, int nvec,
+                     float* grad, int accumulate, double* loss_host, cudaStream_t s);
+cudaError_t cnn_precond(pcx_ctx* c, const KParams& kp, const float* params, const float* gates, const void* R, void* W,
+                        int nvec, cudaStream_t s);
+cudaError_t cnn_pairs(pcx_ctx* c, const KParams& kp, const void* R, const void* E, void* U, void* T, double* enorm2_host,
+                      int nvec, cudaStream_t s);
+cudaError_t cg_solve(pcx_ctx* c, const KParams& kp, const void* R, void* E, int nvec, double tol, int maxit,
+                     int* iters, double* relres, cudaStream_t s);
+// unnormalised 3D DFT of every component, dir > 0: N^{3/2} F3_3, dir < 0: N^{3/2} F3_3^H (Y may be X)
+cudaError_t launch_fft(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, int precision, cudaStream_t s);
 // out[v] = x_v^H K_B x_v, out[nvec + v] = ||x_v||^2 (device doubles, zeroed here)
 cudaError_t launch_div_norms(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, int precision, double* out,
                              cudaStream_t s);

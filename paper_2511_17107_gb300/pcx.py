@@ -89,6 +89,14 @@ def lib():
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
             "pcx_div_norms": (st, [vp, dp, vp, C.c_int, C.c_int, vp, vp]),
+            "pcx_cnn_init": (st, [C.c_uint64, vp, vp]),
+            "pcx_cnn_gates": (st, [vp, vp, vp, vp]),
+            "pcx_cnn_forward": (st, [vp, vp, vp, vp, vp, C.c_int, vp]),
+            "pcx_cnn_grad": (st, [vp, vp, vp, vp, dp, C.c_int, vp, C.c_int, dp, vp]),
+            "pcx_cnn_adam": (st, [vp, vp, vp, vp, C.c_int, C.c_float, vp]),
+            "pcx_cnn_precond": (st, [vp, dp, C.c_double, vp, vp, vp, vp, C.c_int, vp]),
+            "pcx_cnn_pairs": (st, [vp, dp, C.c_double, vp, vp, vp, vp, dp, C.c_int, vp]),
+            "pcx_cg_solve": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_double, C.c_int, ip, dp, vp]),
             "pcx_gram_mixed": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, vp, vp]),
             "pcx_combine": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_double, vp, C.c_size_t, C.c_int, vp]),
             "pcx_residual": (st, [vp, vp, vp, vp, vp, vp, C.c_int, C.c_size_t, C.c_int, vp]),
@@ -106,7 +114,9 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
+                        "pcx_div_norms", "pcx_cnn_init", "pcx_cnn_gates",
+                        "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
+                        "pcx_cg_solve", "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
 
 def _check(status, ctx=None):
@@ -326,6 +336,73 @@ def pcx_div_norms(ctx, k, X, out, stream=None):
     _check(lib().pcx_div_norms(ctx.handle, _dptr(kk), _devptr(X), X.shape[0], _prec_of(X), _devptr(out),
                                _stream(stream)), ctx.handle)
     return out
+
+
+PCX_CNN_HIDDEN = 8
+PCX_CNN_NPARAMS = (PCX_CNN_HIDDEN * 3 * 27 + PCX_CNN_HIDDEN * PCX_CNN_HIDDEN * 27 + 3 * PCX_CNN_HIDDEN * 27
+                   + 2 * (PCX_CNN_HIDDEN * 9 * 27 + PCX_CNN_HIDDEN))
+
+
+def pcx_cnn_init(seed, params, stream=None):
+    """params (float32 CUDA, PCX_CNN_NPARAMS): seeded initial parameters."""
+    _check(lib().pcx_cnn_init(int(seed), _devptr(params), _stream(stream)))
+    return params
+
+
+def pcx_cnn_gates(ctx, params, gates, stream=None):
+    """gates (float32 CUDA, 2 * 8 * N^3): the gate fields of the structure."""
+    _check(lib().pcx_cnn_gates(ctx.handle, _devptr(params), _devptr(gates), _stream(stream)), ctx.handle)
+    return gates
+
+
+def pcx_cnn_forward(ctx, params, gates, U, Y, stream=None):
+    """Y = g(Re U) + i g(Im U) (complex64 real-space fields)."""
+    _check(lib().pcx_cnn_forward(ctx.handle, _devptr(params), _devptr(gates), _devptr(U), _devptr(Y), U.shape[0],
+                                 _stream(stream)), ctx.handle)
+    return Y
+
+
+def pcx_cnn_grad(ctx, params, U, T, w, grad, accumulate=False, stream=None):
+    """Returns L = sum_v w_v ||g(U_v) - T_v||^2; grad (float32 CUDA) receives (or accumulates) dL/dparams."""
+    wv = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    loss = np.zeros(1)
+    _check(lib().pcx_cnn_grad(ctx.handle, _devptr(params), _devptr(U), _devptr(T), _dptr(wv), U.shape[0],
+                              _devptr(grad), int(bool(accumulate)), _dptr(loss), _stream(stream)), ctx.handle)
+    return float(loss[0])
+
+
+def pcx_cnn_adam(params, grad, m, v, step, lr, stream=None):
+    _check(lib().pcx_cnn_adam(_devptr(params), _devptr(grad), _devptr(m), _devptr(v), int(step), float(lr),
+                              _stream(stream)))
+    return params
+
+
+def pcx_cnn_precond(ctx, k, params, gates, R, W, gamma=0.0, stream=None):
+    """W = K_P^{-1} R + F3^H g(F3 K_P^{-1} R) (complex64, Fourier basis)."""
+    kk, kp = _kvec(k)
+    _check(lib().pcx_cnn_precond(ctx.handle, kp, float(gamma), _devptr(params), _devptr(gates), _devptr(R),
+                                 _devptr(W), R.shape[0], _stream(stream)), ctx.handle)
+    return W
+
+
+def pcx_cnn_pairs(ctx, k, R, E, U, T, gamma=0.0, stream=None):
+    """U = F3 K_P^{-1} R, T = F3 (E - K_P^{-1} R); returns ||E_v||^2 (numpy)."""
+    kk, kp = _kvec(k)
+    en2 = np.zeros(R.shape[0])
+    _check(lib().pcx_cnn_pairs(ctx.handle, kp, float(gamma), _devptr(R), _devptr(E), _devptr(U), _devptr(T),
+                               _dptr(en2), R.shape[0], _stream(stream)), ctx.handle)
+    return en2
+
+
+def pcx_cg_solve(ctx, k, R, E, tol=1e-4, maxit=200, gamma=0.0, stream=None):
+    """E = Op^{-1} R by PCG; returns (iterations, relative residuals)."""
+    kk, kp = _kvec(k)
+    its = np.zeros(1, dtype=np.int32)
+    rel = np.zeros(R.shape[0])
+    _check(lib().pcx_cg_solve(ctx.handle, kp, float(gamma), _devptr(R), _devptr(E), R.shape[0], float(tol),
+                              int(maxit), its.ctypes.data_as(C.POINTER(C.c_int)), _dptr(rel), _stream(stream)),
+           ctx.handle)
+    return int(its[0]), rel
 
 
 def pcx_gram_mixed(A, B, G, ctx=None, stream=None):

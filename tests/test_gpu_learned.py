@@ -1,0 +1,165 @@
+"""GPU parity of the learned preconditioner correction against the oracle
+(oracle/learned.py), through the C ABI: gates, forward pass, loss gradient,
+the corrected preconditioner T(r), training pairs, the PCG solve of
+Op e = r, and a short training run.  FP32 kernels: tolerances relative to the
+largest entry, 2e-5 for fields and 2e-4 for parameter gradients (sums over
+N^3 voxels and 27 taps in FP32)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fourier, learned, penalty, permittivity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pcx():
+    from paper_2511_17107_gb300 import build, pcx as binding
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return binding
+
+
+def _params(seed, scale=0.25):
+    rng = np.random.default_rng(seed)
+    p = {name: (rng.standard_normal(shape) * scale).astype(np.float32).astype(np.float64)
+         for name, shape in learned.param_shapes()}
+    return p
+
+
+def _case(pcx, n, seed=3):
+    s = wl.random_inclusions(seed)
+    f = learned.features(permittivity.cell_blocks(s, n))
+    ctx = pcx.setup_structure(s, n)
+    return s, f, ctx
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(dtype)).cuda()
+
+
+def _close(got, want, tol):
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err <= tol, err
+    return err
+
+
+@pytest.mark.parametrize("n", [8, 32])
+def test_gates_and_forward_match_oracle(pcx, n):
+    s, f, ctx = _case(pcx, n)
+    p = _params(1)
+    P = _dev(learned.pack(p), np.float32)
+    G = torch.empty(2 * learned.HIDDEN * n ** 3, dtype=torch.float32, device="cuda")
+    pcx.pcx_cnn_gates(ctx, P, G)
+    g1, g2 = learned.gates(p, f)
+    _close(G.cpu().numpy()[: learned.HIDDEN * n ** 3].reshape(g1.shape), g1, 1e-5)
+    _close(G.cpu().numpy()[learned.HIDDEN * n ** 3:].reshape(g2.shape), g2, 1e-5)
+    U = wl.random_block(2, n, seed=7)
+    Y = torch.empty((2, 3, n, n, n), dtype=torch.complex64, device="cuda")
+    pcx.pcx_cnn_forward(ctx, P, G, _dev(U, np.complex64), Y)
+    _close(Y.cpu().numpy(), learned.forward(p, f, U.astype(np.complex64).astype(np.complex128)), 2e-5)
+
+
+def test_gradient_matches_oracle(pcx):
+    n, nv = 8, 2
+    s, f, ctx = _case(pcx, n, seed=4)
+    p = _params(2)
+    U = wl.random_block(nv, n, seed=8).astype(np.complex64).astype(np.complex128)
+    T = wl.random_block(nv, n, seed=9).astype(np.complex64).astype(np.complex128)
+    w = np.array([0.8, 1.7])
+    want_loss, want = learned.loss_and_grad(p, f, U, T, w)
+    P = _dev(learned.pack(p), np.float32)
+    grad = torch.zeros(pcx.PCX_CNN_NPARAMS, dtype=torch.float32, device="cuda")
+    loss = pcx.pcx_cnn_grad(ctx, P, _dev(U, np.complex64), _dev(T, np.complex64), w, grad)
+    assert abs(loss - want_loss) <= 1e-5 * want_loss
+    got = learned.unpack(grad.cpu().numpy().astype(np.float64))
+    for name, _ in learned.param_shapes():
+        _close(got[name], want[name], 2e-4)
+    # accumulate = 1 adds a second gradient on top
+    pcx.pcx_cnn_grad(ctx, P, _dev(U, np.complex64), _dev(T, np.complex64), w, grad, accumulate=True)
+    _close(grad.cpu().numpy().astype(np.float64), 2 * learned.pack(want), 2e-4)
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_learned_preconditioner_matches_oracle(pcx, n):
+    s, f, ctx = _case(pcx, n, seed=7)
+    k = np.array([0.6, -1.1, 2.0])
+    g = penalty.gamma_practical(k)
+    kap = fourier.kappa(n, s.lattice, k)
+    p = _params(3, 0.2)
+    P = _dev(learned.pack(p), np.float32)
+    G = torch.empty(2 * learned.HIDDEN * n ** 3, dtype=torch.float32, device="cuda")
+    pcx.pcx_cnn_gates(ctx, P, G)
+    nv = 2 if n == 16 else 1
+    R = wl.random_block(nv, n, seed=12).astype(np.complex64)
+    W = torch.empty((nv, 3, n, n, n), dtype=torch.complex64, device="cuda")
+    pcx.pcx_cnn_precond(ctx, k, P, G, _dev(R, np.complex64), W)
+    want = np.stack([learned.precondition(p, f, R[v].astype(np.complex128), kap, g) for v in range(nv)])
+    _close(W.cpu().numpy(), want, 2e-5)
+
+
+def test_training_pairs_match_oracle(pcx):
+    n = 16
+    s, f, ctx = _case(pcx, n, seed=6)
+    k = np.array([1.3, 0.2, -0.7])
+    g = penalty.gamma_practical(k)
+    kap = fourier.kappa(n, s.lattice, k)
+    R = wl.random_block(2, n, seed=14).astype(np.complex64)
+    E = wl.random_block(2, n, seed=15).astype(np.complex64)
+    U = torch.empty((2, 3, n, n, n), dtype=torch.complex64, device="cuda")
+    T = torch.empty_like(U)
+    en2 = pcx.pcx_cnn_pairs(ctx, k, _dev(R, np.complex64), _dev(E, np.complex64), U, T)
+    wu, wt, wen2 = learned.training_pair(R.astype(np.complex128), E.astype(np.complex128), kap, g)
+    _close(U.cpu().numpy(), wu, 2e-5)
+    _close(T.cpu().numpy(), wt, 2e-5)
+    np.testing.assert_allclose(en2, wen2, rtol=1e-5)
+
+
+def test_cg_solve_inverts_the_operator(pcx):
+    """E = Op^{-1} R: the true residual ||Op E - R|| / ||R||, with Op the
+    oracle's symbol form of the compensated operator, is at the requested
+    tolerance (FP32 vectors)."""
+    n = 16
+    s = wl.random_inclusions(2)
+    blocks = permittivity.cell_blocks(s, n)
+    k = np.array([0.9, 0.4, -1.2])
+    g = penalty.gamma_practical(k)
+    kap = fourier.kappa(n, s.lattice, k)
+    ctx = pcx.setup_structure(s, n)
+    R = wl.random_block(3, n, seed=21).astype(np.complex64)
+    E = torch.empty((3, 3, n, n, n), dtype=torch.complex64, device="cuda")
+    its, rel = pcx.pcx_cg_solve(ctx, k, _dev(R, np.complex64), E, tol=1e-4, maxit=300)
+    assert np.all(rel <= 1e-4) and its < 300
+    e = E.cpu().numpy().astype(np.complex128)
+    ope = fourier.apply_symbols(e, kap, lambda x: permittivity.apply_m(blocks, x), g)
+    true = np.linalg.norm((ope - R).reshape(3, -1), axis=1) / np.linalg.norm(R.reshape(3, -1), axis=1)
+    assert np.all(true <= 5e-4), true
+
+
+def test_training_lowers_the_loss(pcx):
+    """Targets e = Op^{-1} r from the PCG solve, 60 Adam steps on one
+    structure: the relative error of T against e must fall well below that
+    of K_P^{-1} alone."""
+    n, nv = 32, 4
+    s = wl.random_inclusions(11)
+    ctx = pcx.setup_structure(s, n)
+    k = np.array([1.0, 0.5, 0.25]) * np.pi
+    R = _dev(wl.random_block(nv, n, seed=30), np.complex64)
+    E = torch.empty_like(R)
+    pcx.pcx_cg_solve(ctx, k, R, E, tol=1e-4, maxit=300)
+    U = torch.empty_like(R)
+    T = torch.empty_like(R)
+    en2 = pcx.pcx_cnn_pairs(ctx, k, R, E, U, T)
+    w = 1.0 / (nv * en2)
+    P = torch.empty(pcx.PCX_CNN_NPARAMS, dtype=torch.float32, device="cuda")
+    pcx.pcx_cnn_init(5, P)
+    m = torch.zeros_like(P)
+    v = torch.zeros_like(P)
+    grad = torch.zeros_like(P)
+    losses = []
+    for step in range(1, 61):
+        losses.append(pcx.pcx_cnn_grad(ctx, P, U, T, w, grad))
+        pcx.pcx_cnn_adam(P, grad, m, v, step, 3e-3)
+    assert losses[-1] < 0.6 * losses[0], (losses[0], losses[-1])

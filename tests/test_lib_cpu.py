@@ -113,3 +113,12 @@ def test_invalid_setup_rejected(pcx, n, m, lat):
     with pytest.raises(pcx.PcxError) as ei:
         pcx.pcx_sample_host(s, n, stencil_m=m)
     assert ei.value.status == pcx.PCX_EINVAL
+
+
+def test_cnn_parameter_count_matches_oracle_layout():
+    import re
+    from oracle import learned
+    from paper_2511_17107_gb300 import pcx as binding
+    assert binding.PCX_CNN_NPARAMS == learned.param_count(binding.PCX_CNN_HIDDEN)
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "pcx.h")).read()
+    assert re.search(r"#define PCX_CNN_HIDDEN 8\b", hdr)
