@@ -1,15 +1,25 @@
 """Learned preconditioner correction (oracle; test infrastructure only).
 
-The paper has no learned component.  This module defines the small network
-that corrects the FFT-diagonal preconditioner K_P^{-1} (Sec. 2.4, eqs.
-matrixfree_diagP / matrixfree_finalform), in plain numpy FP64:
+The paper has no learned component.  This module defines the preconditioner
+that the learned part corrects and the correction, in plain numpy FP64.
 
-    T(r) = K_P^{-1} r + F3_3^H g(F3_3 K_P^{-1} r)
+Base: the curl-sandwich approximate inverse of the compensated operator
+(Johnson and Joannopoulos, Opt. Express 8 (2001) 173, Sec. 3.1, restated for
+the Fourier basis of Sec. 2.4 and the symbols of Prop. 2.8):
 
-with F3_3 the unitary 3D DFT of every component (Sec. 2.4; x = F3_3^H H is
-the Fourier basis, so F3_3 maps back to the real-space grid) and g a
-three-layer circular 3D convolution net on the real-space field whose hidden
-channels are gated by the per-cell permittivity blocks M (Sec. 3.2.1):
+    T0 r = K_A F3_3^H eps F3_3 (K_A^H r / |k|^2) / |k|^2 + K_B r / (gamma |k|^4)
+
+with eps = M^{-1} cell by cell (the inverse of the 3x3 block of Sec. 3.2.1)
+and |k|^2 = sum_i |kappa_i|^2 per mode.  Because K_A K_A^H + K_B = |k|^2 I
+per mode, T0 is the exact inverse of Op = K_A F3_3^H M F3_3 K_A^H + gamma K_B
+for a homogeneous isotropic medium; it differs from K_P^{-1} (eq.
+matrixfree_finalform) only in carrying eps through real space.  Modes with
+|k| = 0 (k = 0, p = 0: the null space H of Prop. 2.5) map to 0.
+
+Correction: a three-layer circular 3D convolution net g acts next to eps on
+the real-space field e = F3_3 (K_A^H r / |k|^2):
+
+    T(r) = T0 r + K_A F3_3^H g(e) / |k|^2,
 
     f      = the 9 reals of the cell block of M: d1, d2, d3,
              Re/Im M_12, Re/Im M_13, Re/Im M_23            (9 x N^3)
@@ -19,16 +29,17 @@ channels are gated by the per-cell permittivity blocks M (Sec. 3.2.1):
     a2     = conv(h1, W2), h2 = a2 * g2                     (C -> C)
     y      = conv(h2, W3)                                   (C -> 3)
 
-The net is linear in u for a fixed structure, and it acts on the real and
-imaginary parts of the complex field with the same weights, so T is a
-complex-linear map.  conv is a cross-correlation with 3 x 3 x 3 taps and
-periodic wrap-around:  conv(x, w)[o, z, y, x] =
-sum_{i, dz, dy, dx} w[o, i, dz+1, dy+1, dx+1] x[i, z+dz, y+dy, x+dx].
+g is linear in u for a fixed structure and acts on the real and imaginary
+parts of the complex field with the same weights, so T is complex-linear.
+conv is a cross-correlation with 3 x 3 x 3 taps and periodic wrap-around:
+conv(x, w)[o, z, y, x] = sum_{i, dz, dy, dx} w[o, i, dz+1, dy+1, dx+1]
+x[i, z+dz, y+dy, x+dx].
 
-Training target: e = Op^{-1} r (Op the compensated operator of eq.
-matrixfree_kcform), the ideal preconditioner for the smallest eigenvalues;
-loss = sum_v w_v ||T(r_v) - e_v||^2, evaluated in real space (F3_3 is
-unitary) as sum_v w_v ||y_v - F3_3 (e_v - K_P^{-1} r_v)||^2.
+Training target: e_r = Op^{-1} r (Op of eq. matrixfree_kcform).  If g(U) = T
+with U = F3_3 (K_A^H r / |k|^2) and T = F3_3 K_A^H (e_r - T0 r), then
+T(r) = T0 r + P (e_r - T0 r) with P = K_A K_A^H / |k|^2 the projector on the
+range of K_A, whose complement T0 already inverts exactly; the loss is
+sum_v w_v ||g(U_v) - T_v||^2 with w_v = 1 / (count ||K_A^H e_v||^2).
 
 Parameters are one flat vector in the order W1, W2, W3, V1, c1, V2, c2, each
 in C order (param_shapes).
@@ -168,17 +179,44 @@ def loss_and_grad(p: dict, f: np.ndarray, U: np.ndarray, T: np.ndarray, w: np.nd
     return loss, grads
 
 
-def precondition(p: dict, f: np.ndarray, r: np.ndarray, kap, gamma) -> np.ndarray:
-    """T(r) = K_P^{-1} r + F3_3^H g(F3_3 K_P^{-1} r), r in the Fourier basis."""
-    base = fourier.precondition(r, kap, gamma)
-    return base + fourier.f3h(forward(p, f, fourier.f3(base)))
+def _k2(kap):
+    k2 = np.sum(np.abs(kap) ** 2, axis=0)
+    return np.where(k2 > 0, k2, np.inf)   # 1 / inf = 0 on the null mode
 
 
-def training_pair(r: np.ndarray, e: np.ndarray, kap, gamma):
-    """Real-space network input U = F3_3 K_P^{-1} r, target T = F3_3 (e - K_P^{-1} r)
-    and ||e||^2 per vector."""
-    base = fourier.precondition(r, kap, gamma)
-    U = fourier.f3(base)
-    T = fourier.f3(e - base)
-    en2 = np.sum(np.abs(e) ** 2, axis=tuple(range(1, e.ndim)))
+def curl_h_scaled(r, kap):
+    """K_A^H r / |k|^2 per mode."""
+    ka = fourier.ka_matrix(kap)
+    return fourier._per_mode(np.conj(np.swapaxes(ka, -1, -2)), r) / _k2(kap)
+
+
+def curl_scaled(w, kap):
+    """K_A w / |k|^2 per mode."""
+    return fourier._per_mode(fourier.ka_matrix(kap), w) / _k2(kap)
+
+
+def sandwich_precondition(r, kap, blocks, gamma):
+    """T0 r (the curl-sandwich approximate inverse, module docstring)."""
+    eps = np.linalg.inv(blocks)
+    e = fourier.f3(curl_h_scaled(r, kap))
+    m = np.einsum("zyxij,...jzyx->...izyx", eps, e)
+    longi = fourier._per_mode(fourier.kb_matrix(kap), r) / (gamma * _k2(kap) ** 2)
+    return curl_scaled(fourier.f3h(m), kap) + longi
+
+
+def precondition(p: dict, f: np.ndarray, r: np.ndarray, kap, gamma, blocks) -> np.ndarray:
+    """T(r) = T0 r + K_A F3_3^H g(F3_3 K_A^H r / |k|^2) / |k|^2."""
+    e = fourier.f3(curl_h_scaled(r, kap))
+    return sandwich_precondition(r, kap, blocks, gamma) + curl_scaled(fourier.f3h(forward(p, f, e)), kap)
+
+
+def training_pair(r: np.ndarray, e: np.ndarray, kap, gamma, blocks):
+    """Network input U = F3_3 (K_A^H r / |k|^2), target T = F3_3 K_A^H (e - T0 r)
+    and ||K_A^H e||^2 per vector."""
+    ka = fourier.ka_matrix(kap)
+    kah = np.conj(np.swapaxes(ka, -1, -2))
+    U = fourier.f3(curl_h_scaled(r, kap))
+    T = fourier.f3(fourier._per_mode(kah, e - sandwich_precondition(r, kap, blocks, gamma)))
+    ce = fourier._per_mode(kah, e)
+    en2 = np.sum(np.abs(ce) ** 2, axis=tuple(range(1, e.ndim)))
     return U, T, en2

@@ -1,7 +1,9 @@
 """Pins of the learned-correction oracle (oracle/learned.py) against
 definitions outside it: scipy's periodic correlation, the circular
 correlation theorem through numpy FFTs, the adjoint identity, central finite
-differences of the loss, and the limits in which T reduces to K_P^{-1}."""
+differences of the loss, the exact inverse of a homogeneous isotropic medium,
+Hermitian symmetry, a dense-solve reconstruction of Op^{-1} r, and the limit
+in which T reduces to the curl-sandwich base T0."""
 import numpy as np
 import pytest
 
@@ -80,28 +82,74 @@ def test_loss_gradient_matches_finite_differences():
         assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (j, fd, gflat[j])
 
 
-def _small_case(n=8):
-    s = wl.random_inclusions(5)
+def _small_case(n=8, seed=7):
+    s = wl.random_inclusions(seed)
     blocks = permittivity.cell_blocks(s, n)
     k = np.array([0.4, -0.9, 1.7])
     kap = fourier.kappa(n, s.lattice, k)
-    return learned.features(blocks), kap, 4 * np.pi ** 2
+    return learned.features(blocks), blocks, kap, 4 * np.pi ** 2
 
 
-def test_preconditioner_is_complex_linear_and_reduces_to_kp():
+def _op(blocks, kap, gam):
+    return lambda x: fourier.apply_symbols(x, kap, lambda e: permittivity.apply_m(blocks, e), gam)
+
+
+def test_sandwich_inverts_the_operator_of_a_homogeneous_isotropic_medium():
+    """M = m0 I: T0 Op r = r, the identity K_A K_A^H + K_B = |k|^2 I at work."""
+    n, m0, gam = 6, 0.37, 4 * np.pi ** 2
+    for lat in (wl.SC, wl.FCC):
+        kap = fourier.kappa(n, lat, np.array([0.7, -1.3, 2.1]))
+        blocks = np.broadcast_to(m0 * np.eye(3), (n, n, n, 3, 3)).astype(np.complex128)
+        r = wl.random_block(2, n, seed=3)
+        got = learned.sandwich_precondition(_op(blocks, kap, gam)(r), kap, blocks, gam)
+        np.testing.assert_allclose(got, r, rtol=0, atol=1e-12 * np.abs(r).max())
+
+
+def test_sandwich_is_hermitian_positive():
+    f, blocks, kap, gam = _small_case()
+    n = f.shape[-1]
+    x = wl.random_block(1, n, seed=4)[0]
+    y = wl.random_block(1, n, seed=5)[0]
+    lhs = np.vdot(x, learned.sandwich_precondition(y, kap, blocks, gam))
+    rhs = np.conj(np.vdot(y, learned.sandwich_precondition(x, kap, blocks, gam)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    assert np.vdot(x, learned.sandwich_precondition(x, kap, blocks, gam)).real > 0
+
+
+def test_preconditioner_is_complex_linear_and_reduces_to_the_sandwich():
     rng = np.random.default_rng(4)
-    f, kap, gam = _small_case()
+    f, blocks, kap, gam = _small_case()
     n = f.shape[-1]
     p = _rand_params(rng, learned.HIDDEN, 0.2)
     r1 = wl.random_block(1, n, seed=8)[0]
     r2 = wl.random_block(1, n, seed=9)[0]
     a, b = 0.3 - 1.1j, -2.0 + 0.5j
-    lhs = learned.precondition(p, f, a * r1 + b * r2, kap, gam)
-    rhs = a * learned.precondition(p, f, r1, kap, gam) + b * learned.precondition(p, f, r2, kap, gam)
+    lhs = learned.precondition(p, f, a * r1 + b * r2, kap, gam, blocks)
+    rhs = a * learned.precondition(p, f, r1, kap, gam, blocks) + b * learned.precondition(p, f, r2, kap, gam, blocks)
     np.testing.assert_allclose(lhs, rhs, rtol=1e-11, atol=1e-11 * np.abs(rhs).max())
     p["W3"][:] = 0.0
-    np.testing.assert_allclose(learned.precondition(p, f, r1, kap, gam), fourier.precondition(r1, kap, gam),
-                               rtol=1e-13, atol=0)
+    np.testing.assert_allclose(learned.precondition(p, f, r1, kap, gam, blocks),
+                               learned.sandwich_precondition(r1, kap, blocks, gam), rtol=1e-13, atol=0)
+
+
+def test_exact_training_pair_reconstructs_the_inverse():
+    """With e = Op^{-1} r from a dense solve (N = 4), T0 r + K_A F3^H T / |k|^2
+    built from the training pair equals e: the target carries exactly the
+    part of the error that the correction can reach."""
+    n = 4
+    s = wl.random_inclusions(3)
+    blocks = permittivity.cell_blocks(s, n)
+    kap = fourier.kappa(n, s.lattice, np.array([0.9, -0.4, 1.3]))
+    gam = 4 * np.pi ** 2
+    op = _op(blocks, kap, gam)
+    dim = 3 * n ** 3
+    mat = np.stack([op(np.eye(dim)[j].reshape(3, n, n, n)).ravel() for j in range(dim)], axis=1)
+    r = wl.random_block(1, n, seed=2)[0]
+    e = np.linalg.solve(mat, r.ravel()).reshape(r.shape)
+    U, T, en2 = learned.training_pair(r[None], e[None], kap, gam, blocks)
+    rec = learned.sandwich_precondition(r, kap, blocks, gam) + learned.curl_scaled(fourier.f3h(T[0]), kap)
+    np.testing.assert_allclose(rec, e, rtol=0, atol=1e-10 * np.abs(e).max())
+    np.testing.assert_allclose(U[0], fourier.f3(learned.curl_h_scaled(r, kap)), rtol=1e-14)
 
 
 def test_open_gates_reduce_to_plain_convolutions():
