@@ -334,16 +334,28 @@ pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol
 pcx_status pcx_div_norms(pcx_ctx* ctx, const double k[3], const void* X, int nvec, int precision, double* out,
                          void* stream);
 
+/*
+ * pcx_sandwich_precond -- W = T0 R, the curl-sandwich approximate inverse of
+ * the compensated operator (Johnson and Joannopoulos, Opt. Express 8 (2001)
+ * 173, restated with the symbols of Prop. 2.8; not in the paper):
+ *   T0 r = K_A F3_3^H eps F3_3 (K_A^H r / |k|^2) / |k|^2 + K_B r / (gamma |k|^4)
+ * with eps = M^{-1} cell by cell and |k|^2 = sum_i |kappa_i|^2 per mode (a
+ * mode with |k| = 0 maps to 0).  Exact inverse for a homogeneous isotropic
+ * medium (K_A K_A^H + K_B = |k|^2 I); K_P^{-1} is T0 with eps = I.  Costs
+ * about two applies.  Device buffers as in pcx_apply; W may alias R.
+ */
+pcx_status pcx_sandwich_precond(pcx_ctx* ctx, const double k[3], double gamma, const void* R, void* W, int nvec,
+                                int precision, void* stream);
+
 /* ---------------------------------------------------------------------------
- * Learned correction of the preconditioner.  The paper has no learned
- * component; this corrects its FFT-diagonal K_P^{-1} (eqs. matrixfree_diagP,
- * matrixfree_finalform) as
+ * Learned correction of the preconditioner (the paper has no learned part):
  *
- *   T(r) = K_P^{-1} r + F3_3^H g(F3_3 K_P^{-1} r)
+ *   T(r) = T0 r + K_A F3_3^H g(e) / |k|^2,   e = F3_3 (K_A^H r / |k|^2),
  *
- * with F3_3 the unitary 3D DFT of each component (Sec. 2.4: x = F3_3^H H) and
- * g a three-layer circular 3D convolution net (3x3x3 taps) on the real-space
- * field, applied with the same weights to its real and imaginary parts:
+ * T0 as in pcx_sandwich_precond, F3_3 the unitary 3D DFT of each component
+ * (Sec. 2.4: x = F3_3^H H), and g a three-layer circular 3D convolution net
+ * (3x3x3 taps) acting next to eps on the real-space field e, with the same
+ * weights on its real and imaginary parts:
  *   g1 = sigmoid(conv(f, V1) + c1),  g2 = sigmoid(conv(f, V2) + c2)
  *   y  = conv(g2 * conv(g1 * conv(u, W1), W2), W3)
  * where f are the 9 reals of the cell blocks of M (Sec. 3.2.1: d1, d2, d3,
@@ -384,13 +396,14 @@ pcx_status pcx_cnn_grad(pcx_ctx* ctx, const float* params, const void* U, const 
 pcx_status pcx_cnn_adam(float* params, const float* grad, float* m, float* v, int step, float lr, void* stream);
 
 /* W = T(R) for nvec Fourier-basis vectors (complex64), gates from
- * pcx_cnn_gates.  gamma <= 0: the rule of Remark 2.6. */
+ * pcx_cnn_gates.  gamma <= 0: the rule of Remark 2.6.  W may alias R. */
 pcx_status pcx_cnn_precond(pcx_ctx* ctx, const double k[3], double gamma, const float* params, const float* gates,
                            const void* R, void* W, int nvec, void* stream);
 
 /* Training pairs from residuals R and targets E = Op^{-1} R (Fourier basis,
- * complex64): U = F3_3 K_P^{-1} R and T = F3_3 (E - K_P^{-1} R) (real space),
- * and enorm2[v] = ||E_v||^2 (HOST doubles; synchronises when not NULL). */
+ * complex64): the net's input U = F3_3 (K_A^H R / |k|^2) and target
+ * T = F3_3 K_A^H (E - T0 R) (real space; g(U) = T makes T(R) = E), and
+ * enorm2[v] = ||K_A^H E_v||^2 (HOST doubles; synchronises when not NULL). */
 pcx_status pcx_cnn_pairs(pcx_ctx* ctx, const double k[3], double gamma, const void* R, const void* E, void* U,
                          void* T, double* enorm2, int nvec, void* stream);
 
@@ -417,6 +430,9 @@ typedef struct {
   double ms_other;       /* preconditioner, combinations, residuals, conversions   */
   int gamma_raises;      /* times the spurious-mode guard raised gamma (all k)     */
   double gamma_last;     /* penalty coefficient used at the last k                 */
+  double ms_precond;     /* preconditioner (K_P^{-1} or the learned T)              */
+  int learned_fallbacks; /* k-points at which the learned correction fell back     */
+  int dumped;            /* residual columns written to dump_R                      */
 } pcx_solve_stats;
 
 /* Eigensolver options (pcx_solve).  Zero-initialised fields take defaults. */
@@ -437,6 +453,19 @@ typedef struct {
                          gamma is then multiplied by 4 and k re-solved, at most
                          4 times (then PCX_ENUMERIC).  0: default 1e-6;
                          negative: guard off                                      */
+  const float* cnn_params; /* DEVICE parameters of the learned correction
+                         (PCX_CNN_NPARAMS floats) or NULL.  With PCX_FP32 the
+                         search directions use T(R) (pcx_cnn_precond) until the
+                         worst wanted residual has not dropped for 3
+                         iterations at a k; then the precond_kind one         */
+  void* dump_R;       /* optional DEVICE complex64 buffer of dump_cap vectors:
+                         the FP32 phase copies its active residual columns
+                         every dump_every iterations until it is full
+                         (training data for the learned correction)           */
+  int dump_cap;
+  int dump_every;     /* 0: every iteration                                    */
+  int precond_kind;   /* 0: K_P^{-1} (eq. matrixfree_finalform, default);
+                         1: the curl-sandwich T0 (pcx_sandwich_precond)        */
 } pcx_solve_opts;
 
 /*

@@ -245,6 +245,18 @@ pcx_status pcx_div_norms(pcx_ctx* c, const double k[3], const void* X, int nvec,
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_div_norms", e);
 }
 
+pcx_status pcx_sandwich_precond(pcx_ctx* c, const double k[3], double gamma, const void* R, void* W, int nvec,
+                                int precision, void* stream) {
+  pcx_status st = check_block(c, "pcx_sandwich_precond", R, W, nvec, precision);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k) return inval(c, "pcx_sandwich_precond: NULL k");
+  const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
+  if (R != W && ranges_overlap(R, bytes, W, bytes)) return inval(c, "pcx_sandwich_precond: R and W partially overlap");
+  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  cudaError_t e = pcx::sandwich_precond(c, kp, R, W, nvec, precision, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_sandwich_precond", e);
+}
+
 static pcx_status check_cnn(pcx_ctx* c, const char* who, int nvec) {
   if (!c) return inval(nullptr, std::string(who) + ": NULL context");
   if (c->n < 8) return inval(c, std::string(who) + ": needs N >= 8");

@@ -25,6 +25,14 @@ template <typename T>
 cudaError_t run_div_norms_t(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, double* out, cudaStream_t s);
 template <typename T>
 cudaError_t run_fft_t(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, cudaStream_t st);
+template <typename T>
+cudaError_t run_curl_h_t(const pcx_ctx* c, const KParams& kp, const void* X, void* U, int nvec, int pow, cudaStream_t s);
+template <typename T>
+cudaError_t run_curl_add_t(const pcx_ctx* c, const KParams& kp, const void* Wm, const void* R, void* Y, int nvec,
+                           double scale_, int accumulate, cudaStream_t s);
+template <typename T>
+cudaError_t run_eps_cells_t(const pcx_ctx* c, const void* E, const void* Add, void* Mo, int nvec, double scale_,
+                            cudaStream_t s);
 extern template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
                                                cudaStream_t);
 extern template cudaError_t run_apply_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
@@ -117,6 +125,24 @@ cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, v
                            cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
   return precision == PCX_FP64 ? run_precond_t<double>(c, kp, R, W, nvec, s) : run_precond_t<float>(c, kp, R, W, nvec, s);
+}
+
+cudaError_t launch_curl_h(const pcx_ctx* c, const KParams& kp, const void* X, void* U, int nvec, int pow, int precision,
+                          cudaStream_t s) {
+  return precision == PCX_FP64 ? run_curl_h_t<double>(c, kp, X, U, nvec, pow, s)
+                               : run_curl_h_t<float>(c, kp, X, U, nvec, pow, s);
+}
+
+cudaError_t launch_curl_add(const pcx_ctx* c, const KParams& kp, const void* Wm, const void* R, void* Y, int nvec,
+                            double scale, int accumulate, int precision, cudaStream_t s) {
+  return precision == PCX_FP64 ? run_curl_add_t<double>(c, kp, Wm, R, Y, nvec, scale, accumulate, s)
+                               : run_curl_add_t<float>(c, kp, Wm, R, Y, nvec, scale, accumulate, s);
+}
+
+cudaError_t launch_eps_cells(const pcx_ctx* c, const void* E, const void* Add, void* Mo, int nvec, double scale,
+                             int precision, cudaStream_t s) {
+  return precision == PCX_FP64 ? run_eps_cells_t<double>(c, E, Add, Mo, nvec, scale, s)
+                               : run_eps_cells_t<float>(c, E, Add, Mo, nvec, scale, s);
 }
 
 cudaError_t launch_fft(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, int precision, cudaStream_t s) {

@@ -8,4 +8,8 @@ template cudaError_t run_precond_t<double>(const pcx_ctx*, const KParams&, const
 template cudaError_t run_div_norms_t<double>(const pcx_ctx*, const KParams&, const void*, int, double*,
                                             cudaStream_t);
 template cudaError_t run_fft_t<double>(const pcx_ctx*, const void*, void*, int, int, cudaStream_t);
+template cudaError_t run_curl_h_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, cudaStream_t);
+template cudaError_t run_curl_add_t<double>(const pcx_ctx*, const KParams&, const void*, const void*, void*, int, double, int,
+                                        cudaStream_t);
+template cudaError_t run_eps_cells_t<double>(const pcx_ctx*, const void*, const void*, void*, int, double, cudaStream_t);
 }  // namespace pcx

@@ -476,6 +476,129 @@ __global__ void __launch_bounds__(256) div_norm_kernel(const cx<T>* __restrict__
   }
 }
 
+// ---- pieces of the curl-sandwich approximate inverse --------------------
+//   T0 r = K_A F3_3^H eps F3_3 (K_A^H r / |k|^2) / |k|^2 + K_B r / (gamma |k|^4)
+// (Johnson and Joannopoulos 2001, with the symbols of Prop. 2.8; eps = M^{-1}
+// cell by cell; |k|^2 = sum_i |kappa_i|^2; a mode with |k| = 0 maps to 0).
+
+// U = K_A^H X / |k|^(2 POW) per mode, K_A^H x = -conj(kappa) x x
+template <typename T>
+__global__ void curl_h_kernel(const cx<T>* __restrict__ X, cx<T>* __restrict__ U, const cx<T>* __restrict__ lam,
+                              int n, int nvec, KParams kp, int pow) {
+  const size_t n3 = (size_t)n * n * n;
+  const size_t total = n3 * nvec;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = e / n3, mode = e % n3;
+    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    cx<T> kap[3];
+    kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
+    const size_t base = v * 3 * n3 + mode;
+    const cx<T> x0 = X[base], x1 = X[base + n3], x2 = X[base + 2 * n3];
+    const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+    const T sc = k2 > (T)0 ? (pow ? (T)1 / k2 : (T)1) : (T)0;
+    const cx<T> z = mk((T)0, (T)0);
+    U[base] = scale(cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, z), (T)-1)), sc);
+    U[base + n3] = scale(cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, z), (T)-1)), sc);
+    U[base + 2 * n3] = scale(cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, z), (T)-1)), sc);
+  }
+}
+
+// Y (+)= s K_A Wm / |k|^2 + [R given] conj(kappa) (kappa . r) / (gamma |k|^4)
+template <typename T>
+__global__ void curl_add_kernel(const cx<T>* __restrict__ Wm, const cx<T>* __restrict__ R, cx<T>* __restrict__ Y,
+                                const cx<T>* __restrict__ lam, int n, int nvec, KParams kp, T s, int accumulate) {
+  const size_t n3 = (size_t)n * n * n;
+  const size_t total = n3 * nvec;
+  const T ig = (T)(1.0 / kp.gamma);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = e / n3, mode = e % n3;
+    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    cx<T> kap[3];
+    kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
+    const size_t base = v * 3 * n3 + mode;
+    const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+    cx<T> y0 = mk((T)0, (T)0), y1 = y0, y2 = y0;
+    if (k2 > (T)0) {
+      const T ik2 = (T)1 / k2;
+      const cx<T> w0 = Wm[base], w1 = Wm[base + n3], w2 = Wm[base + 2 * n3];
+      const T sw = s * ik2;
+      y0 = scale(cfma(kap[1], w2, scale(kap[2] * w1, (T)-1)), sw);
+      y1 = scale(cfma(kap[2], w0, scale(kap[0] * w2, (T)-1)), sw);
+      y2 = scale(cfma(kap[0], w1, scale(kap[1] * w0, (T)-1)), sw);
+      if (R) {
+        const cx<T> r0 = R[base], r1 = R[base + n3], r2 = R[base + 2 * n3];
+        const cx<T> sk = scale(cfma(kap[2], r2, cfma(kap[1], r1, kap[0] * r0)), ig * ik2 * ik2);
+        y0 = cfma_conj(kap[0], sk, y0);
+        y1 = cfma_conj(kap[1], sk, y1);
+        y2 = cfma_conj(kap[2], sk, y2);
+      }
+    }
+    if (accumulate) {
+      y0 = y0 + Y[base];
+      y1 = y1 + Y[base + n3];
+      y2 = y2 + Y[base + 2 * n3];
+    }
+    Y[base] = y0;
+    Y[base + n3] = y1;
+    Y[base + 2 * n3] = y2;
+  }
+}
+
+// Mo = s (M_cell^{-1} E + Add) cell by cell (real-space fields; Add optional;
+// Mo may alias E).  The inverse of the Hermitian 3x3 block (real diagonal
+// d1, d2, d3, off-diagonal o12, o13, o23) by its adjugate.
+template <typename T>
+__global__ void eps_cells_kernel(const cx<T>* E, const cx<T>* __restrict__ Add, cx<T>* Mo, const uchar4* __restrict__ mid,
+                                 const T* __restrict__ mtab, const T* __restrict__ M, int n, int nvec, T s) {
+  const size_t n3 = (size_t)n * n * n;
+  const size_t total = n3 * nvec;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = e / n3, cell = e % n3;
+    T d1, d2, d3;
+    cx<T> o12, o13, o23;
+    if (mid) {
+      const uchar4 id = mid[cell];
+      d1 = mtab[9 * id.x];
+      d2 = mtab[9 * id.y + 1];
+      d3 = mtab[9 * id.z + 2];
+      const T* o = mtab + 9 * id.w;
+      o12 = mk(o[3], o[4]);
+      o13 = mk(o[5], o[6]);
+      o23 = mk(o[7], o[8]);
+    } else {
+      d1 = M[cell];
+      d2 = M[n3 + cell];
+      d3 = M[2 * n3 + cell];
+      o12 = mk(M[3 * n3 + cell], M[4 * n3 + cell]);
+      o13 = mk(M[5 * n3 + cell], M[6 * n3 + cell]);
+      o23 = mk(M[7 * n3 + cell], M[8 * n3 + cell]);
+    }
+    // adjugate entries (the inverse times det), upper triangle
+    const T a11 = d2 * d3 - norm2(o23), a22 = d1 * d3 - norm2(o13), a33 = d1 * d2 - norm2(o12);
+    const cx<T> a12 = o13 * conjg(o23) - scale(o12, d3);
+    const cx<T> a13 = o12 * o23 - scale(o13, d2);
+    const cx<T> a23 = o13 * conjg(o12) - scale(o23, d1);
+    const T det = d1 * a11 + (o12 * conjg(a12)).x + (o13 * conjg(a13)).x;
+    const T sc = s / det;
+    const size_t base = v * 3 * n3 + cell;
+    const cx<T> e0 = E[base], e1 = E[base + n3], e2 = E[base + 2 * n3];
+    cx<T> m0 = cfma(a13, e2, cfma(a12, e1, scale(e0, a11)));
+    cx<T> m1 = cfma(a23, e2, cfma_conj(a12, e0, scale(e1, a22)));
+    cx<T> m2 = cfma_conj(a23, e1, cfma_conj(a13, e0, scale(e2, a33)));
+    m0 = scale(m0, sc);
+    m1 = scale(m1, sc);
+    m2 = scale(m2, sc);
+    if (Add) {
+      m0 = m0 + scale(Add[base], s);
+      m1 = m1 + scale(Add[base + n3], s);
+      m2 = m2 + scale(Add[base + 2 * n3], s);
+    }
+    Mo[base] = m0;
+    Mo[base + n3] = m1;
+    Mo[base + 2 * n3] = m2;
+  }
+}
+
 template <typename T, int N, int AXIS, int OP>
 cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st) {
   auto kern = pass_kernel<T, N, AXIS, OP>;
@@ -579,6 +702,48 @@ cudaError_t run_fft_t(const pcx_ctx* c, const void* X, void* Y, int nvec, int di
     case 256: return fftk::run_fft_n<T, 256>(c, X, Y, nvec, dir, st);
   }
   return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t run_curl_h_t(const pcx_ctx* c, const KParams& kp, const void* X, void* U, int nvec, int pow,
+                         cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const size_t total = (size_t)c->n * c->n * c->n * nvec;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152u * 16u) blocks = 152u * 16u;
+  const void* lam = sizeof(T) == 8 ? c->dev.lam64 : c->dev.lam32;
+  fftk::curl_h_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const cx<T>*>(X), static_cast<cx<T>*>(U),
+                                                          static_cast<const cx<T>*>(lam), c->n, nvec, kp, pow);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_curl_add_t(const pcx_ctx* c, const KParams& kp, const void* Wm, const void* R, void* Y, int nvec,
+                           double scale_, int accumulate, cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const size_t total = (size_t)c->n * c->n * c->n * nvec;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152u * 16u) blocks = 152u * 16u;
+  const void* lam = sizeof(T) == 8 ? c->dev.lam64 : c->dev.lam32;
+  fftk::curl_add_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(
+      static_cast<const cx<T>*>(Wm), static_cast<const cx<T>*>(R), static_cast<cx<T>*>(Y),
+      static_cast<const cx<T>*>(lam), c->n, nvec, kp, (T)scale_, accumulate);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_eps_cells_t(const pcx_ctx* c, const void* E, const void* Add, void* Mo, int nvec, double scale_,
+                            cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const size_t total = (size_t)c->n * c->n * c->n * nvec;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152u * 16u) blocks = 152u * 16u;
+  const bool dbl = sizeof(T) == 8;
+  fftk::eps_cells_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(
+      static_cast<const cx<T>*>(E), static_cast<const cx<T>*>(Add), static_cast<cx<T>*>(Mo),
+      static_cast<const uchar4*>(c->dev.mid), static_cast<const T*>(dbl ? c->dev.mtab64 : c->dev.mtab32),
+      static_cast<const T*>(dbl ? c->dev.m64 : c->dev.m32), c->n, nvec, (T)scale_);
+  return cudaGetLastError();
 }
 
 template <typename T>

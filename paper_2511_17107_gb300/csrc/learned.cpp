@@ -1,9 +1,10 @@
 // Host orchestration of the learned preconditioner correction (cnn.cu):
 // gates, forward and backward passes of the gated convolution net, the
-// corrected preconditioner T(r) = K_P^{-1} r + F3_3^H g(F3_3 K_P^{-1} r), the
-// training pairs (r, e = Op^{-1} r) and a block preconditioned conjugate
-// gradient solver for Op e = r (Op Hermitian positive definite for k != 0;
-// at k = 0 the p = 0 mode is excluded by K_P^{-1}, Prop. 2.5).
+// curl-sandwich approximate inverse T0 and the corrected preconditioner
+// T(r) = T0 r + K_A F3_3^H g(F3_3 K_A^H r / |k|^2) / |k|^2, the training
+// pairs (r, e = Op^{-1} r) and a block preconditioned conjugate gradient
+// solver for Op e = r (Op Hermitian positive definite for k != 0; at k = 0
+// the p = 0 mode is excluded by K_P^{-1}, Prop. 2.5).
 //
 // The paper has no learned component.  Every device step is a kernel of
 // this library; the host only sequences launches and small reductions.
@@ -196,6 +197,41 @@ cudaError_t cnn_grad(pcx_ctx* c, const float* params, const void* U, const void*
   return cudaSuccess;
 }
 
+// vectors per chunk of the sandwich so that its field buffers stay within ~2 GB
+static int sandwich_chunk(const pcx_ctx* c, int nvec, size_t bytes_per_vec) {
+  size_t k = ((size_t)2 << 30) / bytes_per_vec;
+  if (k < 1) k = 1;
+  return (int)(k < (size_t)nvec ? k : (size_t)nvec);
+}
+
+// T0 R = K_A F3^H eps F3 (K_A^H R / |k|^2) / |k|^2 + K_B R / (gamma |k|^4):
+// curl_h, three inverse FFT passes, eps per cell (with the 1/N^3 of the two
+// unnormalised transforms), three forward passes, curl_add.  W may alias R.
+cudaError_t sandwich_precond(pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,
+                             cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const size_t n3 = (size_t)c->n * c->n * c->n;
+  const size_t es = precision == PCX_FP64 ? 16 : 8;
+  const size_t vb = 3 * n3 * es;
+  const int chunk = sandwich_chunk(c, nvec, vb);
+  char* ws;
+  CKE(ws_get(c, align_up((size_t)chunk * vb), &ws));
+  const double inv_n3 = 1.0 / (double)n3;
+  for (int v0 = 0; v0 < nvec; v0 += chunk) {
+    const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
+    const char* r = static_cast<const char*>(R) + (size_t)v0 * vb;
+    char* w = static_cast<char*>(W) + (size_t)v0 * vb;
+    CKE(launch_curl_h(c, kp, r, ws, nv, 1, precision, s));
+    CKE(launch_fft(c, ws, ws, nv, +1, precision, s));
+    CKE(launch_eps_cells(c, ws, nullptr, ws, nv, inv_n3, precision, s));
+    CKE(launch_fft(c, ws, ws, nv, -1, precision, s));
+    CKE(launch_curl_add(c, kp, ws, r, w, nv, 1.0, 0, precision, s));
+  }
+  return cudaSuccess;
+}
+
+// T R = T0 R + K_A F3^H g(e) / |k|^2 with e = F3 (K_A^H R / |k|^2): the net's
+// output joins eps e in real space before the forward transform.
 cudaError_t cnn_precond(pcx_ctx* c, const KParams& kp, const float* params, const float* gates, const void* R, void* W,
                         int nvec, cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
@@ -204,52 +240,55 @@ cudaError_t cnn_precond(pcx_ctx* c, const KParams& kp, const float* params, cons
   const size_t hb = align_up(2 * (size_t)chunk * C * n3 * sizeof(float));
   const size_t tb = align_up((size_t)chunk * 3 * n3 * sizeof(float2));
   char* ws;
-  CKE(ws_get(c, 2 * hb + tb, &ws));
+  CKE(ws_get(c, 2 * hb + 2 * tb, &ws));
   float* h1 = reinterpret_cast<float*>(ws);
   float* h2 = reinterpret_cast<float*>(ws + hb);
-  float2* tmp = reinterpret_cast<float2*>(ws + 2 * hb);
-  CKE(launch_precond(c, kp, R, W, nvec, PCX_FP32, s));
+  float2* e = reinterpret_cast<float2*>(ws + 2 * hb);
+  float2* y = reinterpret_cast<float2*>(ws + 2 * hb + tb);
   const size_t vlen = 3 * n3;
-  const float inv_n3 = (float)(1.0 / (double)n3);
+  const double inv_n3 = 1.0 / (double)n3;
   for (int v0 = 0; v0 < nvec; v0 += chunk) {
     const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
+    const float2* r = static_cast<const float2*>(R) + (size_t)v0 * vlen;
     float2* w = static_cast<float2*>(W) + (size_t)v0 * vlen;
-    // real space (unnormalised), the net (linear), back to Fourier; the two
-    // transforms carry N^{3/2} each, removed by 1/N^3 in the final update
-    CKE(launch_fft(c, w, tmp, nv, +1, PCX_FP32, s));
-    CKE(forward_chunk(c, params, gates, tmp, tmp, nv, h1, h2, 1.f, s));
-    CKE(launch_fft(c, tmp, tmp, nv, -1, PCX_FP32, s));
-    CKE(cnn::lincomb(reinterpret_cast<const float*>(tmp), inv_n3, reinterpret_cast<const float*>(w), 1.f,
-                     reinterpret_cast<float*>(w), (size_t)nv * 2 * vlen, s));
+    CKE(launch_curl_h(c, kp, r, e, nv, 1, PCX_FP32, s));
+    CKE(launch_fft(c, e, e, nv, +1, PCX_FP32, s));
+    CKE(forward_chunk(c, params, gates, e, y, nv, h1, h2, 1.f, s));
+    CKE(launch_eps_cells(c, e, y, e, nv, inv_n3, PCX_FP32, s));
+    CKE(launch_fft(c, e, e, nv, -1, PCX_FP32, s));
+    CKE(launch_curl_add(c, kp, e, r, w, nv, 1.0, 0, PCX_FP32, s));
   }
   return cudaSuccess;
 }
 
+// U = F3 (K_A^H R / |k|^2), T = F3 K_A^H (E - T0 R) (unitary F3), and
+// enorm2 = ||K_A^H E||^2 per vector.
 cudaError_t cnn_pairs(pcx_ctx* c, const KParams& kp, const void* R, const void* E, void* U, void* T, double* enorm2_host,
                       int nvec, cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
   const size_t n3 = (size_t)c->n * c->n * c->n;
   const size_t nf = (size_t)nvec * 6 * n3;
   const float sc = (float)(1.0 / std::pow((double)n3, 0.5));
-  // T = F3_3 (E - K_P^{-1} R), U = F3_3 K_P^{-1} R  (unitary F3_3)
-  CKE(launch_precond(c, kp, R, T, nvec, PCX_FP32, s));
-  CKE(launch_precond(c, kp, R, U, nvec, PCX_FP32, s));
+  CKE(sandwich_precond(c, kp, R, T, nvec, PCX_FP32, s));
   CKE(cnn::lincomb(static_cast<const float*>(E), 1.f, static_cast<const float*>(T), -1.f, static_cast<float*>(T), nf,
                    s));
+  CKE(launch_curl_h(c, kp, T, T, nvec, 0, PCX_FP32, s));
   CKE(launch_fft(c, T, T, nvec, +1, PCX_FP32, s));
-  CKE(launch_fft(c, U, U, nvec, +1, PCX_FP32, s));
   CKE(cnn::lincomb(static_cast<const float*>(T), sc, nullptr, 0.f, static_cast<float*>(T), nf, s));
-  CKE(cnn::lincomb(static_cast<const float*>(U), sc, nullptr, 0.f, static_cast<float*>(U), nf, s));
   if (enorm2_host) {
+    CKE(launch_curl_h(c, kp, E, U, nvec, 0, PCX_FP32, s));
     char* ws;
     CKE(ws_get(c, align_up(2 * nvec * sizeof(double)), &ws));
     double* d = reinterpret_cast<double*>(ws);
-    CKE(cnn::col_dots(E, E, nvec, 3 * n3, d, s));
+    CKE(cnn::col_dots(U, U, nvec, 3 * n3, d, s));
     std::vector<double> h(2 * (size_t)nvec);
     CKE(cudaMemcpyAsync(h.data(), d, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
     CKE(cudaStreamSynchronize(s));
     for (int v = 0; v < nvec; ++v) enorm2_host[v] = h[2 * v];
   }
+  CKE(launch_curl_h(c, kp, R, U, nvec, 1, PCX_FP32, s));
+  CKE(launch_fft(c, U, U, nvec, +1, PCX_FP32, s));
+  CKE(cnn::lincomb(static_cast<const float*>(U), sc, nullptr, 0.f, static_cast<float*>(U), nf, s));
   return cudaSuccess;
 }
 

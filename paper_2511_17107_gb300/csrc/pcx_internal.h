@@ -109,6 +109,18 @@ cudaError_t cnn_pairs(pcx_ctx* c, const KParams& kp, const void* R, const void* 
                       int nvec, cudaStream_t s);
 cudaError_t cg_solve(pcx_ctx* c, const KParams& kp, const void* R, void* E, int nvec, double tol, int maxit,
                      int* iters, double* relres, cudaStream_t s);
+// pieces of the curl-sandwich approximate inverse (fft_kernels.cuh):
+// U = K_A^H X / |k|^(2 pow);  Y (+)= s K_A Wm / |k|^2 [+ conj(kappa)(kappa.R)/(gamma |k|^4)];
+// Mo = s (M^{-1} E + Add) per cell (real space)
+cudaError_t launch_curl_h(const pcx_ctx* c, const KParams& kp, const void* X, void* U, int nvec, int pow, int precision,
+                          cudaStream_t s);
+cudaError_t launch_curl_add(const pcx_ctx* c, const KParams& kp, const void* Wm, const void* R, void* Y, int nvec,
+                            double scale, int accumulate, int precision, cudaStream_t s);
+cudaError_t launch_eps_cells(const pcx_ctx* c, const void* E, const void* Add, void* Mo, int nvec, double scale,
+                             int precision, cudaStream_t s);
+// T0 R (learned.cpp), workspace from the context
+cudaError_t sandwich_precond(pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,
+                             cudaStream_t s);
 // unnormalised 3D DFT of every component, dir > 0: N^{3/2} F3_3, dir < 0: N^{3/2} F3_3^H (Y may be X)
 cudaError_t launch_fft(const pcx_ctx* c, const void* X, void* Y, int nvec, int dir, int precision, cudaStream_t s);
 // out[v] = x_v^H K_B x_v, out[nvec + v] = ||x_v||^2 (device doubles, zeroed here)

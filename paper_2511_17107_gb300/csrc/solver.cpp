@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "cnn.h"
 #include "linalg.h"
 #include "pcx_internal.h"
 
@@ -56,8 +57,20 @@ struct DevBuf {
 // Wall-clock attribution of solver phases (only when statistics are asked
 // for: each tick synchronises the stream and charges the elapsed time).
 struct Times {
-  double apply = 0, gram = 0, rr = 0, other = 0;
+  double apply = 0, gram = 0, rr = 0, other = 0, precond = 0;
   long long applies = 0;
+};
+
+// Learned-correction settings shared by the runs of one pcx_solve call.
+struct Learned {
+  const float* params = nullptr;   // device, cnn::NPARAMS floats (null: plain K_P^{-1})
+  const float* gates = nullptr;    // device, from cnn_gates
+  bool off = false;                // fallback to K_P^{-1} for the rest of this k
+  int fallbacks = 0;
+  int kind = 0;                    // base preconditioner: 0 K_P^{-1}, 1 curl sandwich T0
+  // residual dump for training (FP32 phase)
+  void* dump = nullptr;
+  int dump_cap = 0, dump_every = 1, dumped = 0;
 };
 
 struct Run {
@@ -81,6 +94,7 @@ struct Run {
   bool k_zero;
   int verbose;
   int np = 0;        // P columns at S[n : n+np] (valid when lobpcg returns)
+  Learned* learned = nullptr;
   // device buffers
   DevBuf S, AS, S2, AS2, R, G, C, theta, norms;
   std::string err;
@@ -121,6 +135,21 @@ struct Run {
     cudaError_t e = launch_apply(c, kp, X, Y, nvec, prec, s);
     if (tm) tm->applies += nvec;
     tick(&Times::apply);
+    return e;
+  }
+
+  // W = K_P^{-1} R for one column, or the learned T(R) when it is enabled
+  // (FP32 storage only) and has not fallen back
+  cudaError_t precond_col(const void* r, void* w) {
+    tick(&Times::other);
+    cudaError_t e;
+    if (learned && learned->params && !learned->off && prec == PCX_FP32)
+      e = cnn_precond(c, kp, learned->params, learned->gates, r, w, 1, s);
+    else if (learned && learned->kind == 1)
+      e = sandwich_precond(c, kp, r, w, 1, prec, s);
+    else
+      e = launch_precond(c, kp, r, w, 1, prec, s);
+    tick(&Times::precond);
     return e;
   }
 
@@ -194,6 +223,8 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
   std::vector<double> best_hist;
   double best = INFINITY;
   int since_best = 0;
+  double prev_worst = INFINITY;
+  int no_drop = 0;
   res.assign(n, INFINITY);
   for (iters = 0;; ++iters) {
     // residual R = AX - X theta and norms
@@ -230,15 +261,32 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       return PCX_OK;
     }
     if (iters >= maxit) return PCX_ENOCONV;
+    Learned* lrn = run.learned;
+    // learned correction: back to K_P^{-1} once the residual has not dropped
+    // for 3 iterations
+    if (lrn && lrn->params && !lrn->off) {
+      if (worst < prev_worst) {
+        no_drop = 0;
+      } else if (++no_drop >= 3) {
+        lrn->off = true;
+        ++lrn->fallbacks;
+      }
+    }
+    prev_worst = worst;
 
     // soft locking: active columns get W (and P) columns
     std::vector<int> act;
     for (int j = 0; j < n; ++j)
       if (res[j] > tol) act.push_back(j);
     const int na = (int)act.size();
+    // residual dump (training data of the learned correction)
+    if (lrn && lrn->dump && run.prec == PCX_FP32 && iters % lrn->dump_every == 0)
+      for (int a = 0; a < na && lrn->dumped < lrn->dump_cap; ++a, ++lrn->dumped)
+        CK(cudaMemcpyAsync(static_cast<char*>(lrn->dump) + (size_t)lrn->dumped * L * 8, run.col(run.R, act[a]), L * 8,
+                           cudaMemcpyDeviceToDevice, run.s));
     const int w0 = n + np;   // W at S[w0 : w0+na]
     for (int a = 0; a < na; ++a)
-      CK(launch_precond(run.c, run.kp, run.col(run.R, act[a]), run.col(run.S, w0 + a), 1, run.prec, run.s));
+      CK(run.precond_col(run.col(run.R, act[a]), run.col(run.S, w0 + a)));
     // W <- W - X (X^H W), then orthonormalise W
     {
       std::vector<cd> xw;
@@ -365,6 +413,8 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
   int np = r32.np;          // P32 / AP32 from the FP32 phase stay valid directions
   const int refresh = 20;
   int since_fresh = 0;
+  double prev_worst = INFINITY;
+  int no_drop = 0;
   res.assign(n, INFINITY);
   for (iters = 0;; ++iters) {
     // FP64 residual
@@ -395,6 +445,15 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
       continue;
     }
     if (iters >= maxit) return PCX_ENOCONV;
+    if (r32.learned && r32.learned->params && !r32.learned->off) {
+      if (worst < prev_worst) {
+        no_drop = 0;
+      } else if (++no_drop >= 3) {
+        r32.learned->off = true;
+        ++r32.learned->fallbacks;
+      }
+    }
+    prev_worst = worst;
     if (++since_fresh >= refresh) {   // exact image of X and Rayleigh-Ritz on X; P is kept
       if ((st = fresh_ax()) != PCX_OK) return st;
       if ((st = rr_x()) != PCX_OK) return st;
@@ -411,7 +470,7 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     CK(launch_convert(r64.S.p, PCX_FP64, r32.S.p, PCX_FP32, (size_t)n * L, r64.s));
     for (int a = 0; a < na; ++a) {
       CK(launch_convert(r64.col(r64.R, act[a]), PCX_FP64, r32.col(r32.R, a), PCX_FP32, L, r64.s));
-      CK(launch_precond(r32.c, r32.kp, r32.col(r32.R, a), r32.col(r32.S, w0 + a), 1, PCX_FP32, r64.s));
+      CK(r32.precond_col(r32.col(r32.R, a), r32.col(r32.S, w0 + a)));
     }
     // [P W] is orthogonalised against X and orthonormalised (Cholesky QR,
     // two passes) in FP32, so the FP32 part of the Gram matrices is close to
@@ -538,12 +597,16 @@ struct KSolve {
   uint64_t seed;
   Times *t32, *t64;
   int iters32 = 0, iters64 = 0;
+  Learned* learned = nullptr;
 };
 
 // LOBPCG for one k with penalty coefficient gamma (<= 0: the rule of Sec. 2).
 // On return r64.S[0:nev] holds the FP64 eigenvectors.
 pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run& r64, Run& r32,
                        std::vector<double>& theta, std::vector<double>& res, int& iters_total) {
+  r64.learned = ks.learned;
+  r32.learned = ks.learned;
+  if (ks.learned) ks.learned->off = false;
   pcx_ctx* c = ks.c;
   const cudaStream_t s = ks.s;
   const int n = ks.n, nev = ks.nev, maxit = ks.maxit;
@@ -663,6 +726,14 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
     c->err = "pcx_solve: gamma must be finite and >= 0";
     return PCX_EINVAL;
   }
+  if (o.cnn_params && o.precision != PCX_FP32) {
+    c->err = "pcx_solve: the learned correction needs precision PCX_FP32";
+    return PCX_EINVAL;
+  }
+  if (o.dump_R && (o.dump_cap < 0 || o.dump_every < 0)) {
+    c->err = "pcx_solve: dump_cap and dump_every must be >= 0";
+    return PCX_EINVAL;
+  }
   const double penalty_tol = o.penalty_tol == 0 ? 1e-6 : o.penalty_tol;
   const int max_raises = 4;
   const size_t L = (size_t)3 * c->n * c->n * c->n;
@@ -682,6 +753,29 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
   ks.t64 = &t64;
   int raises = 0;
   double gamma_last = 0.0;
+  Learned lrn;
+  DevBuf gates_buf;
+  if (o.precond_kind != 0 && o.precond_kind != 1) {
+    c->err = "pcx_solve: precond_kind must be 0 or 1";
+    return PCX_EINVAL;
+  }
+  if (o.cnn_params || o.dump_R || o.precond_kind) {
+    lrn.kind = o.precond_kind;
+    lrn.params = o.cnn_params;
+    lrn.dump = o.dump_R;
+    lrn.dump_cap = o.dump_R ? o.dump_cap : 0;
+    lrn.dump_every = o.dump_every > 0 ? o.dump_every : 1;
+    if (o.cnn_params) {
+      cudaError_t e = gates_buf.alloc(sizeof(float) * 2 * cnn::HIDDEN * (size_t)c->n * c->n * c->n);
+      if (e == cudaSuccess) e = cnn_gates(c, o.cnn_params, static_cast<float*>(gates_buf.p), s);
+      if (e != cudaSuccess) {
+        c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? PCX_ENOMEM : PCX_ECUDA;
+      }
+      lrn.gates = static_cast<const float*>(gates_buf.p);
+    }
+    ks.learned = &lrn;
+  }
   const auto t_start = std::chrono::steady_clock::now();
   if (o.stats) std::memset(o.stats, 0, sizeof(*o.stats));
   for (int ik = 0; ik < nk; ++ik) {
@@ -749,6 +843,9 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
     st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     st.gamma_raises = raises;
     st.gamma_last = gamma_last;
+    st.ms_precond = t32.precond + t64.precond;
+    st.learned_fallbacks = lrn.fallbacks;
+    st.dumped = lrn.dumped;
   }
   return result;
 }

@@ -44,7 +44,8 @@ class pcx_solve_stats(C.Structure):
     _fields_ = [("iters_fp32", C.c_int), ("iters_fp64", C.c_int), ("applies_fp32", C.c_longlong),
                 ("applies_fp64", C.c_longlong), ("ms_total", C.c_double), ("ms_apply", C.c_double),
                 ("ms_gram", C.c_double), ("ms_rr", C.c_double), ("ms_other", C.c_double),
-                ("gamma_raises", C.c_int), ("gamma_last", C.c_double)]
+                ("gamma_raises", C.c_int), ("gamma_last", C.c_double), ("ms_precond", C.c_double),
+                ("learned_fallbacks", C.c_int), ("dumped", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -53,7 +54,8 @@ class pcx_solve_stats(C.Structure):
 class pcx_solve_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("maxit", C.c_int), ("precision", C.c_int), ("switch_tol", C.c_double),
                 ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats)),
-                ("gamma", C.c_double), ("penalty_tol", C.c_double)]
+                ("gamma", C.c_double), ("penalty_tol", C.c_double), ("cnn_params", C.c_void_p),
+                ("dump_R", C.c_void_p), ("dump_cap", C.c_int), ("dump_every", C.c_int), ("precond_kind", C.c_int)]
 
 
 _lib = None
@@ -89,6 +91,7 @@ def lib():
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
             "pcx_div_norms": (st, [vp, dp, vp, C.c_int, C.c_int, vp, vp]),
+            "pcx_sandwich_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_cnn_init": (st, [C.c_uint64, vp, vp]),
             "pcx_cnn_gates": (st, [vp, vp, vp, vp]),
             "pcx_cnn_forward": (st, [vp, vp, vp, vp, vp, C.c_int, vp]),
@@ -114,7 +117,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_cnn_init", "pcx_cnn_gates",
+                        "pcx_div_norms", "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
                         "pcx_cg_solve", "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
@@ -343,6 +346,14 @@ PCX_CNN_NPARAMS = (PCX_CNN_HIDDEN * 3 * 27 + PCX_CNN_HIDDEN * PCX_CNN_HIDDEN * 2
                    + 2 * (PCX_CNN_HIDDEN * 9 * 27 + PCX_CNN_HIDDEN))
 
 
+def pcx_sandwich_precond(ctx, k, R, W, gamma=0.0, stream=None):
+    """W = T0 R, the curl-sandwich approximate inverse (complex64 or complex128)."""
+    kk, kp = _kvec(k)
+    _check(lib().pcx_sandwich_precond(ctx.handle, kp, float(gamma), _devptr(R), _devptr(W), R.shape[0], _prec_of(R),
+                                      _stream(stream)), ctx.handle)
+    return W
+
+
 def pcx_cnn_init(seed, params, stream=None):
     """params (float32 CUDA, PCX_CNN_NPARAMS): seeded initial parameters."""
     _check(lib().pcx_cnn_init(int(seed), _devptr(params), _stream(stream)))
@@ -451,13 +462,17 @@ def pcx_rr_eig(ga, gb, drop_tol=1e-13):
 
 
 def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
-              vec_out=None, stream=None, raise_on_noconv=True, stats=None, gamma=0.0, penalty_tol=0.0):
+              vec_out=None, stream=None, raise_on_noconv=True, stats=None, gamma=0.0, penalty_tol=0.0,
+              cnn_params=None, dump_R=None, dump_every=0, precond_kind=0):
     """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status).  Pass a
     pcx_solve_stats instance as ``stats`` to receive counters and timings."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
     nk = kp.shape[0]
     o = pcx_solve_opts(block, maxit, precision, switch_tol, seed, verbose,
-                       C.pointer(stats) if stats is not None else None, float(gamma), float(penalty_tol))
+                       C.pointer(stats) if stats is not None else None, float(gamma), float(penalty_tol),
+                       _devptr(cnn_params) if cnn_params is not None else None,
+                       _devptr(dump_R) if dump_R is not None else None,
+                       int(dump_R.shape[0]) if dump_R is not None else 0, int(dump_every), int(precond_kind))
     eig = np.zeros((nk, nev))
     res = np.zeros((nk, nev))
     its = np.zeros(nk, dtype=np.int32)

@@ -96,8 +96,33 @@ def test_learned_preconditioner_matches_oracle(pcx, n):
     R = wl.random_block(nv, n, seed=12).astype(np.complex64)
     W = torch.empty((nv, 3, n, n, n), dtype=torch.complex64, device="cuda")
     pcx.pcx_cnn_precond(ctx, k, P, G, _dev(R, np.complex64), W)
-    want = np.stack([learned.precondition(p, f, R[v].astype(np.complex128), kap, g) for v in range(nv)])
+    blocks = permittivity.cell_blocks(s, n)
+    want = np.stack([learned.precondition(p, f, R[v].astype(np.complex128), kap, g, blocks) for v in range(nv)])
     _close(W.cpu().numpy(), want, 2e-5)
+
+
+SANDWICH_CASES = [(16, np.complex128, 1e-12), (16, np.complex64, 2e-5), (64, np.complex64, 2e-5),
+                  (32, np.complex128, 1e-12)]
+
+
+@pytest.mark.parametrize("n,dtype,tol", SANDWICH_CASES)
+def test_sandwich_preconditioner_matches_oracle(pcx, n, dtype, tol):
+    s = wl.random_inclusions(8)
+    blocks = permittivity.cell_blocks(s, n)
+    k = np.array([-0.8, 1.9, 0.3])
+    g = penalty.gamma_practical(k)
+    kap = fourier.kappa(n, s.lattice, k)
+    ctx = pcx.setup_structure(s, n)
+    R = wl.random_block(2, n, seed=40).astype(dtype)
+    W = torch.empty((2, 3, n, n, n), dtype=torch.complex64 if dtype == np.complex64 else torch.complex128,
+                    device="cuda")
+    pcx.pcx_sandwich_precond(ctx, k, _dev(R, dtype), W)
+    want = learned.sandwich_precondition(R.astype(np.complex128), kap, blocks, g)
+    _close(W.cpu().numpy(), want, tol)
+    # in place, W = T0 W
+    X = _dev(R, dtype)
+    pcx.pcx_sandwich_precond(ctx, k, X, X)
+    _close(X.cpu().numpy(), want, tol)
 
 
 def test_training_pairs_match_oracle(pcx):
@@ -111,7 +136,8 @@ def test_training_pairs_match_oracle(pcx):
     U = torch.empty((2, 3, n, n, n), dtype=torch.complex64, device="cuda")
     T = torch.empty_like(U)
     en2 = pcx.pcx_cnn_pairs(ctx, k, _dev(R, np.complex64), _dev(E, np.complex64), U, T)
-    wu, wt, wen2 = learned.training_pair(R.astype(np.complex128), E.astype(np.complex128), kap, g)
+    wu, wt, wen2 = learned.training_pair(R.astype(np.complex128), E.astype(np.complex128), kap, g,
+                                         permittivity.cell_blocks(s, n))
     _close(U.cpu().numpy(), wu, 2e-5)
     _close(T.cpu().numpy(), wt, 2e-5)
     np.testing.assert_allclose(en2, wen2, rtol=1e-5)

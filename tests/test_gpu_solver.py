@@ -108,3 +108,18 @@ def test_penalty_guard_raises_gamma(pcx, prec, rtol):
     phys = phys[phys > 1e-9 * phys.max()]
     np.testing.assert_allclose(ev[0], phys[:nev], rtol=rtol)
     np.testing.assert_allclose(ev[0], [0.125, 0.125], rtol=1e-3)
+
+
+@pytest.mark.parametrize("prec,rtol", [(0, 1e-10), (1, 1e-6)])
+def test_solve_with_sandwich_preconditioner(pcx, prec, rtol):
+    """precond_kind = 1 (curl-sandwich T0): the same eigenvalues as the
+    K_P^{-1} solve, in fewer iterations, on configuration 1."""
+    n, nev = 16, 10
+    s = wl.sc_gyro_sphere()
+    k = wl.config_k(s.name)[0]
+    ctx = pcx.setup_structure(s, n)
+    ev0, res0, its0, st0 = pcx.pcx_solve(ctx, [k], nev, 1e-9, block=14, precision=prec)
+    ev1, res1, its1, st1 = pcx.pcx_solve(ctx, [k], nev, 1e-9, block=14, precision=prec, precond_kind=1)
+    assert st0 == pcx.PCX_OK and st1 == pcx.PCX_OK
+    np.testing.assert_allclose(ev1[0], ev0[0], rtol=rtol)
+    assert its1[0] < its0[0], (its0, its1)
