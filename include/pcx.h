@@ -466,6 +466,9 @@ typedef struct {
   int dump_every;     /* 0: every iteration                                    */
   int precond_kind;   /* 0: K_P^{-1} (eq. matrixfree_finalform, default);
                          1: the curl-sandwich T0 (pcx_sandwich_precond)        */
+  int learned_patience; /* iterations without a drop of the worst residual
+                         before the learned correction falls back (0: 3;
+                         negative: never)                                      */
 } pcx_solve_opts;
 
 /*

@@ -68,6 +68,7 @@ struct Learned {
   bool off = false;                // fallback to K_P^{-1} for the rest of this k
   int fallbacks = 0;
   int kind = 0;                    // base preconditioner: 0 K_P^{-1}, 1 curl sandwich T0
+  int patience = 3;                // iterations without a drop before the fallback (< 0: never)
   // residual dump for training (FP32 phase)
   void* dump = nullptr;
   int dump_cap = 0, dump_every = 1, dumped = 0;
@@ -264,10 +265,10 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
     Learned* lrn = run.learned;
     // learned correction: back to K_P^{-1} once the residual has not dropped
     // for 3 iterations
-    if (lrn && lrn->params && !lrn->off) {
+    if (lrn && lrn->params && !lrn->off && lrn->patience >= 0) {
       if (worst < prev_worst) {
         no_drop = 0;
-      } else if (++no_drop >= 3) {
+      } else if (++no_drop >= lrn->patience) {
         lrn->off = true;
         ++lrn->fallbacks;
       }
@@ -445,10 +446,10 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
       continue;
     }
     if (iters >= maxit) return PCX_ENOCONV;
-    if (r32.learned && r32.learned->params && !r32.learned->off) {
+    if (r32.learned && r32.learned->params && !r32.learned->off && r32.learned->patience >= 0) {
       if (worst < prev_worst) {
         no_drop = 0;
-      } else if (++no_drop >= 3) {
+      } else if (++no_drop >= r32.learned->patience) {
         r32.learned->off = true;
         ++r32.learned->fallbacks;
       }
@@ -761,6 +762,7 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
   }
   if (o.cnn_params || o.dump_R || o.precond_kind) {
     lrn.kind = o.precond_kind;
+    lrn.patience = o.learned_patience == 0 ? 3 : o.learned_patience;
     lrn.params = o.cnn_params;
     lrn.dump = o.dump_R;
     lrn.dump_cap = o.dump_R ? o.dump_cap : 0;

@@ -55,7 +55,8 @@ class pcx_solve_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("maxit", C.c_int), ("precision", C.c_int), ("switch_tol", C.c_double),
                 ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats)),
                 ("gamma", C.c_double), ("penalty_tol", C.c_double), ("cnn_params", C.c_void_p),
-                ("dump_R", C.c_void_p), ("dump_cap", C.c_int), ("dump_every", C.c_int), ("precond_kind", C.c_int)]
+                ("dump_R", C.c_void_p), ("dump_cap", C.c_int), ("dump_every", C.c_int), ("precond_kind", C.c_int),
+                ("learned_patience", C.c_int)]
 
 
 _lib = None
@@ -463,7 +464,7 @@ def pcx_rr_eig(ga, gb, drop_tol=1e-13):
 
 def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
               vec_out=None, stream=None, raise_on_noconv=True, stats=None, gamma=0.0, penalty_tol=0.0,
-              cnn_params=None, dump_R=None, dump_every=0, precond_kind=0):
+              cnn_params=None, dump_R=None, dump_every=0, precond_kind=0, learned_patience=0):
     """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status).  Pass a
     pcx_solve_stats instance as ``stats`` to receive counters and timings."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
@@ -472,7 +473,8 @@ def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_
                        C.pointer(stats) if stats is not None else None, float(gamma), float(penalty_tol),
                        _devptr(cnn_params) if cnn_params is not None else None,
                        _devptr(dump_R) if dump_R is not None else None,
-                       int(dump_R.shape[0]) if dump_R is not None else 0, int(dump_every), int(precond_kind))
+                       int(dump_R.shape[0]) if dump_R is not None else 0, int(dump_every), int(precond_kind),
+                       int(learned_patience))
     eig = np.zeros((nk, nev))
     res = np.zeros((nk, nev))
     its = np.zeros(nk, dtype=np.int32)
