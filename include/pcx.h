@@ -238,6 +238,51 @@ pcx_status pcx_apply_noalloc(pcx_ctx* ctx, const double k[3], double gamma, cons
                              int precision, void* stream);
 
 /*
+ * pcx_apply_kbatch -- Y = Op(k_i) X for nk Bloch vectors at once: X and Y hold
+ * nk groups of vec_per_k vectors ([nk][vec_per_k][3][N^3], group i at
+ * kpts[3 i .. 3 i + 2], HOST doubles), gamma as in pcx_apply (<= 0: the rule
+ * per k).  One launch per pass sweeps every (k, vector) pair, each x pass
+ * reading its k from a device table (the y and z passes do not depend on
+ * k).  Same results as nk calls of pcx_apply.  The table lives in the
+ * context: concurrent calls on one context must share one stream.
+ */
+pcx_status pcx_apply_kbatch(pcx_ctx* ctx, const double* kpts, int nk, double gamma, const void* X, void* Y,
+                            int vec_per_k, int precision, void* stream);
+
+/*
+ * pcx_set_apply_graphs -- enable (1) or disable (0) CUDA-graph replay of the
+ * apply launch chain in pcx_apply and pcx_solve: a (buffers, size, k, stream)
+ * combination runs eagerly the first time, is captured the second time and
+ * replayed afterwards (up to 64 graphs per context).  Needs a non-default
+ * stream; on the legacy default stream the apply stays eager.  Disabling
+ * frees the cached graphs.
+ */
+pcx_status pcx_set_apply_graphs(pcx_ctx* ctx, int enable);
+
+/* Result of pcx_autotune. */
+typedef struct {
+  int chunk;            /* vectors per launch chunk chosen                         */
+  int graphs;           /* 1 if graph replay was faster and is enabled            */
+  double us_per_vector; /* measured time of the chosen configuration              */
+  int candidates;       /* configurations timed (0 when from a cache)             */
+  int from_cache;       /* 0 measured, 1 process cache, 2 the PCX_TUNE_CACHE file  */
+} pcx_tune_result;
+
+/*
+ * pcx_autotune -- choose the apply launch configuration of this context for
+ * blocks of nvec vectors at `precision`: every chunk size 1, 2, 4, ... <=
+ * min(nvec, 64) (and nvec) is timed with CUDA events on `stream` (two warm
+ * and three timed applies on random vectors), then graph replay of the best
+ * one when `stream` is not the default stream.  The choice is applied to the
+ * context (as pcx_set_apply_chunk / pcx_set_apply_graphs would) and cached
+ * per device, SM count, N, precision and nvec for the process; when the
+ * environment variable PCX_TUNE_CACHE names a file, results are read from and
+ * appended to it.  Allocates two blocks of nvec vectors while timing;
+ * synchronises `stream`.  *out (optional) receives the result.
+ */
+pcx_status pcx_autotune(pcx_ctx* ctx, int precision, int nvec, void* stream, pcx_tune_result* out);
+
+/*
  * pcx_apply_host -- pcx_apply on HOST buffers: copies X to the device, applies,
  * copies Y back, and synchronises `stream` before returning.  Pinned host
  * memory gives full copy bandwidth; pageable memory also works.  Staging

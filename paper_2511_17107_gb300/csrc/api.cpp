@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "cnn.h"
 #include "linalg.h"
@@ -91,8 +92,9 @@ pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32
 
 void pcx_destroy(pcx_ctx* c) {
   if (!c) return;
+  pcx::free_apply_graphs(c);
   void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64,  c->dev.tw32, c->dev.m64,  c->dev.m32,
-                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->cnn_ws};
+                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->cnn_ws, c->ktab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -243,6 +245,38 @@ pcx_status pcx_div_norms(pcx_ctx* c, const double k[3], const void* X, int nvec,
   pcx::KParams kp = pcx::make_kparams(c, k, 0.0);
   cudaError_t e = pcx::launch_div_norms(c, kp, X, nvec, precision, out, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_div_norms", e);
+}
+
+pcx_status pcx_apply_kbatch(pcx_ctx* c, const double* kpts, int nk, double gamma, const void* X, void* Y,
+                            int vec_per_k, int precision, void* stream) {
+  if (nk < 0 || vec_per_k < 0) return inval(c, "pcx_apply_kbatch: nk, vec_per_k must be >= 0");
+  if ((long long)nk * vec_per_k > (1LL << 24)) return inval(c, "pcx_apply_kbatch: too many vectors");
+  const int nvec = nk * vec_per_k;
+  pcx_status st = check_block(c, "pcx_apply_kbatch", X, Y, nvec, precision);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!kpts) return inval(c, "pcx_apply_kbatch: NULL kpts");
+  const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
+  if (ranges_overlap(X, bytes, Y, bytes)) return inval(c, "pcx_apply_kbatch: X and Y overlap");
+  std::vector<pcx::KParams> kps(nk);
+  for (int i = 0; i < nk; ++i) kps[i] = pcx::make_kparams(c, kpts + 3 * i, gamma);
+  cudaError_t e = pcx::launch_apply_kbatch(c, kps.data(), nk, vec_per_k, X, Y, precision,
+                                           static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply_kbatch", e);
+}
+
+pcx_status pcx_set_apply_graphs(pcx_ctx* c, int enable) {
+  if (!c) return inval(nullptr, "pcx_set_apply_graphs: NULL context");
+  if (!enable) pcx::free_apply_graphs(c);
+  c->use_graphs = enable ? 1 : 0;
+  return PCX_OK;
+}
+
+pcx_status pcx_autotune(pcx_ctx* c, int precision, int nvec, void* stream, pcx_tune_result* out) {
+  if (!c) return inval(nullptr, "pcx_autotune: NULL context");
+  if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, "pcx_autotune: bad precision");
+  if (nvec < 1 || nvec > 1024) return inval(c, "pcx_autotune: need 1 <= nvec <= 1024");
+  cudaError_t e = pcx::autotune_apply(c, precision, nvec, static_cast<cudaStream_t>(stream), out);
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_autotune", e);
 }
 
 pcx_status pcx_sandwich_precond(pcx_ctx* c, const double k[3], double gamma, const void* R, void* W, int nvec,

@@ -4,7 +4,9 @@
 // pcx_apply_noalloc, and the preconditioner launch.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "pcx_internal.h"
 
@@ -18,7 +20,7 @@ namespace pcx {
 
 template <typename T>
 cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
-                        cudaStream_t st);
+                        const KParams* kps, int vec_per_k, cudaStream_t st);
 template <typename T>
 cudaError_t run_precond_t(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, cudaStream_t s);
 template <typename T>
@@ -34,15 +36,15 @@ template <typename T>
 cudaError_t run_eps_cells_t(const pcx_ctx* c, const void* E, const void* Add, void* Mo, int nvec, double scale_,
                             cudaStream_t s);
 extern template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
-                                               cudaStream_t);
+                                               const KParams*, int, cudaStream_t);
 extern template cudaError_t run_apply_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
-                                                cudaStream_t);
+                                                const KParams*, int, cudaStream_t);
 
 namespace {
 template <typename T>
 cudaError_t dispatch_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk,
-                           void* sbuf, cudaStream_t st) {
-  return run_apply_t<T>(c, kp, X, Y, nvec, chunk, sbuf, st);
+                           void* sbuf, cudaStream_t st, const KParams* kps = nullptr, int vec_per_k = 1) {
+  return run_apply_t<T>(c, kp, X, Y, nvec, chunk, sbuf, kps, vec_per_k, st);
 }
 }  // namespace
 
@@ -103,14 +105,15 @@ cudaError_t launch_apply_noalloc(const pcx_ctx* c, const KParams& kp, const void
                                : dispatch_apply<float>(c, kp, X, Y, nvec, chunk, scratch, s);
 }
 
-cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
-                         cudaStream_t s) {
-  if (nvec == 0) return cudaSuccess;
+namespace {
+
+cudaError_t ensure_scratch(pcx_ctx* c, int precision, int nvec) {
   const size_t need = apply_scratch_bytes(c, precision, nvec);
   if (need > c->scratch_bytes) {
     // the previous scratch may still be in use by work queued on another stream
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return e;
+    free_apply_graphs(c);   // graphs hold the old scratch address
     if (c->scratch) cudaFree(c->scratch);
     c->scratch = nullptr;
     c->scratch_bytes = 0;
@@ -118,7 +121,117 @@ cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, 
     if (e != cudaSuccess) return e;
     c->scratch_bytes = need;
   }
-  return launch_apply_scratch(c, kp, X, Y, nvec, precision, c->scratch, s);
+  return cudaSuccess;
+}
+
+// One captured apply chain.  A key runs eagerly the first time it is seen
+// (kernel attributes and module loading happen outside any capture) and is
+// captured on its second use; later uses replay the graph.
+struct GraphEntry {
+  const void* X;
+  void* Y;
+  int nvec, precision, chunk;
+  void* scratch;
+  cudaStream_t stream;
+  KParams kp;
+  int seen = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool same(const GraphEntry& o) const {
+    return X == o.X && Y == o.Y && nvec == o.nvec && precision == o.precision && chunk == o.chunk &&
+           scratch == o.scratch && stream == o.stream && std::memcmp(&kp, &o.kp, sizeof(KParams)) == 0;
+  }
+};
+struct GraphCache {
+  std::vector<GraphEntry> entries;
+};
+constexpr size_t kMaxGraphs = 64;
+
+bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+}  // namespace
+
+void free_apply_graphs(pcx_ctx* c) {
+  if (!c->graphs) return;
+  auto* gc = static_cast<GraphCache*>(c->graphs);
+  for (auto& e : gc->entries)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  delete gc;
+  c->graphs = nullptr;
+}
+
+cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
+                         cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  cudaError_t e = ensure_scratch(c, precision, nvec);
+  if (e != cudaSuccess) return e;
+  if (!c->use_graphs || !capturable(s)) return launch_apply_scratch(c, kp, X, Y, nvec, precision, c->scratch, s);
+  if (!c->graphs) c->graphs = new GraphCache;
+  auto* gc = static_cast<GraphCache*>(c->graphs);
+  GraphEntry key;
+  std::memset(&key, 0, sizeof(key));
+  key.X = X;
+  key.Y = Y;
+  key.nvec = nvec;
+  key.precision = precision;
+  key.chunk = apply_chunk(c, precision);
+  key.scratch = c->scratch;
+  key.stream = s;
+  key.kp = kp;
+  GraphEntry* ent = nullptr;
+  for (auto& g : gc->entries)
+    if (g.same(key)) ent = &g;
+  if (!ent) {
+    if (gc->entries.size() >= kMaxGraphs) {
+      if (gc->entries.front().exec) cudaGraphExecDestroy(gc->entries.front().exec);
+      gc->entries.erase(gc->entries.begin());
+    }
+    gc->entries.push_back(key);
+    ent = &gc->entries.back();
+  }
+  if (ent->exec) return cudaGraphLaunch(ent->exec, s);
+  if (ent->seen++ == 0) return launch_apply_scratch(c, kp, X, Y, nvec, precision, c->scratch, s);
+  // capture the launch chain; on any capture failure run eagerly instead
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t el = launch_apply_scratch(c, kp, X, Y, nvec, precision, c->scratch, s);
+    cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    if (el == cudaSuccess && ec == cudaSuccess && graph)
+      e = cudaGraphInstantiate(&ent->exec, graph, 0);
+    else
+      e = el != cudaSuccess ? el : (ec != cudaSuccess ? ec : cudaErrorUnknown);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  if (e != cudaSuccess || !ent->exec) {
+    cudaGetLastError();   // clear the capture error; this key stays eager
+    ent->exec = nullptr;
+    ent->seen = -1000000;
+    return launch_apply_scratch(c, kp, X, Y, nvec, precision, c->scratch, s);
+  }
+  return cudaGraphLaunch(ent->exec, s);
+}
+
+cudaError_t launch_apply_kbatch(pcx_ctx* c, const KParams* kps_host, int nk, int vec_per_k, const void* X, void* Y,
+                                int precision, cudaStream_t s) {
+  const int nvec = nk * vec_per_k;
+  if (nvec == 0) return cudaSuccess;
+  const size_t bytes = sizeof(KParams) * (size_t)nk;
+  cudaError_t e;
+  if (bytes > c->ktab_bytes) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    if (c->ktab) cudaFree(c->ktab);
+    c->ktab = nullptr;
+    c->ktab_bytes = 0;
+    if ((e = cudaMalloc(&c->ktab, bytes)) != cudaSuccess) return e;
+    c->ktab_bytes = bytes;
+  }
+  // pageable source: the call returns once the table is staged
+  if ((e = cudaMemcpyAsync(c->ktab, kps_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = ensure_scratch(c, precision, nvec)) != cudaSuccess) return e;
+  const int chunk = apply_chunk(c, precision);
+  const KParams* kt = static_cast<const KParams*>(c->ktab);
+  return precision == PCX_FP64 ? dispatch_apply<double>(c, kps_host[0], X, Y, nvec, chunk, c->scratch, s, kt, vec_per_k)
+                               : dispatch_apply<float>(c, kps_host[0], X, Y, nvec, chunk, c->scratch, s, kt, vec_per_k);
 }
 
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,

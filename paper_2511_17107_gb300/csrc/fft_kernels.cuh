@@ -80,6 +80,11 @@ struct PassArgs {
   const void* mtab;    // [n_mat][9] block entries per material
   int n_mat;
   KParams kp;
+  // k-batched sweeps: vector v of the launch (v_base + v overall) uses
+  // kps[(v_base + v) / vec_per_k] instead of kp (x passes only)
+  const KParams* kps;
+  int vec_per_k;
+  int v_base;
 };
 
 template <typename T, int N, int AXIS>
@@ -277,6 +282,8 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
 
   const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
   for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = gtw[i];
+  KParams kp = a.kp;
+  if (AXIS == 0 && a.kps) kp = a.kps[(a.v_base + (int)v) / a.vec_per_k];
   if constexpr (AXIS == 0 && OP < OP_PLAIN_INV) {
     // kappa_i(p) = sum_j b_ji S_j(p_j) + i kq_i L0(p_i),  S_j = L1 + i kt_j L0,
     // split as ka_i(p1) + kb_i(p2, p3)
@@ -285,10 +292,10 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
       if (e < 3 * N) {
         const int i = e / N, p = e % N;
         const cx<T> l1 = glam[p], l0 = glam[N + p];
-        const T b0 = (T)a.kp.b[i];   // b_1i (row j = 0)
-        const T kt = (T)a.kp.kt[0];
+        const T b0 = (T)kp.b[i];   // b_1i (row j = 0)
+        const T kt = (T)kp.kt[0];
         cx<T> r = mk(b0 * fma(-kt, l0.y, l1.x), b0 * fma(kt, l0.x, l1.y));
-        if (i == 0) r = mk(fma(-(T)a.kp.kq[0], l0.y, r.x), fma((T)a.kp.kq[0], l0.x, r.y));
+        if (i == 0) r = mk(fma(-(T)kp.kq[0], l0.y, r.x), fma((T)kp.kq[0], l0.x, r.y));
         ka[e] = r;
       } else {
         const int f = e - 3 * N, t = f / 3, i = f % 3;
@@ -297,9 +304,9 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
 #pragma unroll
         for (int j = 1; j < 3; ++j) {
           const cx<T> l1 = glam[p[j]], l0 = glam[N + p[j]];
-          const T bj = (T)a.kp.b[3 * j + i], kt = (T)a.kp.kt[j];
+          const T bj = (T)kp.b[3 * j + i], kt = (T)kp.kt[j];
           r = mk(fma(bj, fma(-kt, l0.y, l1.x), r.x), fma(bj, fma(kt, l0.x, l1.y), r.y));
-          if (i == j) r = mk(fma(-(T)a.kp.kq[j], l0.y, r.x), fma((T)a.kp.kq[j], l0.x, r.y));
+          if (i == j) r = mk(fma(-(T)kp.kq[j], l0.y, r.x), fma((T)kp.kq[j], l0.x, r.y));
         }
         kb[3 * t + i] = r;
       }
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
     if constexpr (OP == OP_PRE) {
       // u = -conj(kappa) x x per mode, and gamma kappa.x to the scratch
       cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
-      const T gam = (T)a.kp.gamma;
+      const T gam = (T)kp.gamma;
       for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
         const int t = e / N, n = e % N;
         const int g = TL::gidx(qb + t, n);
@@ -612,7 +619,7 @@ cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream
 
 template <typename T, int N>
 cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
-                        cudaStream_t st) {
+                        cudaStream_t st, const KParams* kps, int vec_per_k) {
   using C = Cfg<T, N>;
   const bool dbl = sizeof(T) == 8;
   const int n_mat = c->dev.mid ? c->dev.n_mat : 0;
@@ -625,10 +632,13 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
   a.mtab = dbl ? c->dev.mtab64 : c->dev.mtab32;
   a.n_mat = n_mat;
   a.kp = kp;
+  a.kps = kps;
+  a.vec_per_k = vec_per_k > 0 ? vec_per_k : 1;
   a.sbuf = sbuf;
   const size_t vlen = (size_t)3 * N * N * N;
   for (int v0 = 0; v0 < nvec; v0 += chunk) {
     const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
+    a.v_base = v0;
     const size_t tiles = (size_t)nv * N * N / C::TP;
     const cx<T>* x = static_cast<const cx<T>*>(X) + (size_t)v0 * vlen;
     cx<T>* y = static_cast<cx<T>*>(Y) + (size_t)v0 * vlen;
@@ -649,14 +659,15 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
 
 template <typename T>
 cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
+                        const KParams* kps, int vec_per_k,
                         cudaStream_t st) {
   switch (c->n) {
-    case 8: return fftk::run_apply_n<T, 8>(c, kp, X, Y, nvec, chunk, sbuf, st);
-    case 16: return fftk::run_apply_n<T, 16>(c, kp, X, Y, nvec, chunk, sbuf, st);
-    case 32: return fftk::run_apply_n<T, 32>(c, kp, X, Y, nvec, chunk, sbuf, st);
-    case 64: return fftk::run_apply_n<T, 64>(c, kp, X, Y, nvec, chunk, sbuf, st);
-    case 128: return fftk::run_apply_n<T, 128>(c, kp, X, Y, nvec, chunk, sbuf, st);
-    case 256: return fftk::run_apply_n<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st);
+    case 8: return fftk::run_apply_n<T, 8>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
+    case 16: return fftk::run_apply_n<T, 16>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
+    case 32: return fftk::run_apply_n<T, 32>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
+    case 64: return fftk::run_apply_n<T, 64>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
+    case 128: return fftk::run_apply_n<T, 128>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
+    case 256: return fftk::run_apply_n<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
   }
   return cudaErrorInvalidValue;
 }

@@ -61,6 +61,12 @@ struct pcx_ctx {
   void* scratch = nullptr;     // gamma kappa.x carried from pass 1 to pass 5
   size_t scratch_bytes = 0;
   size_t l2_bytes = 0;
+  // k table of the k-batched apply (device, grown on demand)
+  void* ktab = nullptr;
+  size_t ktab_bytes = 0;
+  // CUDA graphs of the apply launch chain (fft_apply.cu), when enabled
+  int use_graphs = 0;
+  void* graphs = nullptr;
   // workspace of the learned-correction kernels (learned.cpp)
   void* cnn_ws = nullptr;
   size_t cnn_ws_bytes = 0;
@@ -94,6 +100,13 @@ cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void
 cudaError_t launch_apply_noalloc(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
                                  int precision, cudaStream_t s);
 int apply_chunk(const pcx_ctx* c, int precision);
+// k-batched apply: nk groups of vec_per_k vectors, group i at kps_host[i]
+cudaError_t launch_apply_kbatch(pcx_ctx* c, const KParams* kps_host, int nk, int vec_per_k, const void* X, void* Y,
+                                int precision, cudaStream_t s);
+// release the graph cache of a context
+void free_apply_graphs(pcx_ctx* c);
+// tune.cpp
+cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, pcx_tune_result* out);
 size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec);
 cudaError_t launch_precond(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec,
                            int precision, cudaStream_t s);

@@ -1,0 +1,191 @@
+// Autotuner of the apply launch configuration: vectors per launch chunk
+// (how much of the block sweeps the five passes while L2-resident) and
+// whether the launch chain replays as a CUDA graph.  Each candidate is timed
+// with CUDA events on the caller's stream; the choice is cached per
+// (device, SM count, N, precision, block) in the process and, when the
+// environment variable PCX_TUNE_CACHE names a file, in that file (one line
+// per key), so later contexts start tuned.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pcx_internal.h"
+
+namespace pcx {
+
+namespace {
+
+struct Entry {
+  std::string key;
+  pcx_tune_result res;
+};
+
+std::mutex g_mu;
+std::vector<Entry> g_cache;
+
+std::string make_key(const pcx_ctx* c, int precision, int nvec) {
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof(prop));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name(prop.name);
+  for (char& ch : name)
+    if (ch == ' ' || ch == '|') ch = '_';
+  return name + "|" + std::to_string(prop.multiProcessorCount) + "|" + std::to_string(c->n) + "|" +
+         std::to_string(precision) + "|" + std::to_string(nvec);
+}
+
+bool file_lookup(const std::string& key, pcx_tune_result* r) {
+  const char* path = std::getenv("PCX_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), f)) {
+    char k[400];
+    int chunk = 0, graphs = 0;
+    double us = 0;
+    if (std::sscanf(line, "%399s %d %d %lf", k, &chunk, &graphs, &us) == 4 && key == k && chunk > 0) {
+      r->chunk = chunk;
+      r->graphs = graphs;
+      r->us_per_vector = us;
+      found = true;   // the last line for a key wins
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+void file_store(const std::string& key, const pcx_tune_result& r) {
+  const char* path = std::getenv("PCX_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), r.chunk, r.graphs, r.us_per_vector);
+  std::fclose(f);
+}
+
+bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+#define CKT(x)                                    \
+  do {                                            \
+    cudaError_t _e = (x);                         \
+    if (_e != cudaSuccess) {                      \
+      err = _e;                                   \
+      goto done;                                  \
+    }                                             \
+  } while (0)
+
+}  // namespace
+
+cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, pcx_tune_result* out) {
+  const std::string key = make_key(c, precision, nvec);
+  pcx_tune_result r;
+  std::memset(&r, 0, sizeof(r));
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (const Entry& e : g_cache)
+      if (e.key == key) {
+        r = e.res;
+        r.from_cache = 1;
+      }
+    if (!r.from_cache && file_lookup(key, &r)) r.from_cache = 2;
+  }
+  if (r.from_cache) {
+    c->apply_chunk = r.chunk;
+    c->use_graphs = r.graphs;
+    if (out) *out = r;
+    return cudaSuccess;
+  }
+  const size_t vbytes = (size_t)3 * c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  void* X = nullptr;
+  void* Y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaSuccess;
+  const int saved_chunk = c->apply_chunk, saved_graphs = c->use_graphs;
+  const double k[3] = {0.31, 0.67, 1.13};
+  const KParams kp = make_kparams(c, k, 0.0);
+  std::vector<int> cands;
+  double best = 1e300;
+  int best_chunk = 1;
+  const int reps = 3;
+  auto time_apply = [&](double* ms) -> cudaError_t {
+    cudaError_t e2;
+    for (int w = 0; w < 2; ++w)   // warm-up (and the eager + capture uses of a graph key)
+      if ((e2 = launch_apply(c, kp, X, Y, nvec, precision, s)) != cudaSuccess) return e2;
+    if ((e2 = cudaEventRecord(e0, s)) != cudaSuccess) return e2;
+    for (int i = 0; i < reps; ++i)
+      if ((e2 = launch_apply(c, kp, X, Y, nvec, precision, s)) != cudaSuccess) return e2;
+    if ((e2 = cudaEventRecord(e1, s)) != cudaSuccess) return e2;
+    if ((e2 = cudaEventSynchronize(e1)) != cudaSuccess) return e2;
+    float f = 0;
+    if ((e2 = cudaEventElapsedTime(&f, e0, e1)) != cudaSuccess) return e2;
+    *ms = f / reps;
+    return cudaSuccess;
+  };
+  for (int ch = 1; ch <= 64 && ch <= nvec; ch *= 2) cands.push_back(ch);
+  if (std::find(cands.begin(), cands.end(), nvec) == cands.end() && nvec <= 64) cands.push_back(nvec);
+  CKT(cudaMalloc(&X, vbytes * nvec));
+  CKT(cudaMalloc(&Y, vbytes * nvec));
+  CKT(launch_fill_random(X, nvec, vbytes / (precision == PCX_FP64 ? 16 : 8), 12345, precision, s));
+  CKT(cudaEventCreate(&e0));
+  CKT(cudaEventCreate(&e1));
+  c->use_graphs = 0;
+  for (int ch : cands) {
+    c->apply_chunk = ch;
+    double ms = 0;
+    CKT(time_apply(&ms));
+    ++r.candidates;
+    if (ms < best) {
+      best = ms;
+      best_chunk = ch;
+    }
+  }
+  r.chunk = best_chunk;
+  r.graphs = 0;
+  if (capturable(s)) {
+    c->apply_chunk = best_chunk;
+    c->use_graphs = 1;
+    double ms = 0;
+    CKT(time_apply(&ms));
+    ++r.candidates;
+    if (ms < 0.98 * best) {
+      best = ms;
+      r.graphs = 1;
+    }
+  }
+  r.us_per_vector = 1e3 * best / nvec;
+done:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (X || Y) cudaStreamSynchronize(s);
+  if (X) cudaFree(X);
+  if (Y) cudaFree(Y);
+  free_apply_graphs(c);   // the timing buffers are gone
+  if (err != cudaSuccess) {
+    c->apply_chunk = saved_chunk;
+    c->use_graphs = saved_graphs;
+    return err;
+  }
+  c->apply_chunk = r.chunk;
+  c->use_graphs = r.graphs;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_cache.push_back(Entry{key, r});
+    file_store(key, r);
+  }
+  if (out) *out = r;
+  return cudaSuccess;
+}
+
+#undef CKT
+
+}  // namespace pcx

@@ -51,6 +51,14 @@ class pcx_solve_stats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class pcx_tune_result(C.Structure):
+    _fields_ = [("chunk", C.c_int), ("graphs", C.c_int), ("us_per_vector", C.c_double), ("candidates", C.c_int),
+                ("from_cache", C.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class pcx_solve_opts(C.Structure):
     _fields_ = [("block", C.c_int), ("maxit", C.c_int), ("precision", C.c_int), ("switch_tol", C.c_double),
                 ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats)),
@@ -92,6 +100,9 @@ def lib():
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
             "pcx_div_norms": (st, [vp, dp, vp, C.c_int, C.c_int, vp, vp]),
+            "pcx_apply_kbatch": (st, [vp, dp, C.c_int, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+            "pcx_set_apply_graphs": (st, [vp, C.c_int]),
+            "pcx_autotune": (st, [vp, C.c_int, C.c_int, vp, C.POINTER(pcx_tune_result)]),
             "pcx_sandwich_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_cnn_init": (st, [C.c_uint64, vp, vp]),
             "pcx_cnn_gates": (st, [vp, vp, vp, vp]),
@@ -118,7 +129,8 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
+                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_autotune",
+                        "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
                         "pcx_cg_solve", "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
@@ -140,7 +152,7 @@ def _kvec(k):
 
 def _stream(stream):
     if stream is not None:
-        return C.c_void_p(stream)
+        return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -345,6 +357,28 @@ def pcx_div_norms(ctx, k, X, out, stream=None):
 PCX_CNN_HIDDEN = 8
 PCX_CNN_NPARAMS = (PCX_CNN_HIDDEN * 3 * 27 + PCX_CNN_HIDDEN * PCX_CNN_HIDDEN * 27 + 3 * PCX_CNN_HIDDEN * 27
                    + 2 * (PCX_CNN_HIDDEN * 9 * 27 + PCX_CNN_HIDDEN))
+
+
+def pcx_apply_kbatch(ctx, kpts, X, Y, gamma=0.0, stream=None):
+    """Y[i, j] = Op(k_i) X[i, j] for X, Y shaped (nk, vec_per_k, 3, N, N, N)."""
+    kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+    nk, vpk = X.shape[0], X.shape[1]
+    if kp.shape[0] != nk:
+        raise ValueError("pcx_apply_kbatch: one k per group")
+    _check(lib().pcx_apply_kbatch(ctx.handle, _dptr(kp), nk, float(gamma), _devptr(X), _devptr(Y), vpk, _prec_of(X),
+                                  _stream(stream)), ctx.handle)
+    return Y
+
+
+def pcx_set_apply_graphs(ctx, enable):
+    _check(lib().pcx_set_apply_graphs(ctx.handle, int(bool(enable))), ctx.handle)
+
+
+def pcx_autotune(ctx, precision, nvec, stream=None):
+    """Tunes the apply launch configuration; returns the pcx_tune_result as a dict."""
+    r = pcx_tune_result()
+    _check(lib().pcx_autotune(ctx.handle, int(precision), int(nvec), _stream(stream), C.byref(r)), ctx.handle)
+    return r.as_dict()
 
 
 def pcx_sandwich_precond(ctx, k, R, W, gamma=0.0, stream=None):
