@@ -1,18 +1,24 @@
-"""Benchmark: compensated-operator applies per second at 128^3.
+"""Benchmark: compensated-operator applies per second at 128^3, and the
+per-k solve time to a 1e-8 residual.
 
 Workload (one step): the compensated operator A M A^H + gamma B^H B applied
-in the Fourier basis to one block of 16 vectors on the 128^3 diamond-rod
-structure (FCC lattice, four seeded anisotropic rod tensors, air), complex64,
-through the C ABI call pcx_apply.  value = vectors applied per second over
-the whole job.  Inputs (805 MB per block) are larger than the 129 MB L2, so
-no flush is needed between steps.
+in the Fourier basis on the 128^3 diamond-rod structure (FCC lattice, four
+seeded anisotropic rod tensors, air), complex64, to 40 Bloch vectors x a
+block of 16 vectors in one k-batched call (pcx_apply_kbatch: one launch per
+pass sweeps every (k, vector) pair).  The launch configuration comes from
+pcx_autotune on the timing stream.  value = vectors applied per second over
+the whole job.  Inputs (32 GB per step) are far larger than the 129 MB L2,
+so no flush is needed between steps.  e2e: pcx_apply_host on host buffers,
+one Bloch vector x 16 vectors per step, copies inside the timed region.
+
+The line also carries "solve": the per-k time to Res_j <= 1e-8 (12 bands,
+block 16, pcx_solve) on the same structure, in mixed precision with the
+FFT-diagonal K_P^{-1}, with the curl-sandwich T0, with the learned
+correction (trained in the run on random structures at the same N, time
+reported), and plain FP64 with K_P^{-1}; wall-clock around the synchronising
+call (--no-solve skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-
-The line also carries "solve": the per-k solve time to Res_j <= 1e-8
-(12 bands, block 16, pcx_solve) on the same structure and k, mixed precision
-(FP32 apply and directions, FP64 X and Rayleigh-Ritz) against the plain FP64
-solve, wall-clock around the synchronising call (--no-solve skips it).
 
 --impl reference times the CPU oracle (the FP64 numpy definition
 F3^H (A M A^H + gamma B^H B) F3 x) on the same workload, one vector per step.
@@ -33,13 +39,17 @@ sys.path.insert(0, ROOT)
 
 N = 128
 BLOCK = 16
+NK = 40
 K_INDEX = 5
-WORKLOAD = "diamond-rods 128^3 FCC, block of 16 vectors, complex64 apply (pcx_apply)"
+WORKLOAD = ("diamond-rods 128^3 FCC, 40 Bloch vectors x block of 16, complex64, "
+            "one k-batched call per step (pcx_apply_kbatch)")
 METRIC = "compensated-operator applies/s at 128^3"
-# DRAM bytes of one vector through the five pass kernels (sum over the five
-# launches of one chunk), from the ncu capture summarised in
-# profiles/apply_pass_kernels_diamond128_c64.md; None once the kernels change.
-TRAFFIC_BYTES_PER_VECTOR_128_C64 = 292.67e6
+# DRAM bytes of one vector through the five pass kernels at 16 vectors per
+# launch (sum over the five launches of one chunk, divided by 16), from the
+# ncu capture summarised in profiles/apply_pass_kernels_diamond128_c64.md;
+# used only when the run uses that chunk.
+TRAFFIC_BYTES_PER_VECTOR_128_C64 = 8.8128e9 / 16
+TRAFFIC_CHUNK = 16
 UNIT = "vector-applies/s"
 
 
@@ -174,28 +184,68 @@ def run_reference(args):
     return 0
 
 
-def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8):
-    """Per-k time to Res_j <= tol, mixed precision vs plain FP64 (pcx_solve)."""
+def k_list(kpath, nk):
+    return [kpath[(K_INDEX + i) % len(kpath)] for i in range(nk)]
+
+
+def train_learned(pcx, n, n_struct=3, n_pairs=8, steps=120):
+    """The learned correction trained on random structures at grid n."""
     import numpy as np
-    ks = [kpath[(K_INDEX + i) % len(kpath)] for i in range(nk)]
+
+    import workloads as wl
+    from paper_2511_17107_gb300 import learned
+    rng = np.random.default_rng(11)
+    t0 = time.perf_counter()
+    samples, seed = [], 300
+    while len(samples) < n_struct and seed < 340:
+        s = wl.random_inclusions(seed)
+        seed += 1
+        try:
+            ctx = pcx.setup_structure(s, n)
+        except pcx.PcxError:
+            continue
+        smp = learned.collect(ctx, rng.uniform(-np.pi, np.pi, 3), n_pairs=n_pairs, seed=seed)
+        if smp is not None:
+            samples.append(smp)
+    P, losses = learned.train(samples, steps=steps, lr=3e-3)
+    return P, {"structures": len(samples), "pairs_per_structure": n_pairs, "steps": steps,
+               "loss_first": losses[0], "loss_last": losses[-1], "s": time.perf_counter() - t0}
+
+
+def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps=120):
+    """Per-k time to Res_j <= tol: mixed (K_P^{-1}, T0, learned) vs plain FP64."""
+    import numpy as np
+    ks = k_list(kpath, nk)
     out = {"tol": tol, "nev": nev, "block": block, "k_points": nk, "k_first_index": K_INDEX,
            "timer": "host wall-clock around pcx_solve (synchronises its stream)"}
+    P = None
+    if learned_steps > 0:
+        P, out["learned_training"] = train_learned(pcx, n, steps=learned_steps)
+    legs = [("mixed", pcx.PCX_FP32, 0, None), ("mixed_sandwich", pcx.PCX_FP32, 1, None)]
+    if P is not None:
+        legs.append(("mixed_learned", pcx.PCX_FP32, 1, P))
+    legs.append(("fp64", pcx.PCX_FP64, 0, None))
+    legs.append(("fp64_sandwich", pcx.PCX_FP64, 1, None))
     eigs = {}
-    for name, prec in (("mixed", pcx.PCX_FP32), ("fp64", pcx.PCX_FP64)):
+    for name, prec, kind, params in legs:
         stats = pcx.pcx_solve_stats()
         t0 = time.perf_counter()
         ev, res, its, st = pcx.pcx_solve(ctx, ks, nev, tol, block=block, precision=prec, stats=stats,
-                                         raise_on_noconv=False)
+                                         raise_on_noconv=False, precond_kind=kind, cnn_params=params)
         dt = time.perf_counter() - t0
         eigs[name] = ev
         d = stats.as_dict()
         out[name] = {"s_per_k": dt / nk, "status": int(st), "max_res": float(np.max(res)),
                      "iters_per_k": float(np.mean(its)), "iters_fp32": d["iters_fp32"], "iters_fp64": d["iters_fp64"],
                      "applies_fp32": d["applies_fp32"], "applies_fp64": d["applies_fp64"],
-                     "ms_apply": d["ms_apply"], "ms_gram": d["ms_gram"], "ms_rr": d["ms_rr"],
-                     "ms_other": d["ms_other"], "gamma_raises": d["gamma_raises"]}
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["s_per_k"] / out["mixed"]["s_per_k"]
-    out["max_rel_eig_diff"] = float(np.max(np.abs(eigs["mixed"] - eigs["fp64"]) / np.abs(eigs["fp64"])))
+                     "ms_apply": d["ms_apply"], "ms_precond": d["ms_precond"], "ms_gram": d["ms_gram"],
+                     "ms_rr": d["ms_rr"], "ms_other": d["ms_other"], "gamma_raises": d["gamma_raises"],
+                     "learned_fallbacks": d["learned_fallbacks"]}
+    for name in eigs:
+        if name != "fp64" and name in out:
+            out[name]["speedup_vs_fp64"] = out["fp64"]["s_per_k"] / out[name]["s_per_k"]
+            out[name]["max_rel_eig_diff_vs_fp64"] = float(np.max(np.abs(eigs[name] - eigs["fp64"])
+                                                                 / np.abs(eigs["fp64"])))
     return out
 
 
@@ -210,8 +260,12 @@ def main():
     ap.add_argument("--n", type=int, default=N, help="grid size (profiling runs use the default)")
     ap.add_argument("--block", type=int, default=BLOCK, help="vectors per step (profiling runs)")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--nk", type=int, default=NK, help="Bloch vectors per k-batched step")
     ap.add_argument("--no-solve", action="store_true", help="skip the per-k solve-time legs")
     ap.add_argument("--solve-nk", type=int, default=1, help="k-points of the solve legs (from index k_index)")
+    ap.add_argument("--learned-steps", type=int, default=120, help="training steps of the learned leg (0: skip)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
+    ap.add_argument("--chunk", type=int, default=0, help="vectors per launch chunk (implies --no-tune)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -237,23 +291,32 @@ def main():
         _build.build()
     if dist:
         td.barrier()
-    n, block = args.n, args.block
+    n, block, nk = args.n, args.block, args.nk
     cdt, es = (np.complex64, 8) if args.precision == "f32" else (np.complex128, 16)
+    prec = pcx.PCX_FP32 if es == 8 else pcx.PCX_FP64
     s = wl.diamond_rods()
-    k = wl.config_k(s.name)[K_INDEX]
+    kpath = wl.config_k(s.name)
+    ks = np.stack(k_list(kpath, nk))
     ctx = pcx.setup_structure(s, n)
+    stream = torch.cuda.Stream()
+    if args.chunk > 0:
+        args.no_tune = True
+        pcx.pcx_set_apply_chunk(ctx, args.chunk)
+    tune = None if args.no_tune else pcx.pcx_autotune(ctx, prec, block, stream=stream)
     x = wl.random_block(block, n, seed=20251117 + rank).astype(cdt)
-    X = torch.from_numpy(x).cuda()
+    X = torch.empty((nk, block, 3, n, n, n), dtype=torch.complex64 if es == 8 else torch.complex128, device="cuda")
+    X.copy_(torch.from_numpy(x).cuda().unsqueeze(0).expand_as(X))
     Y = torch.empty_like(X)
-    stream = torch.cuda.current_stream()
+    vecs = nk * block
 
     def step():
-        pcx.pcx_apply(ctx, k, X, Y)
+        pcx.pcx_apply_kbatch(ctx, ks, X, Y, stream=stream)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    # per-launch timing of the apply (events on the launching stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    # per-call timing of the k-batched apply (events on the launching stream)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -280,48 +343,51 @@ def main():
         td.all_reduce(t, op=td.ReduceOp.MAX)
         ms = float(t.item())
     per_launch_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps
-    value = world * block * args.steps / (ms / 1e3)
+    value = world * vecs * args.steps / (ms / 1e3)
 
     # end-to-end: host buffers through pcx_apply_host (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(x).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
-        pcx.pcx_apply_host(ctx, k, xh, yh)
+        pcx.pcx_apply_host(ctx, ks[0], xh, yh)
         e2e_steps = max(3, min(args.steps, 10))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            pcx.pcx_apply_host(ctx, k, xh, yh)
+            pcx.pcx_apply_host(ctx, ks[0], xh, yh)
         e2e_dt = time.perf_counter() - t0
         e2e = {"value": world * block * e2e_steps / e2e_dt, "unit": UNIT,
-               "h2d_bytes_per_step": int(xh.numel() * es), "d2h_bytes_per_step": int(yh.numel() * es)}
+               "h2d_bytes_per_step": int(xh.numel() * es), "d2h_bytes_per_step": int(yh.numel() * es),
+               "step": f"one Bloch vector x {block} vectors (pcx_apply_host)"}
 
     peak, peak_kind = peaks()
-    abytes = algorithmic_bytes(n, block, es, 4)
+    abytes = algorithmic_bytes(n, vecs, es, 4)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
+    chunk = pcx.pcx_get_apply_chunk(ctx, prec)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": WORKLOAD if (n, block, es) == (N, BLOCK, 8) else
-                   f"diamond-rods {n}^3 FCC, block of {block} vectors, {args.precision} apply (pcx_apply)",
-                   "N": n, "block": block, "k_index": K_INDEX,
-                   "l2": "inputs larger than L2 (805 MB per block)", "parallelism": f"replicas x{world}"},
+        "config": {"workload": WORKLOAD if (n, block, nk, es) == (N, BLOCK, NK, 8) else
+                   f"diamond-rods {n}^3 FCC, {nk} Bloch vectors x block of {block}, {args.precision}, "
+                   "one k-batched call per step (pcx_apply_kbatch)",
+                   "N": n, "block": block, "k_points": nk, "k_first_index": K_INDEX,
+                   "l2": f"inputs larger than L2 ({vecs * 3 * n ** 3 * es / 1e9:.1f} GB per step)",
+                   "parallelism": f"replicas x{world}", "autotune": tune},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (TRAFFIC_BYTES_PER_VECTOR_128_C64 * block
-                                 if (n, es) == (N, 8) and TRAFFIC_BYTES_PER_VECTOR_128_C64 else None),
+                     "traffic": (TRAFFIC_BYTES_PER_VECTOR_128_C64 * vecs
+                                 if (n, es) == (N, 8) and chunk == TRAFFIC_CHUNK else None),
                      "kernel": "pcx_apply pass chain (5 pass kernels per chunk of vectors)",
                      "peak_kind": peak_kind + " (burst HBM copy)",
                      "algorithmic_bytes_per_launch": abytes},
         "e2e": e2e,
-        "gpu_launches": 5 * -(-block // pcx.pcx_get_apply_chunk(ctx, pcx.PCX_FP32 if es == 8 else pcx.PCX_FP64))
-                        * args.steps,
+        "gpu_launches": 5 * -(-vecs // chunk) * args.steps,
         "clocks": ck,
     }
     if rank == 0 and not args.no_solve:
-        line["solve"] = solve_legs(pcx, ctx, wl.config_k(s.name), args.solve_nk, n)
+        line["solve"] = solve_legs(pcx, ctx, kpath, args.solve_nk, n, learned_steps=args.learned_steps)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess()
     if rank == 0:

@@ -21,6 +21,9 @@ ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
           "-I" + os.path.join(ROOT, "include")]
+# extra nvcc flags for tuning builds (e.g. "-DPCX_E32=8"); a change of this
+# variable needs a clean _build directory
+COMMON += os.environ.get("PCX_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

@@ -54,10 +54,19 @@ template <> struct Plan<64, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 0, NS
 template <> struct Plan<128, 8> { static constexpr int R0 = 8, R1 = 4, R2 = 4, NST = 3; };
 template <> struct Plan<256, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 4, NST = 3; };
 
+// Tile shape of the complex64 passes (elements per thread, pencils x points
+// per component); build-time choices, overridable with -D for tuning builds.
+#ifndef PCX_E32
+#define PCX_E32 16
+#endif
+#ifndef PCX_TN32
+#define PCX_TN32 2048
+#endif
+
 template <typename T, int N>
 struct Cfg {
-  static constexpr int E = sizeof(T) == 4 ? 16 : 8;
-  static constexpr int TN = sizeof(T) == 4 ? 2048 : 1024;        // pencils x points per component
+  static constexpr int E = sizeof(T) == 4 ? PCX_E32 : 8;
+  static constexpr int TN = sizeof(T) == 4 ? PCX_TN32 : 1024;    // pencils x points per component
   static constexpr int TP = (TN / N < N * N) ? TN / N : N * N;   // pencils per CTA
   static constexpr int THREADS = 3 * TP * N / E;
   // padded component stride: y/z tiles use N rows of TP + 1, x tiles TP
@@ -182,6 +191,20 @@ __device__ __forceinline__ void st2(cx<T>* p, cx<T> a, cx<T> b) {
   }
 }
 
+// Asynchronous copy of one complex element global -> shared (8 or 16 bytes).
+template <typename T>
+__device__ __forceinline__ void cp_async_cx(cx<T>* dst, const cx<T>* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Stockham stage of radix R (Ns = product of the radices already done).
 // SRC: 0 = shared memory, 1 = global (first stage only, Ns = 1).
 // DST: 0 = shared memory, 1 = global (last stage only, Ns = N / R).
@@ -262,7 +285,7 @@ __device__ __forceinline__ void fft_tile(cx<T>* s, const cx<T>* tw, const cx<T>*
 }
 
 template <typename T, int N, int AXIS, int OP>
-__global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pass_kernel(PassArgs a) {
   using C = Cfg<T, N>;
   using TL = Tile<T, N, AXIS>;
   constexpr int TP = C::TP;
@@ -329,10 +352,20 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
       // u = -conj(kappa) x x per mode, and gamma kappa.x to the scratch
       cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
       const T gam = (T)kp.gamma;
+      // the x tile lands in shared memory by asynchronous copies (all in
+      // flight at once), then C^H is applied in place
       for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
         const int t = e / N, n = e % N;
         const int g = TL::gidx(qb + t, n);
-        const cx<T> x0 = in[g], x1 = in[N3 + g], x2 = in[2 * N3 + g];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cp_async_cx<T>(&s[TL::sidx(c, t, n)], &in[c * N3 + g]);
+      }
+      cp_async_commit_wait_all();
+      __syncthreads();
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        const int g = TL::gidx(qb + t, n);
+        const cx<T> x0 = s[TL::sidx(0, t, n)], x1 = s[TL::sidx(1, t, n)], x2 = s[TL::sidx(2, t, n)];
         cx<T> kap[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
@@ -345,12 +378,21 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
       __syncthreads();
       fft_tile<T, N, 0, +1, 0, 1>(s, tw, nullptr, out, qb);
     } else {   // OP_POST
-      fft_tile<T, N, 0, -1, 1, 0>(s, tw, in, nullptr, qb);
+      // gamma kappa.x of the tile is fetched into shared memory while the
+      // FFT runs
       const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
+      cx<T>* ssb = kb + 3 * TP;   // [TP * N], POST launches only
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        cp_async_cx<T>(&ssb[e], &sb[TL::gidx(qb + t, n)]);
+      }
+      fft_tile<T, N, 0, -1, 1, 0>(s, tw, in, nullptr, qb);
+      cp_async_commit_wait_all();
+      __syncthreads();
       for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
         const int t = e / N, n = e % N;
         const int g = TL::gidx(qb + t, n);
-        const cx<T> sk = sb[g];
+        const cx<T> sk = ssb[e];
         cx<T> kap[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
@@ -363,9 +405,21 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
   } else if constexpr (OP == OP_SANDWICH) {
     // ---- z-axis: inverse FFT, per-cell M (Sec. 3.2.1), forward FFT ----
     __syncthreads();
-    fft_tile<T, N, 2, +1, 1, 0>(s, tw, in, nullptr, qb);
     const T* M = static_cast<const T*>(a.M);
     const uchar4* mid = static_cast<const uchar4*>(a.mid);
+    // material ids of the tile's cells, fetched into shared memory while
+    // the z FFT runs
+    uchar4* sid = reinterpret_cast<uchar4*>(mtab + 9 * a.n_mat);   // [TP * N], sandwich launches only
+    if (mid) {
+      for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {
+        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(&sid[w]));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(&mid[(w / TP) * N2 + (qb + w % TP)])
+                     : "memory");
+      }
+    }
+    fft_tile<T, N, 2, +1, 1, 0>(s, tw, in, nullptr, qb);
+    cp_async_commit_wait_all();
+    __syncthreads();
     const T inv_n3 = (T)(1.0 / (double)N3);
     for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {   // pencils fastest
       const int t = w % TP, n = w / TP;
@@ -373,7 +427,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS) pass_kernel(PassArgs a) {
       T d1, d2, d3;
       cx<T> o12, o13, o23;
       if (mid) {
-        const uchar4 id = mid[cell];
+        const uchar4 id = sid[w];
         d1 = mtab[9 * id.x];
         d2 = mtab[9 * id.y + 1];
         d3 = mtab[9 * id.z + 2];
@@ -623,7 +677,10 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
   using C = Cfg<T, N>;
   const bool dbl = sizeof(T) == 8;
   const int n_mat = c->dev.mid ? c->dev.n_mat : 0;
-  const size_t smem = C::SMEM + (size_t)9 * n_mat * sizeof(T);
+  const size_t smem = C::SMEM;
+  // + the gamma kappa.x tile (x POST); + the material table and the tile's ids (z sandwich)
+  const size_t post_smem = C::SMEM + (size_t)C::TP * N * sizeof(cx<T>);
+  const size_t sandwich_smem = C::SMEM + (((size_t)9 * n_mat * sizeof(T) + 15) & ~(size_t)15) + (size_t)C::TP * N * 4;
   PassArgs a;
   a.lam = dbl ? c->dev.lam64 : c->dev.lam32;
   a.tw = dbl ? c->dev.tw64 : c->dev.tw32;
@@ -648,9 +705,9 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
     if ((e = launch_pass<T, N, 0, OP_PRE>(a, tiles, smem, st)) != cudaSuccess) return e;
     a.in = y;
     if ((e = launch_pass<T, N, 1, OP_INV>(a, tiles, smem, st)) != cudaSuccess) return e;
-    if ((e = launch_pass<T, N, 2, OP_SANDWICH>(a, tiles, smem, st)) != cudaSuccess) return e;
+    if ((e = launch_pass<T, N, 2, OP_SANDWICH>(a, tiles, sandwich_smem, st)) != cudaSuccess) return e;
     if ((e = launch_pass<T, N, 1, OP_FWD>(a, tiles, smem, st)) != cudaSuccess) return e;
-    if ((e = launch_pass<T, N, 0, OP_POST>(a, tiles, smem, st)) != cudaSuccess) return e;
+    if ((e = launch_pass<T, N, 0, OP_POST>(a, tiles, post_smem, st)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
