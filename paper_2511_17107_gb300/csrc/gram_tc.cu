@@ -65,6 +65,15 @@ __device__ __forceinline__ void put(unsigned char* hi, unsigned char* lo, int ro
   *reinterpret_cast<float*>(lo + o1) = lm;
 }
 
+constexpr int PRODUCERS = THREADS - 32;   // warps 0-6 stage and convert; warp 7 issues the MMAs
+
+// Warp-specialised pipeline.  Producer warps keep raw chunks two ahead in
+// flight (cp.async), convert chunk f into tile stage f % 2 once the MMAs of
+// chunk f - 2 have released it (mbarrier empty[s], committed by the MMA
+// warp) and signal full[s]; they synchronise among themselves with a named
+// barrier only.  Lane 0 of warp 7 waits on full[s] and issues the MMAs.
+// Every wait is bounded; a timeout sets a shared flag that every role reads
+// at a uniform point, and the kernel reports it through g.err.
 __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(GramArgs g) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int abytes = tile_bytes(MT);
@@ -73,17 +82,30 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(GramArgs g) {
   const int ncol = g.same ? g.na : g.na + g.nb;       // raw columns per chunk
   const int raw_bytes = ncol * KC * 8;
   unsigned char* raw0 = sm + 2 * stage_bytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(raw0 + NRAW * raw_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
-  const int tid = threadIdx.x, warp = tid / 32;
+  uint64_t* full = reinterpret_cast<uint64_t*>(raw0 + NRAW * raw_bytes);
+  uint64_t* empty = full + 2;
+  // last: the last chunk whose MMAs were committed (-1: none; 8-byte slot
+  // right after the mbarriers); perr: written by thread 0 only, before the
+  // producers' barrier (so every producer reads the same value after it);
+  // merr: written by the MMA warp.  52 bytes in all.
+  volatile long long* last = reinterpret_cast<volatile long long*>(empty + 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(const_cast<long long*>(last + 1));
+  volatile int* perr = reinterpret_cast<volatile int*>(tslot + 1);
+  volatile int* merr = perr + 1;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
 
   // zero the tiles once (padding rows stay zero), allocate TMEM, init barriers
   for (int i = tid; i < stage_bytes * 2 / 16; i += THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tc::tmem_alloc<TMEM_COLS>(tslot);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    tc::mbar_init(&full[0], PRODUCERS);
+    tc::mbar_init(&full[1], PRODUCERS);
+    tc::mbar_init(&empty[0], 1);
+    tc::mbar_init(&empty[1], 1);
     tc::mbar_fence_init();
+    *perr = 0;
+    *merr = 0;
+    *last = -1;
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -93,86 +115,105 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(GramArgs g) {
   const long c0 = (long)blockIdx.x * g.chunks_per_cta;
   const long c1 = c0 + g.chunks_per_cta < g.nchunks ? c0 + g.chunks_per_cta : g.nchunks;
   const long nfill = c1 > c0 ? c1 - c0 : 0;
-  const uint32_t idesc = tc::idesc_tf32(MT, g.np);
 
-  // raw chunk f -> buffer f % NRAW: column c (A columns, then B columns), KC
-  // complex numbers contiguous per column, 16-byte pieces
-  auto prefetch = [&](long f) {
-    if (f >= nfill) return;
-    unsigned char* rb = raw0 + (f % NRAW) * raw_bytes;
-    const size_t l0 = (size_t)(c0 + f) * KC;
-    for (int e = tid; e < ncol * (KC / 2); e += THREADS) {
-      const int col = e / (KC / 2), piece = e % (KC / 2);
-      const size_t l = l0 + 2 * piece;
-      const float2* base = col < g.na ? g.A + (size_t)col * g.L : g.B + (size_t)(col - g.na) * g.L;
-      const uint32_t bytes = l + 2 <= g.L ? 16u : (l < g.L ? 8u : 0u);
-      tc::cp_async16(rb + (size_t)(col * KC + 2 * piece) * 8, base + (l < g.L ? l : 0), bytes);
-    }
-  };
-  prefetch(0);
-  tc::cp_async_commit();
-  prefetch(1);
-  tc::cp_async_commit();
-
-  bool ok = true;
-  long issued = 0;
-  for (long f = 0; f < nfill && ok; ++f) {
-    prefetch(f + 2);
-    tc::cp_async_commit();
-    tc::cp_async_wait<2>();                      // this thread's copies of chunk f are done
-    const int s = (int)(f & 1);
-    const long use = f >> 1;                     // earlier fills of tile buffer s
-    const bool w_ok = use < 1 || tc::mbar_wait(&mbar[s], (uint32_t)((use - 1) & 1), WAIT_LIMIT);
-    if (!__syncthreads_and(w_ok)) {              // block-uniform; also publishes the raw chunk
-      ok = false;
-      break;
-    }
-    unsigned char* ahi = sm + s * stage_bytes;
-    unsigned char* alo = ahi + abytes;
-    unsigned char* bhi = alo + abytes;
-    unsigned char* blo = bhi + bbytes;
-    const float2* rb = reinterpret_cast<const float2*>(raw0 + (f % NRAW) * raw_bytes);
-    for (int e = tid; e < ncol * KC; e += THREADS) {
-      const int col = e / KC, k = e % KC;
-      const float2 v = rb[e];
-      if (col < g.na) put(ahi, alo, MT, col, g.na, k, v);
-      else put(bhi, blo, g.np, col - g.na, g.nb, k, v);
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      const uint32_t a_hi = tc::smem_addr(ahi), a_lo = tc::smem_addr(alo);
-      const uint32_t b_hi = g.same ? a_hi : tc::smem_addr(bhi), b_lo = g.same ? a_lo : tc::smem_addr(blo);
-      const uint32_t alb = tile_lbo(MT), blb = g.same ? tile_lbo(MT) : tile_lbo(g.np);
-#pragma unroll
-      for (int ks = 0; ks < KC / 8; ++ks) {
-        const uint32_t ao = 2 * ks * alb, bo = 2 * ks * blb;
-        const uint64_t dah = tc::smem_desc(a_hi + ao, alb, 128), dal = tc::smem_desc(a_lo + ao, alb, 128);
-        const uint64_t dbh = tc::smem_desc(b_hi + bo, blb, 128), dbl = tc::smem_desc(b_lo + bo, blb, 128);
-        tc::mma_tf32(tmem, dah, dbh, idesc, issued > 0 ? 1u : 0u);
-        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
-        tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
-        ++issued;
+  if (warp < PRODUCERS / 32) {
+    // raw chunk f -> buffer f % NRAW: column c (A columns, then B columns),
+    // KC complex numbers contiguous per column, 16-byte pieces
+    auto prefetch = [&](long f) {
+      if (f >= nfill) return;
+      unsigned char* rb = raw0 + (f % NRAW) * raw_bytes;
+      const size_t l0 = (size_t)(c0 + f) * KC;
+      for (int e = tid; e < ncol * (KC / 2); e += PRODUCERS) {
+        const int col = e / (KC / 2), piece = e % (KC / 2);
+        const size_t l = l0 + 2 * piece;
+        const float2* base = col < g.na ? g.A + (size_t)col * g.L : g.B + (size_t)(col - g.na) * g.L;
+        const uint32_t bytes = l + 2 <= g.L ? 16u : (l < g.L ? 8u : 0u);
+        tc::cp_async16(rb + (size_t)(col * KC + 2 * piece) * 8, base + (l < g.L ? l : 0), bytes);
       }
-      tc::mma_commit(&mbar[s]);
+    };
+    prefetch(0);
+    tc::cp_async_commit();
+    prefetch(1);
+    tc::cp_async_commit();
+    for (long f = 0; f < nfill; ++f) {
+      tc::cp_async_wait<1>();                    // this thread's copies of chunk f are done
+      const int s = (int)(f & 1);
+      const long use = f >> 1;
+      if (tid == 0 && use > 0 && !tc::mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), WAIT_LIMIT)) *perr = 1;
+      // chunk f has landed for every producer, chunk f - 1 is converted, stage s is free
+      tc::named_barrier(1, PRODUCERS);
+      if (*perr) break;                          // uniform: written before the barrier, read after it
+      prefetch(f + 2);
+      tc::cp_async_commit();
+      unsigned char* ahi = sm + s * stage_bytes;
+      unsigned char* alo = ahi + abytes;
+      unsigned char* bhi = alo + abytes;
+      unsigned char* blo = bhi + bbytes;
+      const float2* rb = reinterpret_cast<const float2*>(raw0 + (f % NRAW) * raw_bytes);
+      for (int e = tid; e < ncol * KC; e += PRODUCERS) {
+        const int col = e / KC, k = e % KC;
+        const float2 v = rb[e];
+        if (col < g.na) put(ahi, alo, MT, col, g.na, k, v);
+        else put(bhi, blo, g.np, col - g.na, g.nb, k, v);
+      }
+      tc::fence_proxy_async();                   // generic writes -> visible to the tensor core
+      tc::mbar_arrive(&full[s]);
+    }
+    tc::cp_async_wait<0>();
+  } else {
+    const uint32_t idesc = tc::idesc_tf32(MT, g.np);
+    long issued = 0;
+    for (long f = 0; f < nfill; ++f) {
+      const int s = (int)(f & 1);
+      const long use = f >> 1;
+      int ok = 1;
+      if (lane == 0) ok = tc::mbar_wait(&full[s], (uint32_t)(use & 1), WAIT_LIMIT) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) *merr = 1;
+        break;
+      }
+      if (lane == 0) {
+        tc::fence_after_sync();
+        unsigned char* ahi = sm + s * stage_bytes;
+        unsigned char* alo = ahi + abytes;
+        unsigned char* bhi = alo + abytes;
+        unsigned char* blo = bhi + bbytes;
+        const uint32_t a_hi = tc::smem_addr(ahi), a_lo = tc::smem_addr(alo);
+        const uint32_t b_hi = g.same ? a_hi : tc::smem_addr(bhi), b_lo = g.same ? a_lo : tc::smem_addr(blo);
+        const uint32_t alb = tile_lbo(MT), blb = g.same ? tile_lbo(MT) : tile_lbo(g.np);
+#pragma unroll
+        for (int ks = 0; ks < KC / 8; ++ks) {
+          const uint32_t ao = 2 * ks * alb, bo = 2 * ks * blb;
+          const uint64_t dah = tc::smem_desc(a_hi + ao, alb, 128), dal = tc::smem_desc(a_lo + ao, alb, 128);
+          const uint64_t dbh = tc::smem_desc(b_hi + bo, blb, 128), dbl = tc::smem_desc(b_lo + bo, blb, 128);
+          tc::mma_tf32(tmem, dah, dbh, idesc, issued > 0 ? 1u : 0u);
+          tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
+          tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
+          ++issued;
+        }
+        tc::mma_commit(&empty[s]);               // releases stage s when these MMAs complete
+        *last = f;
+      }
+      __syncwarp();
     }
   }
-  tc::cp_async_wait<0>();
-  // the last commit covers every MMA issued by thread 0
-  bool last_ok = true;
-  if (nfill > 0) {
-    const int s_last = (int)((nfill - 1) & 1);
-    const long use_last = (nfill - 1) >> 1;
-    last_ok = tc::mbar_wait(&mbar[s_last], (uint32_t)(use_last & 1), ok ? WAIT_LIMIT : WAIT_LIMIT / 16);
+  __syncthreads();
+  // the last commit covers every MMA issued; wait for it also on the error
+  // path (with a shorter limit) so that no MMA is in flight when TMEM is freed
+  bool ok = *perr == 0 && *merr == 0 && *last == nfill - 1;
+  if (tid == 0 && *last >= 0) {
+    const long fl = (long)*last;
+    if (!tc::mbar_wait(&empty[fl & 1], (uint32_t)((fl >> 1) & 1), ok ? WAIT_LIMIT : WAIT_LIMIT / 16)) *merr = 1;
   }
-  ok = __syncthreads_and(ok && last_ok);
+  __syncthreads();
+  ok = ok && *merr == 0;
   tc::fence_after_sync();
   if (!ok) {
     if (tid == 0) atomicExch(g.err, 1);
   } else if (warp < 4) {
     // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of D)
-    const int row = warp * 32 + (tid & 31);
+    const int row = warp * 32 + lane;
     float* out = g.partial + ((size_t)blockIdx.x * MT + row) * g.np;
     for (int cb = 0; cb < g.np; cb += 16) {
       float v[16];
