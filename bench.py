@@ -212,20 +212,23 @@ def train_learned(pcx, n, n_struct=3, n_pairs=8, steps=120):
                "loss_first": losses[0], "loss_last": losses[-1], "s": time.perf_counter() - t0}
 
 
-def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps=120):
+def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps=120, only=""):
     """Per-k time to Res_j <= tol: mixed (K_P^{-1}, T0, learned) vs plain FP64."""
     import numpy as np
     ks = k_list(kpath, nk)
     out = {"tol": tol, "nev": nev, "block": block, "k_points": nk, "k_first_index": K_INDEX,
            "timer": "host wall-clock around pcx_solve (synchronises its stream)"}
+    want = set(x for x in only.split(",") if x)
     P = None
-    if learned_steps > 0:
+    if learned_steps > 0 and (not want or "mixed_learned" in want):
         P, out["learned_training"] = train_learned(pcx, n, steps=learned_steps)
     legs = [("mixed", pcx.PCX_FP32, 0, None), ("mixed_sandwich", pcx.PCX_FP32, 1, None)]
     if P is not None:
         legs.append(("mixed_learned", pcx.PCX_FP32, 1, P))
     legs.append(("fp64", pcx.PCX_FP64, 0, None))
     legs.append(("fp64_sandwich", pcx.PCX_FP64, 1, None))
+    if want:
+        legs = [leg for leg in legs if leg[0] in want]
     eigs = {}
     for name, prec, kind, params in legs:
         stats = pcx.pcx_solve_stats()
@@ -242,7 +245,7 @@ def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps
                      "ms_rr": d["ms_rr"], "ms_other": d["ms_other"], "gamma_raises": d["gamma_raises"],
                      "learned_fallbacks": d["learned_fallbacks"]}
     for name in eigs:
-        if name != "fp64" and name in out:
+        if name != "fp64" and name in out and "fp64" in out:
             out[name]["speedup_vs_fp64"] = out["fp64"]["s_per_k"] / out[name]["s_per_k"]
             out[name]["max_rel_eig_diff_vs_fp64"] = float(np.max(np.abs(eigs[name] - eigs["fp64"])
                                                                  / np.abs(eigs["fp64"])))
@@ -264,6 +267,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the per-k solve-time legs")
     ap.add_argument("--solve-nk", type=int, default=1, help="k-points of the solve legs (from index k_index)")
     ap.add_argument("--learned-steps", type=int, default=120, help="training steps of the learned leg (0: skip)")
+    ap.add_argument("--solve-legs", default="", help="comma list of solve legs to run (default: all)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--chunk", type=int, default=0, help="vectors per launch chunk (implies --no-tune)")
     args = ap.parse_args()
@@ -387,7 +391,8 @@ def main():
         "clocks": ck,
     }
     if rank == 0 and not args.no_solve:
-        line["solve"] = solve_legs(pcx, ctx, kpath, args.solve_nk, n, learned_steps=args.learned_steps)
+        line["solve"] = solve_legs(pcx, ctx, kpath, args.solve_nk, n, learned_steps=args.learned_steps,
+                                   only=args.solve_legs)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess()
     if rank == 0:

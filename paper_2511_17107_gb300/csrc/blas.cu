@@ -79,19 +79,16 @@ __global__ void __launch_bounds__(256) gram_kernel(const cx<T>* __restrict__ A, 
 }
 
 // ---------------------------------------------------------------------------
-// Gram of complex128 blocks on the FP32 pipes with FP64-level accuracy
-// (GB300's FP64 rate is a small fraction of its FP32 rate).  Every FP64
-// entry is split once, when staged, into FP32 hi + lo (about 48 significant
-// bits); each real product x*y is formed as hi*hi exactly (TwoProd with an
-// FMA) plus the cross terms, and accumulated in a double-float pair
-// (Knuth's TwoSum), both error-free transformations of Dekker (1971) and
-// Knuth (TAOCP vol. 2).  __fadd_rn / __fmul_rn keep the compiler from fusing
-// the steps.  Entries must stay inside the FP32 exponent range.
-// CTA tile: 48 x 48 outputs, 256 threads with 3 x 3 outputs each.
+// Double-float arithmetic on the FP32 pipes (GB300's FP64 rate is a small
+// fraction of its FP32 rate) for the complex128 combinations: every FP64
+// entry is split into FP32 hi + lo (about 48 significant bits); each real
+// product x*y is formed as hi*hi exactly (TwoProd with an FMA) plus the cross
+// terms, and accumulated in a double-float pair (Knuth's TwoSum), both
+// error-free transformations of Dekker (1971) and Knuth (TAOCP vol. 2).
+// __fadd_rn / __fmul_rn keep the compiler from fusing the steps.  Entries
+// must stay inside the FP32 exponent range.  (The complex128 Gram products
+// use the same scheme in gram_x.cu.)
 // ---------------------------------------------------------------------------
-constexpr int FT = 48;
-constexpr int FL = 16;
-
 struct DF {
   float s, c;
 };
@@ -110,65 +107,6 @@ __device__ __forceinline__ void df_add_prod(DF& acc, float xh, float xl, float y
   const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
   acc.s = s;
   acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
-}
-
-__global__ void __launch_bounds__(256) gram_ff_kernel(const double2* __restrict__ A, int na,
-                                                      const double2* __restrict__ B, int nb, size_t L,
-                                                      size_t rows_per_cta, double* __restrict__ G) {
-  __shared__ float4 sa[FL][FT + 1];   // (re hi, re lo, im hi, im lo)
-  __shared__ float4 sb[FL][FT + 1];
-  const int ti = blockIdx.x * FT, tj = blockIdx.y * FT;
-  const size_t l0 = (size_t)blockIdx.z * rows_per_cta;
-  const size_t l1 = (l0 + rows_per_cta < L) ? l0 + rows_per_cta : L;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  DF re[3][3], im[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) re[a][b] = im[a][b] = DF{0.f, 0.f};
-  auto split = [](double2 v) {
-    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-    return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
-  };
-  for (size_t base = l0; base < l1; base += FL) {
-    for (int e = threadIdx.x; e < FL * FT; e += 256) {
-      const int r = e % FL, col = e / FL;
-      const size_t l = base + r;
-      const bool ok = l < l1;
-      sa[r][col] = (ok && ti + col < na) ? split(A[(size_t)(ti + col) * L + l]) : make_float4(0, 0, 0, 0);
-      sb[r][col] = (ok && tj + col < nb) ? split(B[(size_t)(tj + col) * L + l]) : make_float4(0, 0, 0, 0);
-    }
-    __syncthreads();
-#pragma unroll 2
-    for (int r = 0; r < FL; ++r) {
-      float4 av[3], bv[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) av[a] = sa[r][ty + 16 * a];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) bv[b] = sb[r][tx + 16 * b];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
-          df_add_prod(re[a][b], av[a].x, av[a].y, bv[b].x, bv[b].y, false);
-          df_add_prod(re[a][b], av[a].z, av[a].w, bv[b].z, bv[b].w, false);
-          df_add_prod(im[a][b], av[a].x, av[a].y, bv[b].z, bv[b].w, false);
-          df_add_prod(im[a][b], av[a].z, av[a].w, bv[b].x, bv[b].y, true);
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int i = ti + ty + 16 * a, j = tj + tx + 16 * b;
-      if (i < na && j < nb) {
-        atomicAdd(&G[2 * ((size_t)i * nb + j)], (double)re[a][b].s + (double)re[a][b].c);
-        atomicAdd(&G[2 * ((size_t)i * nb + j) + 1], (double)im[a][b].s + (double)im[a][b].c);
-      }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -395,7 +333,8 @@ unsigned grid_for(size_t work, int threads, unsigned cap = 152u * 32u) {
 
 cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision, double* G,
                         cudaStream_t s) {
-  if (precision == PCX_FP32 && L > 0 && gram_tc_supported(na, nb, L)) return launch_gram_tc(A, na, B, nb, L, G, s);
+  if (precision == PCX_FP64) return launch_gram_dd(A, na, B, nb, L, G, s);   // gram_x.cu
+  if (L > 0 && gram_tc_supported(na, nb, L)) return launch_gram_tc(A, na, B, nb, L, G, s);
   return launch_gram_cuda_cores(A, na, B, nb, L, precision, G, s);
 }
 
@@ -404,8 +343,9 @@ cudaError_t launch_gram_cuda_cores(const void* A, int na, const void* B, int nb,
   cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * 2 * (size_t)na * nb, s);
   if (e != cudaSuccess) return e;
   if (L == 0) return cudaSuccess;
-  const int tile = precision == PCX_FP64 ? FT : GT;
-  const int rows_step = precision == PCX_FP64 ? FL : GL;
+  if (precision == PCX_FP64) return launch_gram_dd(A, na, B, nb, L, G, s);
+  const int tile = GT;
+  const int rows_step = GL;
   const unsigned gx = (na + tile - 1) / tile, gy = (nb + tile - 1) / tile;
   // enough CTAs to fill the GPU several times over
   const size_t want = std::max<size_t>(1, (size_t)152 * 8 / (gx * gy));
@@ -413,12 +353,8 @@ cudaError_t launch_gram_cuda_cores(const void* A, int na, const void* B, int nb,
   rows = ((rows + rows_step - 1) / rows_step) * rows_step;
   const unsigned gz = (unsigned)((L + rows - 1) / rows);
   dim3 grid(gx, gy, gz);
-  if (precision == PCX_FP64)
-    gram_ff_kernel<<<grid, 256, 0, s>>>(static_cast<const double2*>(A), na, static_cast<const double2*>(B), nb, L,
-                                        rows, G);
-  else
-    gram_kernel<float><<<grid, 256, 0, s>>>(static_cast<const cx<float>*>(A), na, static_cast<const cx<float>*>(B),
-                                            nb, L, rows, G);
+  gram_kernel<float><<<grid, 256, 0, s>>>(static_cast<const cx<float>*>(A), na, static_cast<const cx<float>*>(B), nb,
+                                          L, rows, G);
   return cudaGetLastError();
 }
 

@@ -231,21 +231,41 @@ __global__ void __launch_bounds__(THREADS, 1) gram_tc_kernel(GramArgs g) {
   if (warp == 0) tc::tmem_dealloc<TMEM_COLS>(tmem);
 }
 
-// G[i][j] = sum over CTAs of the stacked-real products (FP64).
-__global__ void gram_reduce_kernel(const float* __restrict__ partial, int nctas, int na, int nb, int np,
-                                   const int* __restrict__ err, double* __restrict__ G) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= na * nb) return;
+// G[i][j] = sum over CTAs of the stacked-real products (FP64): one block per
+// entry, its threads striding over the CTAs' partials, then a tree sum.
+constexpr int RED_THREADS = 256;
+__global__ void __launch_bounds__(RED_THREADS) gram_reduce_kernel(const float* __restrict__ partial, int nctas, int na,
+                                                                 int nb, int np, const int* __restrict__ err,
+                                                                 double* __restrict__ G) {
+  __shared__ double red[2][RED_THREADS / 32];
+  const int idx = blockIdx.x;
   const int i = idx / nb, j = idx % nb;
   double re = 0.0, im = 0.0;
-  for (int c = 0; c < nctas; ++c) {
+  for (int c = threadIdx.x; c < nctas; c += RED_THREADS) {
     const float* p = partial + (size_t)c * MT * np;
     re += (double)p[i * np + j] + (double)p[(na + i) * np + nb + j];
     im += (double)p[i * np + nb + j] - (double)p[(na + i) * np + j];
   }
-  if (*err) re = im = __longlong_as_double(0x7ff8000000000000LL);   // NaN: the kernel gave up
-  G[2 * idx] = re;
-  G[2 * idx + 1] = im;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = re;
+    red[1][threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    re = im = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) {
+      re += red[0][w];
+      im += red[1][w];
+    }
+    if (*err) re = im = __longlong_as_double(0x7ff8000000000000LL);   // NaN: the kernel gave up
+    G[2 * idx] = re;
+    G[2 * idx + 1] = im;
+  }
 }
 
 struct Scratch {
@@ -314,8 +334,7 @@ cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t 
     return e;
   gram_tc_kernel<<<(unsigned)nctas, THREADS, smem, s>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int total = na * nb;
-  gram_reduce_kernel<<<(total + 127) / 128, 128, 0, s>>>(g.partial, (int)nctas, na, nb, g.np, g.err, G);
+  gram_reduce_kernel<<<(unsigned)(na * nb), RED_THREADS, 0, s>>>(g.partial, (int)nctas, na, nb, g.np, g.err, G);
   return cudaGetLastError();
 }
 

@@ -78,6 +78,112 @@ __device__ __forceinline__ void df_mac(DF& acc, float xh, float xl, float y) {
   acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
 }
 
+// acc += (xh + xl) * (yh + yl)  (NEG: acc -= ...)
+template <bool NEG>
+__device__ __forceinline__ void df_mac2(DF& acc, float xh, float xl, float yh, float yl) {
+  float p = __fmul_rn(xh, yh);
+  float e = fmaf(xh, yh, -p);   // p + e == xh * yh exactly
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  e = fmaf(xl, yl, e);
+  if (NEG) {
+    p = -p;
+    e = -e;
+  }
+  const float s = __fadd_rn(acc.s, p);
+  const float bb = __fsub_rn(s, acc.s);
+  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.s = s;
+  acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
+}
+
+// (s, c) <- (s + c, the rounding error of that sum): keeps the compensation
+// at half an ulp of s, so that its own rounding stays at 2^-48 of s per add
+// (Fast2Sum, valid since |c| <= |s| here or s = 0).
+__device__ __forceinline__ void df_renorm(DF& a) {
+  const float s = __fadd_rn(a.s, a.c);
+  a.c = __fsub_rn(a.c, __fsub_rn(s, a.s));
+  a.s = s;
+}
+
+// G = A^H B with A and B complex128, both split into FP32 hi + lo when
+// staged; tile T x T (T = 16 or 32), 256 threads with (T/16)^2 outputs each.
+template <int T>
+__global__ void __launch_bounds__(XTHREADS, 4)
+    gram_dd_kernel(const double2* __restrict__ A, int na, const double2* __restrict__ B, int nb, size_t L,
+                   size_t rows_per_cta, double2* __restrict__ partial) {
+  constexpr int O = T / 16;
+  __shared__ float4 sa[XL][T + 1];
+  __shared__ float4 sb[XL][T + 1];
+  const int ti = blockIdx.x * T, tj = blockIdx.y * T;
+  const size_t l0 = (size_t)blockIdx.z * rows_per_cta;
+  const size_t l1 = (l0 + rows_per_cta < L) ? l0 + rows_per_cta : L;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  DF re[O][O], im[O][O];
+#pragma unroll
+  for (int a = 0; a < O; ++a)
+#pragma unroll
+    for (int b = 0; b < O; ++b) re[a][b] = im[a][b] = DF{0.f, 0.f};
+  for (size_t base = l0; base < l1; base += XL) {
+#pragma unroll
+    for (int k = 0; k < XL * T / XTHREADS; ++k) {
+      const int e = threadIdx.x + k * XTHREADS;
+      const int r = e % XL, col = e / XL;
+      const size_t l = base + r;
+      const bool ok = l < l1;
+      float4 av = make_float4(0.f, 0.f, 0.f, 0.f), bv = av;
+      if (ok && ti + col < na) {
+        const double2 v = A[(size_t)(ti + col) * L + l];
+        split_f64(v.x, av.x, av.y);
+        split_f64(v.y, av.z, av.w);
+      }
+      if (ok && tj + col < nb) {
+        const double2 v = B[(size_t)(tj + col) * L + l];
+        split_f64(v.x, bv.x, bv.y);
+        split_f64(v.y, bv.z, bv.w);
+      }
+      sa[r][col] = av;
+      sb[r][col] = bv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < XL; ++r) {
+      float4 ar[O], br[O];
+#pragma unroll
+      for (int a = 0; a < O; ++a) ar[a] = sa[r][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < O; ++b) br[b] = sb[r][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < O; ++a)
+#pragma unroll
+        for (int b = 0; b < O; ++b) {
+          // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
+          df_mac2<false>(re[a][b], ar[a].x, ar[a].y, br[b].x, br[b].y);
+          df_mac2<false>(re[a][b], ar[a].z, ar[a].w, br[b].z, br[b].w);
+          df_mac2<false>(im[a][b], ar[a].x, ar[a].y, br[b].z, br[b].w);
+          df_mac2<true>(im[a][b], ar[a].z, ar[a].w, br[b].x, br[b].y);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < O; ++a)
+#pragma unroll
+      for (int b = 0; b < O; ++b) {
+        df_renorm(re[a][b]);
+        df_renorm(im[a][b]);
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < O; ++a)
+#pragma unroll
+    for (int b = 0; b < O; ++b) {
+      const int i = ti + ty + 16 * a, j = tj + tx + 16 * b;
+      if (i < na && j < nb)
+        partial[((size_t)blockIdx.z * na + i) * nb + j] =
+            make_double2((double)re[a][b].s + (double)re[a][b].c, (double)im[a][b].s + (double)im[a][b].c);
+    }
+}
+
 __global__ void __launch_bounds__(XTHREADS, 4)
     gram_x_kernel(const double2* __restrict__ A1, int na1, const double2* __restrict__ A2, int na,
                   const float2* __restrict__ B, int nb, size_t L, size_t rows_per_cta, double2* __restrict__ partial) {
@@ -140,18 +246,36 @@ __global__ void __launch_bounds__(XTHREADS, 4)
     }
 }
 
-__global__ void gram_x_reduce_kernel(const double2* __restrict__ partial, int nz, int na, int nb,
-                                     double* __restrict__ G) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= na * nb) return;
+// G[idx] = sum over z of partial[z][idx] in FP64: one block per entry.
+__global__ void __launch_bounds__(XTHREADS) gram_x_reduce_kernel(const double2* __restrict__ partial, int nz, int na,
+                                                                int nb, double* __restrict__ G) {
+  __shared__ double red[2][XTHREADS / 32];
+  const int idx = blockIdx.x;
   double re = 0.0, im = 0.0;
-  for (int z = 0; z < nz; ++z) {
+  for (int z = threadIdx.x; z < nz; z += XTHREADS) {
     const double2 p = partial[(size_t)z * na * nb + idx];
     re += p.x;
     im += p.y;
   }
-  G[2 * idx] = re;
-  G[2 * idx + 1] = im;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = re;
+    red[1][threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    re = im = 0.0;
+    for (int w = 0; w < XTHREADS / 32; ++w) {
+      re += red[0][w];
+      im += red[1][w];
+    }
+    G[2 * idx] = re;
+    G[2 * idx + 1] = im;
+  }
 }
 
 struct XScratch {
@@ -165,6 +289,58 @@ XScratch& xscratch() {
 }
 
 }  // namespace
+
+namespace {
+// per-device partial-sum scratch of at least `bytes`
+cudaError_t x_partials(size_t bytes, double2** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  XScratch& sc = xscratch();
+  std::lock_guard<std::mutex> lock(sc.mu);
+  if (bytes > sc.bytes[dev]) {
+    if (sc.partial[dev]) {
+      if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+      cudaFree(sc.partial[dev]);
+    }
+    sc.partial[dev] = nullptr;
+    sc.bytes[dev] = 0;
+    if ((e = cudaMalloc(&sc.partial[dev], bytes)) != cudaSuccess) return e;
+    sc.bytes[dev] = bytes;
+  }
+  *out = static_cast<double2*>(sc.partial[dev]);
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_gram_dd(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s) {
+  if (na < 1 || nb < 1 || !A || !B) return cudaErrorInvalidValue;
+  if (L == 0) return cudaMemsetAsync(G, 0, sizeof(double) * 2 * (size_t)na * nb, s);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int T = (na <= 16 && nb <= 16) ? 16 : 32;
+  const unsigned gx = (na + T - 1) / T, gy = (nb + T - 1) / T;
+  size_t want = (size_t)8 * sms / (gx * gy);   // short double-float chains
+  if (want < 1) want = 1;
+  size_t rows = (L + want - 1) / want;
+  rows = ((rows + XL - 1) / XL) * XL;
+  const unsigned gz = (unsigned)((L + rows - 1) / rows);
+  double2* partial = nullptr;
+  if ((e = x_partials((size_t)gz * na * nb * sizeof(double2), &partial)) != cudaSuccess) return e;
+  const dim3 grid(gx, gy, gz);
+  if (T == 16)
+    gram_dd_kernel<16><<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A), na, static_cast<const double2*>(B), nb,
+                                                 L, rows, partial);
+  else
+    gram_dd_kernel<32><<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A), na, static_cast<const double2*>(B), nb,
+                                                 L, rows, partial);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  gram_x_reduce_kernel<<<(unsigned)(na * nb), XTHREADS, 0, s>>>(partial, (int)gz, na, nb, G);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, const void* B, int nb, size_t L,
                           double* G, cudaStream_t s) {
@@ -204,8 +380,7 @@ cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, cons
   gram_x_kernel<<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A1), na1, static_cast<const double2*>(A2), na,
                                           static_cast<const float2*>(B), nb, L, rows, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int total = na * nb;
-  gram_x_reduce_kernel<<<(total + 127) / 128, 128, 0, s>>>(partial, (int)gz, na, nb, G);
+  gram_x_reduce_kernel<<<(unsigned)(na * nb), XTHREADS, 0, s>>>(partial, (int)gz, na, nb, G);
   return cudaGetLastError();
 }
 

@@ -150,6 +150,8 @@ bool gram_tc_supported(int na, int nb, size_t L);
 // complex64; double-float accumulation on the FP32 pipes.
 cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, const void* B, int nb, size_t L,
                           double* G, cudaStream_t s);
+// G = A^H B with A, B complex128, double-float sums on the FP32 pipes
+cudaError_t launch_gram_dd(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s);
 cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s);
 cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, double beta, void* Y,
                            size_t L, int precision, cudaStream_t s);
