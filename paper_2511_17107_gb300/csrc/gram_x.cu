@@ -184,47 +184,58 @@ __global__ void __launch_bounds__(XTHREADS, 4)
     }
 }
 
+// TA rows of A (16 or 32) x XT columns of B per tile; thread (ty, tx) owns
+// rows ty + 16 a (a < TA / 16) and columns tx, tx + 16.
+template <int TA>
 __global__ void __launch_bounds__(XTHREADS, 4)
     gram_x_kernel(const double2* __restrict__ A1, int na1, const double2* __restrict__ A2, int na,
                   const float2* __restrict__ B, int nb, size_t L, size_t rows_per_cta, double2* __restrict__ partial) {
-  __shared__ float4 sa[XL][XT + 1];   // (re hi, re lo, im hi, im lo)
+  constexpr int OA = TA / 16;
+  __shared__ float4 sa[XL][TA + 1];   // (re hi, re lo, im hi, im lo)
   __shared__ float2 sb[XL][XT + 1];
-  const int ti = blockIdx.x * XT, tj = blockIdx.y * XT;
+  const int ti = blockIdx.x * TA, tj = blockIdx.y * XT;
   const size_t l0 = (size_t)blockIdx.z * rows_per_cta;
   const size_t l1 = (l0 + rows_per_cta < L) ? l0 + rows_per_cta : L;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  DF re[2][2], im[2][2];
+  DF re[OA][2], im[OA][2];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < OA; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) re[a][b] = im[a][b] = DF{0.f, 0.f};
   for (size_t base = l0; base < l1; base += XL) {
 #pragma unroll
-    for (int k = 0; k < XL * XT / XTHREADS; ++k) {
+    for (int k = 0; k < XL * TA / XTHREADS; ++k) {
       const int e = threadIdx.x + k * XTHREADS;
       const int r = e % XL, col = e / XL;
       const size_t l = base + r;
-      const bool ok = l < l1;
       const int row = ti + col;
       float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (ok && row < na) {
+      if (l < l1 && row < na) {
         const double2 v = row < na1 ? A1[(size_t)row * L + l] : A2[(size_t)(row - na1) * L + l];
         split_f64(v.x, av.x, av.y);
         split_f64(v.y, av.z, av.w);
       }
       sa[r][col] = av;
-      sb[r][col] = (ok && tj + col < nb) ? B[(size_t)(tj + col) * L + l] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < XL * XT / XTHREADS; ++k) {
+      const int e = threadIdx.x + k * XTHREADS;
+      const int r = e % XL, col = e / XL;
+      const size_t l = base + r;
+      sb[r][col] = (l < l1 && tj + col < nb) ? B[(size_t)(tj + col) * L + l] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll 4
     for (int r = 0; r < XL; ++r) {
-      const float4 a0 = sa[r][ty], a1 = sa[r][ty + 16];
+      float4 ar[OA];
+#pragma unroll
+      for (int a = 0; a < OA; ++a) ar[a] = sa[r][ty + 16 * a];
       const float2 b0 = sb[r][tx], b1 = sb[r][tx + 16];
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < OA; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          const float4 av = a ? a1 : a0;
+          const float4 av = ar[a];
           const float2 bv = b ? b1 : b0;
           // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
           df_mac<false>(re[a][b], av.x, av.y, bv.x);
@@ -236,7 +247,7 @@ __global__ void __launch_bounds__(XTHREADS, 4)
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < OA; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       const int i = ti + ty + 16 * a, j = tj + tx + 16 * b;
@@ -351,34 +362,23 @@ cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, cons
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  const unsigned gx = (na + XT - 1) / XT, gy = (nb + XT - 1) / XT;
+  const int TA = na <= 16 ? 16 : 32;
+  const unsigned gx = (na + TA - 1) / TA, gy = (nb + XT - 1) / XT;
   // one resident wave: 4 CTAs of 256 threads per SM
   size_t want = (size_t)4 * sms / (gx * gy);
   if (want < 1) want = 1;
   size_t rows = (L + want - 1) / want;
   rows = ((rows + XL - 1) / XL) * XL;
   const unsigned gz = (unsigned)((L + rows - 1) / rows);
-  const size_t pbytes = (size_t)gz * na * nb * sizeof(double2);
-  XScratch& sc = xscratch();
   double2* partial = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(sc.mu);
-    if (pbytes > sc.bytes[dev]) {
-      if (sc.partial[dev]) {
-        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
-        cudaFree(sc.partial[dev]);
-      }
-      sc.partial[dev] = nullptr;
-      sc.bytes[dev] = 0;
-      if ((e = cudaMalloc(&sc.partial[dev], pbytes)) != cudaSuccess) return e;
-      sc.bytes[dev] = pbytes;
-    }
-    partial = static_cast<double2*>(sc.partial[dev]);
-  }
-  dim3 grid(gx, gy, gz);
-  gram_x_kernel<<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A1), na1, static_cast<const double2*>(A2), na,
-                                          static_cast<const float2*>(B), nb, L, rows, partial);
+  if ((e = x_partials((size_t)gz * na * nb * sizeof(double2), &partial)) != cudaSuccess) return e;
+  const dim3 grid(gx, gy, gz);
+  if (TA == 16)
+    gram_x_kernel<16><<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A1), na1, static_cast<const double2*>(A2),
+                                                na, static_cast<const float2*>(B), nb, L, rows, partial);
+  else
+    gram_x_kernel<32><<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A1), na1, static_cast<const double2*>(A2),
+                                                na, static_cast<const float2*>(B), nb, L, rows, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   gram_x_reduce_kernel<<<(unsigned)(na * nb), XTHREADS, 0, s>>>(partial, (int)gz, na, nb, G);
   return cudaGetLastError();

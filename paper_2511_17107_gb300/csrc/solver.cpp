@@ -469,10 +469,9 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     const int w0 = n + np;
     // X32 rounded from the FP64 columns; W32 = K_P^{-1} R (FP32)
     CK(launch_convert(r64.S.p, PCX_FP64, r32.S.p, PCX_FP32, (size_t)n * L, r64.s));
-    for (int a = 0; a < na; ++a) {
-      CK(launch_convert(r64.col(r64.R, act[a]), PCX_FP64, r32.col(r32.R, a), PCX_FP32, L, r64.s));
-      CK(r32.precond_col(r32.col(r32.R, a), r32.col(r32.S, w0 + a)));
-    }
+    // all n residual columns in FP32 (the AX rows below use them too)
+    CK(launch_convert(r64.R.p, PCX_FP64, r32.R.p, PCX_FP32, (size_t)n * L, r64.s));
+    for (int a = 0; a < na; ++a) CK(r32.precond_col(r32.col(r32.R, act[a]), r32.col(r32.S, w0 + a)));
     // [P W] is orthogonalised against X and orthonormalised (Cholesky QR,
     // two passes) in FP32, so the FP32 part of the Gram matrices is close to
     // the identity; P is dropped when [P W] is numerically rank deficient.
@@ -503,20 +502,30 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     CK(r32.apply(r32.col(r32.S, n), r32.col(r32.AS, n), np + na));
     const int m = n + np + na;
     const int mp = m - n;
-    // Rows of X: X^H [P W] and (AX)^H [P W] from FP64 X, AX against the FP32
-    // directions with double-float sums (these couplings are of the size of
-    // the residual, far below the FP32 rounding of the products).  The X-X
-    // blocks are Theta and I: X and AX are the Ritz vectors and images of the
-    // previous Rayleigh-Ritz step (or of rr_x after an exact refresh).  The
-    // P/W-P/W blocks come from FP32 products on the tensor cores.
-    std::vector<cd> gx, gpa, gpb;
+    // Rows of X: X^H [P W] from the FP64 X against the FP32 directions with
+    // double-float sums (these couplings are of the size of the residual, far
+    // below the FP32 rounding of the products), and
+    //   (AX)^H [P W] = Theta X^H [P W] + R^H [P W],  R = AX - X Theta,
+    // the last term an FP32 product of the rounded FP64 residual (its entries
+    // are of the residual's size, so FP32 relative accuracy is enough).  The
+    // X-X blocks are Theta and I: X and AX are the Ritz vectors and images of
+    // the previous Rayleigh-Ritz step (or of rr_x after an exact refresh).
+    // The P/W-P/W blocks come from FP32 products on the tensor cores.
+    std::vector<cd> gx, grw, gpa, gpb;
     {
       r64.tick(&Times::other);
-      CK(launch_gram_x(r64.S.p, n, r64.AS.p, n, r32.col(r32.S, n), mp, L, static_cast<double*>(r64.G.p), r64.s));
-      gx.resize((size_t)2 * n * mp);
-      CK(cudaMemcpyAsync(gx.data(), r64.G.p, sizeof(cd) * gx.size(), cudaMemcpyDeviceToHost, r64.s));
+      CK(launch_gram_x(r64.S.p, n, nullptr, 0, r32.col(r32.S, n), mp, L, static_cast<double*>(r64.G.p), r64.s));
+      std::vector<cd> gxx((size_t)n * mp);
+      CK(cudaMemcpyAsync(gxx.data(), r64.G.p, sizeof(cd) * gxx.size(), cudaMemcpyDeviceToHost, r64.s));
       CK(cudaStreamSynchronize(r64.s));
       r64.tick(&Times::gram);
+      if ((st = r32.gram(r32.R.p, n, r32.col(r32.S, n), mp, grw)) != PCX_OK) return st;
+      gx.resize((size_t)2 * n * mp);
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < mp; ++j) {
+          gx[(size_t)i * mp + j] = gxx[(size_t)i * mp + j];
+          gx[(size_t)(n + i) * mp + j] = theta[i] * gxx[(size_t)i * mp + j] + grw[(size_t)i * mp + j];
+        }
     }
     if ((st = r32.gram(r32.col(r32.S, n), mp, r32.col(r32.AS, n), mp, gpa)) != PCX_OK) return st;
     if ((st = r32.gram(r32.col(r32.S, n), mp, r32.col(r32.S, n), mp, gpb)) != PCX_OK) return st;
