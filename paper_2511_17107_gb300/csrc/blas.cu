@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "cx.cuh"
+#include "dfloat.cuh"
 #include "pcx_internal.h"
 
 namespace pcx {
@@ -89,25 +90,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const cx<T>* __restrict__ A, 
 // must stay inside the FP32 exponent range.  (The complex128 Gram products
 // use the same scheme in gram_x.cu.)
 // ---------------------------------------------------------------------------
-struct DF {
-  float s, c;
-};
-
-__device__ __forceinline__ void df_add_prod(DF& acc, float xh, float xl, float yh, float yl, bool neg) {
-  float p = __fmul_rn(xh, yh);
-  float e = fmaf(xh, yh, -p);            // p + e == xh * yh exactly
-  e = fmaf(xh, yl, e);
-  e = fmaf(xl, yh, e);
-  if (neg) {
-    p = -p;
-    e = -e;
-  }
-  const float s = __fadd_rn(acc.s, p);     // TwoSum(acc.s, p)
-  const float bb = __fsub_rn(s, acc.s);
-  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.s = s;
-  acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
-}
+using dfloat::DF;
 
 // ---------------------------------------------------------------------------
 // Combine: Y_j = sum_i S_i C[i][j] (+ beta Y_j), one row per thread, up to
@@ -165,8 +148,8 @@ __global__ void __launch_bounds__(128) combine_ff_kernel(const double2* __restri
     float4 v = make_float4(0, 0, 0, 0);
     if (j < nyl) {
       const double re = Cm[2 * ((size_t)i * ny + j0 + j)], im = Cm[2 * ((size_t)i * ny + j0 + j) + 1];
-      const float rh = __double2float_rn(re), ih = __double2float_rn(im);
-      v = make_float4(rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih));
+      dfloat::split(re, v.x, v.y);
+      dfloat::split(im, v.z, v.w);
     }
     c[e] = v;
   }
@@ -177,16 +160,17 @@ __global__ void __launch_bounds__(128) combine_ff_kernel(const double2* __restri
     for (int j = 0; j < CY; ++j) re[j] = im[j] = DF{0.f, 0.f};
     for (int i = 0; i < ns; ++i) {
       const double2 sv = S[(size_t)i * L + l];
-      const float sr = __double2float_rn(sv.x), si = __double2float_rn(sv.y);
-      const float srl = __double2float_rn(sv.x - (double)sr), sil = __double2float_rn(sv.y - (double)si);
+      float sr, srl, si, sil;   // integer splits: no FP64 instruction in the loop
+      dfloat::split(sv.x, sr, srl);
+      dfloat::split(sv.y, si, sil);
 #pragma unroll
       for (int j = 0; j < CY; ++j) {
         const float4 cv = c[i * CY + j];
         // s c: re = sr cr - si ci, im = sr ci + si cr
-        df_add_prod(re[j], sr, srl, cv.x, cv.y, false);
-        df_add_prod(re[j], si, sil, cv.z, cv.w, true);
-        df_add_prod(im[j], sr, srl, cv.z, cv.w, false);
-        df_add_prod(im[j], si, sil, cv.x, cv.y, false);
+        dfloat::mac2<false>(re[j], sr, srl, cv.x, cv.y);
+        dfloat::mac2<true>(re[j], si, sil, cv.z, cv.w);
+        dfloat::mac2<false>(im[j], sr, srl, cv.z, cv.w);
+        dfloat::mac2<false>(im[j], si, sil, cv.x, cv.y);
       }
     }
 #pragma unroll

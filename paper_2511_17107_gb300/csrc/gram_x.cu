@@ -24,6 +24,7 @@
 #include <cstdint>
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "pcx_internal.h"
 
 namespace pcx {
@@ -33,78 +34,8 @@ constexpr int XT = 32;        // tile: 32 rows of A x 32 columns of B
 constexpr int XL = 32;        // vector entries staged per step
 constexpr int XTHREADS = 256; // 16 x 16 threads, 2 x 2 outputs each
 
-// v = hi + lo up to 2^-47 |v| for 2^-126 <= |v| < 2^128.
-__device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const unsigned sign = static_cast<unsigned>(b >> 63) << 31;
-  const int ex = static_cast<int>((b >> 52) & 0x7FF);
-  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-  const int fe = ex - 1023 + 127;
-  if (fe <= 0) {   // zero, FP64 subnormal or below the FP32 normal range
-    hi = lo = 0.f;
-    return;
-  }
-  if (fe >= 255) {   // outside the FP32 range, Inf or NaN
-    hi = lo = __uint_as_float(0x7fc00000u);
-    return;
-  }
-  hi = __uint_as_float(sign | (static_cast<unsigned>(fe) << 23) | static_cast<unsigned>(mant >> 29));
-  // remainder: low 29 significand bits, weight 2^(ex - 1075)
-  const unsigned rem = static_cast<unsigned>(mant & 0x1FFFFFFFull);
-  const int le = ex - 1075 + 127;
-  const float scale = le > 0 ? __uint_as_float(static_cast<unsigned>(le) << 23) : 0.f;
-  const float l = __fmul_rn(__uint2float_rn(rem), scale);
-  lo = sign ? -l : l;
-}
-
-struct DF {
-  float s, c;
-};
-
-// acc += (xh + xl) * y  (NEG: acc -= ...), error-free up to the lo*y rounding.
-template <bool NEG>
-__device__ __forceinline__ void df_mac(DF& acc, float xh, float xl, float y) {
-  float p = __fmul_rn(xh, y);
-  float e = fmaf(xh, y, -p);   // p + e == xh * y exactly
-  e = fmaf(xl, y, e);
-  if (NEG) {
-    p = -p;
-    e = -e;
-  }
-  const float s = __fadd_rn(acc.s, p);
-  const float bb = __fsub_rn(s, acc.s);
-  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.s = s;
-  acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
-}
-
-// acc += (xh + xl) * (yh + yl)  (NEG: acc -= ...)
-template <bool NEG>
-__device__ __forceinline__ void df_mac2(DF& acc, float xh, float xl, float yh, float yl) {
-  float p = __fmul_rn(xh, yh);
-  float e = fmaf(xh, yh, -p);   // p + e == xh * yh exactly
-  e = fmaf(xh, yl, e);
-  e = fmaf(xl, yh, e);
-  e = fmaf(xl, yl, e);
-  if (NEG) {
-    p = -p;
-    e = -e;
-  }
-  const float s = __fadd_rn(acc.s, p);
-  const float bb = __fsub_rn(s, acc.s);
-  const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.s = s;
-  acc.c = __fadd_rn(acc.c, __fadd_rn(err, e));
-}
-
-// (s, c) <- (s + c, the rounding error of that sum): keeps the compensation
-// at half an ulp of s, so that its own rounding stays at 2^-48 of s per add
-// (Fast2Sum, valid since |c| <= |s| here or s = 0).
-__device__ __forceinline__ void df_renorm(DF& a) {
-  const float s = __fadd_rn(a.s, a.c);
-  a.c = __fsub_rn(a.c, __fsub_rn(s, a.s));
-  a.s = s;
-}
+using dfloat::DF;
+using dfloat::split;
 
 // G = A^H B with A and B complex128, both split into FP32 hi + lo when
 // staged; tile T x T (T = 16 or 32), 256 threads with (T/16)^2 outputs each.
@@ -134,13 +65,13 @@ __global__ void __launch_bounds__(XTHREADS, 4)
       float4 av = make_float4(0.f, 0.f, 0.f, 0.f), bv = av;
       if (ok && ti + col < na) {
         const double2 v = A[(size_t)(ti + col) * L + l];
-        split_f64(v.x, av.x, av.y);
-        split_f64(v.y, av.z, av.w);
+        split(v.x, av.x, av.y);
+        split(v.y, av.z, av.w);
       }
       if (ok && tj + col < nb) {
         const double2 v = B[(size_t)(tj + col) * L + l];
-        split_f64(v.x, bv.x, bv.y);
-        split_f64(v.y, bv.z, bv.w);
+        split(v.x, bv.x, bv.y);
+        split(v.y, bv.z, bv.w);
       }
       sa[r][col] = av;
       sb[r][col] = bv;
@@ -158,18 +89,18 @@ __global__ void __launch_bounds__(XTHREADS, 4)
 #pragma unroll
         for (int b = 0; b < O; ++b) {
           // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
-          df_mac2<false>(re[a][b], ar[a].x, ar[a].y, br[b].x, br[b].y);
-          df_mac2<false>(re[a][b], ar[a].z, ar[a].w, br[b].z, br[b].w);
-          df_mac2<false>(im[a][b], ar[a].x, ar[a].y, br[b].z, br[b].w);
-          df_mac2<true>(im[a][b], ar[a].z, ar[a].w, br[b].x, br[b].y);
+          dfloat::mac2<false>(re[a][b], ar[a].x, ar[a].y, br[b].x, br[b].y);
+          dfloat::mac2<false>(re[a][b], ar[a].z, ar[a].w, br[b].z, br[b].w);
+          dfloat::mac2<false>(im[a][b], ar[a].x, ar[a].y, br[b].z, br[b].w);
+          dfloat::mac2<true>(im[a][b], ar[a].z, ar[a].w, br[b].x, br[b].y);
         }
     }
 #pragma unroll
     for (int a = 0; a < O; ++a)
 #pragma unroll
       for (int b = 0; b < O; ++b) {
-        df_renorm(re[a][b]);
-        df_renorm(im[a][b]);
+        dfloat::renorm(re[a][b]);
+        dfloat::renorm(im[a][b]);
       }
     __syncthreads();
   }
@@ -212,8 +143,8 @@ __global__ void __launch_bounds__(XTHREADS, 4)
       float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
       if (l < l1 && row < na) {
         const double2 v = row < na1 ? A1[(size_t)row * L + l] : A2[(size_t)(row - na1) * L + l];
-        split_f64(v.x, av.x, av.y);
-        split_f64(v.y, av.z, av.w);
+        split(v.x, av.x, av.y);
+        split(v.y, av.z, av.w);
       }
       sa[r][col] = av;
     }
@@ -238,10 +169,10 @@ __global__ void __launch_bounds__(XTHREADS, 4)
           const float4 av = ar[a];
           const float2 bv = b ? b1 : b0;
           // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
-          df_mac<false>(re[a][b], av.x, av.y, bv.x);
-          df_mac<false>(re[a][b], av.z, av.w, bv.y);
-          df_mac<false>(im[a][b], av.x, av.y, bv.y);
-          df_mac<true>(im[a][b], av.z, av.w, bv.x);
+          dfloat::mac1<false>(re[a][b], av.x, av.y, bv.x);
+          dfloat::mac1<false>(re[a][b], av.z, av.w, bv.y);
+          dfloat::mac1<false>(im[a][b], av.x, av.y, bv.y);
+          dfloat::mac1<true>(im[a][b], av.z, av.w, bv.x);
         }
     }
     __syncthreads();
