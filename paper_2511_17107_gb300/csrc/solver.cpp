@@ -253,11 +253,11 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       stopped_early = true;
       return PCX_OK;
     }
-    // stagnation guard (mixed phase): no progress for 8 iterations
+    // stagnation guard (mixed phase): no 10% progress for 4 iterations
     if (worst < best * 0.9) {
       best = worst;
       since_best = 0;
-    } else if (++since_best >= 8 && stop_tol > tol) {
+    } else if (++since_best >= 4 && stop_tol > tol) {
       stopped_early = true;
       return PCX_OK;
     }
