@@ -207,9 +207,13 @@ def train_learned(pcx, n, n_struct=3, n_pairs=8, steps=120):
         smp = learned.collect(ctx, rng.uniform(-np.pi, np.pi, 3), n_pairs=n_pairs, seed=seed)
         if smp is not None:
             samples.append(smp)
+    import torch
+    P0 = torch.empty(pcx.PCX_CNN_NPARAMS, dtype=torch.float32, device="cuda")
+    pcx.pcx_cnn_init(1, P0)   # the initial correction is zero: T = T0
     P, losses = learned.train(samples, steps=steps, lr=3e-3)
     return P, {"structures": len(samples), "pairs_per_structure": n_pairs, "steps": steps,
-               "loss_first": losses[0], "loss_last": losses[-1], "s": time.perf_counter() - t0}
+               "loss_T0": learned.relative_error(samples, P0), "loss_trained": learned.relative_error(samples, P),
+               "s": time.perf_counter() - t0}
 
 
 def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps=120, only=""):

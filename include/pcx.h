@@ -283,10 +283,14 @@ typedef struct {
 pcx_status pcx_autotune(pcx_ctx* ctx, int precision, int nvec, void* stream, pcx_tune_result* out);
 
 /*
- * pcx_apply_host -- pcx_apply on HOST buffers: copies X to the device, applies,
- * copies Y back, and synchronises `stream` before returning.  Pinned host
- * memory gives full copy bandwidth; pageable memory also works.  Staging
- * buffers are owned by the context and grow on demand.
+ * pcx_apply_host -- pcx_apply on HOST buffers, synchronising `stream` before
+ * returning.  The block moves in chunks (an eighth of it, at most 4 vectors)
+ * through two device staging slots: the host->device copy of one chunk, the
+ * apply of the previous one (on `stream`) and the device->host copy of the
+ * one before run at the same time, the copies on two streams of the
+ * context.  Pinned host memory gives the overlap and full copy bandwidth;
+ * pageable memory also works.  Staging buffers, streams and events are
+ * owned by the context.
  */
 pcx_status pcx_apply_host(pcx_ctx* ctx, const double k[3], double gamma, const void* X_host,
                           void* Y_host, int nvec, int precision, void* stream);
@@ -511,9 +515,10 @@ typedef struct {
   int dump_every;     /* 0: every iteration                                    */
   int precond_kind;   /* 0: K_P^{-1} (eq. matrixfree_finalform, default);
                          1: the curl-sandwich T0 (pcx_sandwich_precond)        */
-  int learned_patience; /* iterations without a drop of the worst residual
-                         before the learned correction falls back (0: 3;
-                         negative: never)                                      */
+  int learned_patience; /* iterations without a 10% drop of the worst
+                         residual below its best before the learned
+                         correction falls back to the base preconditioner
+                         (0: 3; negative: never)                               */
 } pcx_solve_opts;
 
 /*

@@ -93,6 +93,11 @@ pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32
 void pcx_destroy(pcx_ctx* c) {
   if (!c) return;
   pcx::free_apply_graphs(c);
+  for (auto& st : c->copy_stream)
+    if (st) cudaStreamDestroy(st);
+  for (auto& row : c->slot_event)
+    for (auto& ev : row)
+      if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64,  c->dev.tw32, c->dev.m64,  c->dev.m32,
                   c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->cnn_ws, c->ktab};
   for (void* p : ptrs)
@@ -203,23 +208,57 @@ pcx_status pcx_apply_host(pcx_ctx* c, const double k[3], double gamma, const voi
   if (st != PCX_OK || nvec == 0) return st;
   if (!k) return inval(c, "pcx_apply_host: NULL k");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
-  if (bytes > c->stage_bytes) {
+  const size_t vbytes = pcx_vector_length(c) * (precision == PCX_FP64 ? 16 : 8);
+  // chunks of about an eighth of the block, at most 4 vectors, in two slots:
+  // host->device of chunk i + 1, apply of chunk i and device->host of chunk
+  // i - 1 overlap on three streams, so only one chunk's copies are exposed
+  int cv = (nvec + 7) / 8;
+  cv = cv > 4 ? 4 : cv;
+  const size_t slot = (size_t)cv * vbytes;
+  cudaError_t e = cudaSuccess;
+  if (2 * slot > c->stage_bytes) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
     if (c->stage_x) cudaFree(c->stage_x);
     if (c->stage_y) cudaFree(c->stage_y);
     c->stage_x = c->stage_y = nullptr;
     c->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&c->stage_x, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&c->stage_y, bytes);
+    e = cudaMalloc(&c->stage_x, 2 * slot);
+    if (e == cudaSuccess) e = cudaMalloc(&c->stage_y, 2 * slot);
     if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
-    c->stage_bytes = bytes;
+    c->stage_bytes = 2 * slot;
   }
-  cudaError_t e = cudaMemcpyAsync(c->stage_x, Xh, bytes, cudaMemcpyHostToDevice, s);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (!c->copy_stream[i]) e = cudaStreamCreateWithFlags(&c->copy_stream[i], cudaStreamNonBlocking);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+      if (!c->slot_event[i][j]) e = cudaEventCreateWithFlags(&c->slot_event[i][j], cudaEventDisableTiming);
   if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
-  pcx::KParams kp = pcx::make_kparams(c, k, gamma);
-  e = pcx::launch_apply(c, kp, c->stage_x, c->stage_y, nvec, precision, s);
-  if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
-  e = cudaMemcpyAsync(Yh, c->stage_y, bytes, cudaMemcpyDeviceToHost, s);
+  cudaStream_t h2d = c->copy_stream[0], d2h = c->copy_stream[1];
+  cudaEvent_t* loaded = c->slot_event[0];    // chunk in stage_x[slot]
+  cudaEvent_t* applied = c->slot_event[1];   // stage_x[slot] read, stage_y[slot] written
+  cudaEvent_t* stored = c->slot_event[2];    // stage_y[slot] copied out
+  // earlier work of the caller's stream comes first
+  if ((e = cudaEventRecord(applied[0], s)) != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+  if ((e = cudaStreamWaitEvent(h2d, applied[0], 0)) != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+  const pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  const int nch = (nvec + cv - 1) / cv;
+  for (int ch = 0; ch < nch && e == cudaSuccess; ++ch) {
+    const int sl = ch & 1, nv = nvec - ch * cv < cv ? nvec - ch * cv : cv;
+    char* sx = static_cast<char*>(c->stage_x) + sl * slot;
+    char* sy = static_cast<char*>(c->stage_y) + sl * slot;
+    const size_t off = (size_t)ch * cv * vbytes, bytes = (size_t)nv * vbytes;
+    if (ch >= 2) e = cudaStreamWaitEvent(h2d, applied[sl], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sx, static_cast<const char*>(Xh) + off, bytes, cudaMemcpyHostToDevice, h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(loaded[sl], h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, loaded[sl], 0);
+    if (e == cudaSuccess && ch >= 2) e = cudaStreamWaitEvent(s, stored[sl], 0);
+    if (e == cudaSuccess) e = pcx::launch_apply(c, kp, sx, sy, nv, precision, s);
+    if (e == cudaSuccess) e = cudaEventRecord(applied[sl], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, applied[sl], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(static_cast<char*>(Yh) + off, sy, bytes, cudaMemcpyDeviceToHost, d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(stored[sl], d2h);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d2h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply_host", e);
 }

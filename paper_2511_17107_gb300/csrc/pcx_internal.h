@@ -70,10 +70,13 @@ struct pcx_ctx {
   // workspace of the learned-correction kernels (learned.cpp)
   void* cnn_ws = nullptr;
   size_t cnn_ws_bytes = 0;
-  // staging for pcx_apply_host
+  // staging for pcx_apply_host: two slots of X and Y chunks, copy streams
+  // and slot events (created on first use)
   void* stage_x = nullptr;
   void* stage_y = nullptr;
-  size_t stage_bytes = 0;
+  size_t stage_bytes = 0;       // bytes of the two slots together, per buffer
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};   // host->device, device->host
+  cudaEvent_t slot_event[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   std::string err;
 };
 

@@ -65,10 +65,10 @@ struct Times {
 struct Learned {
   const float* params = nullptr;   // device, cnn::NPARAMS floats (null: plain K_P^{-1})
   const float* gates = nullptr;    // device, from cnn_gates
-  bool off = false;                // fallback to K_P^{-1} for the rest of this k
+  bool off = false;                // fallback to the base preconditioner for the rest of this k
   int fallbacks = 0;
   int kind = 0;                    // base preconditioner: 0 K_P^{-1}, 1 curl sandwich T0
-  int patience = 3;                // iterations without a drop before the fallback (< 0: never)
+  int patience = 3;                // iterations without a 10% drop before the fallback (< 0: never)
   // residual dump for training (FP32 phase)
   void* dump = nullptr;
   int dump_cap = 0, dump_every = 1, dumped = 0;
@@ -224,7 +224,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
   std::vector<double> best_hist;
   double best = INFINITY;
   int since_best = 0;
-  double prev_worst = INFINITY;
+  double lrn_best = INFINITY;
   int no_drop = 0;
   res.assign(n, INFINITY);
   for (iters = 0;; ++iters) {
@@ -263,17 +263,17 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
     }
     if (iters >= maxit) return PCX_ENOCONV;
     Learned* lrn = run.learned;
-    // learned correction: back to K_P^{-1} once the residual has not dropped
-    // for 3 iterations
+    // learned correction: back to the base preconditioner once the worst
+    // residual has not dropped 10% below its best for `patience` iterations
     if (lrn && lrn->params && !lrn->off && lrn->patience >= 0) {
-      if (worst < prev_worst) {
+      if (worst < 0.9 * lrn_best) {
+        lrn_best = worst;
         no_drop = 0;
       } else if (++no_drop >= lrn->patience) {
         lrn->off = true;
         ++lrn->fallbacks;
       }
     }
-    prev_worst = worst;
 
     // soft locking: active columns get W (and P) columns
     std::vector<int> act;
@@ -414,7 +414,7 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
   int np = r32.np;          // P32 / AP32 from the FP32 phase stay valid directions
   const int refresh = 20;
   int since_fresh = 0;
-  double prev_worst = INFINITY;
+  double lrn_best = INFINITY;
   int no_drop = 0;
   res.assign(n, INFINITY);
   for (iters = 0;; ++iters) {
@@ -447,14 +447,14 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     }
     if (iters >= maxit) return PCX_ENOCONV;
     if (r32.learned && r32.learned->params && !r32.learned->off && r32.learned->patience >= 0) {
-      if (worst < prev_worst) {
+      if (worst < 0.9 * lrn_best) {
+        lrn_best = worst;
         no_drop = 0;
       } else if (++no_drop >= r32.learned->patience) {
         r32.learned->off = true;
         ++r32.learned->fallbacks;
       }
     }
-    prev_worst = worst;
     if (++since_fresh >= refresh) {   // exact image of X and Rayleigh-Ritz on X; P is kept
       if ((st = fresh_ax()) != PCX_OK) return st;
       if ((st = rr_x()) != PCX_OK) return st;

@@ -82,6 +82,32 @@ def test_apply_at_k_zero_and_host_entry(pcx, dtype):
     assert np.abs(y[:, :, 0, 0, 0]).max() <= TOL[dtype] * np.abs(want).max()
 
 
+@pytest.mark.parametrize("nvec,pinned", [(7, False), (10, True), (17, True)])
+def test_apply_host_pipelined_chunks(pcx, nvec, pinned):
+    """pcx_apply_host moves the block in chunks through two staging slots on
+    three streams; every chunking (1, 2 and 3 vectors, ragged tails, slot
+    reuse) gives the device entry's result bit for bit, from pageable and
+    pinned host memory."""
+    n = 32
+    s = wl.fcc_air_spheres()
+    k = wl.config_k(s.name)[3]
+    x = wl.random_block(nvec, n, seed=40 + nvec).astype(np.complex64)
+    ctx = pcx.setup_structure(s, n)
+    X = torch.from_numpy(x).cuda()
+    Y = torch.empty_like(X)
+    pcx.pcx_apply(ctx, k, X, Y)
+    torch.cuda.synchronize()
+    want = Y.cpu().numpy()
+    xh = torch.from_numpy(x)
+    yh = torch.zeros_like(xh)
+    if pinned:
+        xh, yh = xh.pin_memory(), yh.pin_memory()
+    for _ in range(2):   # the second call reuses the staging slots and events
+        yh.zero_()
+        pcx.pcx_apply_host(ctx, k, xh, yh)
+        assert np.array_equal(yh.numpy(), want)
+
+
 def test_apply_full_size_bench_workload(pcx):
     """The benchmark's workload: 128^3 diamond rods, complex64, checked on a
     full vector against the oracle (2 vectors of the timed launch shape)."""

@@ -196,7 +196,7 @@ def test_learned_gain_on_held_out_structures(pcx, capsys):
     32^3 (residual dump of the mixed solve, PCG targets, 300 Adam steps),
     3 held-out structures solved to 1e-8 (12 bands, mixed precision) with
     K_P^{-1}, with the curl-sandwich T0 and with the learned T (fallback to T0
-    after 3 iterations without a drop).  Every variant must reach the same
+    after 3 iterations without a 10% drop).  Every variant must reach the same
     eigenvalues; T0 and the learned T must need fewer iterations than
     K_P^{-1}.  The iteration counts are printed."""
     from paper_2511_17107_gb300 import learned as lrn
