@@ -311,15 +311,31 @@ pcx_status pcx_precond(pcx_ctx* ctx, const double k[3], double gamma, const void
  * G[i*nb + j] = sum_l conj(A_i[l]) B_j[l], written as na x nb complex128
  * (interleaved doubles) to the DEVICE buffer G.  The Gram products of the
  * Rayleigh-Ritz step (Sec. 4: LOBPCG).  Column i of A starts at
- * A + i * L elements.  precision PCX_FP32: FP32 products on tensor cores
- * (tcgen05 TF32 with hi/lo error compensation; na, nb <= 64 and even L,
- * else CUDA-core FP32) accumulated per chunk and summed in FP64;
- * PCX_FP64: double-float products and sums on the FP32 pipes (error-free
- * product and sum transformations, about 2^-44 relative per term) with the
- * per-block partials summed in FP64.  1 <= na, nb <= 128.
+ * A + i * L elements.  precision PCX_FP32: FP32 products accumulated per
+ * chunk of rows and summed in FP64, on the path pcx_set_gram_path selects:
+ * the tensor cores (tcgen05 TF32 with hi/lo error compensation) or the
+ * FP32 pipes (register-blocked FMAs, double-float sums across chunks), for
+ * na, nb <= 64, even L and 16-byte aligned A, B; a generic CUDA-core
+ * kernel otherwise.  PCX_FP64: double-float products and sums on the FP32
+ * pipes (error-free product and sum transformations, about 2^-44 relative
+ * per term) with the per-block partials summed in FP64.  1 <= na, nb <= 128.
  */
 pcx_status pcx_gram(pcx_ctx* ctx, const void* A, int na, const void* B, int nb, size_t L,
                     int precision, void* G, void* stream);
+
+/*
+ * pcx_set_gram_path -- process-wide choice of the complex64 Gram kernel
+ * (pcx_gram and every Gram product inside pcx_solve): PCX_GRAM_AUTO (the
+ * default choice for the shape), PCX_GRAM_TENSOR (tcgen05 TF32 hi/lo) or
+ * PCX_GRAM_FP32 (FP32 pipes).  Both paths agree to FP32 accuracy; the
+ * choice changes speed only.  Returns PCX_EINVAL for another value.
+ * pcx_get_gram_path returns the current choice.
+ */
+#define PCX_GRAM_AUTO 0
+#define PCX_GRAM_TENSOR 1
+#define PCX_GRAM_FP32 2
+pcx_status pcx_set_gram_path(int path);
+int pcx_get_gram_path(void);
 
 /*
  * pcx_gram_mixed -- G = A^H B with A complex128 (na columns) and B complex64
@@ -519,6 +535,12 @@ typedef struct {
                          residual below its best before the learned
                          correction falls back to the base preconditioner
                          (0: 3; negative: never)                               */
+  double fp32_floor;  /* mixed: the FP32 phase also ends once the worst wanted
+                         residual is <= fp32_floor * 2^-24 * theta_top, with
+                         theta_top the largest Ritz value of the search space
+                         (FP32 rounding of Op x, of size 2^-24 ||Op|| ||x||,
+                         bounds the residual that phase can reach).
+                         0: default 64; negative: off                         */
 } pcx_solve_opts;
 
 /*

@@ -417,6 +417,14 @@ pcx_status pcx_cg_solve(pcx_ctx* c, const double k[3], double gamma, const void*
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_cg_solve", e);
 }
 
+pcx_status pcx_set_gram_path(int path) {
+  if (path != PCX_GRAM_AUTO && path != PCX_GRAM_TENSOR && path != PCX_GRAM_FP32) return PCX_EINVAL;
+  pcx::set_gram_path(path);
+  return PCX_OK;
+}
+
+int pcx_get_gram_path(void) { return pcx::get_gram_path(); }
+
 pcx_status pcx_gram(pcx_ctx* c, const void* A, int na, const void* B, int nb, size_t L, int precision, void* G,
                     void* stream) {
   if (precision != PCX_FP64 && precision != PCX_FP32) return inval(c, "pcx_gram: bad precision");

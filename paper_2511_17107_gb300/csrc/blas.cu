@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "cx.cuh"
@@ -23,6 +24,14 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int GT = 32;
 constexpr int GL = 32;
+// Default complex64 Gram path by shape, from CUDA-event timings of both
+// kernels at L = 3 * 128^3 on GB300 (ms, tensor cores / FP32 pipes):
+// 16x16 0.73 / 0.52, 16x32 1.46 / 0.84, 16x48 1.88 / 1.25, 32x48 2.12 / 2.06,
+// 48x48 2.37 / 3.65; A^H A: 16 0.76 / 0.34, 32 0.91 / 0.86, 48 1.11 / 2.21.
+// The FMA count grows with na nb while the tensor-core kernel's cost is
+// dominated by its per-element hi/lo conversion, so small products go to the
+// FP32 pipes.
+bool gram_fp32_pipes_faster(bool herm, int na, int nb) { return herm ? na <= 32 : na * nb <= 32 * 48; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) gram_kernel(const cx<T>* __restrict__ A, int na, const cx<T>* __restrict__ B,
@@ -315,10 +324,23 @@ unsigned grid_for(size_t work, int threads, unsigned cap = 152u * 32u) {
 
 }  // namespace
 
+namespace {
+std::atomic<int> g_gram_path{0};
+}  // namespace
+
+void set_gram_path(int path) { g_gram_path.store(path); }
+int get_gram_path() { return g_gram_path.load(); }
+
 cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision, double* G,
                         cudaStream_t s) {
   if (precision == PCX_FP64) return launch_gram_dd(A, na, B, nb, L, G, s);   // gram_x.cu
-  if (L > 0 && gram_tc_supported(na, nb, L)) return launch_gram_tc(A, na, B, nb, L, G, s);
+  const int path = g_gram_path.load();
+  const bool cc = L > 0 && gram_cc_supported(A, B, na, nb, L);
+  const bool tc = L > 0 && gram_tc_supported(na, nb, L);
+  if (cc && (path == 2 || (path == 0 && gram_fp32_pipes_faster(A == B && na == nb, na, nb))))
+    return launch_gram_cc(A, na, B, nb, L, G, s);
+  if (tc && path != 2) return launch_gram_tc(A, na, B, nb, L, G, s);
+  if (cc) return launch_gram_cc(A, na, B, nb, L, G, s);
   return launch_gram_cuda_cores(A, na, B, nb, L, precision, G, s);
 }
 

@@ -467,11 +467,12 @@ template <typename T>
 __global__ void precond_kernel(const cx<T>* __restrict__ R, cx<T>* __restrict__ W, const cx<T>* __restrict__ lam,
                                int n, int nvec, KParams kp) {
   const size_t n3 = (size_t)n * n * n;
+  const int lg = __ffs(n) - 1;   // n is a power of two
   const size_t total = n3 * nvec;
   const T cg = (T)(1.0 / kp.gamma - 1.0);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t v = e / n3, mode = e % n3;
-    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    const size_t v = e >> (3 * lg), mode = e & (n3 - 1);
+    const int p1 = (int)(mode & (n - 1)), p2 = (int)((mode >> lg) & (n - 1)), p3 = (int)(mode >> (2 * lg));
     cx<T> kap[3];
     kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
     const size_t base = v * 3 * n3 + mode;
@@ -502,11 +503,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) div_norm_kernel(const cx<T>* __restrict__ X, const cx<T>* __restrict__ lam,
                                                       int n, int nvec, KParams kp, double* __restrict__ out) {
   const size_t n3 = (size_t)n * n * n;
+  const int lg = __ffs(n) - 1;   // n is a power of two
   const int v = blockIdx.y;
   const cx<T>* x = X + (size_t)v * 3 * n3;
   double sb = 0.0, sx = 0.0;
   for (size_t mode = (size_t)blockIdx.x * blockDim.x + threadIdx.x; mode < n3; mode += (size_t)gridDim.x * blockDim.x) {
-    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    const int p1 = (int)(mode & (n - 1)), p2 = (int)((mode >> lg) & (n - 1)), p3 = (int)(mode >> (2 * lg));
     cx<T> kap[3];
     kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
     const cx<T> x0 = x[mode], x1 = x[mode + n3], x2 = x[mode + 2 * n3];
@@ -547,10 +549,11 @@ template <typename T>
 __global__ void curl_h_kernel(const cx<T>* __restrict__ X, cx<T>* __restrict__ U, const cx<T>* __restrict__ lam,
                               int n, int nvec, KParams kp, int pow) {
   const size_t n3 = (size_t)n * n * n;
+  const int lg = __ffs(n) - 1;   // n is a power of two
   const size_t total = n3 * nvec;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t v = e / n3, mode = e % n3;
-    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    const size_t v = e >> (3 * lg), mode = e & (n3 - 1);
+    const int p1 = (int)(mode & (n - 1)), p2 = (int)((mode >> lg) & (n - 1)), p3 = (int)(mode >> (2 * lg));
     cx<T> kap[3];
     kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
     const size_t base = v * 3 * n3 + mode;
@@ -569,11 +572,12 @@ template <typename T>
 __global__ void curl_add_kernel(const cx<T>* __restrict__ Wm, const cx<T>* __restrict__ R, cx<T>* __restrict__ Y,
                                 const cx<T>* __restrict__ lam, int n, int nvec, KParams kp, T s, int accumulate) {
   const size_t n3 = (size_t)n * n * n;
+  const int lg = __ffs(n) - 1;   // n is a power of two
   const size_t total = n3 * nvec;
   const T ig = (T)(1.0 / kp.gamma);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t v = e / n3, mode = e % n3;
-    const int p1 = (int)(mode % n), p2 = (int)((mode / n) % n), p3 = (int)(mode / ((size_t)n * n));
+    const size_t v = e >> (3 * lg), mode = e & (n3 - 1);
+    const int p1 = (int)(mode & (n - 1)), p2 = (int)((mode >> lg) & (n - 1)), p3 = (int)(mode >> (2 * lg));
     cx<T> kap[3];
     kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
     const size_t base = v * 3 * n3 + mode;
@@ -612,9 +616,10 @@ template <typename T>
 __global__ void eps_cells_kernel(const cx<T>* E, const cx<T>* __restrict__ Add, cx<T>* Mo, const uchar4* __restrict__ mid,
                                  const T* __restrict__ mtab, const T* __restrict__ M, int n, int nvec, T s) {
   const size_t n3 = (size_t)n * n * n;
+  const int lg = __ffs(n) - 1;   // n is a power of two
   const size_t total = n3 * nvec;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t v = e / n3, cell = e % n3;
+    const size_t v = e >> (3 * lg), cell = e & (n3 - 1);
     T d1, d2, d3;
     cx<T> o12, o13, o23;
     if (mid) {

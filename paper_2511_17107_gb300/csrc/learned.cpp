@@ -198,8 +198,12 @@ cudaError_t cnn_grad(pcx_ctx* c, const float* params, const void* U, const void*
 }
 
 // vectors per chunk of the sandwich so that its field buffers stay within ~2 GB
+// vectors per chunk of the sandwich: the chunk's intermediate (written by
+// one pass, read by the next) stays within about 96 MB so that it lives in
+// L2 between the passes
 static int sandwich_chunk(const pcx_ctx* c, int nvec, size_t bytes_per_vec) {
-  size_t k = ((size_t)2 << 30) / bytes_per_vec;
+  (void)c;
+  size_t k = ((size_t)96 << 20) / bytes_per_vec;
   if (k < 1) k = 1;
   return (int)(k < (size_t)nvec ? k : (size_t)nvec);
 }

@@ -142,13 +142,19 @@ cudaError_t launch_fft(const pcx_ctx* c, const void* X, void* Y, int nvec, int d
 // out[v] = x_v^H K_B x_v, out[nvec + v] = ||x_v||^2 (device doubles, zeroed here)
 cudaError_t launch_div_norms(const pcx_ctx* c, const KParams& kp, const void* X, int nvec, int precision, double* out,
                              cudaStream_t s);
-// Gram G = A^H B: tensor cores (gram_tc.cu) for complex64 with na, nb <= 64 and even L,
-// CUDA cores (blas.cu) otherwise
+// Gram G = A^H B.  complex128: double-float sums (gram_x.cu).  complex64:
+// the FP32-pipe kernel of gram_cc.cu or the tensor-core kernel of gram_tc.cu
+// as set_gram_path chooses (0: by shape, 1: tensor cores, 2: FP32 pipes),
+// the generic CUDA-core kernel of blas.cu where neither applies
 cudaError_t launch_gram(const void* A, int na, const void* B, int nb, size_t L, int precision,
                         double* G, cudaStream_t s);
 cudaError_t launch_gram_cuda_cores(const void* A, int na, const void* B, int nb, size_t L, int precision,
                                    double* G, cudaStream_t s);
 bool gram_tc_supported(int na, int nb, size_t L);
+bool gram_cc_supported(const void* A, const void* B, int na, int nb, size_t L);
+cudaError_t launch_gram_cc(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s);
+void set_gram_path(int path);
+int get_gram_path();
 // G = [A1 | A2]^H B: A1 (na1 columns) and A2 (na2 columns) complex128, B
 // complex64; double-float accumulation on the FP32 pipes.
 cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, const void* B, int nb, size_t L,

@@ -94,6 +94,8 @@ struct Run {
   KParams kp;
   bool k_zero;
   int verbose;
+  double fp32_floor = 0;   // FP32 phase: stop once worst <= fp32_floor 2^-24 theta_top (0: off)
+  double theta_top = 0;    // largest Ritz value of the last Rayleigh-Ritz step
   int np = 0;        // P columns at S[n : n+np] (valid when lobpcg returns)
   Learned* learned = nullptr;
   // device buffers
@@ -141,15 +143,26 @@ struct Run {
 
   // W = K_P^{-1} R for one column, or the learned T(R) when it is enabled
   // (FP32 storage only) and has not fallen back
-  cudaError_t precond_col(const void* r, void* w) {
+  // W[:, w0 + a] = T R[:, act[a]] for the active columns, one batched call
+  // per run of consecutive active columns
+  cudaError_t precond_active(const std::vector<int>& act, int w0) {
     tick(&Times::other);
-    cudaError_t e;
-    if (learned && learned->params && !learned->off && prec == PCX_FP32)
-      e = cnn_precond(c, kp, learned->params, learned->gates, r, w, 1, s);
-    else if (learned && learned->kind == 1)
-      e = sandwich_precond(c, kp, r, w, 1, prec, s);
-    else
-      e = launch_precond(c, kp, r, w, 1, prec, s);
+    cudaError_t e = cudaSuccess;
+    const int na = (int)act.size();
+    for (int a0 = 0; a0 < na && e == cudaSuccess;) {
+      int a1 = a0 + 1;
+      while (a1 < na && act[a1] == act[a1 - 1] + 1) ++a1;
+      const void* r = col(R, act[a0]);
+      void* w = col(S, w0 + a0);
+      const int cnt = a1 - a0;
+      if (learned && learned->params && !learned->off && prec == PCX_FP32)
+        e = cnn_precond(c, kp, learned->params, learned->gates, r, w, cnt, s);
+      else if (learned && learned->kind == 1)
+        e = sandwich_precond(c, kp, r, w, cnt, prec, s);
+      else
+        e = launch_precond(c, kp, r, w, cnt, prec, s);
+      a0 = a1;
+    }
     tick(&Times::precond);
     return e;
   }
@@ -213,6 +226,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       return PCX_ENUMERIC;
     }
     theta.assign(th.begin(), th.begin() + n);
+    run.theta_top = th[r - 1];
     if ((st = run.upload_c(cm)) != PCX_OK) return st;
     CK(launch_combine(run.S.p, n, static_cast<double*>(run.C.p), n, 0.0, run.S2.p, L, run.prec, run.s));
     CK(launch_combine(run.AS.p, n, static_cast<double*>(run.C.p), n, 0.0, run.AS2.p, L, run.prec, run.s));
@@ -245,11 +259,18 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       if (j < nev) worst = std::max(worst, res[j]);
     }
     if (run.verbose) {
-      std::fprintf(stderr, "[pcx] %s it %d worst %.3e theta0 %.12g\n", run.prec == PCX_FP64 ? "fp64" : "fp32", iters,
-                   worst, theta[0]);
+      std::fprintf(stderr, "[pcx] %s it %d worst %.3e theta0 %.12g theta_top %.4e\n",
+                   run.prec == PCX_FP64 ? "fp64" : "fp32", iters, worst, theta[0], run.theta_top);
     }
     if (worst <= tol) return PCX_OK;
     if (worst <= stop_tol) {
+      stopped_early = true;
+      return PCX_OK;
+    }
+    // FP32 phase: the residual has reached the size of the FP32 rounding of
+    // Op x (2^-24 ||Op|| ||x||, ||Op|| estimated by the largest Ritz value)
+    if (stop_tol > tol && run.prec == PCX_FP32 && run.fp32_floor > 0 &&
+        worst <= run.fp32_floor * 0x1p-24 * run.theta_top) {
       stopped_early = true;
       return PCX_OK;
     }
@@ -286,8 +307,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
         CK(cudaMemcpyAsync(static_cast<char*>(lrn->dump) + (size_t)lrn->dumped * L * 8, run.col(run.R, act[a]), L * 8,
                            cudaMemcpyDeviceToDevice, run.s));
     const int w0 = n + np;   // W at S[w0 : w0+na]
-    for (int a = 0; a < na; ++a)
-      CK(run.precond_col(run.col(run.R, act[a]), run.col(run.S, w0 + a)));
+    CK(run.precond_active(act, w0));
     // W <- W - X (X^H W), then orthonormalise W
     {
       std::vector<cd> xw;
@@ -313,6 +333,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       const double drop = run.prec == PCX_FP64 ? 1e-13 : 1e-7;
       r = gen_eig(m, ga, gb, drop, th, cm);
       run.tick(&Times::rr);
+      if (r > 0) run.theta_top = th[r - 1];
       if (r >= n) break;
       if (np == 0) break;
       // drop P and retry: move W down to S[n : n+na]
@@ -471,7 +492,7 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     CK(launch_convert(r64.S.p, PCX_FP64, r32.S.p, PCX_FP32, (size_t)n * L, r64.s));
     // all n residual columns in FP32 (the AX rows below use them too)
     CK(launch_convert(r64.R.p, PCX_FP64, r32.R.p, PCX_FP32, (size_t)n * L, r64.s));
-    for (int a = 0; a < na; ++a) CK(r32.precond_col(r32.col(r32.R, act[a]), r32.col(r32.S, w0 + a)));
+    CK(r32.precond_active(act, w0));
     // [P W] is orthogonalised against X and orthonormalised (Cholesky QR,
     // two passes) in FP32, so the FP32 part of the Gram matrices is close to
     // the identity; P is dropped when [P W] is numerically rank deficient.
@@ -648,6 +669,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
     r32.kp = r64.kp;
     r32.k_zero = kz;
     r32.verbose = ks.o->verbose;
+    r32.fp32_floor = ks.o->fp32_floor == 0 ? 64.0 : (ks.o->fp32_floor > 0 ? ks.o->fp32_floor : 0.0);
     r32.t0 = r64.t0;
     if (ks.o->stats) r32.tm = ks.t32;
     if ((st = r32.alloc_all()) != PCX_OK) {

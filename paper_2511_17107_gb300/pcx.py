@@ -64,7 +64,7 @@ class pcx_solve_opts(C.Structure):
                 ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats)),
                 ("gamma", C.c_double), ("penalty_tol", C.c_double), ("cnn_params", C.c_void_p),
                 ("dump_R", C.c_void_p), ("dump_cap", C.c_int), ("dump_every", C.c_int), ("precond_kind", C.c_int),
-                ("learned_patience", C.c_int)]
+                ("learned_patience", C.c_int), ("fp32_floor", C.c_double)]
 
 
 _lib = None
@@ -99,6 +99,8 @@ def lib():
             "pcx_apply_host": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_gram": (st, [vp, vp, C.c_int, vp, C.c_int, C.c_size_t, C.c_int, vp, vp]),
+            "pcx_set_gram_path": (st, [C.c_int]),
+            "pcx_get_gram_path": (C.c_int, []),
             "pcx_div_norms": (st, [vp, dp, vp, C.c_int, C.c_int, vp, vp]),
             "pcx_apply_kbatch": (st, [vp, dp, C.c_int, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_set_apply_graphs": (st, [vp, C.c_int]),
@@ -132,7 +134,7 @@ def exported_symbols():
                         "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_autotune",
                         "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
-                        "pcx_cg_solve", "pcx_gram", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
+                        "pcx_cg_solve", "pcx_gram", "pcx_set_gram_path", "pcx_get_gram_path", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
 
 
 def _check(status, ctx=None):
@@ -346,6 +348,18 @@ def pcx_gram(A, B, G, L=None, ctx=None, stream=None):
     return G
 
 
+PCX_GRAM_AUTO, PCX_GRAM_TENSOR, PCX_GRAM_FP32 = 0, 1, 2
+
+
+def pcx_set_gram_path(path):
+    """Process-wide complex64 Gram kernel: PCX_GRAM_AUTO, PCX_GRAM_TENSOR or PCX_GRAM_FP32."""
+    _check(lib().pcx_set_gram_path(int(path)), None)
+
+
+def pcx_get_gram_path():
+    return int(lib().pcx_get_gram_path())
+
+
 def pcx_div_norms(ctx, k, X, out, stream=None):
     """out (float64 CUDA, 2 nvec) = [x_j^H K_B x_j, ||x_j||^2] per column of X."""
     kk = np.ascontiguousarray(np.asarray(k, dtype=np.float64).reshape(3))
@@ -498,7 +512,7 @@ def pcx_rr_eig(ga, gb, drop_tol=1e-13):
 
 def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
               vec_out=None, stream=None, raise_on_noconv=True, stats=None, gamma=0.0, penalty_tol=0.0,
-              cnn_params=None, dump_R=None, dump_every=0, precond_kind=0, learned_patience=0):
+              cnn_params=None, dump_R=None, dump_every=0, precond_kind=0, learned_patience=0, fp32_floor=0.0):
     """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status).  Pass a
     pcx_solve_stats instance as ``stats`` to receive counters and timings."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
@@ -508,7 +522,7 @@ def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_
                        _devptr(cnn_params) if cnn_params is not None else None,
                        _devptr(dump_R) if dump_R is not None else None,
                        int(dump_R.shape[0]) if dump_R is not None else 0, int(dump_every), int(precond_kind),
-                       int(learned_patience))
+                       int(learned_patience), float(fp32_floor))
     eig = np.zeros((nk, nev))
     res = np.zeros((nk, nev))
     its = np.zeros(nk, dtype=np.int32)

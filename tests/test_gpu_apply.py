@@ -227,6 +227,45 @@ def test_gram_tensor_cores_long_blocks(pcx, same, na, nb):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("path", ["tensor", "fp32"])
+@pytest.mark.parametrize("same,na,nb,L", [(False, 16, 16, 3 * 64 ** 3), (True, 48, 48, 3 * 64 ** 3),
+                                          (False, 48, 48, 3 * 32 ** 3 + 2), (False, 13, 29, 1234),
+                                          (True, 29, 29, 3 * 16 ** 3), (False, 64, 7, 66), (True, 1, 1, 2),
+                                          (False, 3, 5, 200002)])
+def test_gram_paths_agree_with_fp64(pcx, path, same, na, nb, L):
+    """Both complex64 Gram kernels (tensor cores, FP32 pipes), selected with
+    pcx_set_gram_path, against FP64 products of the same FP32 data: shapes
+    of the eigensolver's blocks, ragged column counts, row counts that end
+    inside a stage, A^H A (upper triangle mirrored) and a column block that
+    starts inside a larger allocation."""
+    rng = np.random.default_rng(na * 31 + nb + L % 97)
+    a = (rng.standard_normal((na + 2, L)) + 1j * rng.standard_normal((na + 2, L))).astype(np.complex64)
+    b = a[2:] if same else (rng.standard_normal((nb, L)) + 1j * rng.standard_normal((nb, L))).astype(np.complex64)
+    Afull = torch.from_numpy(a).cuda()
+    A = Afull[2:]                       # starts two columns into the allocation
+    B = A if same else torch.from_numpy(b).cuda()
+    G = torch.empty((na, nb), dtype=torch.complex128, device="cuda")
+    pcx.pcx_set_gram_path(pcx.PCX_GRAM_TENSOR if path == "tensor" else pcx.PCX_GRAM_FP32)
+    try:
+        pcx.pcx_gram(A, B, G)
+    finally:
+        pcx.pcx_set_gram_path(pcx.PCX_GRAM_AUTO)
+    a64 = a[2:].astype(np.complex128)
+    want = a64.conj() @ b.astype(np.complex128).T
+    err = np.abs(G.cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= 1e-5, err
+    if same and path == "fp32":   # the lower triangle mirrors the upper one, bit for bit
+        g = G.cpu().numpy()
+        assert np.array_equal(g, g.conj().T)
+
+
+def test_gram_path_setting(pcx):
+    assert pcx.pcx_get_gram_path() == pcx.PCX_GRAM_AUTO
+    with pytest.raises(pcx.PcxError):
+        pcx.pcx_set_gram_path(7)
+    assert pcx.pcx_get_gram_path() == pcx.PCX_GRAM_AUTO
+
+
 @pytest.mark.parametrize("same", [True, False])
 def test_gram_fp64_on_fp32_pipes(pcx, same):
     """complex128 Gram products by split FP32 hi/lo products and double-float
