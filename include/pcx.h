@@ -539,8 +539,9 @@ typedef struct {
                          residual is <= fp32_floor * 2^-24 * theta_top, with
                          theta_top the largest Ritz value of the search space
                          (FP32 rounding of Op x, of size 2^-24 ||Op|| ||x||,
-                         bounds the residual that phase can reach).
-                         0: default 64; negative: off                         */
+                         bounds the residual that phase can reach; at 128^3
+                         the FP32 phase stalls near 1000 * 2^-24 * theta_top).
+                         0: default 1024; negative: off                       */
 } pcx_solve_opts;
 
 /*

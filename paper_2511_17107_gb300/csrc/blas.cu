@@ -141,6 +141,99 @@ __global__ void __launch_bounds__(256) combine_kernel(const cx<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Combine of complex64 columns with even L and 16-byte aligned columns: two
+// rows l per thread (one 16-byte load of S_i per thread and i) and the
+// coefficient pair (c_j, c_j+1) as one 16-byte shared load, so that each
+// shared load feeds 16 FMAs (a shared load per 4 FMAs would saturate the
+// shared-memory pipe before the FMA pipes).  ADD64: Y is complex128 and the
+// FP32 sums are added to it (combine_add32); otherwise Y = sum (+ beta Y).
+// ---------------------------------------------------------------------------
+template <bool ADD64>
+__global__ void __launch_bounds__(256) combine2_kernel(const float4* __restrict__ S, int ns,
+                                                       const double* __restrict__ Cm, int ny, int j0, double beta,
+                                                       void* __restrict__ Yv, size_t L2) {
+  constexpr int CP = CY / 2;
+  extern __shared__ __align__(16) unsigned char csm[];
+  float4* c = reinterpret_cast<float4*>(csm);   // [ns][CP]: (c_j, c_j+1) of column pair jp
+  const int nyl = (ny - j0 < CY) ? ny - j0 : CY;
+  for (int e = threadIdx.x; e < ns * CP; e += blockDim.x) {
+    const int i = e / CP, j = 2 * (e % CP);
+    const double* ci = Cm + 2 * ((size_t)i * ny + j0 + j);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < nyl) {
+      v.x = (float)ci[0];
+      v.y = (float)ci[1];
+    }
+    if (j + 1 < nyl) {
+      v.z = (float)ci[2];
+      v.w = (float)ci[3];
+    }
+    c[e] = v;
+  }
+  __syncthreads();
+  const float fb = (float)beta;
+  for (size_t f = (size_t)blockIdx.x * blockDim.x + threadIdx.x; f < L2; f += (size_t)gridDim.x * blockDim.x) {
+    float2 a0[CY], a1[CY];   // rows 2f and 2f + 1
+#pragma unroll
+    for (int j = 0; j < CY; ++j) a0[j] = a1[j] = make_float2(0.f, 0.f);
+    // the loads of PF columns are issued before their products, so that
+    // every thread keeps several 16-byte loads in flight
+    constexpr int PF = 4;
+    for (int i0 = 0; i0 < ns; i0 += PF) {
+      float4 sv[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u)
+        sv[u] = i0 + u < ns ? S[(size_t)(i0 + u) * L2 + f] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        if (i0 + u >= ns) break;
+        const float4* ci = c + (i0 + u) * CP;
+#pragma unroll
+        for (int jp = 0; jp < CP; ++jp) {
+          const float4 cc = ci[jp];
+          const float4 v = sv[u];
+          // (s.re + i s.im)(c.re + i c.im) for the two rows and c_j, c_j+1
+          a0[2 * jp].x = fmaf(-v.y, cc.y, fmaf(v.x, cc.x, a0[2 * jp].x));
+          a0[2 * jp].y = fmaf(v.y, cc.x, fmaf(v.x, cc.y, a0[2 * jp].y));
+          a1[2 * jp].x = fmaf(-v.w, cc.y, fmaf(v.z, cc.x, a1[2 * jp].x));
+          a1[2 * jp].y = fmaf(v.w, cc.x, fmaf(v.z, cc.y, a1[2 * jp].y));
+          a0[2 * jp + 1].x = fmaf(-v.y, cc.w, fmaf(v.x, cc.z, a0[2 * jp + 1].x));
+          a0[2 * jp + 1].y = fmaf(v.y, cc.z, fmaf(v.x, cc.w, a0[2 * jp + 1].y));
+          a1[2 * jp + 1].x = fmaf(-v.w, cc.w, fmaf(v.z, cc.z, a1[2 * jp + 1].x));
+          a1[2 * jp + 1].y = fmaf(v.w, cc.z, fmaf(v.z, cc.w, a1[2 * jp + 1].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CY; ++j) {
+      if (j < nyl) {
+        if constexpr (ADD64) {
+          double2* yp = static_cast<double2*>(Yv) + (size_t)(j0 + j) * 2 * L2 + 2 * f;
+          double2 y0 = yp[0], y1 = yp[1];
+          y0.x += (double)a0[j].x;
+          y0.y += (double)a0[j].y;
+          y1.x += (double)a1[j].x;
+          y1.y += (double)a1[j].y;
+          yp[0] = y0;
+          yp[1] = y1;
+        } else {
+          float4* yp = static_cast<float4*>(Yv) + (size_t)(j0 + j) * L2 + f;
+          float4 r = make_float4(a0[j].x, a0[j].y, a1[j].x, a1[j].y);
+          if (beta != 0.0) {
+            const float4 o = *yp;
+            r.x = fmaf(fb, o.x, r.x);
+            r.y = fmaf(fb, o.y, r.y);
+            r.z = fmaf(fb, o.z, r.z);
+            r.w = fmaf(fb, o.w, r.w);
+          }
+          *yp = r;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Combine for complex128 on the FP32 pipes with FP64-level accuracy: the
 // same split / TwoProd / TwoSum scheme as gram_ff_kernel.  Each row's inputs
 // are split once and reused for the CY outputs of the sweep; C is split once
@@ -318,6 +411,12 @@ __global__ void convert_kernel(const S* __restrict__ src, D* __restrict__ dst, s
     dst[e] = (D)src[e];
 }
 
+// columns of even length starting on 16-byte boundaries (pairs of complex64
+// entries load as one float4)
+bool pair_ok(const void* S, const void* Y, size_t L) {
+  return L % 2 == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+}
+
 unsigned grid_for(size_t work, int threads, unsigned cap = 152u * 32u) {
   return (unsigned)std::max<size_t>(1, std::min<size_t>((work + threads - 1) / threads, cap));
 }
@@ -378,6 +477,10 @@ cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, doubl
       }
       combine_ff_kernel<<<grid_for(L, 128, 152u * 16u), 128, smem, s>>>(static_cast<const double2*>(S), ns, C, ny,
                                                                          j0, beta, static_cast<double2*>(Y), L);
+    } else if (pair_ok(S, Y, L)) {
+      const size_t smem = (size_t)ns * CY * sizeof(cx<float>);
+      combine2_kernel<false><<<grid_for(L / 2, threads, 152u * 8u), threads, smem, s>>>(
+          static_cast<const float4*>(S), ns, C, ny, j0, beta, Y, L / 2);
     } else {
       const size_t smem = (size_t)ns * CY * sizeof(cx<float>);
       combine_kernel<float><<<blocks, threads, smem, s>>>(static_cast<const cx<float>*>(S), ns, C, ny, j0, beta,
@@ -393,10 +496,15 @@ cudaError_t launch_combine_add32(const void* S32, int ns, const double* C, int n
                                 cudaStream_t s) {
   if (L == 0) return cudaSuccess;
   const unsigned blocks = grid_for(L, 256, 152u * 8u);
+  const bool pairs = pair_ok(S32, Y64, L);
   for (int j0 = 0; j0 < ny; j0 += CY) {
     const size_t smem = (size_t)ns * CY * sizeof(cx<float>);
-    combine_add32_kernel<<<blocks, 256, smem, s>>>(static_cast<const cx<float>*>(S32), ns, C, ny, j0,
-                                                   static_cast<double2*>(Y64), L);
+    if (pairs)
+      combine2_kernel<true><<<grid_for(L / 2, 256, 152u * 8u), 256, smem, s>>>(static_cast<const float4*>(S32), ns,
+                                                                              C, ny, j0, 0.0, Y64, L / 2);
+    else
+      combine_add32_kernel<<<blocks, 256, smem, s>>>(static_cast<const cx<float>*>(S32), ns, C, ny, j0,
+                                                     static_cast<double2*>(Y64), L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

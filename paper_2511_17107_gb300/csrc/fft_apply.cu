@@ -20,7 +20,7 @@ namespace pcx {
 
 template <typename T>
 cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
-                        const KParams* kps, int vec_per_k, cudaStream_t st);
+                        const KParams* kps, int vec_per_k, cudaStream_t st, bool t0);
 template <typename T>
 cudaError_t run_precond_t(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, cudaStream_t s);
 template <typename T>
@@ -36,15 +36,15 @@ template <typename T>
 cudaError_t run_eps_cells_t(const pcx_ctx* c, const void* E, const void* Add, void* Mo, int nvec, double scale_,
                             cudaStream_t s);
 extern template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
-                                               const KParams*, int, cudaStream_t);
+                                               const KParams*, int, cudaStream_t, bool);
 extern template cudaError_t run_apply_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
-                                                const KParams*, int, cudaStream_t);
+                                                const KParams*, int, cudaStream_t, bool);
 
 namespace {
 template <typename T>
 cudaError_t dispatch_apply(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk,
                            void* sbuf, cudaStream_t st, const KParams* kps = nullptr, int vec_per_k = 1) {
-  return run_apply_t<T>(c, kp, X, Y, nvec, chunk, sbuf, kps, vec_per_k, st);
+  return run_apply_t<T>(c, kp, X, Y, nvec, chunk, sbuf, kps, vec_per_k, st, false);
 }
 }  // namespace
 
@@ -157,6 +157,17 @@ void free_apply_graphs(pcx_ctx* c) {
     if (e.exec) cudaGraphExecDestroy(e.exec);
   delete gc;
   c->graphs = nullptr;
+}
+
+cudaError_t launch_t0(pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,
+                      cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  cudaError_t e = ensure_scratch(c, precision, nvec);
+  if (e != cudaSuccess) return e;
+  const int chunk = apply_chunk(c, precision);
+  return precision == PCX_FP64
+             ? run_apply_t<double>(c, kp, R, W, nvec, chunk, c->scratch, nullptr, 1, s, true)
+             : run_apply_t<float>(c, kp, R, W, nvec, chunk, c->scratch, nullptr, 1, s, true);
 }
 
 cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,

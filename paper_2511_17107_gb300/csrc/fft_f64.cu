@@ -3,8 +3,7 @@
 
 namespace pcx {
 template cudaError_t run_apply_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,
-                                        const KParams*, int,
-                                         cudaStream_t);
+                                        const KParams*, int, cudaStream_t, bool);
 template cudaError_t run_precond_t<double>(const pcx_ctx*, const KParams&, const void*, void*, int, cudaStream_t);
 template cudaError_t run_div_norms_t<double>(const pcx_ctx*, const KParams&, const void*, int, double*,
                                             cudaStream_t);

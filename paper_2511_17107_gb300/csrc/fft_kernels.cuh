@@ -35,7 +35,16 @@ namespace fftk {
 
 // OP_PLAIN_INV / OP_PLAIN_FWD: a bare unnormalised 1D DFT along the pass axis
 // (positive / negative exponent), used for F3_3 and F3_3^H of whole vectors.
-enum { OP_PRE = 0, OP_INV = 1, OP_SANDWICH = 2, OP_FWD = 3, OP_POST = 4, OP_PLAIN_INV = 5, OP_PLAIN_FWD = 6 };
+// OP_PRE_T0 / OP_SANDWICH_EPS / OP_POST_T0: the same five-pass chain for the
+// curl-sandwich approximate inverse
+//   T0 r = K_A F3^H eps F3 (K_A^H r / |k|^2) / |k|^2 + K_B r / (gamma |k|^4)
+// (u and the scratch scaled by 1/|k|^2 and 1/(gamma |k|^4), eps = M^{-1}
+// per cell by its adjugate, K_A w scaled by 1/|k|^2; a mode with |k| = 0
+// maps to 0).
+enum {
+  OP_PRE = 0, OP_INV = 1, OP_SANDWICH = 2, OP_FWD = 3, OP_POST = 4, OP_PLAIN_INV = 5, OP_PLAIN_FWD = 6,
+  OP_PRE_T0 = 7, OP_SANDWICH_EPS = 8, OP_POST_T0 = 9
+};
 
 // Radix plans: elements held per thread per stage E (16 complex floats or 8
 // complex doubles), radices R0..R2 with N = R0 R1 R2 and every R <= E.
@@ -307,7 +316,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
   for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = gtw[i];
   KParams kp = a.kp;
   if (AXIS == 0 && a.kps) kp = a.kps[(a.v_base + (int)v) / a.vec_per_k];
-  if constexpr (AXIS == 0 && OP < OP_PLAIN_INV) {
+  if constexpr (AXIS == 0 && OP != OP_PLAIN_INV && OP != OP_PLAIN_FWD) {
     // kappa_i(p) = sum_j b_ji S_j(p_j) + i kq_i L0(p_i),  S_j = L1 + i kt_j L0,
     // split as ka_i(p1) + kb_i(p2, p3)
     const cx<T>* glam = static_cast<const cx<T>*>(a.lam);
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
       }
     }
   }
-  if constexpr (OP == OP_SANDWICH) {
+  if constexpr (OP == OP_SANDWICH || OP == OP_SANDWICH_EPS) {
     if (a.mid) {
       const T* gt = static_cast<const T*>(a.mtab);
       for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) mtab[i] = gt[i];
@@ -348,10 +357,12 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
   } else if constexpr (AXIS == 0) {
     // ---- x-axis passes: staged through shared memory, points fastest ----
     __syncthreads();   // tables visible
-    if constexpr (OP == OP_PRE) {
+    if constexpr (OP == OP_PRE || OP == OP_PRE_T0) {
       // u = -conj(kappa) x x per mode, and gamma kappa.x to the scratch
+      // (T0: u / |k|^2 and kappa.x / (gamma |k|^4))
       cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
       const T gam = (T)kp.gamma;
+      const T igam = (T)(1.0 / kp.gamma);
       // the x tile lands in shared memory by asynchronous copies (all in
       // flight at once), then C^H is applied in place
       for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
@@ -369,11 +380,25 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
         cx<T> kap[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
-        sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), gam);
+        T su = (T)1, ss = gam;
+        if constexpr (OP == OP_PRE_T0) {
+          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+          su = k2 > (T)0 ? (T)1 / k2 : (T)0;
+          ss = su * su * igam;
+        }
+        sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), ss);
         const cx<T> z = mk((T)0, (T)0);
-        s[TL::sidx(0, t, n)] = cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, z), (T)-1));
-        s[TL::sidx(1, t, n)] = cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, z), (T)-1));
-        s[TL::sidx(2, t, n)] = cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, z), (T)-1));
+        cx<T> u0 = cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, z), (T)-1));
+        cx<T> u1 = cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, z), (T)-1));
+        cx<T> u2 = cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, z), (T)-1));
+        if constexpr (OP == OP_PRE_T0) {
+          u0 = scale(u0, su);
+          u1 = scale(u1, su);
+          u2 = scale(u2, su);
+        }
+        s[TL::sidx(0, t, n)] = u0;
+        s[TL::sidx(1, t, n)] = u1;
+        s[TL::sidx(2, t, n)] = u2;
       }
       __syncthreads();
       fft_tile<T, N, 0, +1, 0, 1>(s, tw, nullptr, out, qb);
@@ -397,13 +422,24 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
 #pragma unroll
         for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
         const cx<T> w0 = s[TL::sidx(0, t, n)], w1 = s[TL::sidx(1, t, n)], w2 = s[TL::sidx(2, t, n)];
-        out[g] = cfma_conj(kap[0], sk, cfma(kap[1], w2, scale(kap[2] * w1, (T)-1)));
-        out[N3 + g] = cfma_conj(kap[1], sk, cfma(kap[2], w0, scale(kap[0] * w2, (T)-1)));
-        out[2 * N3 + g] = cfma_conj(kap[2], sk, cfma(kap[0], w1, scale(kap[1] * w0, (T)-1)));
+        cx<T> c0 = cfma(kap[1], w2, scale(kap[2] * w1, (T)-1));
+        cx<T> c1 = cfma(kap[2], w0, scale(kap[0] * w2, (T)-1));
+        cx<T> c2 = cfma(kap[0], w1, scale(kap[1] * w0, (T)-1));
+        if constexpr (OP == OP_POST_T0) {
+          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+          const T su = k2 > (T)0 ? (T)1 / k2 : (T)0;
+          c0 = scale(c0, su);
+          c1 = scale(c1, su);
+          c2 = scale(c2, su);
+        }
+        out[g] = cfma_conj(kap[0], sk, c0);
+        out[N3 + g] = cfma_conj(kap[1], sk, c1);
+        out[2 * N3 + g] = cfma_conj(kap[2], sk, c2);
       }
     }
-  } else if constexpr (OP == OP_SANDWICH) {
-    // ---- z-axis: inverse FFT, per-cell M (Sec. 3.2.1), forward FFT ----
+  } else if constexpr (OP == OP_SANDWICH || OP == OP_SANDWICH_EPS) {
+    // ---- z-axis: inverse FFT, per-cell M (Sec. 3.2.1; or eps = M^{-1}),
+    // forward FFT ----
     __syncthreads();
     const T* M = static_cast<const T*>(a.M);
     const uchar4* mid = static_cast<const uchar4*>(a.mid);
@@ -445,12 +481,29 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
       }
       const int i0 = TL::sidx(0, t, n), i1 = TL::sidx(1, t, n), i2 = TL::sidx(2, t, n);
       const cx<T> e0 = s[i0], e1 = s[i1], e2 = s[i2];
+      T sc = inv_n3;
+      if constexpr (OP == OP_SANDWICH_EPS) {
+        // eps = M^{-1} = adj(M) / det(M): the adjugate of the Hermitian block
+        // (upper triangle) replaces M, the determinant joins the scale
+        const T a11 = d2 * d3 - norm2(o23), a22 = d1 * d3 - norm2(o13), a33 = d1 * d2 - norm2(o12);
+        const cx<T> a12 = o13 * conjg(o23) - scale(o12, d3);
+        const cx<T> a13 = o12 * o23 - scale(o13, d2);
+        const cx<T> a23 = o13 * conjg(o12) - scale(o23, d1);
+        const T det = d1 * a11 + (o12 * conjg(a12)).x + (o13 * conjg(a13)).x;
+        sc = inv_n3 / det;
+        d1 = a11;
+        d2 = a22;
+        d3 = a33;
+        o12 = a12;
+        o13 = a13;
+        o23 = a23;
+      }
       const cx<T> m0 = cfma(o13, e2, cfma(o12, e1, scale(e0, d1)));
       const cx<T> m1 = cfma(o23, e2, cfma_conj(o12, e0, scale(e1, d2)));
       const cx<T> m2 = cfma_conj(o23, e1, cfma_conj(o13, e0, scale(e2, d3)));
-      s[i0] = scale(m0, inv_n3);
-      s[i1] = scale(m1, inv_n3);
-      s[i2] = scale(m2, inv_n3);
+      s[i0] = scale(m0, sc);
+      s[i1] = scale(m1, sc);
+      s[i2] = scale(m2, sc);
     }
     __syncthreads();
     fft_tile<T, N, 2, -1, 0, 1>(s, tw, nullptr, out, qb);
@@ -678,7 +731,7 @@ cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream
 
 template <typename T, int N>
 cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
-                        cudaStream_t st, const KParams* kps, int vec_per_k) {
+                        cudaStream_t st, const KParams* kps, int vec_per_k, bool t0) {
   using C = Cfg<T, N>;
   const bool dbl = sizeof(T) == 8;
   const int n_mat = c->dev.mid ? c->dev.n_mat : 0;
@@ -707,12 +760,18 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
     cudaError_t e;
     a.in = x;
     a.out = y;
-    if ((e = launch_pass<T, N, 0, OP_PRE>(a, tiles, smem, st)) != cudaSuccess) return e;
+    if ((e = t0 ? launch_pass<T, N, 0, OP_PRE_T0>(a, tiles, smem, st) : launch_pass<T, N, 0, OP_PRE>(a, tiles, smem, st))
+        != cudaSuccess)
+      return e;
     a.in = y;
     if ((e = launch_pass<T, N, 1, OP_INV>(a, tiles, smem, st)) != cudaSuccess) return e;
-    if ((e = launch_pass<T, N, 2, OP_SANDWICH>(a, tiles, sandwich_smem, st)) != cudaSuccess) return e;
+    if ((e = t0 ? launch_pass<T, N, 2, OP_SANDWICH_EPS>(a, tiles, sandwich_smem, st)
+                : launch_pass<T, N, 2, OP_SANDWICH>(a, tiles, sandwich_smem, st)) != cudaSuccess)
+      return e;
     if ((e = launch_pass<T, N, 1, OP_FWD>(a, tiles, smem, st)) != cudaSuccess) return e;
-    if ((e = launch_pass<T, N, 0, OP_POST>(a, tiles, post_smem, st)) != cudaSuccess) return e;
+    if ((e = t0 ? launch_pass<T, N, 0, OP_POST_T0>(a, tiles, post_smem, st)
+                : launch_pass<T, N, 0, OP_POST>(a, tiles, post_smem, st)) != cudaSuccess)
+      return e;
   }
   return cudaSuccess;
 }
@@ -721,15 +780,14 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
 
 template <typename T>
 cudaError_t run_apply_t(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
-                        const KParams* kps, int vec_per_k,
-                        cudaStream_t st) {
+                        const KParams* kps, int vec_per_k, cudaStream_t st, bool t0) {
   switch (c->n) {
-    case 8: return fftk::run_apply_n<T, 8>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
-    case 16: return fftk::run_apply_n<T, 16>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
-    case 32: return fftk::run_apply_n<T, 32>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
-    case 64: return fftk::run_apply_n<T, 64>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
-    case 128: return fftk::run_apply_n<T, 128>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
-    case 256: return fftk::run_apply_n<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k);
+    case 8: return fftk::run_apply_n<T, 8>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k, t0);
+    case 16: return fftk::run_apply_n<T, 16>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k, t0);
+    case 32: return fftk::run_apply_n<T, 32>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k, t0);
+    case 64: return fftk::run_apply_n<T, 64>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k, t0);
+    case 128: return fftk::run_apply_n<T, 128>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k, t0);
+    case 256: return fftk::run_apply_n<T, 256>(c, kp, X, Y, nvec, chunk, sbuf, st, kps, vec_per_k, t0);
   }
   return cudaErrorInvalidValue;
 }

@@ -197,41 +197,12 @@ cudaError_t cnn_grad(pcx_ctx* c, const float* params, const void* U, const void*
   return cudaSuccess;
 }
 
-// vectors per chunk of the sandwich so that its field buffers stay within ~2 GB
-// vectors per chunk of the sandwich: the chunk's intermediate (written by
-// one pass, read by the next) stays within about 96 MB so that it lives in
-// L2 between the passes
-static int sandwich_chunk(const pcx_ctx* c, int nvec, size_t bytes_per_vec) {
-  (void)c;
-  size_t k = ((size_t)96 << 20) / bytes_per_vec;
-  if (k < 1) k = 1;
-  return (int)(k < (size_t)nvec ? k : (size_t)nvec);
-}
-
-// T0 R = K_A F3^H eps F3 (K_A^H R / |k|^2) / |k|^2 + K_B R / (gamma |k|^4):
-// curl_h, three inverse FFT passes, eps per cell (with the 1/N^3 of the two
-// unnormalised transforms), three forward passes, curl_add.  W may alias R.
+// T0 R = K_A F3^H eps F3 (K_A^H R / |k|^2) / |k|^2 + K_B R / (gamma |k|^4)
+// on the five fused passes of the apply (fft_kernels.cuh, OP_*_T0).  W may
+// alias R.
 cudaError_t sandwich_precond(pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,
                              cudaStream_t s) {
-  if (nvec == 0) return cudaSuccess;
-  const size_t n3 = (size_t)c->n * c->n * c->n;
-  const size_t es = precision == PCX_FP64 ? 16 : 8;
-  const size_t vb = 3 * n3 * es;
-  const int chunk = sandwich_chunk(c, nvec, vb);
-  char* ws;
-  CKE(ws_get(c, align_up((size_t)chunk * vb), &ws));
-  const double inv_n3 = 1.0 / (double)n3;
-  for (int v0 = 0; v0 < nvec; v0 += chunk) {
-    const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
-    const char* r = static_cast<const char*>(R) + (size_t)v0 * vb;
-    char* w = static_cast<char*>(W) + (size_t)v0 * vb;
-    CKE(launch_curl_h(c, kp, r, ws, nv, 1, precision, s));
-    CKE(launch_fft(c, ws, ws, nv, +1, precision, s));
-    CKE(launch_eps_cells(c, ws, nullptr, ws, nv, inv_n3, precision, s));
-    CKE(launch_fft(c, ws, ws, nv, -1, precision, s));
-    CKE(launch_curl_add(c, kp, ws, r, w, nv, 1.0, 0, precision, s));
-  }
-  return cudaSuccess;
+  return launch_t0(c, kp, R, W, nvec, precision, s);
 }
 
 // T R = T0 R + K_A F3^H g(e) / |k|^2 with e = F3 (K_A^H R / |k|^2): the net's

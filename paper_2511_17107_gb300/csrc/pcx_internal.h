@@ -92,6 +92,9 @@ KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma);
 double gamma_rule(const double k[3]);
 
 // kernels (fft_apply.cu, blas.cu)
+// curl-sandwich approximate inverse T0 (W may be R) on the five-pass chain of
+// the apply, with the context-owned scratch
+cudaError_t launch_t0(pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision, cudaStream_t s);
 // apply with the context-owned scratch (allocated on first use / growth)
 cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
                          cudaStream_t s);

@@ -669,7 +669,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
     r32.kp = r64.kp;
     r32.k_zero = kz;
     r32.verbose = ks.o->verbose;
-    r32.fp32_floor = ks.o->fp32_floor == 0 ? 64.0 : (ks.o->fp32_floor > 0 ? ks.o->fp32_floor : 0.0);
+    r32.fp32_floor = ks.o->fp32_floor == 0 ? 1024.0 : (ks.o->fp32_floor > 0 ? ks.o->fp32_floor : 0.0);
     r32.t0 = r64.t0;
     if (ks.o->stats) r32.tm = ks.t32;
     if ((st = r32.alloc_all()) != PCX_OK) {
