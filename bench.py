@@ -150,6 +150,63 @@ def cpu_baseline_subprocess():
             "sample": f"{done} whole-vector applies of the 128^3 workload in FP64 numpy ({dt:.1f} s)"}
 
 
+def blockops_table(n, reps=5):
+    """CUDA-event timings (median of reps, L2 flushed before each) of the
+    eigensolver's block operations at grid n: the complex64 Gram products on
+    both paths (tensor cores, FP32 pipes) for the shapes LOBPCG uses, and the
+    complex64 combinations.  One JSON line per shape."""
+    import numpy as np
+    import torch
+
+    from paper_2511_17107_gb300 import build as _build
+    from paper_2511_17107_gb300 import pcx
+    _build.build()
+    L = 3 * n ** 3
+    g = torch.Generator(device="cuda").manual_seed(7)
+
+    def block(m):
+        return torch.complex(torch.randn(m, L, device="cuda", generator=g),
+                             torch.randn(m, L, device="cuda", generator=g))
+
+    S, AS = block(48), block(48)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def timeit(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for na, nb, herm in ((16, 16, False), (16, 16, True), (16, 32, False), (32, 32, True), (16, 48, False),
+                         (32, 48, False), (48, 48, True), (48, 48, False)):
+        A = S[:na]
+        B = A if herm else AS[:nb]
+        G = torch.empty((na, nb), dtype=torch.complex128, device="cuda")
+        row = {"op": "gram", "na": na, "nb": nb, "hermitian": herm, "L": L}
+        for path, name in ((pcx.PCX_GRAM_TENSOR, "tensor"), (pcx.PCX_GRAM_FP32, "fp32"), (pcx.PCX_GRAM_AUTO, "auto")):
+            pcx.pcx_set_gram_path(path)
+            ms = timeit(lambda: pcx.pcx_gram(A, B, G))
+            row[name + "_ms"] = round(ms, 4)
+            row[name + "_gbs"] = round((na if herm else na + nb) * L * 8 / ms / 1e6, 1)
+        pcx.pcx_set_gram_path(pcx.PCX_GRAM_AUTO)
+        print(json.dumps(row), flush=True)
+    for ns, ny in ((16, 16), (32, 16), (48, 16), (48, 32)):
+        C = torch.complex(torch.randn(ns, ny, dtype=torch.float64, device="cuda", generator=g),
+                          torch.randn(ns, ny, dtype=torch.float64, device="cuda", generator=g))
+        Y = torch.empty((ny, L), dtype=torch.complex64, device="cuda")
+        ms = timeit(lambda: pcx.pcx_combine(S[:ns], C, Y))
+        print(json.dumps({"op": "combine", "ns": ns, "ny": ny, "L": L, "ms": round(ms, 4),
+                          "gbs": round((ns + ny) * L * 8 / ms / 1e6, 1)}), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -274,9 +331,13 @@ def main():
     ap.add_argument("--solve-legs", default="", help="comma list of solve legs to run (default: all)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--chunk", type=int, default=0, help="vectors per launch chunk (implies --no-tune)")
+    ap.add_argument("--blockops", action="store_true",
+                    help="print timings of the eigensolver's Gram products and combinations instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.blockops:
+        return blockops_table(args.n)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -373,6 +434,7 @@ def main():
     abytes = algorithmic_bytes(n, vecs, es, 4)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
     chunk = pcx.pcx_get_apply_chunk(ctx, prec)
+    traffic = TRAFFIC_BYTES_PER_VECTOR_128_C64 * vecs if (n, es) == (N, 8) and chunk == TRAFFIC_CHUNK else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -385,8 +447,10 @@ def main():
                    "parallelism": f"replicas x{world}", "autotune": tune},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (TRAFFIC_BYTES_PER_VECTOR_128_C64 * vecs
-                                 if (n, es) == (N, 8) and chunk == TRAFFIC_CHUNK else None),
+                     "traffic": traffic,
+                     # DRAM bytes the pass chain moves (ncu) over the same launch time
+                     "traffic_gbs": traffic / (per_launch_ms / 1e3) / 1e9 if traffic else None,
+                     "traffic_frac": traffic / (per_launch_ms / 1e3) / 1e9 / peak if traffic else None,
                      "kernel": "pcx_apply pass chain (5 pass kernels per chunk of vectors)",
                      "peak_kind": peak_kind + " (burst HBM copy)",
                      "algorithmic_bytes_per_launch": abytes},
