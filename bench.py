@@ -207,6 +207,67 @@ def blockops_table(n, reps=5):
     return 0
 
 
+def apply_sizes_table(n, reps=5):
+    """CUDA-event timings of pcx_apply (one Bloch vector, the diamond-rod
+    workload) at n vectors per call for n in {1, 16, 48}, complex64 and
+    complex128, each after pcx_autotune for that shape, with the L2 flushed
+    before each call.  complex128 also
+    reports its FP64 rate against a measured FP64 GEMM peak (torch float64
+    matmul, best of 3), since the FP64 pipes bound it.  One JSON line each."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_2511_17107_gb300 import build as _build
+    from paper_2511_17107_gb300 import pcx
+    _build.build()
+    s = wl.diamond_rods()
+    k = wl.config_k(s.name)[K_INDEX]
+    ctx = pcx.setup_structure(s, n)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    fp64_tflops = 2 * 4096 ** 3 / (best / 1e3) / 1e12
+    del a
+    # FFT flop convention 5 N log2 N per complex transform of N points:
+    # 6 transforms of N^3 points per vector, plus about 200 flops per cell
+    flops = 6 * 5 * n ** 3 * np.log2(n ** 3) + 200 * n ** 3
+    for dt, es in ((torch.complex64, 8), (torch.complex128, 16)):
+        for nv in (1, 16, 48):
+            x = torch.complex(torch.randn(nv, 3, n, n, n, device="cuda", dtype=torch.float64),
+                              torch.randn(nv, 3, n, n, n, device="cuda", dtype=torch.float64)).to(dt)
+            y = torch.empty_like(x)
+            tune = pcx.pcx_autotune(ctx, pcx.PCX_FP32 if es == 8 else pcx.PCX_FP64, nv)
+            pcx.pcx_apply(ctx, k, x, y)
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                pcx.pcx_apply(ctx, k, x, y)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = float(np.median(ts))
+            row = {"op": "apply", "N": n, "dtype": "c64" if es == 8 else "c128", "vectors": nv,
+                   "us_per_vector": round(1e3 * ms / nv, 2), "applies_per_s": round(nv / (ms / 1e3), 1),
+                   "algorithmic_gbs": round(2 * nv * 3 * n ** 3 * es / (ms / 1e3) / 1e9, 1),
+                   "chunk": tune["chunk"] if isinstance(tune, dict) else None}
+            if es == 16:
+                row["fp64_tflops"] = round(nv * flops / (ms / 1e3) / 1e12, 3)
+                row["fp64_gemm_peak_tflops"] = round(fp64_tflops, 3)
+            print(json.dumps(row), flush=True)
+            del x, y
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -333,11 +394,15 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="vectors per launch chunk (implies --no-tune)")
     ap.add_argument("--blockops", action="store_true",
                     help="print timings of the eigensolver's Gram products and combinations instead")
+    ap.add_argument("--sizes", action="store_true",
+                    help="print pcx_apply timings at 1, 16 and 48 vectors per call, complex64 and complex128, instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.blockops:
         return blockops_table(args.n)
+    if args.sizes:
+        return apply_sizes_table(args.n)
     if args.impl == "reference":
         return run_reference(args)
 
