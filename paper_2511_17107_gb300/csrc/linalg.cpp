@@ -176,7 +176,7 @@ void upper_inverse(int n, const std::vector<cd>& r, std::vector<cd>& ri) {
 }
 
 int gen_eig(int m, const std::vector<cd>& ga, const std::vector<cd>& gb, double drop_tol, std::vector<double>& theta,
-            std::vector<cd>& c) {
+            std::vector<cd>& c, double* lam_min_rel) {
   // D = diag(gb)^{-1/2};  eig(D gb D) = V diag(lam) V^H;  keep lam > drop_tol * max
   std::vector<double> dsc(m);
   for (int i = 0; i < m; ++i) {
@@ -206,6 +206,7 @@ int gen_eig(int m, const std::vector<cd>& ga, const std::vector<cd>& gb, double 
       for (const cd& x : ri) fro2 += std::norm(x);
       if (std::isfinite(fro2) && 1.0 / fro2 > 1e3 * drop_tol * m) {
         r = m;
+        if (lam_min_rel) *lam_min_rel = 1.0 / (fro2 * m);
         t.assign((size_t)m * m, cd(0, 0));
         for (int i = 0; i < m; ++i)
           for (int j = i; j < m; ++j) t[(size_t)i * m + j] = dsc[i] * ri[(size_t)i * m + j];
@@ -222,6 +223,7 @@ int gen_eig(int m, const std::vector<cd>& ga, const std::vector<cd>& gb, double 
     for (int j = 0; j < m; ++j)
       if (lam[j] > drop_tol * lmax) keep.push_back(j);
     r = (int)keep.size();
+    if (lam_min_rel) *lam_min_rel = r > 0 ? lam[keep[0]] / lmax : 0.0;
     t.assign((size_t)m * r, cd(0, 0));
     for (int i = 0; i < m; ++i)
       for (int jj = 0; jj < r; ++jj)

@@ -22,8 +22,11 @@ void upper_inverse(int n, const std::vector<cd>& r, std::vector<cd>& ri);
 // Generalised Hermitian eigenproblem ga c = theta gb c on the span that gb
 // resolves: directions whose scaled gb eigenvalue is <= drop_tol * max are
 // dropped.  Returns the rank r kept (or -1 on breakdown); theta[r]
-// ascending, c is m x r row-major with gb-orthonormal columns.
+// ascending, c is m x r row-major with gb-orthonormal columns.  lam_min_rel
+// (optional) receives the smallest kept eigenvalue of the unit-diagonal
+// scaled gb over the largest (a lower bound of it on the Cholesky path): the
+// rounding errors of ga reach theta amplified by about its inverse.
 int gen_eig(int m, const std::vector<cd>& ga, const std::vector<cd>& gb, double drop_tol, std::vector<double>& theta,
-            std::vector<cd>& c);
+            std::vector<cd>& c, double* lam_min_rel = nullptr);
 
 }  // namespace pcx

@@ -331,10 +331,17 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       if ((st = run.gram(run.S.p, m, run.AS.p, m, ga)) != PCX_OK) return st;
       if ((st = run.gram(run.S.p, m, run.S.p, m, gb)) != PCX_OK) return st;
       const double drop = run.prec == PCX_FP64 ? 1e-13 : 1e-7;
-      r = gen_eig(m, ga, gb, drop, th, cm);
+      double lam_min_rel = 1.0;
+      r = gen_eig(m, ga, gb, drop, th, cm, &lam_min_rel);
       run.tick(&Times::rr);
       if (r > 0) run.theta_top = th[r - 1];
-      if (r >= n) break;
+      // FP64: P is not orthonormalised, and over hundreds of iterations it
+      // can drift towards span[X W]; the rounding of S^H (AS) then reaches
+      // the Ritz values amplified by 1 / lam_min_rel (10th-order stencils at
+      // 32^3 turned them to noise).  Such a step drops P, a restart of the
+      // search direction, and keeps the basis well conditioned.
+      const bool ill = run.prec == PCX_FP64 && lam_min_rel < 1e-9;
+      if (r >= n && !(ill && np > 0)) break;
       if (np == 0) break;
       // drop P and retry: move W down to S[n : n+na]
       CK(cudaMemcpyAsync(run.col(run.S, n), run.col(run.S, w0), (size_t)na * L * es, cudaMemcpyDeviceToDevice, run.s));

@@ -47,6 +47,8 @@ CASES = [
     ("sc32-f32", wl.sc_gyro_sphere, 32, np.complex64, 3, 1, "summed"),
     ("fcc32-f32", wl.fcc_air_spheres, 32, np.complex64, 2, 1, "summed"),
     ("woodpile16-m3-f64", wl.woodpile, 16, np.complex128, 2, 3, "summed"),
+    ("sc16-m5-f64", wl.sc_gyro_sphere, 16, np.complex128, 1, 5, "summed"),
+    ("fcc16-m4-f32", wl.fcc_air_spheres, 16, np.complex64, 1, 4, "summed"),
     ("fcc16-literal-f64", wl.fcc_air_spheres, 16, np.complex128, 1, 1, "literal"),
     ("random64-f32", lambda: wl.random_inclusions(3), 64, np.complex64, 1, 2, "summed"),
 ]
