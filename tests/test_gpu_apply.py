@@ -261,13 +261,6 @@ def test_gram_paths_agree_with_fp64(pcx, path, same, na, nb, L):
         assert np.array_equal(g, g.conj().T)
 
 
-def test_gram_path_setting(pcx):
-    assert pcx.pcx_get_gram_path() == pcx.PCX_GRAM_AUTO
-    with pytest.raises(pcx.PcxError):
-        pcx.pcx_set_gram_path(7)
-    assert pcx.pcx_get_gram_path() == pcx.PCX_GRAM_AUTO
-
-
 @pytest.mark.parametrize("same", [True, False])
 def test_gram_fp64_on_fp32_pipes(pcx, same):
     """complex128 Gram products by split FP32 hi/lo products and double-float

@@ -122,3 +122,17 @@ def test_cnn_parameter_count_matches_oracle_layout():
     assert binding.PCX_CNN_NPARAMS == learned.param_count(binding.PCX_CNN_HIDDEN)
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "pcx.h")).read()
     assert re.search(r"#define PCX_CNN_HIDDEN 8\b", hdr)
+
+
+def test_gram_path_setting_is_validated(pcx):
+    """pcx_set_gram_path takes the three documented values and rejects
+    others without changing the current choice (host-side state only)."""
+    assert pcx.pcx_get_gram_path() == pcx.PCX_GRAM_AUTO
+    for path in (pcx.PCX_GRAM_TENSOR, pcx.PCX_GRAM_FP32, pcx.PCX_GRAM_AUTO):
+        pcx.pcx_set_gram_path(path)
+        assert pcx.pcx_get_gram_path() == path
+    for bad in (-1, 3, 7):
+        with pytest.raises(pcx.PcxError):
+            pcx.pcx_set_gram_path(bad)
+    assert pcx.pcx_get_gram_path() == pcx.PCX_GRAM_AUTO
+
