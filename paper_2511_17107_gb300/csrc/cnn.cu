@@ -62,42 +62,67 @@ template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(CT) conv_fwd_kernel(View in, View out, const float* __restrict__ w,
                                                       const float* __restrict__ bias, View gate, View pre, int n,
                                                       float out_scale) {
+  // Each thread produces two neighbouring voxels along x for every output
+  // channel.  The weights sit in shared memory as [ci][tap][co] (co padded
+  // to a multiple of 4), so one 16-byte broadcast load feeds 8 FMAs, and
+  // the four input values of a halo row serve the three x taps of both
+  // voxels.
+  constexpr int CP = (COUT + 3) / 4 * 4;
+  static_assert(TV == 2 * CT, "two voxels per thread");
   __shared__ float sx[CIN][HV];
-  __shared__ float sw[COUT * CIN * 27];
+  __shared__ __align__(16) float sw[CIN * 27 * CP];
   const int b = blockIdx.y;
   int z0, y0, x0;
   tile_origin(blockIdx.x, n, z0, y0, x0);
-  for (int i = threadIdx.x; i < COUT * CIN * 27; i += CT) sw[i] = w[i];
+  for (int i = threadIdx.x; i < CIN * 27 * CP; i += CT) {
+    const int co = i % CP, t = (i / CP) % 27, ci = i / (CP * 27);
+    sw[i] = co < COUT ? w[(co * CIN + ci) * 27 + t] : 0.f;
+  }
   load_halo<CIN>(sx, in, b, n, z0, y0, x0);
   __syncthreads();
+  const int lz = threadIdx.x / (TS * TS / 2), ly = (threadIdx.x / (TS / 2)) % TS, lx = 2 * (threadIdx.x % (TS / 2));
+  float a0[CP], a1[CP];
+#pragma unroll
+  for (int co = 0; co < CP; ++co) a0[co] = a1[co] = 0.f;
 #pragma unroll 1
-  for (int rep = 0; rep < TV / CT; ++rep) {
-    const int lv = threadIdx.x + rep * CT;
-    const int lz = lv / (TS * TS), ly = (lv / TS) % TS, lx = lv % TS;
-    float acc[COUT];
+  for (int ci = 0; ci < CIN; ++ci) {
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
-#pragma unroll 1
-    for (int ci = 0; ci < CIN; ++ci) {
+    for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-      for (int t = 0; t < 27; ++t) {
-        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-        const float xv = sx[ci][((lz + dz) * HS + (ly + dy)) * HS + (lx + dx)];
+      for (int dy = 0; dy < 3; ++dy) {
+        const float* row = &sx[ci][((lz + dz) * HS + (ly + dy)) * HS + lx];
+        const float xr[4] = {row[0], row[1], row[2], row[3]};
 #pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(sw[(co * CIN + ci) * 27 + t], xv, acc[co]);
+        for (int dx = 0; dx < 3; ++dx) {
+          const float4* wt = reinterpret_cast<const float4*>(&sw[(ci * 27 + dz * 9 + dy * 3 + dx) * CP]);
+#pragma unroll
+          for (int q = 0; q < CP / 4; ++q) {
+            const float4 w4 = wt[q];
+            a0[4 * q] = fmaf(w4.x, xr[dx], a0[4 * q]);
+            a0[4 * q + 1] = fmaf(w4.y, xr[dx], a0[4 * q + 1]);
+            a0[4 * q + 2] = fmaf(w4.z, xr[dx], a0[4 * q + 2]);
+            a0[4 * q + 3] = fmaf(w4.w, xr[dx], a0[4 * q + 3]);
+            a1[4 * q] = fmaf(w4.x, xr[dx + 1], a1[4 * q]);
+            a1[4 * q + 1] = fmaf(w4.y, xr[dx + 1], a1[4 * q + 1]);
+            a1[4 * q + 2] = fmaf(w4.z, xr[dx + 1], a1[4 * q + 2]);
+            a1[4 * q + 3] = fmaf(w4.w, xr[dx + 1], a1[4 * q + 3]);
+          }
+        }
       }
-    }
-    const long long gv = ((long long)(z0 + lz) * n + (y0 + ly)) * n + (x0 + lx);
+  }
+  const long long gv = ((long long)(z0 + lz) * n + (y0 + ly)) * n + (x0 + lx);
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
 #pragma unroll
     for (int co = 0; co < COUT; ++co) {
-      float r = acc[co];
+      float r = v == 0 ? a0[co] : a1[co];
       if constexpr (MODE == MODE_SIGMOID) {
         r = 1.f / (1.f + expf(-(r + bias[co])));
       } else if constexpr (MODE == MODE_GATE) {
-        if (pre.p) pre.p[voff(pre, b, co, gv)] = r;
-        r *= gate.p[voff(gate, b, co, gv)];
+        if (pre.p) pre.p[voff(pre, b, co, gv + v)] = r;
+        r *= gate.p[voff(gate, b, co, gv + v)];
       }
-      out.p[voff(out, b, co, gv)] = r * out_scale;
+      out.p[voff(out, b, co, gv + v)] = r * out_scale;
     }
   }
 }
