@@ -406,8 +406,10 @@ pcx_status pcx_div_norms(pcx_ctx* ctx, const double k[3], const void* X, int nve
  *   T0 r = K_A F3_3^H eps F3_3 (K_A^H r / |k|^2) / |k|^2 + K_B r / (gamma |k|^4)
  * with eps = M^{-1} cell by cell and |k|^2 = sum_i |kappa_i|^2 per mode (a
  * mode with |k| = 0 maps to 0).  Exact inverse for a homogeneous isotropic
- * medium (K_A K_A^H + K_B = |k|^2 I); K_P^{-1} is T0 with eps = I.  Costs
- * about two applies.  Device buffers as in pcx_apply; W may alias R.
+ * medium (K_A K_A^H + K_B = |k|^2 I); K_P^{-1} is T0 with eps = I.  Runs
+ * on the five fused passes of the apply (eps = adj(M) / det(M) in the
+ * middle pass), so it costs one apply.  Device buffers as in pcx_apply;
+ * W may alias R.
  */
 pcx_status pcx_sandwich_precond(pcx_ctx* ctx, const double k[3], double gamma, const void* R, void* W, int nvec,
                                 int precision, void* stream);
