@@ -302,6 +302,21 @@ def run_reference(args):
     return 0
 
 
+def whole_job_rate(ms_local, units_per_rank, steps, world, device=None):
+    """Max-over-ranks step time and the whole-job rate.  Every rank processes
+    units_per_rank units per step (weak scaling); with world > 1 the local
+    times are reduced with MAX over the initialised process group, so every
+    rank returns the same pair."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank * steps / (ms / 1e3)
+
+
 def k_list(kpath, nk):
     return [kpath[(K_INDEX + i) % len(kpath)] for i in range(nk)]
 
@@ -471,13 +486,8 @@ def main():
     if dist:
         td.barrier()
     ck = clocks.stop()
-    ms = start.elapsed_time(end)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = whole_job_rate(start.elapsed_time(end), vecs, args.steps, world, "cuda")
     per_launch_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps
-    value = world * vecs * args.steps / (ms / 1e3)
 
     # end-to-end: host buffers through pcx_apply_host (copies inside the timed region)
     e2e = None
