@@ -17,6 +17,8 @@ yee           real-space Yee operators A, A^H, B, B^H and the compensated
               operator A M A^H + gamma B^H B (Sec. 2.1-2.3)
 permittivity  staggered sampling of a structure and the per-cell discrete
               inverse permittivity M_Trivial (Sec. 2.1, Sec. 3.1-3.2.1)
+crossdof      M_CrossDoF, the symmetrised cross-DoF transfer form of the
+              discrete inverse permittivity (Sec. 3.2.2)
 fourier       DFT matrix, circulant symbols, Fourier-basis operator and the
               FFT-diagonal preconditioner (Lemma 2.1, Prop. 2.8, Sec. 2.4)
 penalty       the penalty-coefficient rules (Prop. 2.5, Remark 2.6)

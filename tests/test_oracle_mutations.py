@@ -101,3 +101,19 @@ def test_dft_with_wrong_sign(monkeypatch):
     orig = fourier.dft_matrix
     monkeypatch.setattr(fourier, "dft_matrix", lambda n: np.conj(orig(n)))
     _fails(st_pins.test_fft_route_equals_dft_matrix, 4)
+
+
+def test_cross_dof_transfer_mistakes(monkeypatch):
+    """M_CrossDoF: a transfer that pairs the wrong neighbours (D0 and D0^T
+    swapped) fails the geometry pin, and a (j, i) block built with T_ij in
+    place of its transpose fails the Hermiticity pin."""
+    import test_oracle_crossdof as cd_pins
+    from oracle import crossdof
+
+    with monkeypatch.context() as mp:
+        mp.setattr(crossdof, "_T_AXES", {k: (v[1], v[0]) for k, v in crossdof._T_AXES.items()})
+        _fails(cd_pins.test_transfer_averages_the_four_nearest_dofs, 0, 1)
+
+    with monkeypatch.context() as mp:
+        mp.setattr(crossdof, "transfer_t", crossdof.transfer)   # the transpose forgotten
+        _fails(cd_pins.test_hermitian_on_an_anisotropic_structure)
