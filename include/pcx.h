@@ -93,7 +93,25 @@ typedef struct {
                             d1, d2, d3, re o12, im o12, re o13, im o13, re o23,
                             im o23 (M_k = [[d1,o12,o13],[.,d2,o23],[.,.,d3]],
                             Hermitian)                                           */
+  int m_kind;            /* PCX_M_TRIVIAL (0, default) or PCX_M_CROSSDOF, below  */
 } pcx_setup_desc;
+
+/* m_kind: the discrete inverse permittivity M of the apply (Sec. 3.2).
+ * PCX_M_TRIVIAL: eq. trivial_trivial, one 3x3 block per cell (diagonal from
+ *   the E1, E2, E3 points, off-diagonals from the volume centre).
+ * PCX_M_CROSSDOF: eq. crossdof_herm, the off-diagonal couplings carried
+ *   between the staggered E points by symmetrised four-point means,
+ *   block (i, j) = (diag(e_ij at E_i) T_ij + T_ij diag(e_ij at E_j)) / 2
+ *   with e_ij = (eps^{-1})_ij of the material at each point and T_ij of eq.
+ *   crossdof_Tmat read from the componentwise template eq.
+ *   crossdof_xytemplate (T_12: mean over x in {i-1, i}, y in {j-1/2,
+ *   j+1/2}; T_13, T_23 alike).  It needs a structure sampled from shapes
+ *   (not cell_blocks, at most 255 materials); the HPD check stays the
+ *   per-cell one of M_Trivial.  The apply then runs seven passes: the
+ *   z-axis sandwich is split into an inverse z transform, a real-space
+ *   stencil pass and a forward z transform.  pcx_sandwich_precond keeps
+ *   the per-cell M_Trivial inverse (an approximate inverse either way). */
+enum { PCX_M_TRIVIAL = 0, PCX_M_CROSSDOF = 1 };
 
 /*
  * pcx_setup -- build a context: sample the structure and assemble M.

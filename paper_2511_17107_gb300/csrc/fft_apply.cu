@@ -56,10 +56,13 @@ int apply_chunk(const pcx_ctx* c, int precision) {
   return (int)(k < 1 ? 1 : (k > 64 ? 64 : k));
 }
 
+// gamma kappa.x per vector of a chunk, and for M_CrossDoF the real-space
+// field of the stencil pass (3 N^3) after it
 size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec) {
   const int chunk = apply_chunk(c, precision);
   const int nv = nvec < chunk ? nvec : chunk;
-  return (size_t)nv * c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  const size_t per = (size_t)c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  return (size_t)nv * per * (c->m_kind == PCX_M_CROSSDOF ? 4 : 1);
 }
 
 cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
@@ -93,7 +96,8 @@ static cudaError_t noalloc_scratch(void** out) {
 cudaError_t launch_apply_noalloc(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
                                  cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;
-  const size_t per_vec = (size_t)c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  const size_t per_vec =
+      (size_t)c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8) * (c->m_kind == PCX_M_CROSSDOF ? 4 : 1);
   if (per_vec > (size_t)PCX_NOALLOC_SCRATCH_BYTES) return cudaErrorInvalidValue;
   void* scratch = nullptr;
   cudaError_t e = noalloc_scratch(&scratch);

@@ -718,6 +718,92 @@ __global__ void eps_cells_kernel(const cx<T>* E, const cx<T>* __restrict__ Add, 
   }
 }
 
+// Mo = s M_CrossDoF E on real-space fields (Sec. 3.2.2, eq. crossdof_herm;
+// Mo must not alias E).  Diagonal entries as in M_Trivial; off the diagonal
+// the symmetrised transfers
+//   block (i, j) = ( diag(e_ij at E_i) T_ij + T_ij diag(e_ij at E_j) ) / 2,
+//   block (j, i) = its conjugate transpose,
+// with e_ij = (eps_1)_ij of the material at each point (from the material
+// ids of the E1, E2, E3 point sets) and the four-point means of the
+// componentwise template eq. crossdof_xytemplate, in array slots [z][y][x]:
+//   T_01 f = (f + f[x-1] + f[y+1] + f[y+1, x-1]) / 4     (D0 on x, D0^T on y)
+//   T_02 f = (f + f[x-1] + f[z+1] + f[z+1, x-1]) / 4     (D0 on x, D0^T on z)
+//   T_12 f = (f + f[y-1] + f[z+1] + f[z+1, y-1]) / 4     (D0 on y, D0^T on z)
+// and their transposes with every offset negated.  One thread per cell and
+// vector; neighbours wrap periodically (N is a power of two).
+template <typename T>
+__global__ void crossdof_kernel(const cx<T>* __restrict__ E, cx<T>* __restrict__ Mo, const uchar4* __restrict__ mid,
+                                const T* __restrict__ mtab, int n, int nvec, T s) {
+  const size_t n3 = (size_t)n * n * n;
+  const int lg = __ffs(n) - 1;   // n is a power of two
+  const int msk = n - 1;
+  const size_t total = n3 * nvec;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = e >> (3 * lg);
+    const int cell = (int)(e & (n3 - 1));
+    const int x = cell & msk, y = (cell >> lg) & msk, z = cell >> (2 * lg);
+    const cx<T>* ev = E + v * 3 * n3;
+    auto at = [&](int dz, int dy, int dx) -> int {
+      return (((z + dz) & msk) << (2 * lg)) | (((y + dy) & msk) << lg) | ((x + dx) & msk);
+    };
+    // (eps_1)_ij of the material at point set c of cell q; pair 0: 12, 1: 13, 2: 23
+    auto off = [&](int q, int c, int pair) -> cx<T> {
+      const uchar4 id = mid[q];
+      const int m = c == 0 ? id.x : (c == 1 ? id.y : id.z);
+      return mk(mtab[9 * m + 3 + 2 * pair], mtab[9 * m + 4 + 2 * pair]);
+    };
+    // T_ij (a f) at this cell, with f = component jc and a = e_pair at point set jc
+    // (or 1); the four offsets (d0 along one axis, d0^T along another)
+    auto tmean = [&](int jc, int pair, bool weighted, const int (*o)[3]) -> cx<T> {
+      cx<T> r = mk((T)0, (T)0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int q = at(o[k][0], o[k][1], o[k][2]);
+        cx<T> f = ev[(size_t)jc * n3 + q];
+        if (weighted) f = off(q, jc, pair) * f;
+        r = r + f;
+      }
+      return scale(r, (T)0.25);
+    };
+    auto tmean_c = [&](int jc, int pair, int wc, const int (*o)[3]) -> cx<T> {   // T^T (conj(a) f), a at set wc
+      cx<T> r = mk((T)0, (T)0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int q = at(o[k][0], o[k][1], o[k][2]);
+        r = r + conjg(off(q, wc, pair)) * ev[(size_t)jc * n3 + q];
+      }
+      return scale(r, (T)0.25);
+    };
+    // offsets (dz, dy, dx)
+    const int t01[4][3] = {{0, 0, 0}, {0, 0, -1}, {0, 1, 0}, {0, 1, -1}};
+    const int t01t[4][3] = {{0, 0, 0}, {0, 0, 1}, {0, -1, 0}, {0, -1, 1}};
+    const int t02[4][3] = {{0, 0, 0}, {0, 0, -1}, {1, 0, 0}, {1, 0, -1}};
+    const int t02t[4][3] = {{0, 0, 0}, {0, 0, 1}, {-1, 0, 0}, {-1, 0, 1}};
+    const int t12[4][3] = {{0, 0, 0}, {0, -1, 0}, {1, 0, 0}, {1, -1, 0}};
+    const int t12t[4][3] = {{0, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {-1, 1, 0}};
+    const uchar4 id = mid[cell];
+    const T d1 = mtab[9 * id.x], d2 = mtab[9 * id.y + 1], d3 = mtab[9 * id.z + 2];
+    const cx<T> e0 = ev[cell], e1 = ev[n3 + cell], e2 = ev[2 * n3 + cell];
+    const T h = (T)0.5;
+    // component 0 (E1 points): blocks (0, 1) and (0, 2)
+    cx<T> m0 = scale(e0, d1);
+    m0 = m0 + scale(off(cell, 0, 0) * tmean(1, 0, false, t01) + tmean(1, 0, true, t01), h);
+    m0 = m0 + scale(off(cell, 0, 1) * tmean(2, 1, false, t02) + tmean(2, 1, true, t02), h);
+    // component 1 (E2 points): block (1, 0) = (0, 1)^H and block (1, 2)
+    cx<T> m1 = scale(e1, d2);
+    m1 = m1 + scale(tmean_c(0, 0, 0, t01t) + conjg(off(cell, 1, 0)) * tmean(0, 0, false, t01t), h);
+    m1 = m1 + scale(off(cell, 1, 2) * tmean(2, 2, false, t12) + tmean(2, 2, true, t12), h);
+    // component 2 (E3 points): blocks (2, 0) = (0, 2)^H and (2, 1) = (1, 2)^H
+    cx<T> m2 = scale(e2, d3);
+    m2 = m2 + scale(tmean_c(0, 1, 0, t02t) + conjg(off(cell, 2, 1)) * tmean(0, 1, false, t02t), h);
+    m2 = m2 + scale(tmean_c(1, 2, 1, t12t) + conjg(off(cell, 2, 2)) * tmean(1, 2, false, t12t), h);
+    cx<T>* mo = Mo + v * 3 * n3;
+    mo[cell] = scale(m0, s);
+    mo[n3 + cell] = scale(m1, s);
+    mo[2 * n3 + cell] = scale(m2, s);
+  }
+}
+
 template <typename T, int N, int AXIS, int OP>
 cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st) {
   auto kern = pass_kernel<T, N, AXIS, OP>;
@@ -751,6 +837,12 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
   a.vec_per_k = vec_per_k > 0 ? vec_per_k : 1;
   a.sbuf = sbuf;
   const size_t vlen = (size_t)3 * N * N * N;
+  // M_CrossDoF: the z sandwich becomes an inverse z transform, the
+  // real-space stencil pass into the scratch after the kappa.x part, and a
+  // forward z transform
+  const bool crossdof = c->m_kind == PCX_M_CROSSDOF && !t0;
+  const int cap = nvec < chunk ? nvec : chunk;   // vectors the scratch holds
+  cx<T>* tmp = static_cast<cx<T>*>(sbuf) + (size_t)cap * N * N * N;
   for (int v0 = 0; v0 < nvec; v0 += chunk) {
     const int nv = nvec - v0 < chunk ? nvec - v0 : chunk;
     a.v_base = v0;
@@ -758,6 +850,27 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
     const cx<T>* x = static_cast<const cx<T>*>(X) + (size_t)v0 * vlen;
     cx<T>* y = static_cast<cx<T>*>(Y) + (size_t)v0 * vlen;
     cudaError_t e;
+    if (crossdof) {
+      a.in = x;
+      a.out = y;
+      if ((e = launch_pass<T, N, 0, OP_PRE>(a, tiles, smem, st)) != cudaSuccess) return e;
+      a.in = y;
+      if ((e = launch_pass<T, N, 1, OP_INV>(a, tiles, smem, st)) != cudaSuccess) return e;
+      if ((e = launch_pass<T, N, 2, OP_PLAIN_INV>(a, tiles, C::SMEM, st)) != cudaSuccess) return e;
+      const size_t total = (size_t)nv * N * N * N;
+      size_t blocks = (total + 255) / 256;
+      if (blocks > 152u * 16u) blocks = 152u * 16u;
+      crossdof_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(y, tmp, static_cast<const uchar4*>(c->dev.mid),
+                                                           static_cast<const T*>(a.mtab), N, nv,
+                                                           (T)(1.0 / ((double)N * N * N)));
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      a.in = tmp;
+      if ((e = launch_pass<T, N, 2, OP_PLAIN_FWD>(a, tiles, C::SMEM, st)) != cudaSuccess) return e;
+      a.in = y;
+      if ((e = launch_pass<T, N, 1, OP_FWD>(a, tiles, smem, st)) != cudaSuccess) return e;
+      if ((e = launch_pass<T, N, 0, OP_POST>(a, tiles, post_smem, st)) != cudaSuccess) return e;
+      continue;
+    }
     a.in = x;
     a.out = y;
     if ((e = t0 ? launch_pass<T, N, 0, OP_PRE_T0>(a, tiles, smem, st) : launch_pass<T, N, 0, OP_PRE>(a, tiles, smem, st))

@@ -49,6 +49,7 @@ struct pcx_ctx {
   int n = 0;
   int m = 1;
   int reading = PCX_CT_SUMMED;
+  int m_kind = PCX_M_TRIVIAL;   // discrete inverse permittivity of the apply
   int device = 0;
   double A[9] = {0};
   double b[9] = {0};

@@ -347,6 +347,14 @@ pcx_status validate_desc(const pcx_setup_desc* d, std::string& err) {
     err = "pcx_setup: unknown ct_reading";
     return PCX_EINVAL;
   }
+  if (d->m_kind != PCX_M_TRIVIAL && d->m_kind != PCX_M_CROSSDOF) {
+    err = "pcx_setup: unknown m_kind";
+    return PCX_EINVAL;
+  }
+  if (d->m_kind == PCX_M_CROSSDOF && (d->cell_blocks || d->n_mat > 255)) {
+    err = "pcx_setup: M_CrossDoF needs a structure sampled from shapes with at most 255 materials";
+    return PCX_EINVAL;
+  }
   double inv[9];
   if (!invert3(d->lattice, inv)) {
     err = "pcx_setup: singular lattice matrix";
@@ -362,6 +370,7 @@ pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c) {
   c->n = n;
   c->m = d->stencil_m;
   c->reading = d->ct_reading;
+  c->m_kind = d->m_kind;
   std::memcpy(c->A, d->lattice, sizeof(c->A));
   invert3(c->A, c->b);
   const size_t n3 = (size_t)n * n * n;

@@ -37,7 +37,8 @@ class pcx_shape(C.Structure):
 class pcx_setup_desc(C.Structure):
     _fields_ = [("n", C.c_int), ("stencil_m", C.c_int), ("ct_reading", C.c_int), ("lattice", C.c_double * 9),
                 ("n_mat", C.c_int), ("eps", C.POINTER(C.c_double)), ("background", C.c_int),
-                ("n_shape", C.c_int), ("shapes", C.POINTER(pcx_shape)), ("cell_blocks", C.POINTER(C.c_double))]
+                ("n_shape", C.c_int), ("shapes", C.POINTER(pcx_shape)), ("cell_blocks", C.POINTER(C.c_double)),
+                ("m_kind", C.c_int)]
 
 
 class pcx_solve_stats(C.Structure):
@@ -198,9 +199,13 @@ class Context:
             pass
 
 
-def _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks):
+PCX_M_TRIVIAL, PCX_M_CROSSDOF = 0, 1
+
+
+def _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks, m_kind=PCX_M_TRIVIAL):
     d = pcx_setup_desc()
     d.n = n
+    d.m_kind = m_kind
     d.stencil_m = stencil_m
     d.ct_reading = ct_reading
     lat = np.eye(3) if lattice is None else np.asarray(lattice, dtype=np.float64)
@@ -231,11 +236,11 @@ def _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_block
 
 
 def pcx_setup(n, lattice=None, eps=None, background=0, shapes=(), stencil_m=1, ct_reading=PCX_CT_SUMMED,
-              cell_blocks=None):
+              cell_blocks=None, m_kind=PCX_M_TRIVIAL):
     """Create a context.  ``eps``: (n_mat, 3, 3) complex permittivities;
     ``shapes``: objects with .kind, .material, .params; ``cell_blocks``:
     optional (N^3, 9) float64 packed blocks overriding the structure."""
-    d, keep = _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks)
+    d, keep = _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks, m_kind)
     h = C.c_void_p()
     st = lib().pcx_setup(C.byref(d), C.byref(h))
     if st != PCX_OK:
@@ -246,16 +251,16 @@ def pcx_setup(n, lattice=None, eps=None, background=0, shapes=(), stencil_m=1, c
     return Context(h, n)
 
 
-def setup_structure(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED):
+def setup_structure(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED, m_kind=PCX_M_TRIVIAL):
     """pcx_setup from a ``workloads.Structure``."""
     return pcx_setup(n, structure.lattice, structure.eps, structure.background, structure.shapes,
-                     stencil_m=stencil_m, ct_reading=ct_reading)
+                     stencil_m=stencil_m, ct_reading=ct_reading, m_kind=m_kind)
 
 
-def pcx_sample_host(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED):
+def pcx_sample_host(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED, m_kind=PCX_M_TRIVIAL, cell_blocks=None):
     """Host sampling (no GPU): (blocks (N^3, 9), ids (4, N^3) int32, first_bad)."""
     d, keep = _desc(n, structure.lattice, structure.eps, structure.background, structure.shapes, stencil_m,
-                    ct_reading, None)
+                    ct_reading, cell_blocks, m_kind)
     n3 = n ** 3
     blocks = np.zeros((n3, 9))
     ids = np.zeros((4, n3), dtype=np.int32)

@@ -110,6 +110,38 @@ def test_apply_host_pipelined_chunks(pcx, nvec, pinned):
         assert np.array_equal(yh.numpy(), want)
 
 
+@pytest.mark.parametrize("name,maker,n,dtype,nvec,chunk", [
+    ("sc16-f64", wl.sc_gyro_sphere, 16, np.complex128, 3, 0),
+    ("sc16-f64-chunk1", wl.sc_gyro_sphere, 16, np.complex128, 3, 1),
+    ("fcc16-f64", wl.fcc_air_spheres, 16, np.complex128, 2, 0),
+    ("sc32-f32", wl.sc_gyro_sphere, 32, np.complex64, 2, 0),
+], ids=lambda v: v if isinstance(v, str) else None)
+def test_apply_crossdof_matches_oracle(pcx, name, maker, n, dtype, nvec, chunk):
+    """M_CrossDoF (Sec. 3.2.2): the seven-pass apply (z sandwich split into
+    transforms around the real-space cross-DoF stencil) against the oracle's
+    operator on the oracle's M_CrossDoF; chunked launches and the k-batched
+    entry give the same bits as one launch per k."""
+    from oracle import crossdof, penalty
+    s = maker()
+    k = wl.config_k(s.name)[min(3, len(wl.config_k(s.name)) - 1)]
+    x = wl.random_block(nvec, n, seed=31).astype(dtype)
+    ops = yee.YeeOperators(n, s.lattice, k)
+    want = fourier.apply_definition(x.astype(np.complex128), ops, crossdof.CrossDofM(s, n).apply,
+                                    penalty.gamma_practical(k))
+    ctx = pcx.setup_structure(s, n, m_kind=pcx.PCX_M_CROSSDOF)
+    if chunk:
+        pcx.pcx_set_apply_chunk(ctx, chunk)
+    X = torch.from_numpy(x).cuda()
+    Y = torch.empty_like(X)
+    pcx.pcx_apply(ctx, k, X, Y)
+    torch.cuda.synchronize()
+    _close(Y.cpu().numpy(), want, dtype)
+    Yb = torch.empty((2,) + tuple(X.shape), dtype=X.dtype, device="cuda")
+    pcx.pcx_apply_kbatch(ctx, np.stack([k, k]), torch.stack([X, X]), Yb)
+    torch.cuda.synchronize()
+    assert torch.equal(Yb[0], Y) and torch.equal(Yb[1], Y)
+
+
 def test_apply_full_size_bench_workload(pcx):
     """The benchmark's workload: 128^3 diamond rods, complex64, checked on a
     full vector against the oracle (2 vectors of the timed launch shape)."""

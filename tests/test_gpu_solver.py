@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import eig, fourier, penalty, permittivity, yee
+from oracle import crossdof, eig, fourier, penalty, permittivity, yee
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -20,11 +20,11 @@ def pcx():
     return binding
 
 
-def _dense_lowest(structure, n, k, nev):
+def _dense_lowest(structure, n, k, nev, apply_m=None):
     blocks = permittivity.cell_blocks(structure, n)
     ops = yee.YeeOperators(n, structure.lattice, k)
     g = penalty.gamma_practical(k)
-    am = lambda e: permittivity.apply_m(blocks, e)
+    am = apply_m or (lambda e: permittivity.apply_m(blocks, e))
     mat = eig.dense_matrix(lambda c: ops.compensated(c.reshape(-1, 3, n, n, n), am, g).reshape(c.shape[0], -1),
                            3 * n ** 3)
     ev = np.linalg.eigvalsh(0.5 * (mat + mat.conj().T))
@@ -42,6 +42,23 @@ def test_solve_matches_dense_8(pcx, prec, rtol, kvec):
     ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-10, block=nev + 4, precision=prec)
     assert st == pcx.PCX_OK and np.all(res <= 1e-10)
     np.testing.assert_allclose(ev[0], want, rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [(0, 1e-10), (1, 1e-6)])
+def test_solve_crossdof_matches_dense_8(pcx, prec, rtol):
+    """M_CrossDoF (Sec. 3.2.2, eq. crossdof_herm): the GPU solve against the
+    dense spectrum of the oracle's compensated operator built on the
+    oracle's M_CrossDoF (gyrotropic sphere, off-diagonal couplings)."""
+    n, nev = 8, 6
+    s = wl.sc_gyro_sphere()
+    k = np.array([0.6, 1.3, -0.5])
+    want = _dense_lowest(s, n, k, nev, crossdof.CrossDofM(s, n).apply)
+    ctx = pcx.setup_structure(s, n, m_kind=pcx.PCX_M_CROSSDOF)
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-10, block=nev + 4, precision=prec)
+    assert st == pcx.PCX_OK and np.all(res <= 1e-10)
+    np.testing.assert_allclose(ev[0], want, rtol=rtol)
+    # and M_CrossDoF moves them away from M_Trivial's
+    assert np.abs(ev[0] - _dense_lowest(s, n, k, nev)).max() > 1e-6
 
 
 @pytest.mark.parametrize("lat,n", [("SC", 32), ("FCC", 16)])

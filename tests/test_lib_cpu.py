@@ -136,3 +136,18 @@ def test_gram_path_setting_is_validated(pcx):
             pcx.pcx_set_gram_path(bad)
     assert pcx.pcx_get_gram_path() == pcx.PCX_GRAM_AUTO
 
+
+
+def test_crossdof_setup_validation(pcx):
+    """m_kind takes PCX_M_TRIVIAL or PCX_M_CROSSDOF; M_CrossDoF needs the
+    material ids of a structure, so caller-supplied cell blocks are refused
+    (host-side validation, before any device work)."""
+    s = wl.sc_gyro_sphere()
+    blocks, ids, bad = pcx.pcx_sample_host(s, 8, m_kind=pcx.PCX_M_CROSSDOF)
+    assert bad == -1 and blocks.shape == (8 ** 3, 9)
+    with pytest.raises(pcx.PcxError) as ei:
+        pcx.pcx_sample_host(s, 8, m_kind=7)
+    assert ei.value.status == pcx.PCX_EINVAL
+    with pytest.raises(pcx.PcxError) as ei:
+        pcx.pcx_sample_host(s, 8, m_kind=pcx.PCX_M_CROSSDOF, cell_blocks=blocks)
+    assert ei.value.status == pcx.PCX_EINVAL
