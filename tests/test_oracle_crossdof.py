@@ -98,3 +98,20 @@ def test_homogeneous_spectrum_is_the_union_of_mode_blocks():
                 want.extend(np.linalg.eigvalsh(b))
     got = np.linalg.eigvalsh(m)
     assert np.abs(np.sort(got) - np.sort(want)).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_hpd_under_the_papers_assumptions():
+    """Sec. 3.3: M_CrossDoF is HPD when the eigenvalues of eps_1 lie in
+    (0, 1] and eps_1 is strictly diagonally dominant or has a zero
+    off-diagonal.  The paper's anisotropic eps_1 (eq. display:exp_permittivity,
+    beta = 0.875, eps_lattice = 16) satisfies all three; a gyroid of it on
+    the BCC lattice gives a dense M_CrossDoF with a positive spectrum."""
+    eps = wl.paper_anisotropic(16.0)
+    e1 = np.linalg.inv(eps)
+    lam = np.linalg.eigvalsh(e1)
+    assert lam.min() > 0 and lam.max() <= 1
+    assert np.all(np.diag(e1).real > np.sum(np.abs(e1), axis=1) - np.abs(np.diag(e1)))
+    s = wl.Structure("g", wl.BCC.copy(), np.stack([wl.VACUUM, eps]), 0, [wl.Shape(wl.SHAPE_GYROID, 1, (1.1, 0))])
+    m = crossdof.CrossDofM(s, 6).dense()
+    ev = np.linalg.eigvalsh(0.5 * (m + m.conj().T))
+    assert ev.min() > 0
