@@ -52,13 +52,17 @@ def _inside(shape_kind, params, p):
     Distances are evaluated left to right (see _dot3) so that a point on a
     boundary is classified the same way on every machine."""
     images = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], dtype=np.float64)
+    # After d -= round(d) every |d_i| <= 1/2, so an image other than (0,0,0)
+    # has a coordinate of size >= 1/2 and lies at distance >= 1/2 from the
+    # shape's centre: a shape whose reach is below 1/2 needs only image 0.
+    centre_only = images[13:14]
     if shape_kind == SHAPE_SPHERE:
         c = np.array(params[:3])
         r = params[3]
         d = p - c
         d = d - np.round(d)
         hit = np.zeros(p.shape[:-1], dtype=bool)
-        for im in images:
+        for im in (centre_only if r < 0.5 else images):
             q = d + im
             hit |= _dot3(q, q) < r * r
         return hit
@@ -73,7 +77,8 @@ def _inside(shape_kind, params, p):
         d = p - mid
         d = d - np.round(d)
         hit = np.zeros(p.shape[:-1], dtype=bool)
-        for im in images:
+        # a hit needs |q|^2 = t^2 + |perp|^2 < (length/2)^2 + r^2
+        for im in (centre_only if 0.5 * length + r < 0.5 else images):
             q = d + im
             t = _dot3(q, u)
             perp = q - t[..., None] * u
