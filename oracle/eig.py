@@ -92,6 +92,14 @@ def lobpcg(apply, precond, x0, nev, tol=1e-10, maxit=1000, deflate=False, histor
                 a_s = np.concatenate([ax, aw], axis=1)
             ga = s.conj().T @ a_s
             gb = s.conj().T @ s
+            if use_p and p is not None:
+                # P nearly inside span[X W]: the Rayleigh-Ritz step would
+                # amplify the rounding of ga by 1 / lambda_min of the scaled
+                # gb; restart without P instead
+                d = 1 / np.sqrt(np.diag(gb).real)
+                lam = np.linalg.eigvalsh(0.5 * (gb + gb.conj().T) * d[:, None] * d[None, :])
+                if lam[0] < 1e-12 * lam[-1]:
+                    continue
             try:
                 th, c = scipy.linalg.eigh(0.5 * (ga + ga.conj().T), 0.5 * (gb + gb.conj().T))
                 break
