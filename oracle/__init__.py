@@ -29,6 +29,8 @@ learned       the gated 3D convolution correction of K_P^{-1} (no counterpart
               the corrected preconditioner T(r) and its training pairs
 
 Every function that has no independent pin says "parity unpinned" in its
-docstring; at present every function is pinned by a test in
-``tests/test_oracle_*.py``.
+docstring.  At present every function, and every shape branch of the
+staggered sampling (sphere, rod, box, gyroid), is pinned by a test in
+``tests/test_oracle_*.py`` that a planted slip fails
+(``tests/test_oracle_mutations.py``).
 """

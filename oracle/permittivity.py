@@ -49,8 +49,16 @@ def _dot3(a, b):
 
 def _inside(shape_kind, params, p):
     """Membership of Cartesian points p (..., 3) in a unit-cube-periodic shape.
-    Distances are evaluated left to right (see _dot3) so that a point on a
-    boundary is classified the same way on every machine."""
+
+    sphere: |p - c| < r (surface outside); rod (flat-capped cylinder from a
+    to b): the foot point on the axis lies within the closed segment and the
+    distance to the axis is below r (caps closed, lateral surface open); box:
+    lo <= p < hi per axis; gyroid: g(p) > t (mode 0) or |g(p)| > t (mode 1)
+    with g = sin X cos Y + sin Y cos Z + sin Z cos X, X = 2 pi x.  Distances
+    are evaluated left to right (see _dot3) so that a point on a boundary is
+    classified the same way on every machine.  Pinned branch by branch in
+    tests/test_oracle_permittivity.py (brute force over images, hand points,
+    volume fractions, gyroid values)."""
     images = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], dtype=np.float64)
     # After d -= round(d) every |d_i| <= 1/2, so an image other than (0,0,0)
     # has a coordinate of size >= 1/2 and lies at distance >= 1/2 from the

@@ -117,3 +117,112 @@ def test_cross_dof_transfer_mistakes(monkeypatch):
     with monkeypatch.context() as mp:
         mp.setattr(crossdof, "transfer_t", crossdof.transfer)   # the transpose forgotten
         _fails(cd_pins.test_hermitian_on_an_anisotropic_structure)
+
+
+def _patched_inside(kind, branch):
+    """permittivity._inside with one shape kind routed to a faulty branch."""
+    orig = permittivity._inside
+
+    def f(shape_kind, params, p):
+        return branch(params, p) if shape_kind == kind else orig(shape_kind, params, p)
+
+    return f
+
+
+def _segment_variant(cap_strict=False, lateral_closed=False, reach_without_r=False, raw_axis=False):
+    """The oracle's rod test with one slip switched on."""
+    images = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], dtype=float)
+
+    def branch(params, p):
+        a = np.array(params[:3])
+        b = np.array(params[3:6])
+        r = params[6]
+        mid = 0.5 * (a + b)
+        axis = b - a
+        length = np.sqrt(axis @ axis)
+        u = axis if raw_axis else axis / length
+        d = p - mid
+        d = d - np.round(d)
+        reach = 0.5 * length if reach_without_r else 0.5 * length + r
+        hit = np.zeros(p.shape[:-1], dtype=bool)
+        for im in (images[13:14] if reach < 0.5 else images):
+            q = d + im
+            t = q @ u
+            perp = q - t[..., None] * u
+            in_len = np.abs(t) < 0.5 * length if cap_strict else np.abs(t) <= 0.5 * length
+            pp = np.sum(perp * perp, axis=-1)
+            hit |= in_len & ((pp <= r * r) if lateral_closed else (pp < r * r))
+        return hit
+
+    return branch
+
+
+@pytest.mark.parametrize("slip", ["cap_strict", "lateral_closed", "reach_without_r", "raw_axis"])
+def test_rod_membership_slips(monkeypatch, slip):
+    """Open caps, a closed lateral surface, an image bound that forgets the
+    radius and an unnormalised axis each fail a rod pin."""
+    import test_oracle_permittivity as pp
+
+    monkeypatch.setattr(permittivity, "_inside", _patched_inside(permittivity.SHAPE_SEGMENT,
+                                                                _segment_variant(**{slip: True})))
+    failures = 0
+    for fn, args in [(pp.test_segment_hand_points, ()), (pp.test_segment_image_only_point, ())] + \
+            [(pp.test_segment_membership_matches_brute_force, (s,)) for s in pp._SEGMENTS]:
+        try:
+            fn(*args)
+        except AssertionError:
+            failures += 1
+    assert failures > 0, slip
+
+
+def test_box_closed_upper_face(monkeypatch):
+    import test_oracle_permittivity as pp
+
+    def bad(params, p):
+        lo, hi = np.array(params[:3]), np.array(params[3:6])
+        w = p - np.floor(p)
+        hit = np.zeros(p.shape[:-1], dtype=bool)
+        for a in (-1, 0, 1):
+            for b in (-1, 0, 1):
+                for c in (-1, 0, 1):
+                    q = w + np.array([a, b, c])
+                    hit |= np.all((q >= lo) & (q <= hi), axis=-1)
+        return hit
+
+    monkeypatch.setattr(permittivity, "_inside", _patched_inside(permittivity.SHAPE_BOX, bad))
+    _fails(pp.test_box_membership)
+
+
+@pytest.mark.parametrize("slip", ["swap", "sign", "abs"])
+def test_gyroid_slips(monkeypatch, slip):
+    """sin and cos swapped, a flipped term, or the two modes exchanged each
+    fail the gyroid point values."""
+    import test_oracle_permittivity as pp
+
+    def bad(params, p):
+        t, mode = params[0], int(params[1])
+        x, y, z = (2 * np.pi * p[..., i] for i in range(3))
+        if slip == "swap":
+            g = np.cos(x) * np.sin(y) + np.cos(y) * np.sin(z) + np.cos(z) * np.sin(x)
+        elif slip == "sign":
+            g = np.sin(x) * np.cos(y) - np.sin(y) * np.cos(z) + np.sin(z) * np.cos(x)
+        else:
+            g = np.sin(x) * np.cos(y) + np.sin(y) * np.cos(z) + np.sin(z) * np.cos(x)
+            mode = 1 - mode
+        return (np.abs(g) > t) if mode == 1 else (g > t)
+
+    monkeypatch.setattr(permittivity, "_inside", _patched_inside(permittivity.SHAPE_GYROID, bad))
+    _fails(pp.test_gyroid_point_values)
+
+
+def test_sphere_closed_surface(monkeypatch):
+    import test_oracle_permittivity as pp
+
+    def bad(params, p):
+        c, r = np.array(params[:3]), params[3]
+        d = p - c
+        d = d - np.round(d)
+        return np.sum(d * d, axis=-1) <= r * r
+
+    monkeypatch.setattr(permittivity, "_inside", _patched_inside(permittivity.SHAPE_SPHERE, bad))
+    _fails(pp.test_sphere_hand_points)
