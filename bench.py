@@ -45,9 +45,9 @@ WORKLOAD = ("diamond-rods 128^3 FCC, 40 Bloch vectors x block of 16, complex64, 
             "one k-batched call per step (pcx_apply_kbatch)")
 METRIC = "compensated-operator applies/s at 128^3"
 # DRAM bytes of one vector through the five pass kernels at 16 vectors per
-# launch (sum over the five launches of one chunk, divided by 16), from the
-# ncu capture summarised in profiles/apply_pass_kernels_diamond128_c64.md;
-# used only when the run uses that chunk.
+# launch: dram__bytes_read.sum + dram__bytes_write.sum of the five launches
+# of one chunk in an ncu capture of this benchmark, divided by 16; used only
+# when the run uses that chunk and the five-pass chain.
 TRAFFIC_BYTES_PER_VECTOR_128_C64 = 8.8128e9 / 16
 TRAFFIC_CHUNK = 16
 UNIT = "vector-applies/s"
@@ -407,6 +407,8 @@ def main():
     ap.add_argument("--solve-legs", default="", help="comma list of solve legs to run (default: all)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--chunk", type=int, default=0, help="vectors per launch chunk (implies --no-tune)")
+    ap.add_argument("--apply-path", default="auto", choices=["auto", "five", "three"],
+                    help="pass structure of the apply (pcx_set_apply_path)")
     ap.add_argument("--blockops", action="store_true",
                     help="print timings of the eigensolver's Gram products and combinations instead")
     ap.add_argument("--sizes", action="store_true",
@@ -448,6 +450,8 @@ def main():
     ks = np.stack(k_list(kpath, nk))
     ctx = pcx.setup_structure(s, n)
     stream = torch.cuda.Stream()
+    pcx.pcx_set_apply_path(ctx, {"auto": pcx.PCX_APPLY_AUTO, "five": pcx.PCX_APPLY_FIVE_PASS,
+                                 "three": pcx.PCX_APPLY_THREE_PASS}[args.apply_path])
     if args.chunk > 0:
         args.no_tune = True
         pcx.pcx_set_apply_chunk(ctx, args.chunk)
@@ -509,7 +513,10 @@ def main():
     abytes = algorithmic_bytes(n, vecs, es, 4)
     achieved = abytes / (per_launch_ms / 1e3) / 1e9
     chunk = pcx.pcx_get_apply_chunk(ctx, prec)
-    traffic = TRAFFIC_BYTES_PER_VECTOR_128_C64 * vecs if (n, es) == (N, 8) and chunk == TRAFFIC_CHUNK else None
+    passes = pcx.pcx_get_apply_path(ctx, prec)
+    passes = 3 if passes == pcx.PCX_APPLY_THREE_PASS else (5 if passes == pcx.PCX_APPLY_FIVE_PASS else passes)
+    traffic = TRAFFIC_BYTES_PER_VECTOR_128_C64 * vecs if (n, es, passes) == (N, 8, 5) and chunk == TRAFFIC_CHUNK \
+        else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -526,11 +533,11 @@ def main():
                      # DRAM bytes the pass chain moves (ncu) over the same launch time
                      "traffic_gbs": traffic / (per_launch_ms / 1e3) / 1e9 if traffic else None,
                      "traffic_frac": traffic / (per_launch_ms / 1e3) / 1e9 / peak if traffic else None,
-                     "kernel": "pcx_apply pass chain (5 pass kernels per chunk of vectors)",
+                     "kernel": f"pcx_apply pass chain ({passes} pass kernels per chunk of vectors)",
                      "peak_kind": peak_kind + " (burst HBM copy)",
                      "algorithmic_bytes_per_launch": abytes},
         "e2e": e2e,
-        "gpu_launches": 5 * -(-vecs // chunk) * args.steps,
+        "gpu_launches": passes * -(-vecs // chunk) * args.steps,
         "clocks": ck,
     }
     if rank == 0 and not args.no_solve:

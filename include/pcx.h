@@ -234,17 +234,21 @@ pcx_status pcx_apply(pcx_ctx* ctx, const double k[3], double gamma, const void* 
  * pcx_apply may allocate (its scratch grows on demand); this variant never
  * does: no cudaMalloc, no cudaFree, no allocating library routine.
  *
- * Its scratch (gamma kappa . x for one chunk of vectors) lives in a
- * file-scope device array of PCX_NOALLOC_SCRATCH_BYTES (32 MiB) that every
- * GPU loading the library holds until the process exits.  Limit: one
- * vector's scratch, N^3 complex entries, must fit, i.e. N^3 * 8 bytes
- * (PCX_FP32) or N^3 * 16 bytes (PCX_FP64) <= 32 MiB -- every N <= 128 in
- * both precisions; larger grids are rejected with PCX_EINVAL before any
- * launch.  Vectors are processed in chunks that fit the array.
+ * Its scratch (gamma kappa . x for one chunk of vectors, and for M_CrossDoF
+ * also the real-space field of its stencil pass) lives in a file-scope
+ * device array of PCX_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading
+ * the library holds until the process exits.  Limit: one vector's scratch
+ * must fit: N^3 complex entries (M_Trivial), 4 N^3 (M_CrossDoF), i.e.
+ * entries * 8 bytes (PCX_FP32) or * 16 bytes (PCX_FP64) <= 32 MiB -- every
+ * N <= 128 in both precisions for M_Trivial, N <= 64 for M_CrossDoF; larger
+ * grids are rejected with PCX_EINVAL before any launch.  Vectors are
+ * processed in chunks that fit the array.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The context's device must be current.
+ * before any stream capture.  The address is kept for the life of the
+ * process: a cudaDeviceReset while the library is loaded is not supported.
+ * The context's device must be current (PCX_EINVAL otherwise).
  * The array is shared by every call and keeps the last call's contents;
  * nothing in it needs to start at zero (the first FFT pass writes all of it
  * before the last pass reads it).  Calls whose execution overlaps on the GPU
@@ -276,6 +280,30 @@ pcx_status pcx_apply_kbatch(pcx_ctx* ctx, const double* kpts, int nk, double gam
  * frees the cached graphs.
  */
 pcx_status pcx_set_apply_graphs(pcx_ctx* ctx, int enable);
+
+/*
+ * pcx_set_apply_path -- pass structure of the apply (and of the T0
+ * preconditioner, which runs on the same chain) in this context:
+ *   PCX_APPLY_FIVE_PASS   five HBM round trips per vector: one batch of 1D
+ *                         transforms per axis x, y, z (the z pass carrying the
+ *                         M sandwich), then y, x;
+ *   PCX_APPLY_THREE_PASS  three round trips: the y transforms split four-step
+ *                         (N = RA RB) and folded into the x and z passes,
+ *                         the intermediates kept in place in Y; complex64 at
+ *                         N = 32, 64, 128 (elsewhere the five-pass chain runs);
+ *   PCX_APPLY_AUTO        (default) the three-pass form where it exists.
+ * Both compute the same operator (Sec. 2.4 eq. matrixfree_kcform); the
+ * rounding differs.  M_CrossDoF contexts always use their seven-pass chain.
+ * PCX_EINVAL for another value.
+ */
+#define PCX_APPLY_AUTO 0
+#define PCX_APPLY_FIVE_PASS 1
+#define PCX_APPLY_THREE_PASS 2
+pcx_status pcx_set_apply_path(pcx_ctx* ctx, int path);
+/* The pass structure the apply of this context runs at `precision`:
+ * PCX_APPLY_FIVE_PASS or PCX_APPLY_THREE_PASS (7 for the seven-pass
+ * M_CrossDoF chain); -1 for a NULL context or a bad precision. */
+int pcx_get_apply_path(const pcx_ctx* ctx, int precision);
 
 /* Result of pcx_autotune. */
 typedef struct {

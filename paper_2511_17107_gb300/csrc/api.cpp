@@ -191,10 +191,18 @@ pcx_status pcx_apply_noalloc(pcx_ctx* c, const double k[3], double gamma, const 
   pcx_status st = check_block(c, "pcx_apply_noalloc", X, Y, nvec, precision);
   if (st != PCX_OK || nvec == 0) return st;
   if (!k) return inval(c, "pcx_apply_noalloc: NULL k");
-  const size_t per_vec = (size_t)c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8);
+  // one vector's scratch: N^3 entries of gamma kappa.x, and for M_CrossDoF
+  // the real-space field of its stencil pass (3 N^3 more)
+  const bool crossdof = c->m_kind == PCX_M_CROSSDOF;
+  const size_t per_vec = (size_t)c->n * c->n * c->n * (precision == PCX_FP64 ? 16 : 8) * (crossdof ? 4 : 1);
   if (per_vec > (size_t)PCX_NOALLOC_SCRATCH_BYTES)
-    return inval(c, "pcx_apply_noalloc: N^3 scratch entries of one vector (" + std::to_string(per_vec) +
-                        " bytes) exceed the 32 MiB static scratch; use pcx_apply");
+    return inval(c, std::string("pcx_apply_noalloc: the scratch of one vector (") + std::to_string(per_vec) +
+                        (crossdof ? " bytes: 4 N^3 entries for M_CrossDoF" : " bytes: N^3 entries") +
+                        ") exceeds the 32 MiB static scratch; use pcx_apply");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+    return inval(c, "pcx_apply_noalloc: the context's device " + std::to_string(c->device) +
+                        " is not the current device " + std::to_string(dev));
   const size_t bytes = pcx_vector_length(c) * nvec * (precision == PCX_FP64 ? 16 : 8);
   if (ranges_overlap(X, bytes, Y, bytes)) return inval(c, "pcx_apply_noalloc: X and Y overlap");
   pcx::KParams kp = pcx::make_kparams(c, k, gamma);
@@ -308,6 +316,20 @@ pcx_status pcx_set_apply_graphs(pcx_ctx* c, int enable) {
   if (!enable) pcx::free_apply_graphs(c);
   c->use_graphs = enable ? 1 : 0;
   return PCX_OK;
+}
+
+pcx_status pcx_set_apply_path(pcx_ctx* c, int path) {
+  if (!c) return inval(nullptr, "pcx_set_apply_path: NULL context");
+  if (path != PCX_APPLY_AUTO && path != PCX_APPLY_FIVE_PASS && path != PCX_APPLY_THREE_PASS)
+    return inval(c, "pcx_set_apply_path: path must be PCX_APPLY_AUTO, PCX_APPLY_FIVE_PASS or PCX_APPLY_THREE_PASS");
+  if (path != c->apply_path) pcx::free_apply_graphs(c);   // captured chains hold the old kernels
+  c->apply_path = path;
+  return PCX_OK;
+}
+
+int pcx_get_apply_path(const pcx_ctx* c, int precision) {
+  if (!c || (precision != PCX_FP64 && precision != PCX_FP32)) return -1;
+  return pcx::effective_apply_path(c, precision);
 }
 
 pcx_status pcx_autotune(pcx_ctx* c, int precision, int nvec, void* stream, pcx_tune_result* out) {

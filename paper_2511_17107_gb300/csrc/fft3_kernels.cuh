@@ -1,0 +1,387 @@
+// Three-pass form of the compensated-operator apply (Sec. 2.4 eq.
+// matrixfree_kcform, factorised as in Prop. 2.8) for complex64 at
+// N = 32, 64, 128.
+//
+// The five-pass chain (fft_kernels.cuh) moves every vector through HBM five
+// times.  Here the two y transforms are split four-step (N = RA RB) and
+// folded into the other passes, so each vector makes three round trips:
+//
+//   pass A (x tiles)  C^H and the gamma kappa.x scratch on load, inverse x
+//                     DFT, then the RA-point half of the inverse y DFT
+//   pass B (z tiles)  the RB-point half of the inverse y DFT on load,
+//                     inverse z DFT, M per cell, forward z DFT, the RB-point
+//                     half of the forward y DFT on store
+//   pass C (x tiles)  the RA-point half of the forward y DFT on load,
+//                     forward x DFT, C w + gamma conj(kappa) (kappa.x) on
+//                     store
+//
+// Inverse y DFT (positive exponent), input row p = RB n1 + n2, output row
+// k = k1 + RA k2:
+//   T[k1][n2] = e^{+2 pi i n2 k1 / N} sum_n1 X[RB n1 + n2] e^{+2 pi i n1 k1 / RA}   (pass A)
+//   Y[k1 + RA k2] = sum_n2 T[k1][n2] e^{+2 pi i n2 k2 / RB}                           (pass B)
+// Forward y DFT (negative exponent), input row y = k1 + RA k2, output row
+// m = m1 + RB m2:
+//   U[k1][m1] = e^{-2 pi i k1 m1 / N} sum_k2 E[k1 + RA k2] e^{-2 pi i k2 m1 / RB}     (pass B)
+//   W[m1 + RB m2] = sum_k1 U[k1][m1] e^{-2 pi i k1 m2 / RA}                           (pass C)
+// The intermediates T and U are kept in the natural [c][z][y][x] layout of
+// the output buffer with T[k1][n2] (and U[k1][m1]) in row RB k1 + n2.  Then
+// pass A writes exactly the rows it reads (RB n1 + n2 for its n2), pass B
+// reads and writes the RB consecutive rows RB k1 .. RB k1 + RB - 1 of its
+// x columns, and pass C reads and writes the rows m1 + RB m2 of its m1: all
+// three run in place on the output buffer.
+#pragma once
+
+#include "fft_kernels.cuh"
+
+namespace pcx {
+namespace fftk {
+
+template <int N>
+struct YSplit;
+template <> struct YSplit<32> { static constexpr int RA = 8, RB = 4; };
+template <> struct YSplit<64> { static constexpr int RA = 8, RB = 8; };
+template <> struct YSplit<128> { static constexpr int RA = 16, RB = 8; };
+
+template <typename T, int N>
+struct Cfg3 {
+  using C = Cfg<T, N>;
+  static constexpr int TP = C::TP;                  // pencils per tile (both tile kinds)
+  static constexpr int THREADS = C::THREADS;
+  static constexpr int RA = YSplit<N>::RA, RB = YSplit<N>::RB;
+  static constexpr int G = TP / RA;                 // row groups of RA rows per x tile
+  static constexpr int TPX = TP / RB;               // x columns per z tile
+  static constexpr int TILES = N * N / TP;          // tiles per vector, every pass
+  static constexpr int XI_PER_THREAD = 3 * G * N / THREADS;         // row-DFT items (RA points)
+  static constexpr int ZI_PER_THREAD = 3 * N * (TPX / 2) / THREADS; // row-DFT items (2 x RB points)
+  static_assert(RA * RB == N && G >= 1 && G * RA == TP && TPX * RB == TP, "tile split");
+  static_assert(TPX % 2 == 0 && XI_PER_THREAD >= 1 && ZI_PER_THREAD >= 1, "work split");
+  static_assert(XI_PER_THREAD * THREADS == 3 * G * N && ZI_PER_THREAD * THREADS == 3 * N * (TPX / 2), "work split");
+};
+
+// Row of pencil t of x tile `tile` (within one vector): z, y, and the n2
+// (or m1) index its row group carries.
+template <typename T, int N>
+__device__ __forceinline__ void x_row(int tile, int t, int& z, int& y, int& j) {
+  using C3 = Cfg3<T, N>;
+  const int gi = t / C3::RA, n1 = t % C3::RA;
+  const int gg = tile * C3::G + gi;
+  z = gg / C3::RB;
+  j = gg % C3::RB;
+  y = C3::RB * n1 + j;
+}
+
+// The kappa tables of the x tiles: ka[i][p1] and kb[t][i] with
+// kappa_i(p) = ka[i][p1] + kb[t][i] (see pass_kernel).
+template <typename T, int N>
+__device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams& kp, int tile, cx<T>* ka, cx<T>* kb) {
+  using C3 = Cfg3<T, N>;
+  for (int e = threadIdx.x; e < 3 * N + 3 * C3::TP; e += C3::THREADS) {
+    if (e < 3 * N) {
+      const int i = e / N, p = e % N;
+      const cx<T> l1 = glam[p], l0 = glam[N + p];
+      const T b0 = (T)kp.b[i];
+      const T kt = (T)kp.kt[0];
+      cx<T> r = mk(b0 * fma(-kt, l0.y, l1.x), b0 * fma(kt, l0.x, l1.y));
+      if (i == 0) r = mk(fma(-(T)kp.kq[0], l0.y, r.x), fma((T)kp.kq[0], l0.x, r.y));
+      ka[e] = r;
+    } else {
+      const int f = e - 3 * N, t = f / 3, i = f % 3;
+      int z, y, j;
+      x_row<T, N>(tile, t, z, y, j);
+      const int p[3] = {0, y, z};
+      cx<T> r = mk((T)0, (T)0);
+#pragma unroll
+      for (int jj = 1; jj < 3; ++jj) {
+        const cx<T> l1 = glam[p[jj]], l0 = glam[N + p[jj]];
+        const T bj = (T)kp.b[3 * jj + i], kt = (T)kp.kt[jj];
+        r = mk(fma(bj, fma(-kt, l0.y, l1.x), r.x), fma(bj, fma(kt, l0.x, l1.y), r.y));
+        if (i == jj) r = mk(fma(-(T)kp.kq[jj], l0.y, r.x), fma((T)kp.kq[jj], l0.x, r.y));
+      }
+      kb[3 * t + i] = r;
+    }
+  }
+}
+
+template <typename T, int N, int OP>
+__global__ void __launch_bounds__(Cfg<T, N>::THREADS, 3) pass3_kernel(PassArgs a) {
+  using C = Cfg<T, N>;
+  using C3 = Cfg3<T, N>;
+  constexpr bool ZP = OP == OP_SANDWICH || OP == OP_SANDWICH_EPS;
+  constexpr int AXIS = ZP ? 2 : 0;
+  using TL = Tile<T, N, AXIS>;
+  constexpr int TP = C::TP, RA = C3::RA, RB = C3::RB;
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = s + 3 * C::CS;
+  cx<T>* ka = tw + N;          // [3][N]
+  cx<T>* kb = ka + 3 * N;      // [TP][3]
+  T* mtab = reinterpret_cast<T*>(kb + 3 * TP);
+
+  const size_t v = blockIdx.x / C3::TILES;
+  const int tile = (int)(blockIdx.x % C3::TILES);
+  const cx<T>* in = static_cast<const cx<T>*>(a.in) + v * 3 * N3;
+  cx<T>* out = static_cast<cx<T>*>(a.out) + v * 3 * N3;
+
+  const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
+  for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = gtw[i];
+
+  if constexpr (!ZP) {
+    // ================= x tiles: pass A (PRE) and pass C (POST) =================
+    KParams kp = a.kp;
+    if (a.kps) kp = a.kps[(a.v_base + (int)v) / a.vec_per_k];
+    x_kappa_tables<T, N>(static_cast<const cx<T>*>(a.lam), kp, tile, ka, kb);
+    constexpr bool PRE = OP == OP_PRE || OP == OP_PRE_T0;
+    constexpr bool T0 = OP == OP_PRE_T0 || OP == OP_POST_T0;
+    if constexpr (PRE) {
+      cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
+      const T gam = (T)kp.gamma;
+      const T igam = (T)(1.0 / kp.gamma);
+      // the tile's rows land in shared memory by asynchronous copies
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        int z, y, j;
+        x_row<T, N>(tile, t, z, y, j);
+        const int g = z * N2 + y * N + n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cp_async_cx<T>(&s[TL::sidx(c, t, n)], &in[c * N3 + g]);
+      }
+      cp_async_commit_wait_all();
+      __syncthreads();
+      // u = -conj(kappa) x x per mode and gamma kappa.x to the scratch
+      // (T0: u / |k|^2 and kappa.x / (gamma |k|^4))
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        int z, y, j;
+        x_row<T, N>(tile, t, z, y, j);
+        const int g = z * N2 + y * N + n;
+        const cx<T> x0 = s[TL::sidx(0, t, n)], x1 = s[TL::sidx(1, t, n)], x2 = s[TL::sidx(2, t, n)];
+        cx<T> kap[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
+        T su = (T)1, ss = gam;
+        if constexpr (T0) {
+          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+          su = k2 > (T)0 ? (T)1 / k2 : (T)0;
+          ss = su * su * igam;
+        }
+        sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), ss);
+        const cx<T> zr = mk((T)0, (T)0);
+        cx<T> u0 = cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, zr), (T)-1));
+        cx<T> u1 = cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, zr), (T)-1));
+        cx<T> u2 = cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, zr), (T)-1));
+        if constexpr (T0) {
+          u0 = scale(u0, su);
+          u1 = scale(u1, su);
+          u2 = scale(u2, su);
+        }
+        s[TL::sidx(0, t, n)] = u0;
+        s[TL::sidx(1, t, n)] = u1;
+        s[TL::sidx(2, t, n)] = u2;
+      }
+      __syncthreads();
+      fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
+      // RA-point inverse y DFT over the rows of each group, twiddle
+      // e^{+2 pi i n2 k1 / N}, store to row RB k1 + n2
+#pragma unroll
+      for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
+        const int w = threadIdx.x + it * C::THREADS;
+        const int n = w % N, gi = (w / N) % C3::G, c = w / (N * C3::G);
+        int z, y, n2;
+        x_row<T, N>(tile, gi * RA, z, y, n2);
+        cx<T> r[RA];
+#pragma unroll
+        for (int i = 0; i < RA; ++i) r[i] = s[TL::sidx(c, gi * RA + i, n)];
+        dft<RA, +1>(r);
+        cx<T>* o = out + (size_t)c * N3 + z * N2 + n2 * N + n;
+#pragma unroll
+        for (int k1 = 0; k1 < RA; ++k1) {
+          cx<T> wt = tw[n2 * k1];
+          wt.y = -wt.y;
+          o[(RB * k1) * N] = r[k1] * wt;
+        }
+      }
+    } else {
+      // pass C: gamma kappa.x of the tile is fetched into shared memory while
+      // the rows are transformed
+      const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
+      cx<T>* ssb = kb + 3 * TP;   // [TP * N]
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        int z, y, j;
+        x_row<T, N>(tile, t, z, y, j);
+        cp_async_cx<T>(&ssb[e], &sb[z * N2 + y * N + n]);
+      }
+      // RA-point forward y DFT: rows RB k1 + m1 -> Fourier rows m1 + RB m2
+#pragma unroll
+      for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
+        const int w = threadIdx.x + it * C::THREADS;
+        const int n = w % N, gi = (w / N) % C3::G, c = w / (N * C3::G);
+        int z, y, m1;
+        x_row<T, N>(tile, gi * RA, z, y, m1);
+        const cx<T>* ip = in + (size_t)c * N3 + z * N2 + m1 * N + n;
+        cx<T> r[RA];
+#pragma unroll
+        for (int k1 = 0; k1 < RA; ++k1) r[k1] = ip[(RB * k1) * N];
+        dft<RA, -1>(r);
+#pragma unroll
+        for (int m2 = 0; m2 < RA; ++m2) s[TL::sidx(c, gi * RA + m2, n)] = r[m2];
+      }
+      __syncthreads();
+      fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
+      cp_async_commit_wait_all();
+      __syncthreads();
+      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
+        const int t = e / N, n = e % N;
+        int z, y, j;
+        x_row<T, N>(tile, t, z, y, j);
+        const int g = z * N2 + y * N + n;
+        const cx<T> sk = ssb[e];
+        cx<T> kap[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
+        const cx<T> w0 = s[TL::sidx(0, t, n)], w1 = s[TL::sidx(1, t, n)], w2 = s[TL::sidx(2, t, n)];
+        cx<T> c0 = cfma(kap[1], w2, scale(kap[2] * w1, (T)-1));
+        cx<T> c1 = cfma(kap[2], w0, scale(kap[0] * w2, (T)-1));
+        cx<T> c2 = cfma(kap[0], w1, scale(kap[1] * w0, (T)-1));
+        if constexpr (T0) {
+          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+          const T su = k2 > (T)0 ? (T)1 / k2 : (T)0;
+          c0 = scale(c0, su);
+          c1 = scale(c1, su);
+          c2 = scale(c2, su);
+        }
+        out[g] = cfma_conj(kap[0], sk, c0);
+        out[N3 + g] = cfma_conj(kap[1], sk, c1);
+        out[2 * N3 + g] = cfma_conj(kap[2], sk, c2);
+      }
+    }
+  } else {
+    // ================= z tiles: pass B =================
+    // tile = k1 * (N / TPX) + xr; pencil t = k2 * TPX + xo holds the real
+    // row y = k1 + RA k2 at x = xr TPX + xo
+    constexpr int TPX = C3::TPX;
+    const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
+    if (a.mid) {
+      const T* gt = static_cast<const T*>(a.mtab);
+      for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) mtab[i] = gt[i];
+    }
+    const T* M = static_cast<const T*>(a.M);
+    const uchar4* mid = static_cast<const uchar4*>(a.mid);
+    uchar4* sid = reinterpret_cast<uchar4*>(mtab + 9 * a.n_mat);   // [TP * N]
+    if (mid) {
+      for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {
+        const int t = w % TP, n = w / TP;
+        const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
+        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(&sid[w]));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(&mid[cell]) : "memory");
+      }
+    }
+    // RB-point inverse y DFT of rows RB k1 + n2 (two x columns per item)
+#pragma unroll
+    for (int it = 0; it < C3::ZI_PER_THREAD; ++it) {
+      const int w = threadIdx.x + it * C::THREADS;
+      const int xp = w % (TPX / 2), z = (w / (TPX / 2)) % N, c = w / ((TPX / 2) * N);
+      const cx<T>* ip = in + (size_t)c * N3 + z * N2 + (RB * k1) * N + x0 + 2 * xp;
+      cx<T> r0[RB], r1[RB];
+#pragma unroll
+      for (int n2 = 0; n2 < RB; ++n2) ld2(ip + n2 * N, r0[n2], r1[n2]);
+      dft<RB, +1>(r0);
+      dft<RB, +1>(r1);
+#pragma unroll
+      for (int k2 = 0; k2 < RB; ++k2) {
+        s[TL::sidx(c, k2 * TPX + 2 * xp, z)] = r0[k2];
+        s[TL::sidx(c, k2 * TPX + 2 * xp + 1, z)] = r1[k2];
+      }
+    }
+    __syncthreads();
+    fft_tile<T, N, 2, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
+    cp_async_commit_wait_all();
+    __syncthreads();
+    const T inv_n3 = (T)(1.0 / (double)N3);
+    for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {   // pencils fastest
+      const int t = w % TP, n = w / TP;
+      const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
+      T d1, d2, d3;
+      cx<T> o12, o13, o23;
+      if (mid) {
+        const uchar4 id = sid[w];
+        d1 = mtab[9 * id.x];
+        d2 = mtab[9 * id.y + 1];
+        d3 = mtab[9 * id.z + 2];
+        const T* o = mtab + 9 * id.w;
+        o12 = mk(o[3], o[4]);
+        o13 = mk(o[5], o[6]);
+        o23 = mk(o[7], o[8]);
+      } else {
+        d1 = M[cell];
+        d2 = M[N3 + cell];
+        d3 = M[2 * N3 + cell];
+        o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
+        o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
+        o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
+      }
+      const int i0 = TL::sidx(0, t, n), i1 = TL::sidx(1, t, n), i2 = TL::sidx(2, t, n);
+      const cx<T> e0 = s[i0], e1 = s[i1], e2 = s[i2];
+      T sc = inv_n3;
+      if constexpr (OP == OP_SANDWICH_EPS) {
+        // eps = M^{-1} = adj(M) / det(M) on the Hermitian block
+        const T a11 = d2 * d3 - norm2(o23), a22 = d1 * d3 - norm2(o13), a33 = d1 * d2 - norm2(o12);
+        const cx<T> a12 = o13 * conjg(o23) - scale(o12, d3);
+        const cx<T> a13 = o12 * o23 - scale(o13, d2);
+        const cx<T> a23 = o13 * conjg(o12) - scale(o23, d1);
+        const T det = d1 * a11 + (o12 * conjg(a12)).x + (o13 * conjg(a13)).x;
+        sc = inv_n3 / det;
+        d1 = a11;
+        d2 = a22;
+        d3 = a33;
+        o12 = a12;
+        o13 = a13;
+        o23 = a23;
+      }
+      const cx<T> m0 = cfma(o13, e2, cfma(o12, e1, scale(e0, d1)));
+      const cx<T> m1 = cfma(o23, e2, cfma_conj(o12, e0, scale(e1, d2)));
+      const cx<T> m2 = cfma_conj(o23, e1, cfma_conj(o13, e0, scale(e2, d3)));
+      s[i0] = scale(m0, sc);
+      s[i1] = scale(m1, sc);
+      s[i2] = scale(m2, sc);
+    }
+    __syncthreads();
+    fft_tile<T, N, 2, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
+    // RB-point forward y DFT over k2, twiddle e^{-2 pi i k1 m1 / N}, store
+    // to rows RB k1 + m1
+#pragma unroll
+    for (int it = 0; it < C3::ZI_PER_THREAD; ++it) {
+      const int w = threadIdx.x + it * C::THREADS;
+      const int xp = w % (TPX / 2), z = (w / (TPX / 2)) % N, c = w / ((TPX / 2) * N);
+      cx<T> r0[RB], r1[RB];
+#pragma unroll
+      for (int k2 = 0; k2 < RB; ++k2) {
+        r0[k2] = s[TL::sidx(c, k2 * TPX + 2 * xp, z)];
+        r1[k2] = s[TL::sidx(c, k2 * TPX + 2 * xp + 1, z)];
+      }
+      dft<RB, -1>(r0);
+      dft<RB, -1>(r1);
+      cx<T>* op = out + (size_t)c * N3 + z * N2 + (RB * k1) * N + x0 + 2 * xp;
+#pragma unroll
+      for (int m1 = 0; m1 < RB; ++m1) {
+        const cx<T> wt = tw[k1 * m1];
+        st2(op + m1 * N, r0[m1] * wt, r1[m1] * wt);
+      }
+    }
+  }
+}
+
+template <typename T, int N, int OP>
+cudaError_t launch_pass3(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st) {
+  auto kern = pass3_kernel<T, N, OP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)tiles, Cfg<T, N>::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace fftk
+}  // namespace pcx

@@ -56,6 +56,12 @@ int apply_chunk(const pcx_ctx* c, int precision) {
   return (int)(k < 1 ? 1 : (k > 64 ? 64 : k));
 }
 
+int effective_apply_path(const pcx_ctx* c, int precision) {
+  if (c->m_kind == PCX_M_CROSSDOF) return 7;
+  const bool three = precision == PCX_FP32 && (c->n == 32 || c->n == 64 || c->n == 128);
+  return three && c->apply_path != PCX_APPLY_FIVE_PASS ? PCX_APPLY_THREE_PASS : PCX_APPLY_FIVE_PASS;
+}
+
 // gamma kappa.x per vector of a chunk, and for M_CrossDoF the real-space
 // field of the stencil pass (3 N^3) after it
 size_t apply_scratch_bytes(const pcx_ctx* c, int precision, int nvec) {

@@ -1,5 +1,5 @@
 // complex64 instantiation of the apply and preconditioner kernels.
-#include "fft_kernels.cuh"
+#include "fft3_kernels.cuh"
 
 namespace pcx {
 template cudaError_t run_apply_t<float>(const pcx_ctx*, const KParams&, const void*, void*, int, int, void*,

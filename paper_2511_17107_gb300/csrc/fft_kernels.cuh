@@ -815,6 +815,14 @@ cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream
   return cudaGetLastError();
 }
 
+// Three-pass form of the apply (fft3_kernels.cuh): complex64 at N = 32, 64, 128.
+template <typename T, int N>
+constexpr bool has_pass3() {
+  return sizeof(T) == 4 && (N == 32 || N == 64 || N == 128);
+}
+template <typename T, int N, int OP>
+cudaError_t launch_pass3(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st);
+
 template <typename T, int N>
 cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
                         cudaStream_t st, const KParams* kps, int vec_per_k, bool t0) {
@@ -873,6 +881,22 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
     }
     a.in = x;
     a.out = y;
+    if constexpr (has_pass3<T, N>()) {
+      if (c->apply_path != PCX_APPLY_FIVE_PASS) {
+        // three passes, in place on y after the first
+        if ((e = t0 ? launch_pass3<T, N, OP_PRE_T0>(a, tiles, smem, st) : launch_pass3<T, N, OP_PRE>(a, tiles, smem, st))
+            != cudaSuccess)
+          return e;
+        a.in = y;
+        if ((e = t0 ? launch_pass3<T, N, OP_SANDWICH_EPS>(a, tiles, sandwich_smem, st)
+                    : launch_pass3<T, N, OP_SANDWICH>(a, tiles, sandwich_smem, st)) != cudaSuccess)
+          return e;
+        if ((e = t0 ? launch_pass3<T, N, OP_POST_T0>(a, tiles, post_smem, st)
+                    : launch_pass3<T, N, OP_POST>(a, tiles, post_smem, st)) != cudaSuccess)
+          return e;
+        continue;
+      }
+    }
     if ((e = t0 ? launch_pass<T, N, 0, OP_PRE_T0>(a, tiles, smem, st) : launch_pass<T, N, 0, OP_PRE>(a, tiles, smem, st))
         != cudaSuccess)
       return e;

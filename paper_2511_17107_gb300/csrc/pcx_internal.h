@@ -59,6 +59,8 @@ struct pcx_ctx {
   pcx::DeviceTables dev;
   // apply tuning and scratch: vectors per L2-resident chunk (0 = from L2 size)
   int apply_chunk = 0;
+  // apply pass structure: PCX_APPLY_AUTO, PCX_APPLY_FIVE_PASS or PCX_APPLY_THREE_PASS
+  int apply_path = 0;
   void* scratch = nullptr;     // gamma kappa.x carried from pass 1 to pass 5
   size_t scratch_bytes = 0;
   size_t l2_bytes = 0;
@@ -107,6 +109,8 @@ cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void
 cudaError_t launch_apply_noalloc(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
                                  int precision, cudaStream_t s);
 int apply_chunk(const pcx_ctx* c, int precision);
+// pass structure the apply runs: PCX_APPLY_FIVE_PASS, PCX_APPLY_THREE_PASS, or 7 (M_CrossDoF)
+int effective_apply_path(const pcx_ctx* c, int precision);
 // k-batched apply: nk groups of vec_per_k vectors, group i at kps_host[i]
 cudaError_t launch_apply_kbatch(pcx_ctx* c, const KParams* kps_host, int nk, int vec_per_k, const void* X, void* Y,
                                 int precision, cudaStream_t s);

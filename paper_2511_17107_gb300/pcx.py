@@ -18,6 +18,7 @@ import numpy as np
 PCX_OK, PCX_EINVAL, PCX_ENOMEM, PCX_ENOTHPD, PCX_ENOCONV, PCX_ENUMERIC, PCX_ECUDA = 0, -1, -2, -3, -4, -5, -6
 PCX_FP64, PCX_FP32 = 0, 1
 PCX_CT_SUMMED, PCX_CT_LITERAL = 0, 1
+PCX_APPLY_AUTO, PCX_APPLY_FIVE_PASS, PCX_APPLY_THREE_PASS = 0, 1, 2
 STATUS_NAMES = {0: "PCX_OK", -1: "PCX_EINVAL", -2: "PCX_ENOMEM", -3: "PCX_ENOTHPD", -4: "PCX_ENOCONV",
                 -5: "PCX_ENUMERIC", -6: "PCX_ECUDA"}
 
@@ -105,6 +106,8 @@ def lib():
             "pcx_div_norms": (st, [vp, dp, vp, C.c_int, C.c_int, vp, vp]),
             "pcx_apply_kbatch": (st, [vp, dp, C.c_int, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_set_apply_graphs": (st, [vp, C.c_int]),
+            "pcx_set_apply_path": (st, [vp, C.c_int]),
+            "pcx_get_apply_path": (C.c_int, [vp, C.c_int]),
             "pcx_autotune": (st, [vp, C.c_int, C.c_int, vp, C.POINTER(pcx_tune_result)]),
             "pcx_sandwich_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_cnn_init": (st, [C.c_uint64, vp, vp]),
@@ -132,7 +135,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_autotune",
+                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_autotune",
                         "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
                         "pcx_cg_solve", "pcx_gram", "pcx_set_gram_path", "pcx_get_gram_path", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
@@ -391,6 +394,14 @@ def pcx_apply_kbatch(ctx, kpts, X, Y, gamma=0.0, stream=None):
 
 def pcx_set_apply_graphs(ctx, enable):
     _check(lib().pcx_set_apply_graphs(ctx.handle, int(bool(enable))), ctx.handle)
+
+
+def pcx_set_apply_path(ctx, path):
+    _check(lib().pcx_set_apply_path(ctx.handle, int(path)), ctx.handle)
+
+
+def pcx_get_apply_path(ctx, precision):
+    return int(lib().pcx_get_apply_path(ctx.handle, int(precision)))
 
 
 def pcx_autotune(ctx, precision, nvec, stream=None):
