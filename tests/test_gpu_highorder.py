@@ -3,18 +3,24 @@
 Sec. 4.2 (eq. display:num:testsmooth, table tab:num:convergence_highord)
 solves the SC unit cell with the smooth scalar permittivity
 eps(x, y, z) = 8.9 sin(2 pi (x + y + z)) + 13 at k = (pi, pi, pi) with the
-m = 5 stencils of Sec. 2.5 and prints |omega_h^2 - omega_2h^2| for the first
-eight eigenvalues.  Here the GPU solver (FP64, cell blocks passed in through
-the dense-block path of pcx_setup) is checked three ways:
+m = 5 stencils of Sec. 2.5 and prints, under the heading
+|omega_h^2 - omega_2h^2|, the differences between grid levels for the
+first eight eigenvalues.  The printed values are differences of the
+normalised frequency omega / (2 pi) (omega a / 2 pi c, a = 1), where
+omega^2 is the eigenvalue: |sqrt(lambda_h) - sqrt(lambda_2h)| / (2 pi)
+reproduces every printed h = 1/32 entry (N = 32 against N = 16) to 0.2%,
+and the eigenvalue differences themselves are 16-18 times the printed
+numbers, the factor 4 pi sqrt(lambda) with lambda = 1.68 and 2.15.  Here
+the GPU solver (FP64, cell blocks passed in through the dense-block path of
+pcx_setup) is checked three ways:
 
 - against the oracle's LOBPCG on the same discretisation at 16^3;
+- the frequency differences at h = 1/32 equal the printed ones to 1%;
 - the convergence rate between h = 1/32 and 1/64 is the stencils' tenth
-  order, as printed (log2 of the printed ratio is 9.8);
-- the differences themselves are about 16 times the printed ones (the
-  discretisation of Sec. 2.5 as read here; the oracle, written from the
-  same equations without the CUDA path, gives the same numbers).  The
-  test records that ratio and bounds it, so that a change of the
-  discretisation shows.
+  order, as printed (log2 of the printed ratio is 9.8).  The h = 1/64
+  differences (near 1e-10 in the eigenvalue) sit at the FP64 rounding of
+  the Rayleigh quotients (eps_mach times ||Op||, with gamma |kappa|^2 up to
+  ~1e6 at 64^3), so they agree with the printed column only to a factor 2.
 
 For an isotropic eps the M_Trivial block of a cell is diag(1/eps(E1),
 1/eps(E2), 1/eps(E3)), sampled at the edge DoFs of Sec. 2.1,
@@ -101,19 +107,21 @@ def _oracle_eigs(n):
 def test_tenth_order_convergence_on_the_smooth_permittivity(pcx, capsys):
     e16, e32, e64 = (_gpu_eigs(pcx, n) for n in (16, 32, 64))
     o16 = _oracle_eigs(16)
-    d32, d64 = np.abs(e32 - e16), np.abs(e64 - e32)
+    # normalised frequency omega / (2 pi) with omega^2 the eigenvalue
+    f16, f32, f64 = (np.sqrt(e) / (2 * np.pi) for e in (e16, e32, e64))
+    d32, d64 = np.abs(f32 - f16), np.abs(f64 - f32)
     p32, p64 = _printed()
-    order = np.log2(d32 / d64)
+    order = np.log2(np.abs(e32 - e16) / np.abs(e64 - e32))
     with capsys.disabled():
         print("\nomega^2 at 64^3:", e64)
-        print("|diff| h=1/32:", d32, "\n|diff| h=1/64:", d64, "\norder:", order)
+        print("|d omega/2pi| h=1/32:", d32, "\n|d omega/2pi| h=1/64:", d64, "\norder:", order)
         print("ratio to the printed differences:", d32 / p32, d64 / p64)
     # GPU solver and oracle on the same discretisation, to the FP64
     # eigenvalue tolerance (1e-10 relative)
     np.testing.assert_allclose(e16, o16, rtol=1e-10)
-    # tenth order between h = 1/32 and 1/64, like the printed table (9.8)
+    # the printed constants at h = 1/32
+    np.testing.assert_allclose(d32, p32, rtol=1e-2)
+    # tenth order between h = 1/32 and 1/64, like the printed table (9.8);
+    # the h = 1/64 column to the FP64 noise of the eigenvalues
     assert np.all(order > 8.5) and np.all(order < 11.0), order
-    assert np.all(np.abs(order - np.log2(p32 / p64)) < 1.2), (order, np.log2(p32 / p64))
-    # the constants: 16-19 times the printed ones with this reading
-    r32 = d32 / p32
-    assert np.all(r32 > 12) and np.all(r32 < 24), r32
+    assert np.all(d64 / p64 > 0.4) and np.all(d64 / p64 < 2.0), d64 / p64
