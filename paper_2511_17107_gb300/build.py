@@ -81,5 +81,25 @@ def build(verbose: bool = False) -> str:
     return LIB
 
 
+BASE_SRC = os.path.join(HERE, "baselines", "cufft_baseline.cu")
+BASE_LIB = os.path.join(HERE, "libpcx_baselines.so")
+
+
+def build_baselines() -> str:
+    """libpcx_baselines.so: the cuFFT / cuBLAS baselines that the benchmark
+    times beside libpcx (never loaded by libpcx itself)."""
+    os.makedirs(BUILD, exist_ok=True)
+    if os.path.exists(BASE_LIB) and os.path.getmtime(BASE_LIB) >= os.path.getmtime(BASE_SRC):
+        return BASE_LIB
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+    cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+                             "-o", BASE_LIB + ".tmp", BASE_SRC, "-lcufft", "-lcublas", "-Xlinker", "-rpath=" + cudalib]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"baseline build failed:\n{res.stdout}\n{res.stderr}")
+    os.replace(BASE_LIB + ".tmp", BASE_LIB)
+    return BASE_LIB
+
+
 if __name__ == "__main__":
     print(build(verbose="-v" in sys.argv))
