@@ -268,6 +268,67 @@ def apply_sizes_table(n, reps=5):
     return 0
 
 
+def library_baselines(pcx, ctx, k, n, block=16, reps=5):
+    """The cuFFT / cuBLAS versions of the apply and of the Gram products
+    (libpcx_baselines.so, timed only) next to libpcx on the same inputs:
+    CUDA events on one stream, L2 flushed before each call, median of reps."""
+    import numpy as np
+    import torch
+
+    from paper_2511_17107_gb300 import baselines
+    st = torch.cuda.Stream()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def timeit(fn):
+        with torch.cuda.stream(st):
+            fn()
+            fn()
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                st.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    out = {"workload": f"diamond rods {n}^3, one Bloch vector x {block} vectors; Gram at L = 3 N^3",
+           "timer": "CUDA events, L2 flushed, median of 5"}
+    for dt, prec, name, chunk in ((torch.complex64, pcx.PCX_FP32, "c64", block),
+                                  (torch.complex128, pcx.PCX_FP64, "c128", block // 2)):
+        x = torch.complex(torch.randn(block, 3, n, n, n, device="cuda", dtype=torch.float64),
+                          torch.randn(block, 3, n, n, n, device="cuda", dtype=torch.float64)).to(dt)
+        y = torch.empty_like(x)
+        base = baselines.CufftApply(pcx, ctx, k, prec, chunk)
+        ms_b = timeit(lambda: base(x, y, st))
+        ms_o = timeit(lambda: pcx.pcx_apply(ctx, k, x, y, stream=st))
+        out["apply_" + name] = {"cufft_us_per_vector": round(1e3 * ms_b / block, 2),
+                                "pcx_us_per_vector": round(1e3 * ms_o / block, 2),
+                                "pcx_over_cufft": round(ms_b / ms_o, 3)}
+        base.close()
+        del x, y
+    L = 3 * n ** 3
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for dt, name in ((torch.complex64, "c64"), (torch.complex128, "c128")):
+        A = torch.complex(torch.randn(48, L, device="cuda", generator=g, dtype=torch.float64),
+                          torch.randn(48, L, device="cuda", generator=g, dtype=torch.float64)).to(dt)
+        B = torch.complex(torch.randn(48, L, device="cuda", generator=g, dtype=torch.float64),
+                          torch.randn(48, L, device="cuda", generator=g, dtype=torch.float64)).to(dt)
+        rows = []
+        for na, nb in ((16, 16), (16, 48), (48, 48)):
+            G = torch.empty((na, nb), dtype=torch.complex128, device="cuda")
+            Gb = torch.empty((nb, na), dtype=dt, device="cuda")
+            ms_b = timeit(lambda: baselines.cublas_gram(A[:na], B[:nb], Gb, st))
+            ms_o = timeit(lambda: pcx.pcx_gram(A[:na], B[:nb], G, stream=st))
+            rows.append({"na": na, "nb": nb, "cublas_ms": round(ms_b, 4), "pcx_ms": round(ms_o, 4),
+                         "pcx_over_cublas": round(ms_b / ms_o, 3)})
+        out["gram_" + name] = rows
+        del A, B
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -321,6 +382,21 @@ def k_list(kpath, nk):
     return [kpath[(K_INDEX + i) % len(kpath)] for i in range(nk)]
 
 
+def rank_k_points(nk, rank, world):
+    """The Bloch vectors of one rank.  One GPU: nk points of the
+    configuration's 40-point path (from K_INDEX).  N GPUs (weak scaling):
+    the whole job is the same polyline X-U-L-G-X-W-K sampled at nk N points,
+    and rank r takes every N-th of them (r, r + N, ...), so the ranks' k-points
+    are distinct, each rank has nk of them, and together they are the path."""
+    import numpy as np
+
+    import workloads as wl
+    if world == 1:
+        return np.stack(k_list(wl.config_k("diamond-rods"), nk))
+    full = wl.k_path(wl.FCC_POINTS, ["X", "U", "L", "G", "X", "W", "K"], nk * world)
+    return full[rank::world]
+
+
 def train_learned(pcx, n, n_struct=3, n_pairs=8, steps=120):
     """The learned correction trained on random structures at grid n."""
     import numpy as np
@@ -349,8 +425,11 @@ def train_learned(pcx, n, n_struct=3, n_pairs=8, steps=120):
                "s": time.perf_counter() - t0}
 
 
-def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps=120, only=""):
-    """Per-k time to Res_j <= tol: mixed (K_P^{-1}, T0, learned) vs plain FP64."""
+def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps=120, only="", batched_nk=0,
+               k_concurrency=4):
+    """Per-k time to Res_j <= tol: mixed (K_P^{-1}, T0, learned) vs plain FP64;
+    with batched_nk, also the mixed T0 solve of batched_nk k-points of the
+    path with k_concurrency of them in flight (total and mean per k)."""
     import numpy as np
     ks = k_list(kpath, nk)
     out = {"tol": tol, "nev": nev, "block": block, "k_points": nk, "k_first_index": K_INDEX,
@@ -381,6 +460,20 @@ def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps
                      "ms_apply": d["ms_apply"], "ms_precond": d["ms_precond"], "ms_gram": d["ms_gram"],
                      "ms_rr": d["ms_rr"], "ms_other": d["ms_other"], "gamma_raises": d["gamma_raises"],
                      "learned_fallbacks": d["learned_fallbacks"]}
+    if batched_nk > 0 and (not want or "mixed_sandwich_all_k" in want):
+        # the whole band path: every k of the path, several in flight
+        kall = k_list(kpath, batched_nk)
+        stats = pcx.pcx_solve_stats()
+        t0 = time.perf_counter()
+        ev, res, its, st = pcx.pcx_solve(ctx, kall, nev, tol, block=block, precision=pcx.PCX_FP32, stats=stats,
+                                         raise_on_noconv=False, precond_kind=1, k_concurrency=k_concurrency)
+        dt = time.perf_counter() - t0
+        out["mixed_sandwich_all_k"] = {"k_points": batched_nk, "k_concurrency": k_concurrency, "s_total": dt,
+                                       "s_per_k": dt / batched_nk, "status": int(st), "max_res": float(np.max(res)),
+                                       "iters_per_k": float(np.mean(its)), "iters_max": int(np.max(its))}
+        if "mixed_sandwich" in out and nk >= 1:
+            out["mixed_sandwich_all_k"]["max_rel_eig_diff_vs_per_k_leg"] = float(
+                np.max(np.abs(ev[:nk] - eigs["mixed_sandwich"]) / np.abs(eigs["mixed_sandwich"])))
     for name in eigs:
         if name != "fp64" and name in out and "fp64" in out:
             out[name]["speedup_vs_fp64"] = out["fp64"]["s_per_k"] / out[name]["s_per_k"]
@@ -402,7 +495,11 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--nk", type=int, default=NK, help="Bloch vectors per k-batched step")
     ap.add_argument("--no-solve", action="store_true", help="skip the per-k solve-time legs")
+    ap.add_argument("--no-baselines", action="store_true", help="skip the cuFFT / cuBLAS baseline timings")
     ap.add_argument("--solve-nk", type=int, default=1, help="k-points of the solve legs (from index k_index)")
+    ap.add_argument("--solve-all-k", type=int, default=NK,
+                    help="k-points of the batched mixed T0 leg over the band path (0: skip)")
+    ap.add_argument("--k-concurrency", type=int, default=4, help="k-points in flight in the batched leg")
     ap.add_argument("--learned-steps", type=int, default=120, help="training steps of the learned leg (0: skip)")
     ap.add_argument("--solve-legs", default="", help="comma list of solve legs to run (default: all)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
@@ -447,7 +544,7 @@ def main():
     prec = pcx.PCX_FP32 if es == 8 else pcx.PCX_FP64
     s = wl.diamond_rods()
     kpath = wl.config_k(s.name)
-    ks = np.stack(k_list(kpath, nk))
+    ks = rank_k_points(nk, rank, world)
     ctx = pcx.setup_structure(s, n)
     stream = torch.cuda.Stream()
     pcx.pcx_set_apply_path(ctx, {"auto": pcx.PCX_APPLY_AUTO, "five": pcx.PCX_APPLY_FIVE_PASS,
@@ -540,9 +637,14 @@ def main():
         "gpu_launches": passes * -(-vecs // chunk) * args.steps,
         "clocks": ck,
     }
+    if rank == 0 and not args.no_baselines:
+        del X, Y
+        torch.cuda.empty_cache()
+        line["baselines"] = library_baselines(pcx, ctx, ks[0], n)
     if rank == 0 and not args.no_solve:
         line["solve"] = solve_legs(pcx, ctx, kpath, args.solve_nk, n, learned_steps=args.learned_steps,
-                                   only=args.solve_legs)
+                                   only=args.solve_legs, batched_nk=args.solve_all_k,
+                                   k_concurrency=args.k_concurrency)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess()
     if rank == 0:

@@ -590,6 +590,21 @@ typedef struct {
                          bounds the residual that phase can reach; at 128^3
                          the FP32 phase stalls near 1000 * 2^-24 * theta_top).
                          0: default 1024; negative: off                       */
+  const void* x0;     /* optional DEVICE initial block, block vectors in the FP64
+                         layout ([block][3 N^3] complex128), used at every k in
+                         place of the seeded random block (a warm start, e.g.
+                         the previous k's eigenvectors along a band path); the
+                         p = 0 mode is deflated from it at k = 0.  NaN/Inf or a
+                         rank-deficient block gives PCX_ENUMERIC.  NULL: random */
+  int k_concurrency;  /* k-points solved at the same time (0 or 1: one after the
+                         other).  Each k in flight gets its own host thread,
+                         stream, search-space buffers and apply scratch (about
+                         13 block x 3 N^3 complex entries per precision in use:
+                         10.5 GB at 128^3, block 16, complex64), so the GPU
+                         runs one k's kernels while another k's host does its
+                         Rayleigh-Ritz step.  Same results as one after the
+                         other.  Not with cnn_params or dump_R (they share the
+                         context's workspace): those solve one k at a time.  */
 } pcx_solve_opts;
 
 /*

@@ -75,7 +75,8 @@ pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32
   std::vector<double> blocks;
   std::vector<int32_t> ids;
   try {
-    st = pcx::sample_blocks(desc, desc->lattice, blocks, ids_out ? &ids : nullptr, err);
+    st = pcx::sample_blocks(desc, desc->lattice, blocks, (ids_out || desc->m_kind == PCX_M_CROSSDOF) ? &ids : nullptr,
+                            err);
   } catch (const std::bad_alloc&) {
     g_err = "pcx_sample_host: out of host memory";
     return PCX_ENOMEM;
@@ -86,7 +87,9 @@ pcx_status pcx_sample_host(const pcx_setup_desc* desc, double* blocks_out, int32
   }
   std::memcpy(blocks_out, blocks.data(), blocks.size() * sizeof(double));
   if (ids_out) std::memcpy(ids_out, ids.data(), ids.size() * sizeof(int32_t));
-  if (first_bad) *first_bad = pcx::first_non_hpd(blocks);
+  if (first_bad)
+    *first_bad = desc->m_kind == PCX_M_CROSSDOF ? pcx::crossdof_unproven(desc->n, desc->n_mat, desc->eps, ids, nullptr)
+                                                : pcx::first_non_hpd(blocks);
   return PCX_OK;
 }
 
@@ -95,11 +98,18 @@ void pcx_destroy(pcx_ctx* c) {
   pcx::free_apply_graphs(c);
   for (auto& st : c->copy_stream)
     if (st) cudaStreamDestroy(st);
+  for (cudaStream_t st : c->solve_streams) {
+    pcx::gram_cc_release_stream(st);
+    pcx::gram_tc_release_stream(st);
+    pcx::gram_x_release_stream(st);
+    cudaStreamDestroy(st);
+  }
   for (auto& row : c->slot_event)
     for (auto& ev : row)
       if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64,  c->dev.tw32, c->dev.m64,  c->dev.m32,
-                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->cnn_ws, c->ktab};
+                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->cnn_ws, c->ktab,
+                  c->dev.mid3};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;

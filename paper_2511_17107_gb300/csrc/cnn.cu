@@ -1,6 +1,7 @@
-// Kernels of the learned correction of the preconditioner K_P^{-1}:
+// Kernels of the learned preconditioner correction, which acts next to eps
+// inside the curl-sandwich base preconditioner T0:
 //
-//   T(r) = K_P^{-1} r + F3_3^H g(F3_3 K_P^{-1} r)
+//   T(r) = T0 r + K_A F3_3^H g(F3_3 K_A^H r / |k|^2) / |k|^2
 //
 // with g a three-layer circular 3D convolution net (3 x 3 x 3 taps) on the
 // real-space field, its hidden channels gated by sigmoid convolutions of the

@@ -31,6 +31,8 @@
 // three run in place on the output buffer.
 #pragma once
 
+#include <type_traits>
+
 #include "fft_kernels.cuh"
 
 namespace pcx {
@@ -42,21 +44,53 @@ template <> struct YSplit<32> { static constexpr int RA = 8, RB = 4; };
 template <> struct YSplit<64> { static constexpr int RA = 8, RB = 8; };
 template <> struct YSplit<128> { static constexpr int RA = 16, RB = 8; };
 
+// Geometry of the z tiles (pass B): RB rows x TPX columns of z pencils, at
+// least 32 bytes of consecutive x per row so that every global access of
+// the pass fills whole 32-byte sectors.  At N = 128 that is 32 pencils
+// (96 KB of complex64 for the three components), two CTAs per SM with 32
+// elements per thread and stage.
+template <int N>
+struct ZGeom {
+  static constexpr int TN = 2048, E = 16, MINB = 3;
+};
+template <> struct ZGeom<128> { static constexpr int TN = 4096, E = 32, MINB = 2; };
+
 template <typename T, int N>
 struct Cfg3 {
-  using C = Cfg<T, N>;
-  static constexpr int TP = C::TP;                  // pencils per tile (both tile kinds)
+  using C = Cfg<T, N>;                              // x tiles (passes A and C)
+  using CZ = CfgG<T, N, ZGeom<N>::TN, ZGeom<N>::E>; // z tiles (pass B)
+  static constexpr int TP = C::TP;                  // pencils (rows) per x tile
   static constexpr int THREADS = C::THREADS;
+  static constexpr int TPZ = CZ::TP;                // pencils per z tile
+  static constexpr int THREADSZ = CZ::THREADS;
   static constexpr int RA = YSplit<N>::RA, RB = YSplit<N>::RB;
   static constexpr int G = TP / RA;                 // row groups of RA rows per x tile
-  static constexpr int TPX = TP / RB;               // x columns per z tile
-  static constexpr int TILES = N * N / TP;          // tiles per vector, every pass
-  static constexpr int XI_PER_THREAD = 3 * G * N / THREADS;         // row-DFT items (RA points)
-  static constexpr int ZI_PER_THREAD = 3 * N * (TPX / 2) / THREADS; // row-DFT items (2 x RB points)
-  static_assert(RA * RB == N && G >= 1 && G * RA == TP && TPX * RB == TP, "tile split");
-  static_assert(TPX % 2 == 0 && XI_PER_THREAD >= 1 && ZI_PER_THREAD >= 1, "work split");
-  static_assert(XI_PER_THREAD * THREADS == 3 * G * N && ZI_PER_THREAD * THREADS == 3 * N * (TPX / 2), "work split");
+  static constexpr int TPX = TPZ / RB;              // x columns per z tile
+  static constexpr int TILES = N * N / TP;          // x tiles per vector
+  static constexpr int ZTILES = N * N / TPZ;        // z tiles per vector
+  static constexpr int XI_PER_THREAD = 3 * G * N / THREADS;           // row-DFT items (RA points)
+  static constexpr int ZI_PER_THREAD = 3 * N * (TPX / 2) / THREADSZ;  // row-DFT items (2 x RB points)
+  static constexpr int MI_PER_THREAD = (TPZ * N + THREADSZ - 1) / THREADSZ;   // cells per thread in the M step
+  static_assert(RA * RB == N && G >= 1 && G * RA == TP && TPX * RB == TPZ, "tile split");
+  static_assert(TPX % 4 == 0 && XI_PER_THREAD >= 1 && ZI_PER_THREAD >= 1, "work split");
+  static_assert(XI_PER_THREAD * THREADS == 3 * G * N && ZI_PER_THREAD * THREADSZ == 3 * N * (TPX / 2),
+                "work split");
+  // shared memory of the z tile: three components at stride CS (Tile)
+  static constexpr size_t ZSMEM_TILE = (size_t)3 * CZ::CS * sizeof(cx<T>);
 };
+
+template <int OP>
+__host__ __device__ constexpr bool is_z_op() {
+  return OP == OP_SANDWICH || OP == OP_SANDWICH_EPS;
+}
+template <typename T, int N, int OP>
+__host__ __device__ constexpr int pass3_threads() {
+  return is_z_op<OP>() ? Cfg3<T, N>::THREADSZ : Cfg3<T, N>::THREADS;
+}
+template <typename T, int N, int OP>
+__host__ __device__ constexpr int pass3_minb() {
+  return is_z_op<OP>() ? ZGeom<N>::MINB : 3;
+}
 
 // Row of pencil t of x tile `tile` (within one vector): z, y, and the n2
 // (or m1) index its row group carries.
@@ -103,23 +137,24 @@ __device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams&
 }
 
 template <typename T, int N, int OP>
-__global__ void __launch_bounds__(Cfg<T, N>::THREADS, 3) pass3_kernel(PassArgs a) {
-  using C = Cfg<T, N>;
+__global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP>()) pass3_kernel(PassArgs a) {
+  constexpr bool ZP = is_z_op<OP>();
   using C3 = Cfg3<T, N>;
-  constexpr bool ZP = OP == OP_SANDWICH || OP == OP_SANDWICH_EPS;
+  using C = std::conditional_t<ZP, typename C3::CZ, typename C3::C>;
   constexpr int AXIS = ZP ? 2 : 0;
-  using TL = Tile<T, N, AXIS>;
+  using TL = Tile<T, N, AXIS, C>;
   constexpr int TP = C::TP, RA = C3::RA, RB = C3::RB;
   constexpr int N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* tw = s + 3 * C::CS;
-  cx<T>* ka = tw + N;          // [3][N]
-  cx<T>* kb = ka + 3 * N;      // [TP][3]
-  T* mtab = reinterpret_cast<T*>(kb + 3 * TP);
+  cx<T>* tw = s + 3 * C::CS;    // the three components at stride CS (see Tile)
+  cx<T>* ka = tw + N;          // [3][N]   (x tiles)
+  cx<T>* kb = ka + 3 * N;      // [TP][3]  (x tiles)
+  T* mtab = reinterpret_cast<T*>(tw + N);   // [n_mat][9] (z tiles)
 
-  const size_t v = blockIdx.x / C3::TILES;
-  const int tile = (int)(blockIdx.x % C3::TILES);
+  constexpr int TILES = ZP ? C3::ZTILES : C3::TILES;
+  const size_t v = blockIdx.x / TILES;
+  const int tile = (int)(blockIdx.x % TILES);
   const cx<T>* in = static_cast<const cx<T>*>(a.in) + v * 3 * N3;
   cx<T>* out = static_cast<cx<T>*>(a.out) + v * 3 * N3;
 
@@ -267,16 +302,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, 3) pass3_kernel(PassArgs a
       for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) mtab[i] = gt[i];
     }
     const T* M = static_cast<const T*>(a.M);
-    const uchar4* mid = static_cast<const uchar4*>(a.mid);
-    uchar4* sid = reinterpret_cast<uchar4*>(mtab + 9 * a.n_mat);   // [TP * N]
-    if (mid) {
-      for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {
-        const int t = w % TP, n = w / TP;
-        const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
-        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(&sid[w]));
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(&mid[cell]) : "memory");
-      }
-    }
+    const uchar4* mid3 = static_cast<const uchar4*>(a.mid3);
     // RB-point inverse y DFT of rows RB k1 + n2 (two x columns per item)
 #pragma unroll
     for (int it = 0; it < C3::ZI_PER_THREAD; ++it) {
@@ -295,17 +321,28 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, 3) pass3_kernel(PassArgs a
       }
     }
     __syncthreads();
-    fft_tile<T, N, 2, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
-    cp_async_commit_wait_all();
-    __syncthreads();
+    fft_tile<T, N, 2, +1, 0, 0, C>(s, tw, nullptr, nullptr, 0);
+    // material ids of the tile's cells in the pass's own order (mid3: one
+    // contiguous run of TP N ids per tile), all loads in flight at once
+    uchar4 idr[C3::MI_PER_THREAD];
+    if (mid3) {
+      const uchar4* tid3 = mid3 + (size_t)tile * TP * N;
+#pragma unroll
+      for (int i = 0; i < C3::MI_PER_THREAD; ++i) {
+        const int w = threadIdx.x + i * C::THREADS;
+        if (w < TP * N) idr[i] = tid3[w];
+      }
+    }
     const T inv_n3 = (T)(1.0 / (double)N3);
-    for (int w = threadIdx.x; w < TP * N; w += C::THREADS) {   // pencils fastest
+#pragma unroll
+    for (int i = 0; i < C3::MI_PER_THREAD; ++i) {   // pencils fastest
+      const int w = threadIdx.x + i * C::THREADS;
+      if (w >= TP * N) break;
       const int t = w % TP, n = w / TP;
-      const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
       T d1, d2, d3;
       cx<T> o12, o13, o23;
-      if (mid) {
-        const uchar4 id = sid[w];
+      if (mid3) {
+        const uchar4 id = idr[i];
         d1 = mtab[9 * id.x];
         d2 = mtab[9 * id.y + 1];
         d3 = mtab[9 * id.z + 2];
@@ -314,6 +351,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, 3) pass3_kernel(PassArgs a
         o13 = mk(o[5], o[6]);
         o23 = mk(o[7], o[8]);
       } else {
+        const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
         d1 = M[cell];
         d2 = M[N3 + cell];
         d3 = M[2 * N3 + cell];
@@ -347,7 +385,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, 3) pass3_kernel(PassArgs a
       s[i2] = scale(m2, sc);
     }
     __syncthreads();
-    fft_tile<T, N, 2, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
+    fft_tile<T, N, 2, -1, 0, 0, C>(s, tw, nullptr, nullptr, 0);
     // RB-point forward y DFT over k2, twiddle e^{-2 pi i k1 m1 / N}, store
     // to rows RB k1 + m1
 #pragma unroll
@@ -372,14 +410,52 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, 3) pass3_kernel(PassArgs a
   }
 }
 
+// mid3[tile][w] = mid[cell] for the z tiles of pass B: tile = k1 (N / TPX) +
+// xr, w = n TP + t, pencil t = k2 TPX + xo, cell (x, y, z) = (xr TPX + xo,
+// k1 + RA k2, n).
+template <int N>
+__global__ void pass3_ids_kernel(const uchar4* __restrict__ mid, uchar4* __restrict__ mid3) {
+  using C3 = Cfg3<float, N>;
+  constexpr int TP = C3::TPZ, TPX = C3::TPX, RA = C3::RA;
+  const size_t total = (size_t)N * N * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int tile = (int)(e / ((size_t)TP * N)), w = (int)(e % ((size_t)TP * N));
+    const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
+    const int t = w % TP, n = w / TP;
+    mid3[e] = mid[(size_t)n * N * N + (size_t)(k1 + RA * (t / TPX)) * N + x0 + t % TPX];
+  }
+}
+
+// One pass of the three-pass chain over nv vectors; the shared memory of
+// each tile kind is fixed by its geometry (x tiles: the five-pass x layout
+// plus the kappa tables and, for pass C, the scratch tile; z tiles: the
+// tile, the twiddles and the material table).
 template <typename T, int N, int OP>
-cudaError_t launch_pass3(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st) {
+cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st) {
+  using C3 = Cfg3<T, N>;
+  constexpr bool ZP = is_z_op<OP>();
+  size_t smem;
+  if constexpr (ZP)
+    smem = C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) + (((size_t)9 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);
+  else
+    smem = C3::C::SMEM + ((OP == OP_POST || OP == OP_POST_T0) ? (size_t)C3::TP * N * sizeof(cx<T>) : 0);
+  const size_t tiles = (size_t)nv * (ZP ? C3::ZTILES : C3::TILES);
   auto kern = pass3_kernel<T, N, OP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)tiles, Cfg<T, N>::THREADS, smem, st>>>(a);
+  kern<<<(unsigned)tiles, pass3_threads<T, N, OP>(), smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// the pass-B order of the material ids (device, N^3 uchar4), built once per context
+template <int N>
+cudaError_t build_pass3_ids_n(const void* mid, void* mid3, cudaStream_t st) {
+  const size_t total = (size_t)N * N * N;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 152u * 16u) blocks = 152u * 16u;
+  pass3_ids_kernel<N><<<(unsigned)blocks, 256, 0, st>>>(static_cast<const uchar4*>(mid), static_cast<uchar4*>(mid3));
   return cudaGetLastError();
 }
 

@@ -180,6 +180,14 @@ cudaError_t launch_t0(pcx_ctx* c, const KParams& kp, const void* R, void* W, int
              : run_apply_t<float>(c, kp, R, W, nvec, chunk, c->scratch, nullptr, 1, s, true);
 }
 
+cudaError_t launch_t0_scratch(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,
+                              void* scratch, cudaStream_t s) {
+  if (nvec == 0) return cudaSuccess;
+  const int chunk = apply_chunk(c, precision);
+  return precision == PCX_FP64 ? run_apply_t<double>(c, kp, R, W, nvec, chunk, scratch, nullptr, 1, s, true)
+                               : run_apply_t<float>(c, kp, R, W, nvec, chunk, scratch, nullptr, 1, s, true);
+}
+
 cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
                          cudaStream_t s) {
   if (nvec == 0) return cudaSuccess;

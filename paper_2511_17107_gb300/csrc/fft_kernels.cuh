@@ -61,6 +61,7 @@ template <> struct Plan<16, 8> { static constexpr int R0 = 4, R1 = 4, R2 = 0, NS
 template <> struct Plan<32, 8> { static constexpr int R0 = 8, R1 = 4, R2 = 0, NST = 2; };
 template <> struct Plan<64, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 0, NST = 2; };
 template <> struct Plan<128, 8> { static constexpr int R0 = 8, R1 = 4, R2 = 4, NST = 3; };
+template <> struct Plan<128, 32> { static constexpr int R0 = 16, R1 = 8, R2 = 0, NST = 2; };
 template <> struct Plan<256, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 4, NST = 3; };
 
 // Tile shape of the complex64 passes (elements per thread, pencils x points
@@ -72,10 +73,12 @@ template <> struct Plan<256, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 4, N
 #define PCX_TN32 2048
 #endif
 
-template <typename T, int N>
-struct Cfg {
-  static constexpr int E = sizeof(T) == 4 ? PCX_E32 : 8;
-  static constexpr int TN = sizeof(T) == 4 ? PCX_TN32 : 1024;    // pencils x points per component
+// Tile geometry: E elements per thread and stage, TN pencils x points per
+// component (TP pencils per CTA).
+template <typename T, int N, int TN_, int E_>
+struct CfgG {
+  static constexpr int E = E_;
+  static constexpr int TN = TN_;
   static constexpr int TP = (TN / N < N * N) ? TN / N : N * N;   // pencils per CTA
   static constexpr int THREADS = 3 * TP * N / E;
   // padded component stride: y/z tiles use N rows of TP + 1, x tiles TP
@@ -86,6 +89,9 @@ struct Cfg {
   using P = Plan<N, E>;
   static constexpr int RL = P::NST == 1 ? P::R0 : (P::NST == 2 ? P::R1 : P::R2);   // last radix
 };
+// the pass kernels' default geometry per precision
+template <typename T, int N>
+struct Cfg : CfgG<T, N, sizeof(T) == 4 ? PCX_TN32 : 1024, sizeof(T) == 4 ? PCX_E32 : 8> {};
 
 struct PassArgs {
   const void* in;
@@ -95,6 +101,7 @@ struct PassArgs {
   const void* tw;      // [N] exp(-2 pi i m / N)
   const void* M;       // [9][N^3] dense cell blocks (when mid == nullptr)
   const void* mid;     // [N^3] uchar4 material ids (E1, E2, E3, V)
+  const void* mid3;    // the same ids in the order of the three-pass z tiles (or null)
   const void* mtab;    // [n_mat][9] block entries per material
   int n_mat;
   KParams kp;
@@ -105,10 +112,10 @@ struct PassArgs {
   int v_base;
 };
 
-template <typename T, int N, int AXIS>
+template <typename T, int N, int AXIS, class CF = Cfg<T, N>>
 struct Tile {
-  static constexpr int TP = Cfg<T, N>::TP;
-  static constexpr int CS = Cfg<T, N>::CS;
+  static constexpr int TP = CF::TP;
+  static constexpr int CS = CF::CS;
   // y/z tiles: pencils fastest, odd row stride TP + 1 (conflict-free for
   // pencil-fastest and point-fastest walks).
   static constexpr int SN = TP + 1;
@@ -218,10 +225,10 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // SRC: 0 = shared memory, 1 = global (first stage only, Ns = 1).
 // DST: 0 = shared memory, 1 = global (last stage only, Ns = N / R).
 // Threads walk butterflies with the pencil index fastest.
-template <typename T, int N, int AXIS, int R, int DIR, int SRC, int DST>
+template <typename T, int N, int AXIS, int R, int DIR, int SRC, int DST, class CF = Cfg<T, N>>
 __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const cx<T>* gin, cx<T>* gout, int qb) {
-  using C = Cfg<T, N>;
-  using TL = Tile<T, N, AXIS>;
+  using C = CF;
+  using TL = Tile<T, N, AXIS, CF>;
   constexpr int NB = N / R;
   constexpr int PER = C::E / R;
   constexpr int N3 = N * N * N;
@@ -278,18 +285,18 @@ __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const c
 
 // Full 1D transform of the tile.  FROM_G: the first stage reads global
 // memory; TO_G: the last stage writes global memory.
-template <typename T, int N, int AXIS, int DIR, int FROM_G, int TO_G>
+template <typename T, int N, int AXIS, int DIR, int FROM_G, int TO_G, class CF = Cfg<T, N>>
 __device__ __forceinline__ void fft_tile(cx<T>* s, const cx<T>* tw, const cx<T>* gin, cx<T>* gout, int qb) {
-  using P = typename Cfg<T, N>::P;
+  using P = typename CF::P;
   if constexpr (P::NST == 1) {
-    stage<T, N, AXIS, P::R0, DIR, FROM_G, TO_G>(s, tw, 1, gin, gout, qb);
+    stage<T, N, AXIS, P::R0, DIR, FROM_G, TO_G, CF>(s, tw, 1, gin, gout, qb);
   } else if constexpr (P::NST == 2) {
-    stage<T, N, AXIS, P::R0, DIR, FROM_G, 0>(s, tw, 1, gin, gout, qb);
-    stage<T, N, AXIS, P::R1, DIR, 0, TO_G>(s, tw, P::R0, gin, gout, qb);
+    stage<T, N, AXIS, P::R0, DIR, FROM_G, 0, CF>(s, tw, 1, gin, gout, qb);
+    stage<T, N, AXIS, P::R1, DIR, 0, TO_G, CF>(s, tw, P::R0, gin, gout, qb);
   } else {
-    stage<T, N, AXIS, P::R0, DIR, FROM_G, 0>(s, tw, 1, gin, gout, qb);
-    stage<T, N, AXIS, P::R1, DIR, 0, 0>(s, tw, P::R0, gin, gout, qb);
-    stage<T, N, AXIS, P::R2, DIR, 0, TO_G>(s, tw, P::R0 * P::R1, gin, gout, qb);
+    stage<T, N, AXIS, P::R0, DIR, FROM_G, 0, CF>(s, tw, 1, gin, gout, qb);
+    stage<T, N, AXIS, P::R1, DIR, 0, 0, CF>(s, tw, P::R0, gin, gout, qb);
+    stage<T, N, AXIS, P::R2, DIR, 0, TO_G, CF>(s, tw, P::R0 * P::R1, gin, gout, qb);
   }
 }
 
@@ -817,11 +824,11 @@ cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream
 
 // Three-pass form of the apply (fft3_kernels.cuh): complex64 at N = 32, 64, 128.
 template <typename T, int N>
-constexpr bool has_pass3() {
+__host__ __device__ constexpr bool has_pass3() {
   return sizeof(T) == 4 && (N == 32 || N == 64 || N == 128);
 }
 template <typename T, int N, int OP>
-cudaError_t launch_pass3(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st);
+cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st);
 
 template <typename T, int N>
 cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
@@ -838,6 +845,7 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
   a.tw = dbl ? c->dev.tw64 : c->dev.tw32;
   a.M = dbl ? c->dev.m64 : c->dev.m32;
   a.mid = c->dev.mid;
+  a.mid3 = nullptr;
   a.mtab = dbl ? c->dev.mtab64 : c->dev.mtab32;
   a.n_mat = n_mat;
   a.kp = kp;
@@ -882,17 +890,16 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
     a.in = x;
     a.out = y;
     if constexpr (has_pass3<T, N>()) {
-      if (c->apply_path != PCX_APPLY_FIVE_PASS) {
+      if (c->apply_path != PCX_APPLY_FIVE_PASS && (c->dev.mid3 || !c->dev.mid)) {
         // three passes, in place on y after the first
-        if ((e = t0 ? launch_pass3<T, N, OP_PRE_T0>(a, tiles, smem, st) : launch_pass3<T, N, OP_PRE>(a, tiles, smem, st))
-            != cudaSuccess)
+        a.mid3 = c->dev.mid3;
+        if ((e = t0 ? launch_pass3<T, N, OP_PRE_T0>(a, nv, st) : launch_pass3<T, N, OP_PRE>(a, nv, st)) != cudaSuccess)
           return e;
         a.in = y;
-        if ((e = t0 ? launch_pass3<T, N, OP_SANDWICH_EPS>(a, tiles, sandwich_smem, st)
-                    : launch_pass3<T, N, OP_SANDWICH>(a, tiles, sandwich_smem, st)) != cudaSuccess)
+        if ((e = t0 ? launch_pass3<T, N, OP_SANDWICH_EPS>(a, nv, st) : launch_pass3<T, N, OP_SANDWICH>(a, nv, st))
+            != cudaSuccess)
           return e;
-        if ((e = t0 ? launch_pass3<T, N, OP_POST_T0>(a, tiles, post_smem, st)
-                    : launch_pass3<T, N, OP_POST>(a, tiles, post_smem, st)) != cudaSuccess)
+        if ((e = t0 ? launch_pass3<T, N, OP_POST_T0>(a, nv, st) : launch_pass3<T, N, OP_POST>(a, nv, st)) != cudaSuccess)
           return e;
         continue;
       }

@@ -25,6 +25,7 @@
 
 #include "dfloat.cuh"
 #include "pcx_internal.h"
+#include "stream_scratch.h"
 
 namespace pcx {
 namespace {
@@ -210,13 +211,9 @@ __global__ void __launch_bounds__(RED) gram_cc_sum_kernel(const double2* __restr
   }
 }
 
-struct Scratch {
-  std::mutex mu;
-  void* part[64] = {};
-  size_t bytes[64] = {};
-};
-Scratch& scratch() {
-  static Scratch s;
+// per-CTA partial sums, one buffer per (device, stream)
+StreamScratch& scratch() {
+  static StreamScratch s;
   return s;
 }
 
@@ -267,24 +264,10 @@ cudaError_t launch_gram_cc(const void* A, int na, const void* B, int nb, size_t 
   const long long L2 = (long long)(L / 2);
   // partials for up to 8 CTAs per SM
   const size_t need = (size_t)8 * sms * na * nb * sizeof(double2);
-  double2* part;
-  size_t cap;
-  {
-    Scratch& sc = scratch();
-    std::lock_guard<std::mutex> lock(sc.mu);
-    if (need > sc.bytes[dev]) {
-      if (sc.part[dev]) {
-        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
-        cudaFree(sc.part[dev]);
-      }
-      sc.part[dev] = nullptr;
-      sc.bytes[dev] = 0;
-      if ((e = cudaMalloc(&sc.part[dev], need)) != cudaSuccess) return e;
-      sc.bytes[dev] = need;
-    }
-    part = static_cast<double2*>(sc.part[dev]);
-    cap = sc.bytes[dev];
-  }
+  void* pv = nullptr;
+  if ((e = scratch().get(s, need, &pv)) != cudaSuccess) return e;
+  double2* part = static_cast<double2*>(pv);
+  const size_t cap = scratch().capacity(s);
   const float4* a4 = static_cast<const float4*>(A);
   const float4* b4 = static_cast<const float4*>(B);
   int nctas = 0;
@@ -305,5 +288,7 @@ cudaError_t launch_gram_cc(const void* A, int na, const void* B, int nb, size_t 
   gram_cc_sum_kernel<<<(unsigned)(na * nb), RED, 0, s>>>(part, nctas, na, nb, sym ? 1 : 0, G);
   return cudaGetLastError();
 }
+
+void gram_cc_release_stream(cudaStream_t s) { scratch().release(s); }
 
 }  // namespace pcx

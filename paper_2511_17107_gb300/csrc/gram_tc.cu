@@ -20,6 +20,7 @@
 
 #include "cx.cuh"
 #include "pcx_internal.h"
+#include "stream_scratch.h"
 #include "tc.cuh"
 
 namespace pcx {
@@ -268,14 +269,9 @@ __global__ void __launch_bounds__(RED_THREADS) gram_reduce_kernel(const float* _
   }
 }
 
-struct Scratch {
-  std::mutex mu;
-  void* partial[64] = {nullptr};
-  size_t bytes[64] = {0};
-  int* err[64] = {nullptr};
-};
-Scratch& scratch() {
-  static Scratch s;
+// per-CTA partial sums and the give-up flag, one buffer per (device, stream)
+StreamScratch& scratch() {
+  static StreamScratch s;
   return s;
 }
 
@@ -307,25 +303,10 @@ cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t 
   g.chunks_per_cta = (g.nchunks + nctas - 1) / nctas;
   nctas = g.nchunks > 0 ? (g.nchunks + g.chunks_per_cta - 1) / g.chunks_per_cta : 1;
   const size_t pbytes = (size_t)nctas * MT * g.np * sizeof(float);
-  Scratch& sc = scratch();
-  {
-    std::lock_guard<std::mutex> lock(sc.mu);
-    if (!sc.err[dev]) {
-      if ((e = cudaMalloc(&sc.err[dev], sizeof(int))) != cudaSuccess) return e;
-    }
-    if (pbytes > sc.bytes[dev]) {
-      if (sc.partial[dev]) {
-        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
-        cudaFree(sc.partial[dev]);
-      }
-      sc.partial[dev] = nullptr;
-      sc.bytes[dev] = 0;
-      if ((e = cudaMalloc(&sc.partial[dev], pbytes)) != cudaSuccess) return e;
-      sc.bytes[dev] = pbytes;
-    }
-    g.partial = static_cast<float*>(sc.partial[dev]);
-    g.err = sc.err[dev];
-  }
+  void* buf = nullptr;   // [flag (256 bytes)][partials]
+  if ((e = scratch().get(s, 256 + pbytes, &buf)) != cudaSuccess) return e;
+  g.err = static_cast<int*>(buf);
+  g.partial = reinterpret_cast<float*>(static_cast<char*>(buf) + 256);
   const int stage_bytes = 2 * tile_bytes(MT) + (g.same ? 0 : 2 * tile_bytes(g.np));
   const int ncol = g.same ? na : na + nb;
   const size_t smem = 2 * (size_t)stage_bytes + (size_t)NRAW * ncol * KC * 8 + 64;
@@ -337,5 +318,7 @@ cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t 
   gram_reduce_kernel<<<(unsigned)(na * nb), RED_THREADS, 0, s>>>(g.partial, (int)nctas, na, nb, g.np, g.err, G);
   return cudaGetLastError();
 }
+
+void gram_tc_release_stream(cudaStream_t s) { scratch().release(s); }
 
 }  // namespace pcx

@@ -26,6 +26,7 @@
 
 #include "dfloat.cuh"
 #include "pcx_internal.h"
+#include "stream_scratch.h"
 
 namespace pcx {
 namespace {
@@ -220,39 +221,21 @@ __global__ void __launch_bounds__(XTHREADS) gram_x_reduce_kernel(const double2* 
   }
 }
 
-struct XScratch {
-  std::mutex mu;
-  void* partial[64] = {nullptr};
-  size_t bytes[64] = {0};
-};
-XScratch& xscratch() {
-  static XScratch s;
+// partial sums, one buffer per (device, stream)
+StreamScratch& xscratch() {
+  static StreamScratch s;
   return s;
 }
 
 }  // namespace
 
 namespace {
-// per-device partial-sum scratch of at least `bytes`
-cudaError_t x_partials(size_t bytes, double2** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  XScratch& sc = xscratch();
-  std::lock_guard<std::mutex> lock(sc.mu);
-  if (bytes > sc.bytes[dev]) {
-    if (sc.partial[dev]) {
-      if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
-      cudaFree(sc.partial[dev]);
-    }
-    sc.partial[dev] = nullptr;
-    sc.bytes[dev] = 0;
-    if ((e = cudaMalloc(&sc.partial[dev], bytes)) != cudaSuccess) return e;
-    sc.bytes[dev] = bytes;
-  }
-  *out = static_cast<double2*>(sc.partial[dev]);
-  return cudaSuccess;
+// partial-sum scratch of at least `bytes` for work on stream s
+cudaError_t x_partials(size_t bytes, double2** out, cudaStream_t s) {
+  void* p = nullptr;
+  cudaError_t e = xscratch().get(s, bytes, &p);
+  *out = static_cast<double2*>(p);
+  return e;
 }
 }  // namespace
 
@@ -271,7 +254,7 @@ cudaError_t launch_gram_dd(const void* A, int na, const void* B, int nb, size_t 
   rows = ((rows + XL - 1) / XL) * XL;
   const unsigned gz = (unsigned)((L + rows - 1) / rows);
   double2* partial = nullptr;
-  if ((e = x_partials((size_t)gz * na * nb * sizeof(double2), &partial)) != cudaSuccess) return e;
+  if ((e = x_partials((size_t)gz * na * nb * sizeof(double2), &partial, s)) != cudaSuccess) return e;
   const dim3 grid(gx, gy, gz);
   if (T == 16)
     gram_dd_kernel<16><<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A), na, static_cast<const double2*>(B), nb,
@@ -302,7 +285,7 @@ cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, cons
   rows = ((rows + XL - 1) / XL) * XL;
   const unsigned gz = (unsigned)((L + rows - 1) / rows);
   double2* partial = nullptr;
-  if ((e = x_partials((size_t)gz * na * nb * sizeof(double2), &partial)) != cudaSuccess) return e;
+  if ((e = x_partials((size_t)gz * na * nb * sizeof(double2), &partial, s)) != cudaSuccess) return e;
   const dim3 grid(gx, gy, gz);
   if (TA == 16)
     gram_x_kernel<16><<<grid, XTHREADS, 0, s>>>(static_cast<const double2*>(A1), na1, static_cast<const double2*>(A2),
@@ -314,5 +297,7 @@ cudaError_t launch_gram_x(const void* A1, int na1, const void* A2, int na2, cons
   gram_x_reduce_kernel<<<(unsigned)(na * nb), XTHREADS, 0, s>>>(partial, (int)gz, na, nb, G);
   return cudaGetLastError();
 }
+
+void gram_x_release_stream(cudaStream_t s) { xscratch().release(s); }
 
 }  // namespace pcx

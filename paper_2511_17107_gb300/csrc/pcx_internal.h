@@ -38,6 +38,7 @@ struct DeviceTables {
   void* mtab64 = nullptr;  // [n_mat][9] double: e11 e22 e33 re12 im12 re13 im13 re23 im23
   void* mtab32 = nullptr;  // [n_mat][9] float
   int n_mat = 0;
+  void* mid3 = nullptr;    // [N^3] uchar4: mid in the order of the three-pass z tiles (N = 32, 64, 128)
   // M as dense blocks (caller-supplied cell blocks, or more than 255 materials)
   void* m64 = nullptr;     // [9][N^3] double: d1 d2 d3 re12 im12 re13 im13 re23 im23
   void* m32 = nullptr;     // [9][N^3] float
@@ -79,6 +80,8 @@ struct pcx_ctx {
   void* stage_y = nullptr;
   size_t stage_bytes = 0;       // bytes of the two slots together, per buffer
   cudaStream_t copy_stream[2] = {nullptr, nullptr};   // host->device, device->host
+  // streams of the k-points that pcx_solve runs at the same time (created on first use)
+  std::vector<cudaStream_t> solve_streams;
   cudaEvent_t slot_event[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   std::string err;
 };
@@ -90,6 +93,7 @@ pcx_status validate_desc(const pcx_setup_desc* d, std::string& err);
 pcx_status sample_blocks(const pcx_setup_desc* d, const double* A, std::vector<double>& blocks,
                          std::vector<int32_t>* ids, std::string& err);
 long long first_non_hpd(const std::vector<double>& blocks);
+long long crossdof_unproven(int n, int n_mat, const double* eps, const std::vector<int32_t>& ids, std::string* why);
 pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c);
 KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma);
 double gamma_rule(const double k[3]);
@@ -101,6 +105,9 @@ cudaError_t launch_t0(pcx_ctx* c, const KParams& kp, const void* R, void* W, int
 // apply with the context-owned scratch (allocated on first use / growth)
 cudaError_t launch_apply(pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int precision,
                          cudaStream_t s);
+// T0 with caller-provided scratch of apply_scratch_bytes(c, precision, nvec) bytes
+cudaError_t launch_t0_scratch(const pcx_ctx* c, const KParams& kp, const void* R, void* W, int nvec, int precision,
+                              void* scratch, cudaStream_t s);
 // apply with caller-provided scratch of apply_scratch_bytes(c, precision, nvec) bytes
 cudaError_t launch_apply_scratch(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec,
                                  int precision, void* scratch, cudaStream_t s);
@@ -111,6 +118,8 @@ cudaError_t launch_apply_noalloc(const pcx_ctx* c, const KParams& kp, const void
 int apply_chunk(const pcx_ctx* c, int precision);
 // pass structure the apply runs: PCX_APPLY_FIVE_PASS, PCX_APPLY_THREE_PASS, or 7 (M_CrossDoF)
 int effective_apply_path(const pcx_ctx* c, int precision);
+// dev.mid3 from dev.mid (allocates; a no-op where the three-pass form does not exist)
+cudaError_t build_pass3_ids(pcx_ctx* c);
 // k-batched apply: nk groups of vec_per_k vectors, group i at kps_host[i]
 cudaError_t launch_apply_kbatch(pcx_ctx* c, const KParams* kps_host, int nk, int vec_per_k, const void* X, void* Y,
                                 int precision, cudaStream_t s);
@@ -162,6 +171,10 @@ bool gram_tc_supported(int na, int nb, size_t L);
 bool gram_cc_supported(const void* A, const void* B, int na, int nb, size_t L);
 cudaError_t launch_gram_cc(const void* A, int na, const void* B, int nb, size_t L, double* G, cudaStream_t s);
 void set_gram_path(int path);
+// free the per-stream partial-sum buffers of the Gram kernels for stream s
+void gram_cc_release_stream(cudaStream_t s);
+void gram_tc_release_stream(cudaStream_t s);
+void gram_x_release_stream(cudaStream_t s);
 int get_gram_path();
 // G = [A1 | A2]^H B: A1 (na1 columns) and A2 (na2 columns) complex128, B
 // complex64; double-float accumulation on the FP32 pipes.

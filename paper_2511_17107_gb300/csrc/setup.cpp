@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "linalg.h"
 #include "pcx_internal.h"
 
 namespace pcx {
@@ -333,6 +334,81 @@ long long first_non_hpd(const std::vector<double>& blocks) {
   return -1;
 }
 
+// Sec. 3.3: sufficient conditions for M_CrossDoF (Sec. 3.2.2) to be HPD.
+// Assumption 3.1 (the eigenvalues of every material's eps_1 lie in (0, 1])
+// together with either Assumption 3.2 (strict diagonal dominance; with
+// several materials it is checked row by row on the assembled matrix, whose
+// off-diagonal rows hold the four-point means (e_ij(q) + e_ij(q')) / 8 of the
+// symmetrised transfers) or Assumption 3.3 (a zero off-diagonal entry; with
+// several materials, a position that is zero in every material, so that
+// every eps_1 is tridiagonal in one common ordering).  Returns -1 when they
+// hold, else the first cell where the guarantee fails (0 when a material
+// breaks Assumption 3.1) and the reason in *why.
+long long crossdof_unproven(int n, int n_mat, const double* eps, const std::vector<int32_t>& ids, std::string* why) {
+  std::vector<cd> inv(9 * (size_t)n_mat);
+  for (int mt = 0; mt < n_mat; ++mt) {
+    cd a[9];
+    for (int i = 0; i < 9; ++i) a[i] = cd(eps[18 * mt + 2 * i], eps[18 * mt + 2 * i + 1]);
+    if (!invert3c(a, &inv[9 * mt])) {
+      if (why) *why = "singular permittivity of material " + std::to_string(mt);
+      return 0;
+    }
+    std::vector<cd> h(inv.begin() + 9 * mt, inv.begin() + 9 * mt + 9), v;
+    std::vector<double> w;
+    herm_eig(3, h, w, v);
+    if (!(w[0] > 0) || w[2] > 1 + 1e-12) {
+      if (why)
+        *why = "eps_1 of material " + std::to_string(mt) + " has eigenvalues outside (0, 1] (Assumption 3.1)";
+      return 0;
+    }
+  }
+  // Assumption 3.3: an off-diagonal position that is zero in every material
+  const int pos[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  for (const auto& pq : pos) {
+    bool zero = true;
+    for (int mt = 0; mt < n_mat && zero; ++mt) zero = inv[9 * mt + 3 * pq[0] + pq[1]] == cd(0, 0);
+    if (zero) return -1;
+  }
+  // Assumption 3.2 on the assembled rows
+  const size_t n3 = (size_t)n * n * n;
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;   // n is a power of two
+  const int msk = n - 1;
+  auto at = [&](size_t q, const int* o) -> size_t {
+    const int x = (int)(q & msk), y = (int)((q >> lg) & msk), z = (int)(q >> (2 * lg));
+    return ((size_t)((z + o[0]) & msk) << (2 * lg)) | ((size_t)((y + o[1]) & msk) << lg) | (size_t)((x + o[2]) & msk);
+  };
+  auto e = [&](int mt, int i, int j) { return inv[9 * mt + 3 * i + j]; };
+  // neighbour offsets (dz, dy, dx) of the transfers T_01, T_02, T_12 and of their transposes
+  const int t01[4][3] = {{0, 0, 0}, {0, 0, -1}, {0, 1, 0}, {0, 1, -1}};
+  const int t02[4][3] = {{0, 0, 0}, {0, 0, -1}, {1, 0, 0}, {1, 0, -1}};
+  const int t12[4][3] = {{0, 0, 0}, {0, -1, 0}, {1, 0, 0}, {1, -1, 0}};
+  const int* id0 = &ids[0];
+  const int* id1 = &ids[n3];
+  const int* id2 = &ids[2 * n3];
+  for (size_t q = 0; q < n3; ++q) {
+    double r0 = 0, r1 = 0, r2 = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int m01[3] = {-t01[k][0], -t01[k][1], -t01[k][2]};
+      const int m02[3] = {-t02[k][0], -t02[k][1], -t02[k][2]};
+      const int m12[3] = {-t12[k][0], -t12[k][1], -t12[k][2]};
+      r0 += std::abs(e(id0[q], 0, 1) + e(id1[at(q, t01[k])], 0, 1)) / 8;
+      r0 += std::abs(e(id0[q], 0, 2) + e(id2[at(q, t02[k])], 0, 2)) / 8;
+      r1 += std::abs(e(id0[at(q, m01)], 0, 1) + e(id1[q], 0, 1)) / 8;
+      r1 += std::abs(e(id1[q], 1, 2) + e(id2[at(q, t12[k])], 1, 2)) / 8;
+      r2 += std::abs(e(id0[at(q, m02)], 0, 2) + e(id2[q], 0, 2)) / 8;
+      r2 += std::abs(e(id1[at(q, m12)], 1, 2) + e(id2[q], 1, 2)) / 8;
+    }
+    if (!(e(id0[q], 0, 0).real() > r0) || !(e(id1[q], 1, 1).real() > r1) || !(e(id2[q], 2, 2).real() > r2)) {
+      if (why)
+        *why = "no material position zero in every eps_1 (Assumption 3.3) and the assembled M_CrossDoF is "
+               "not strictly diagonally dominant (Assumption 3.2)";
+      return (long long)q;
+    }
+  }
+  return -1;
+}
+
 pcx_status validate_desc(const pcx_setup_desc* d, std::string& err) {
   const int n = d->n;
   if (!is_pow2(n) || n < 8 || n > 256) {
@@ -378,8 +454,19 @@ pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c) {
   const bool use_ids = !d->cell_blocks && d->n_mat <= 255;
   st = sample_blocks(d, c->A, c->blocks, use_ids ? &ids : nullptr, c->err);
   if (st != PCX_OK) return st;
+  if (c->m_kind == PCX_M_CROSSDOF) {
+    // M_CrossDoF: the sufficient conditions of Sec. 3.3
+    std::string why;
+    const long long bad = crossdof_unproven(n, d->n_mat, d->eps, ids, &why);
+    if (bad >= 0) {
+      long long x = bad % n, y = (bad / n) % n, z = bad / ((long long)n * n);
+      c->err = "pcx_setup: M_CrossDoF not proven HPD (Sec. 3.3): " + why + "; first cell (x, y, z) = (" +
+               std::to_string(x) + ", " + std::to_string(y) + ", " + std::to_string(z) + ")";
+      return PCX_ENOTHPD;
+    }
+  }
   // HPD check of every cell block (Lemma 3.5: spectrum of M = union of blocks)
-  const long long bad = first_non_hpd(c->blocks);
+  const long long bad = c->m_kind == PCX_M_CROSSDOF ? -1 : first_non_hpd(c->blocks);
   if (bad >= 0) {
     long long x = bad % n, y = (bad / n) % n, z = bad / ((long long)n * n);
     c->err = "pcx_setup: cell block not HPD at (x, y, z) = (" + std::to_string(x) + ", " +
@@ -434,7 +521,7 @@ pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c) {
     std::vector<float> t32(t64.begin(), t64.end());
     c->dev.n_mat = d->n_mat;
     if ((e = upload(&c->dev.mid, mid)) != cudaSuccess || (e = upload(&c->dev.mtab64, t64)) != cudaSuccess ||
-        (e = upload(&c->dev.mtab32, t32)) != cudaSuccess)
+        (e = upload(&c->dev.mtab32, t32)) != cudaSuccess || (e = build_pass3_ids(c)) != cudaSuccess)
       goto cuda_error;
   } else {
     std::vector<double> m64(9 * n3);

@@ -17,11 +17,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cnn.h"
@@ -133,9 +136,10 @@ struct Run {
     return PCX_OK;
   }
 
+  void* ascr = nullptr;   // apply / T0 scratch owned by the caller (k-points in flight), else the context's
   cudaError_t apply(const void* X, void* Y, int nvec) {
     tick(&Times::other);
-    cudaError_t e = launch_apply(c, kp, X, Y, nvec, prec, s);
+    cudaError_t e = ascr ? launch_apply_scratch(c, kp, X, Y, nvec, prec, ascr, s) : launch_apply(c, kp, X, Y, nvec, prec, s);
     if (tm) tm->applies += nvec;
     tick(&Times::apply);
     return e;
@@ -158,7 +162,7 @@ struct Run {
       if (learned && learned->params && !learned->off && prec == PCX_FP32)
         e = cnn_precond(c, kp, learned->params, learned->gates, r, w, cnt, s);
       else if (learned && learned->kind == 1)
-        e = sandwich_precond(c, kp, r, w, cnt, prec, s);
+        e = ascr ? launch_t0_scratch(c, kp, r, w, cnt, prec, ascr, s) : sandwich_precond(c, kp, r, w, cnt, prec, s);
       else
         e = launch_precond(c, kp, r, w, cnt, prec, s);
       a0 = a1;
@@ -316,9 +320,11 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       if ((st = run.upload_c(xw)) != PCX_OK) return st;
       CK(launch_combine(run.S.p, n, static_cast<double*>(run.C.p), na, 1.0, run.col(run.S, w0), L, run.prec, run.s));
       if ((st = run.cholqr(run.col(run.S, w0), na, run.R.p, ok)) != PCX_OK) return st;
-      if (!ok) {   // rank-deficient W: second orthogonalisation pass with SVQB fallback below
-        ok = true;
-      }
+      // A rank-deficient W (Cholesky of its Gram matrix fails) stays as it
+      // is: the Rayleigh-Ritz step below works on the scaled Gram matrix of
+      // [X P W] and drops every direction whose eigenvalue is below `drop`
+      // of the largest, which removes W's dependent columns.
+      ok = true;
     }
     CK(run.apply(run.col(run.S, w0), run.col(run.AS, w0), na));
     // Rayleigh-Ritz on S = [X P W]
@@ -636,6 +642,7 @@ struct KSolve {
   Times *t32, *t64;
   int iters32 = 0, iters64 = 0;
   Learned* learned = nullptr;
+  std::string* err = nullptr;   // where messages go (the context's, or a worker's own)
 };
 
 // LOBPCG for one k with penalty coefficient gamma (<= 0: the rule of Sec. 2).
@@ -663,7 +670,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
   r64.verbose = ks.o->verbose;
   if (ks.o->stats) r64.tm = ks.t64;
   if ((st = r64.alloc_all()) != PCX_OK) {
-    c->err = r64.err;
+    *ks.err = r64.err;
     return st;
   }
   if (ks.o->precision == PCX_FP32) {
@@ -680,13 +687,14 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
     r32.t0 = r64.t0;
     if (ks.o->stats) r32.tm = ks.t32;
     if ((st = r32.alloc_all()) != PCX_OK) {
-      c->err = r32.err;
+      *ks.err = r32.err;
       return st;
     }
-    cudaError_t e = launch_fill_random(r32.S.p, n, L, ks.seed + ik, PCX_FP32, s);
+    cudaError_t e = ks.o->x0 ? launch_convert(ks.o->x0, PCX_FP64, r32.S.p, PCX_FP32, (size_t)n * L, s)
+                             : launch_fill_random(r32.S.p, n, L, ks.seed + ik, PCX_FP32, s);
     if (e == cudaSuccess && kz) e = launch_deflate_p0(r32.S.p, n, c->n, PCX_FP32, s);
     if (e != cudaSuccess) {
-      c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+      *ks.err = std::string("pcx_solve: ") + cudaGetErrorString(e);
       return PCX_ECUDA;
     }
     int it32 = 0;
@@ -697,7 +705,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
     iters_total += it32;
     ks.iters32 += it32;
     if (st != PCX_OK && st != PCX_ENOCONV) {
-      c->err = r32.err;
+      *ks.err = r32.err;
       return st;
     }
     // refine: X, AX in FP64, directions in FP32
@@ -707,13 +715,14 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
     r64.tick(&Times::other);
     iters_total += itr;
     ks.iters64 += itr;
-    if (st != PCX_OK && st != PCX_ENOCONV) c->err = r64.err.empty() ? r32.err : r64.err;
+    if (st != PCX_OK && st != PCX_ENOCONV) *ks.err = r64.err.empty() ? r32.err : r64.err;
     return st;
   }
-  cudaError_t e = launch_fill_random(r64.S.p, n, L, ks.seed + ik, PCX_FP64, s);
+  cudaError_t e = ks.o->x0 ? cudaMemcpyAsync(r64.S.p, ks.o->x0, (size_t)n * L * 16, cudaMemcpyDeviceToDevice, s)
+                           : launch_fill_random(r64.S.p, n, L, ks.seed + ik, PCX_FP64, s);
   if (e == cudaSuccess && kz) e = launch_deflate_p0(r64.S.p, n, c->n, PCX_FP64, s);
   if (e != cudaSuccess) {
-    c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+    *ks.err = std::string("pcx_solve: ") + cudaGetErrorString(e);
     return PCX_ECUDA;
   }
   int it64 = 0;
@@ -723,7 +732,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
   r64.tick(&Times::other);
   iters_total += it64;
   ks.iters64 += it64;
-  if (st != PCX_OK && st != PCX_ENOCONV) c->err = r64.err;
+  if (st != PCX_OK && st != PCX_ENOCONV) *ks.err = r64.err;
   return st;
 }
 
@@ -743,6 +752,187 @@ pcx_status penalty_share(Run& r64, int nev, const std::vector<double>& theta, do
     const double den = std::fabs(theta[j]) * q[nev + j];
     const double share = den > 0 ? r64.kp.gamma * q[j] / den : INFINITY;
     worst = std::max(worst, share);
+  }
+  return PCX_OK;
+}
+
+// Host outputs of pcx_solve (any may be null) and the device eigenvector buffer.
+struct KOut {
+  double* eig;
+  double* res;
+  int* iters;
+  void* vec;
+};
+
+// One k of pcx_solve: LOBPCG with the spurious-mode guard (gamma x4 while a
+// wanted pair is a penalty mode), then the k's outputs.  r64 / r32 are the
+// caller's runs, whose buffers carry over from one k to the next.
+pcx_status solve_k(KSolve& ks, const double* k, int ik, double penalty_tol, const KOut& out, Run& r64, Run& r32,
+                   int& raises, double& gamma_last, bool& noconv) {
+  pcx_ctx* c = ks.c;
+  const int nev = ks.nev;
+  const int max_raises = 4;
+  const size_t L = (size_t)3 * c->n * c->n * c->n;
+  double gamma = ks.o->gamma > 0 ? ks.o->gamma : make_kparams(c, k, 0.0).gamma;
+  std::vector<double> theta, res;
+  int iters_total = 0;
+  pcx_status st;
+  for (int attempt = 0;; ++attempt) {
+    iters_total = 0;
+    st = solve_one_k(ks, k, gamma, ik, r64, r32, theta, res, iters_total);
+    if (st != PCX_OK && st != PCX_ENOCONV) return st;
+    if (st != PCX_OK || penalty_tol < 0) break;
+    double share = 0.0;
+    pcx_status sg = penalty_share(r64, nev, theta, share);
+    if (sg != PCX_OK) {
+      *ks.err = r64.err;
+      return sg;
+    }
+    if (r64.verbose) std::fprintf(stderr, "[pcx] k %d gamma %.6g penalty share %.3e\n", ik, gamma, share);
+    if (share <= penalty_tol) break;
+    if (attempt >= max_raises) {
+      *ks.err = "pcx_solve: penalty modes among the wanted eigenpairs after raising gamma " +
+                std::to_string(max_raises) + " times";
+      return PCX_ENUMERIC;
+    }
+    gamma *= 4.0;   // lift gamma * lambda_1^B above the wanted part of the spectrum
+    ++raises;
+  }
+  gamma_last = gamma;
+  noconv = st == PCX_ENOCONV;
+  if (noconv) *ks.err = "pcx_solve: iteration cap reached";
+  for (int j = 0; j < nev; ++j) {
+    if (out.eig) out.eig[(size_t)ik * nev + j] = theta[j];
+    if (out.res) out.res[(size_t)ik * nev + j] = res[j];
+  }
+  if (out.iters) out.iters[ik] = iters_total;
+  if (out.vec) {
+    cudaError_t e = cudaMemcpyAsync(static_cast<char*>(out.vec) + (size_t)ik * nev * L * 16, r64.S.p,
+                                    (size_t)nev * L * 16, cudaMemcpyDeviceToDevice, ks.s);
+    if (e != cudaSuccess) {
+      *ks.err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+      return PCX_ECUDA;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(ks.s);
+  if (e != cudaSuccess) {
+    *ks.err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+    return PCX_ECUDA;
+  }
+  return PCX_OK;
+}
+
+// pcx_solve with `conc` k-points in flight: one host thread per slot, each
+// with its own stream (kept in the context), search-space buffers, apply
+// scratch and counters, taking the next k from a shared counter.  The GPU
+// runs one k's kernels while another k's host does its Rayleigh-Ritz step.
+// The slots' streams start after the work already queued on the caller's
+// stream; every slot is synchronised before this returns.
+pcx_status solve_concurrent(KSolve& base, const double* kpts, int nk, double penalty_tol, const KOut& out, int conc,
+                            int& raises, double& gamma_last, pcx_status& result) {
+  pcx_ctx* c = base.c;
+  cudaError_t e;
+  while ((int)c->solve_streams.size() < conc) {
+    cudaStream_t st = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+      c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+      return PCX_ECUDA;
+    }
+    c->solve_streams.push_back(st);
+  }
+  cudaEvent_t ready = nullptr;
+  if ((e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventRecord(ready, base.s)) != cudaSuccess) {
+    if (ready) cudaEventDestroy(ready);
+    c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
+    return PCX_ECUDA;
+  }
+  // apply / T0 scratch of one slot: the larger of the two precisions' needs
+  const int n3cols = 3 * base.n;
+  const size_t scr = std::max(apply_scratch_bytes(c, PCX_FP64, n3cols), apply_scratch_bytes(c, PCX_FP32, n3cols));
+  std::atomic<int> next{0};
+  std::atomic<bool> failed{false};
+  std::mutex mu;
+  pcx_status first_err = PCX_OK;
+  std::string first_msg;
+  struct Slot {
+    KSolve ks;
+    Times t32, t64;
+    Learned lrn;
+    std::string err;
+    int raises = 0;
+    double gamma_last = 0.0;
+    bool noconv = false;
+  };
+  std::vector<Slot> slots(conc);
+  auto work = [&](int w) {
+    Slot& sl = slots[w];
+    sl.ks = base;
+    sl.ks.s = c->solve_streams[w];
+    sl.ks.t32 = &sl.t32;
+    sl.ks.t64 = &sl.t64;
+    sl.ks.iters32 = sl.ks.iters64 = 0;
+    sl.ks.err = &sl.err;
+    if (base.learned) {
+      sl.lrn = *base.learned;
+      sl.ks.learned = &sl.lrn;
+    }
+    auto fail = [&](pcx_status st, const std::string& msg) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (first_err == PCX_OK) {
+        first_err = st;
+        first_msg = msg;
+      }
+      failed = true;
+    };
+    cudaError_t ee = cudaSetDevice(c->device);
+    if (ee == cudaSuccess) ee = cudaStreamWaitEvent(sl.ks.s, ready, 0);
+    DevBuf ascr;
+    if (ee == cudaSuccess) ee = ascr.alloc(scr);
+    if (ee != cudaSuccess) {
+      fail(ee == cudaErrorMemoryAllocation ? PCX_ENOMEM : PCX_ECUDA,
+           std::string("pcx_solve: ") + cudaGetErrorString(ee));
+      return;
+    }
+    Run r64, r32;
+    r64.ascr = ascr.p;
+    r32.ascr = ascr.p;
+    for (int ik = next++; ik < nk && !failed; ik = next++) {
+      bool noconv = false;
+      pcx_status st = solve_k(sl.ks, kpts + 3 * ik, ik, penalty_tol, out, r64, r32, sl.raises, sl.gamma_last, noconv);
+      if (st != PCX_OK) {
+        fail(st, sl.err);
+        break;
+      }
+      sl.noconv = sl.noconv || noconv;
+    }
+    cudaStreamSynchronize(sl.ks.s);
+  };
+  std::vector<std::thread> threads;
+  for (int w = 0; w < conc; ++w) threads.emplace_back(work, w);
+  for (auto& t : threads) t.join();
+  cudaEventDestroy(ready);
+  // counters of the slots
+  for (Slot& sl : slots) {
+    for (double Times::*f : {&Times::apply, &Times::gram, &Times::rr, &Times::other, &Times::precond}) {
+      base.t32->*f += sl.t32.*f;
+      base.t64->*f += sl.t64.*f;
+    }
+    base.t32->applies += sl.t32.applies;
+    base.t64->applies += sl.t64.applies;
+    base.iters32 += sl.ks.iters32;
+    base.iters64 += sl.ks.iters64;
+    raises += sl.raises;
+    gamma_last = std::max(gamma_last, sl.gamma_last);
+    if (sl.noconv) {
+      result = PCX_ENOCONV;
+      c->err = "pcx_solve: iteration cap reached";
+    }
+    if (base.learned) base.learned->fallbacks += sl.lrn.fallbacks;
+  }
+  if (first_err != PCX_OK) {
+    c->err = first_msg;
+    return first_err;
   }
   return PCX_OK;
 }
@@ -774,8 +964,6 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
     return PCX_EINVAL;
   }
   const double penalty_tol = o.penalty_tol == 0 ? 1e-6 : o.penalty_tol;
-  const int max_raises = 4;
-  const size_t L = (size_t)3 * c->n * c->n * c->n;
   pcx_status result = PCX_OK;
   Times t32, t64;
   KSolve ks;
@@ -818,56 +1006,19 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
   }
   const auto t_start = std::chrono::steady_clock::now();
   if (o.stats) std::memset(o.stats, 0, sizeof(*o.stats));
-  for (int ik = 0; ik < nk; ++ik) {
-    const double* k = kpts + 3 * ik;
-    double gamma = o.gamma > 0 ? o.gamma : make_kparams(c, k, 0.0).gamma;
-    std::vector<double> theta, res;
-    int iters_total = 0;
-    Run r64, r32;
-    pcx_status st;
-    for (int attempt = 0;; ++attempt) {
-      iters_total = 0;
-      st = solve_one_k(ks, k, gamma, ik, r64, r32, theta, res, iters_total);
-      if (st != PCX_OK && st != PCX_ENOCONV) return st;
-      if (st != PCX_OK || penalty_tol < 0) break;
-      double share = 0.0;
-      pcx_status sg = penalty_share(r64, nev, theta, share);
-      if (sg != PCX_OK) {
-        c->err = r64.err;
-        return sg;
-      }
-      if (r64.verbose) std::fprintf(stderr, "[pcx] k %d gamma %.6g penalty share %.3e\n", ik, gamma, share);
-      if (share <= penalty_tol) break;
-      if (attempt >= max_raises) {
-        c->err = "pcx_solve: penalty modes among the wanted eigenpairs after raising gamma " +
-                 std::to_string(max_raises) + " times";
-        return PCX_ENUMERIC;
-      }
-      gamma *= 4.0;   // lift gamma * lambda_1^B above the wanted part of the spectrum
-      ++raises;
-    }
-    gamma_last = gamma;
-    if (st == PCX_ENOCONV) {
-      result = PCX_ENOCONV;
-      c->err = "pcx_solve: iteration cap reached";
-    }
-    for (int j = 0; j < nev; ++j) {
-      if (eig_out) eig_out[(size_t)ik * nev + j] = theta[j];
-      if (res_out) res_out[(size_t)ik * nev + j] = res[j];
-    }
-    if (iters_out) iters_out[ik] = iters_total;
-    if (vec_out) {
-      cudaError_t e = cudaMemcpyAsync(static_cast<char*>(vec_out) + (size_t)ik * nev * L * 16, r64.S.p,
-                                      (size_t)nev * L * 16, cudaMemcpyDeviceToDevice, s);
-      if (e != cudaSuccess) {
-        c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
-        return PCX_ECUDA;
-      }
-    }
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      c->err = std::string("pcx_solve: ") + cudaGetErrorString(e);
-      return PCX_ECUDA;
+  ks.err = &c->err;
+  const KOut kout{eig_out, res_out, iters_out, vec_out};
+  const int conc = std::min(o.k_concurrency, nk);
+  if (conc > 1 && !o.cnn_params && !o.dump_R) {
+    pcx_status st = solve_concurrent(ks, kpts, nk, penalty_tol, kout, conc, raises, gamma_last, result);
+    if (st != PCX_OK) return st;
+  } else {
+    Run r64, r32;   // buffers reused from one k to the next
+    for (int ik = 0; ik < nk; ++ik) {
+      bool noconv = false;
+      pcx_status st = solve_k(ks, kpts + 3 * ik, ik, penalty_tol, kout, r64, r32, raises, gamma_last, noconv);
+      if (st != PCX_OK) return st;
+      if (noconv) result = PCX_ENOCONV;
     }
   }
   if (o.stats) {

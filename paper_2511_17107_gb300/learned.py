@@ -1,10 +1,13 @@
 """Training of the learned preconditioner correction on solver-generated data.
 
-The correction T(r) = K_P^{-1} r + F3^H g(F3 K_P^{-1} r) (pcx_cnn_precond) is
-trained on pairs (r, e = Op^{-1} r): r are residual columns that the mixed
+The corrected preconditioner T(r) = T0 r + K_A F3^H g(F3 K_A^H r / |k|^2) / |k|^2
+(pcx_cnn_precond; T0 the curl-sandwich approximate inverse, g the gated
+convolution net acting next to eps on the real-space field) is trained on
+pairs (r, e = Op^{-1} r): r are residual columns that the mixed
 precision eigensolver itself produces (pcx_solve's residual dump), e comes
 from the preconditioned conjugate gradient solve pcx_cg_solve, and the loss
-sum_v ||T(r_v) - e_v||^2 / ||e_v||^2 is minimised by Adam.  Every device step
+on the part the correction can reach, sum_v ||g(U_v) - F3 K_A^H (e_v - T0 r_v)||^2
+/ ||K_A^H e_v||^2, is minimised by Adam.  Every device step
 runs in libpcx kernels through the C ABI; this module only sequences the
 calls and holds the tensors.
 """

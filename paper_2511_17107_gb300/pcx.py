@@ -66,7 +66,8 @@ class pcx_solve_opts(C.Structure):
                 ("seed", C.c_uint64), ("verbose", C.c_int), ("stats", C.POINTER(pcx_solve_stats)),
                 ("gamma", C.c_double), ("penalty_tol", C.c_double), ("cnn_params", C.c_void_p),
                 ("dump_R", C.c_void_p), ("dump_cap", C.c_int), ("dump_every", C.c_int), ("precond_kind", C.c_int),
-                ("learned_patience", C.c_int), ("fp32_floor", C.c_double)]
+                ("learned_patience", C.c_int), ("fp32_floor", C.c_double), ("x0", C.c_void_p),
+                ("k_concurrency", C.c_int)]
 
 
 _lib = None
@@ -528,7 +529,8 @@ def pcx_rr_eig(ga, gb, drop_tol=1e-13):
 
 def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
               vec_out=None, stream=None, raise_on_noconv=True, stats=None, gamma=0.0, penalty_tol=0.0,
-              cnn_params=None, dump_R=None, dump_every=0, precond_kind=0, learned_patience=0, fp32_floor=0.0):
+              cnn_params=None, dump_R=None, dump_every=0, precond_kind=0, learned_patience=0, fp32_floor=0.0,
+              x0=None, k_concurrency=0):
     """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status).  Pass a
     pcx_solve_stats instance as ``stats`` to receive counters and timings."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
@@ -538,7 +540,8 @@ def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_
                        _devptr(cnn_params) if cnn_params is not None else None,
                        _devptr(dump_R) if dump_R is not None else None,
                        int(dump_R.shape[0]) if dump_R is not None else 0, int(dump_every), int(precond_kind),
-                       int(learned_patience), float(fp32_floor))
+                       int(learned_patience), float(fp32_floor), _devptr(x0) if x0 is not None else None,
+                       int(k_concurrency))
     eig = np.zeros((nk, nev))
     res = np.zeros((nk, nev))
     its = np.zeros(nk, dtype=np.int32)

@@ -1,9 +1,12 @@
 """GPU parity of the operator apply, the preconditioner and the block
 kernels against the CPU oracle (element by element), through the C ABI.
 
-Tolerances (derived in DESIGN.md, "Parity tolerances"): every output is
-compared as |y_gpu - y_oracle| <= tol * max|y_oracle| with tol = 1e-12 for
-FP64 and 2e-5 for FP32 storage and arithmetic.
+Tolerances: every output is compared as |y_gpu - y_oracle| <= tol *
+max|y_oracle|.  Each 1D transform stage adds at most a few units in the last
+place relative to the largest entry, over log2 N^3 <= 24 stages plus the
+pointwise products (the symbols reach |kappa| <= 2 sqrt 3 / h, absorbed by
+normalising with max|y|): tol = 1e-12 for FP64, and 24 * 4u * 3 ~ 2e-5 with
+u = 6e-8 for FP32 storage and arithmetic.
 """
 import numpy as np
 import pytest

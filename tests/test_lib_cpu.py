@@ -151,3 +151,34 @@ def test_crossdof_setup_validation(pcx):
     with pytest.raises(pcx.PcxError) as ei:
         pcx.pcx_sample_host(s, 8, m_kind=pcx.PCX_M_CROSSDOF, cell_blocks=blocks)
     assert ei.value.status == pcx.PCX_EINVAL
+
+
+def test_crossdof_sec33_conditions(pcx):
+    """M_CrossDoF's HPD check follows Sec. 3.3: Assumption 3.1 (eps_1 in
+    (0, 1]) with a zero off-diagonal shared by every material (3.3) or a
+    strictly diagonally dominant assembled matrix (3.2).  Where the check
+    passes, the oracle's dense M_CrossDoF is HPD; a material outside (0, 1]
+    and a dense rotated tensor that is not diagonally dominant are reported
+    as unproven."""
+    from oracle import crossdof
+    n = 8
+    # the paper's anisotropic eps_1 (zero xz and yz entries, SDD) on a BCC gyroid
+    paper = wl.Structure("g", wl.BCC.copy(), np.stack([wl.VACUUM, wl.paper_anisotropic(16.0)]), 0,
+                         [wl.Shape(wl.SHAPE_GYROID, 1, (1.1, 0))])
+    assert pcx.pcx_sample_host(paper, n, m_kind=pcx.PCX_M_CROSSDOF)[2] == -1
+    m = crossdof.CrossDofM(paper, 6).dense()
+    assert np.linalg.eigvalsh(0.5 * (m + m.conj().T)).min() > 0
+    # a dense, weakly diagonal eps_1 (every off-diagonal nonzero, SDD fails) ...
+    rng = np.random.default_rng(2)
+    u = wl.seeded_unitary(rng)
+    inv = (u * np.array([0.06, 0.5, 0.95])) @ u.conj().T
+    dense = wl.Structure("d", wl.SC.copy(), np.stack([wl.VACUUM, np.linalg.inv(inv)]), 0,
+                         [wl.Shape(wl.SHAPE_SPHERE, 1, (0.5, 0.5, 0.5, 0.3))])
+    assert np.all(np.abs(inv[np.triu_indices(3, 1)]) > 1e-3)
+    assert pcx.pcx_sample_host(dense, n, m_kind=pcx.PCX_M_CROSSDOF)[2] >= 0
+    # ... and a material whose eps_1 has an eigenvalue above 1 (eps below vacuum)
+    weak = wl.Structure("w", wl.SC.copy(), np.stack([wl.VACUUM, 0.5 * wl.VACUUM]), 0,
+                        [wl.Shape(wl.SHAPE_SPHERE, 1, (0.5, 0.5, 0.5, 0.3))])
+    assert pcx.pcx_sample_host(weak, n, m_kind=pcx.PCX_M_CROSSDOF)[2] == 0
+    # the same structures under M_Trivial are judged cell by cell instead
+    assert pcx.pcx_sample_host(dense, n)[2] == -1
