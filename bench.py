@@ -137,8 +137,45 @@ def cpu_oracle_applies(n, seconds_budget=20.0, max_vectors=3):
     return done / dt, done, dt
 
 
+def cpu_oracle_solve16():
+    """The oracle's textbook LOBPCG (FP64 numpy, K_P^{-1}) on configuration 1:
+    16^3 gyrotropic sphere, 10 bands, block 14, to Res <= 1e-8 (1 thread)."""
+    import numpy as np
+
+    import workloads as wl
+    from oracle import eig, fourier, penalty, permittivity
+    n, nev = 16, 10
+    s = wl.sc_gyro_sphere()
+    k = wl.config_k(s.name)[0]
+    g = penalty.gamma_practical(k)
+    blocks = permittivity.cell_blocks(s, n)
+    kap = fourier.kappa(n, s.lattice, k)
+    t0 = time.perf_counter()
+    th, _, res, its = eig.lobpcg(lambda x: fourier.apply_symbols(x, kap, lambda e: permittivity.apply_m(blocks, e), g),
+                                 lambda r: fourier.precondition(r, kap, g), wl.random_block(nev + 4, n, seed=1), nev,
+                                 tol=1e-8, maxit=600)
+    return time.perf_counter() - t0, int(its), float(np.max(res))
+
+
+def cpu_model():
+    """The host CPU's model name and core count (lscpu, else the platform)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return model, os.cpu_count()
+
+
 def cpu_baseline_subprocess():
-    """Run the oracle timing single-threaded in a child process."""
+    """The oracle timed on the host: its whole-vector apply single-threaded in
+    a child process (the line's value), the same apply in one child process
+    per core at once (aggregate rate on all cores), and its LOBPCG solve of
+    configuration 1 (16^3) to Res <= 1e-8."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
             "r = bench.cpu_oracle_applies(%d); print(json.dumps(r))" % (ROOT, N))
@@ -146,8 +183,31 @@ def cpu_baseline_subprocess():
     if out.returncode != 0:
         return None
     v, done, dt = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} whole-vector applies of the 128^3 workload in FP64 numpy ({dt:.1f} s)"}
+    model, ncores = cpu_model()
+    res = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{done} whole-vector applies of the 128^3 workload in FP64 numpy ({dt:.1f} s)",
+           "cpu_model": model, "nproc": ncores}
+    # all cores: one single-threaded child per core, one whole vector each
+    one = ("import sys, json; sys.path.insert(0, %r); import bench; "
+           "r = bench.cpu_oracle_applies(%d, seconds_budget=0.0, max_vectors=1); print(json.dumps(r))" % (ROOT, N))
+    procs = [subprocess.Popen([sys.executable, "-c", one], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, env=env,
+                              text=True) for _ in range(ncores or 1)]
+    rates = []
+    for p in procs:
+        o, _ = p.communicate(timeout=900)
+        if p.returncode == 0:
+            rates.append(json.loads(o.strip().splitlines()[-1])[0])
+    res["all_cores"] = {"value": sum(rates), "unit": UNIT, "cores": len(procs),
+                        "sample": f"{len(rates)} single-threaded children, one per core, each timing one "
+                                  "whole-vector apply while the others run; their rates summed"}
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_oracle_solve16()))" % ROOT)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode == 0:
+        sec, its, mres = json.loads(out.stdout.strip().splitlines()[-1])
+        res["solve_config1"] = {"s": sec, "iterations": its, "max_res": mres, "cores": 1,
+                                "sample": "oracle LOBPCG, 16^3 gyrotropic sphere, 10 bands, Res <= 1e-8"}
+    return res
 
 
 def blockops_table(n, reps=5):
@@ -329,6 +389,171 @@ def library_baselines(pcx, ctx, k, n, block=16, reps=5):
     return out
 
 
+def study_bcc_convergence(pcx, grids=(16, 32, 64, 128), nev=8, tol=1e-7):
+    """Sec. 4.2, tables tab:num:convergence_type1 / type2: BCC-SG in the
+    anisotropic medium at k = (pi, pi, pi), 10th-order stencils (m = 5),
+    M_Trivial and M_CrossDoF, the first eight eigenvalues at N = 16 ... 128;
+    differences between grid levels of the normalised frequency omega/(2 pi)
+    next to the printed ones.  Mixed precision with the curl-sandwich
+    preconditioner; one JSON line."""
+    import numpy as np
+
+    import workloads as wl
+    printed = {"trivial": [[2.58e-02, 7.70e-03, 2.64e-03], [3.09e-02, 1.10e-02, 3.43e-03], [1.65e-02, 1.89e-02, 8.63e-03],
+                           [9.54e-03, 1.62e-02, 1.02e-02], [4.71e-02, 1.45e-02, 4.85e-03], [3.15e-02, 2.10e-02, 7.67e-03],
+                           [3.85e-02, 2.06e-02, 6.66e-03], [5.69e-02, 2.10e-02, 5.73e-03]],
+               "crossdof": [[2.90e-02, 8.21e-03, 2.90e-03], [3.31e-02, 1.21e-02, 3.81e-03], [1.91e-02, 2.30e-02, 1.08e-02],
+                            [1.39e-02, 1.58e-02, 1.27e-02], [5.01e-02, 2.16e-02, 6.28e-03], [4.01e-02, 2.59e-02, 9.60e-03],
+                            [5.10e-02, 2.43e-02, 8.81e-03], [7.02e-02, 2.55e-02, 6.14e-03]]}
+    s = wl.bcc_gyroid()
+    k = np.array([np.pi, np.pi, np.pi])
+    out = {"study": "bcc-sg-convergence", "structure": s.name, "k": "(pi, pi, pi)", "stencil_m": 5, "nev": nev,
+           "tol": tol, "grids": list(grids)}
+    for name, mk in (("trivial", pcx.PCX_M_TRIVIAL), ("crossdof", pcx.PCX_M_CROSSDOF)):
+        lam = []
+        t0 = time.perf_counter()
+        for n in grids:
+            ctx = pcx.setup_structure(s, n, stencil_m=5, m_kind=mk)
+            ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, tol, block=nev + 4, precision=pcx.PCX_FP32,
+                                             precond_kind=1, raise_on_noconv=False)
+            lam.append(ev[0])
+        lam = np.array(lam)
+        f = np.sqrt(lam) / (2 * np.pi)
+        d = np.abs(np.diff(f, axis=0)).T          # [eigenvalue][level]
+        p = np.array(printed[name])
+        out[name] = {"omega2": lam.tolist(), "diff_freq": d.tolist(), "printed": p.tolist(),
+                     "ratio_to_printed": (d / p).tolist(), "s": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def study_frequency_difference(pcx, n=128, nk=30, nev=10, tol=1e-6, m=1, k_concurrency=4):
+    """Sec. 4.1, table tab:frequency_difference: the relative difference of
+    the band frequencies computed with M_Trivial and M_CrossDoF over the
+    band path (max and mean over k and the first nev bands) for BCC-SG and
+    BCC-DG in the anisotropic medium.  The paper uses N = 120; the grid here
+    is a power of two (N = 128).  Path H'-Gamma-P-N-H through the BCC points
+    in the order the paper lists them, nk points uniform in arc length."""
+    import numpy as np
+
+    import workloads as wl
+    printed = {"bcc-sg": (4.71e-3, 1.47e-3), "bcc-dg": (4.72e-3, 1.08e-3)}
+    path = wl.k_path(wl.BCC_POINTS, ["H'", "G", "P", "N", "H"], nk)
+    out = {"study": "frequency-difference", "N": n, "k_points": nk, "nev": nev, "stencil_m": m, "tol": tol}
+    for dbl in (False, True):
+        s = wl.bcc_gyroid(double=dbl)
+        key = "bcc-dg" if dbl else "bcc-sg"
+        omega = {}
+        t0 = time.perf_counter()
+        for name, mk in (("trivial", pcx.PCX_M_TRIVIAL), ("crossdof", pcx.PCX_M_CROSSDOF)):
+            ctx = pcx.setup_structure(s, n, stencil_m=m, m_kind=mk)
+            ev, res, its, st = pcx.pcx_solve(ctx, path, nev, tol, block=nev + 4, precision=pcx.PCX_FP32,
+                                             precond_kind=1, raise_on_noconv=False, k_concurrency=k_concurrency)
+            omega[name] = np.sqrt(np.maximum(ev, 0.0))
+        rel = np.abs(omega["trivial"] - omega["crossdof"]) / np.abs(omega["crossdof"])
+        out[key] = {"d_omega_max": float(rel.max()), "d_omega_mean": float(rel.mean()),
+                    "printed_max": printed[key][0], "printed_mean": printed[key][1], "s": time.perf_counter() - t0}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def study_woodpile(pcx, n=256, nev=20, tol=1e-8):
+    """Configuration 5: the 256^3 simple cubic woodpile of anisotropic rods at
+    k = 2 pi (0.1, 0.2, 0.3), 20 bands, mixed precision with the
+    curl-sandwich preconditioner and the FP64 refinement, to Res <= 1e-8.
+    The block is sized to the free device memory: each block column costs
+    13 complex64 and 5 complex128 vectors of 3 N^3 entries (805 MB at
+    256^3), capped at 32 and at least nev + 4.  One JSON line."""
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    s = wl.woodpile()
+    k = wl.config_k(s.name)[0]
+    ctx = pcx.setup_structure(s, n)
+    free, total = torch.cuda.mem_get_info()
+    per_col = 3 * n ** 3 * (13 * 8 + 5 * 16)
+    block = int(min(32, max(nev + 4, (0.85 * free) // per_col)))
+    stats = pcx.pcx_solve_stats()
+    t0 = time.perf_counter()
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, tol, block=block, precision=pcx.PCX_FP32, precond_kind=1,
+                                     stats=stats, raise_on_noconv=False)
+    dt = time.perf_counter() - t0
+    d = stats.as_dict()
+    print(json.dumps({"study": "woodpile-256", "N": n, "nev": nev, "block": block, "tol": tol, "status": int(st),
+                      "s": dt, "iters": int(its[0]), "iters_fp32": d["iters_fp32"], "iters_fp64": d["iters_fp64"],
+                      "max_res": float(np.max(res)), "omega2": ev[0].tolist(),
+                      "free_gb_before": free / 1e9, "ms_apply": d["ms_apply"], "ms_gram": d["ms_gram"],
+                      "ms_precond": d["ms_precond"], "ms_other": d["ms_other"]}), flush=True)
+    return 0
+
+
+def study_learned(pcx, n=64, n_train=200, n_eval=50, pairs=8, steps=800, nev=12, tol=1e-8):
+    """Configuration 4: the learned correction (Hermitian form, BF16 weights,
+    FP32 accumulation) trained on the GPU on residual/error pairs that the
+    solver dumps on n_train seeded random structures at 64^3 (1-4 spheres or
+    rods, tensors with eigenvalues in [2, 16]), then evaluated on n_eval
+    held-out structures at 12 bands to Res <= 1e-8 in mixed precision:
+    iterations and wall time with K_P^{-1} (the plain preconditioner), with
+    T0 (the learned correction's base) and with the learned T.  Structures
+    whose M_Trivial blocks are not HPD are skipped.  One JSON line."""
+    import numpy as np
+
+    import workloads as wl
+    from paper_2511_17107_gb300 import learned as lrn
+    rng = np.random.default_rng(4)
+    t0 = time.perf_counter()
+    samples, seed = [], 100
+    while len(samples) < n_train and seed < 100 + 4 * n_train:
+        s = wl.random_inclusions(seed)
+        seed += 1
+        try:
+            ctx = pcx.setup_structure(s, n)
+        except pcx.PcxError:
+            continue
+        smp = lrn.collect(ctx, rng.uniform(-np.pi, np.pi, 3), n_pairs=pairs, seed=seed)
+        if smp is not None:
+            samples.append(smp)
+    t_collect = time.perf_counter() - t0
+    P, losses = lrn.train(samples, steps=steps, lr=3e-3)
+    t_train = time.perf_counter() - t0 - t_collect
+    import torch
+    P0 = torch.empty_like(P)
+    pcx.pcx_cnn_init(1, P0)
+    res = {"K_P": {"iters": [], "s": []}, "T0": {"iters": [], "s": []}, "learned": {"iters": [], "s": []}}
+    worst_rel = 0.0
+    seed = 5000
+    while len(res["K_P"]["iters"]) < n_eval and seed < 5000 + 4 * n_eval:
+        s = wl.random_inclusions(seed)
+        seed += 1
+        try:
+            ctx = pcx.setup_structure(s, n)
+        except pcx.PcxError:
+            continue
+        pcx.pcx_set_cnn_form(ctx, lrn.FORM)
+        k = rng.uniform(-np.pi, np.pi, 3)
+        ev = {}
+        for name, cp, kind in (("K_P", None, 0), ("T0", None, 1), ("learned", P, 1)):
+            a = time.perf_counter()
+            e, r, it, st = pcx.pcx_solve(ctx, [k], nev, tol, block=nev + 4, precision=pcx.PCX_FP32, cnn_params=cp,
+                                         precond_kind=kind, raise_on_noconv=False)
+            res[name]["s"].append(time.perf_counter() - a)
+            res[name]["iters"].append(int(it[0]))
+            ev[name] = e[0]
+        worst_rel = max(worst_rel, float(np.max(np.abs(ev["learned"] - ev["K_P"]) / np.abs(ev["K_P"]))))
+    out = {"study": "learned-64", "N": n, "train_structures": len(samples), "pairs_per_structure": pairs,
+           "steps": steps, "form": "hermitian, bf16 weights, fp32 accumulation", "collect_s": t_collect,
+           "train_s": t_train, "loss_start": float(losses[0]), "loss_end": float(np.mean(losses[-20:])),
+           "relative_error_T0": lrn.relative_error(samples[:20], P0),
+           "relative_error_trained": lrn.relative_error(samples[:20], P),
+           "eval_structures": len(res["K_P"]["iters"]), "max_rel_eig_diff_learned_vs_K_P": worst_rel}
+    for name, d in res.items():
+        out[name] = {"iters_mean": float(np.mean(d["iters"])), "s_mean": float(np.mean(d["s"])),
+                     "iters": d["iters"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -440,6 +665,8 @@ def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps
         P, out["learned_training"] = train_learned(pcx, n, steps=learned_steps)
     legs = [("mixed", pcx.PCX_FP32, 0, None), ("mixed_sandwich", pcx.PCX_FP32, 1, None)]
     if P is not None:
+        from paper_2511_17107_gb300 import learned as lrn
+        pcx.pcx_set_cnn_form(ctx, lrn.FORM)   # the form the correction was trained in
         legs.append(("mixed_learned", pcx.PCX_FP32, 1, P))
     legs.append(("fp64", pcx.PCX_FP64, 0, None))
     legs.append(("fp64_sandwich", pcx.PCX_FP64, 1, None))
@@ -510,7 +737,16 @@ def main():
                     help="print timings of the eigensolver's Gram products and combinations instead")
     ap.add_argument("--sizes", action="store_true",
                     help="print pcx_apply timings at 1, 16 and 48 vectors per call, complex64 and complex128, instead")
+    ap.add_argument("--study", default="",
+                    choices=["", "bcc-convergence", "frequency-difference", "woodpile-256", "learned-64"],
+                    help="run one of the paper's studies or configuration 5 instead of the benchmark (one JSON line)")
     args = ap.parse_args()
+    if args.study:
+        from paper_2511_17107_gb300 import build as _build
+        from paper_2511_17107_gb300 import pcx
+        _build.build()
+        return {"bcc-convergence": study_bcc_convergence, "frequency-difference": study_frequency_difference,
+                "woodpile-256": study_woodpile, "learned-64": study_learned}[args.study](pcx)
     if args.warmup < 3:
         args.warmup = 3
     if args.blockops:
@@ -547,12 +783,12 @@ def main():
     ks = rank_k_points(nk, rank, world)
     ctx = pcx.setup_structure(s, n)
     stream = torch.cuda.Stream()
-    pcx.pcx_set_apply_path(ctx, {"auto": pcx.PCX_APPLY_AUTO, "five": pcx.PCX_APPLY_FIVE_PASS,
-                                 "three": pcx.PCX_APPLY_THREE_PASS}[args.apply_path])
     if args.chunk > 0:
         args.no_tune = True
         pcx.pcx_set_apply_chunk(ctx, args.chunk)
     tune = None if args.no_tune else pcx.pcx_autotune(ctx, prec, block, stream=stream)
+    if args.apply_path != "auto":   # an explicit pass structure overrides the tuner's choice
+        pcx.pcx_set_apply_path(ctx, {"five": pcx.PCX_APPLY_FIVE_PASS, "three": pcx.PCX_APPLY_THREE_PASS}[args.apply_path])
     x = wl.random_block(block, n, seed=20251117 + rank).astype(cdt)
     X = torch.empty((nk, block, 3, n, n, n), dtype=torch.complex64 if es == 8 else torch.complex128, device="cuda")
     X.copy_(torch.from_numpy(x).cuda().unsqueeze(0).expand_as(X))

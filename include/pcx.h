@@ -312,15 +312,20 @@ typedef struct {
   double us_per_vector; /* measured time of the chosen configuration              */
   int candidates;       /* configurations timed (0 when from a cache)             */
   int from_cache;       /* 0 measured, 1 process cache, 2 the PCX_TUNE_CACHE file  */
+  int path;             /* pass structure chosen: PCX_APPLY_FIVE_PASS or
+                           PCX_APPLY_THREE_PASS                                    */
 } pcx_tune_result;
 
 /*
  * pcx_autotune -- choose the apply launch configuration of this context for
- * blocks of nvec vectors at `precision`: every chunk size 1, 2, 4, ... <=
+ * blocks of nvec vectors at `precision`: for each pass structure the
+ * context has (the five-pass chain, and the three-pass one where it
+ * exists; see pcx_set_apply_path), every chunk size 1, 2, 4, ... <=
  * min(nvec, 64) (and nvec) is timed with CUDA events on `stream` (two warm
  * and three timed applies on random vectors), then graph replay of the best
  * one when `stream` is not the default stream.  The choice is applied to the
- * context (as pcx_set_apply_chunk / pcx_set_apply_graphs would) and cached
+ * context (as pcx_set_apply_path / pcx_set_apply_chunk /
+ * pcx_set_apply_graphs would) and cached
  * per device, SM count, N, precision and nvec for the process; when the
  * environment variable PCX_TUNE_CACHE names a file, results are read from and
  * appended to it.  Allocates two blocks of nvec vectors while timing;
@@ -485,6 +490,23 @@ pcx_status pcx_sandwich_precond(pcx_ctx* ctx, const double k[3], double gamma, c
 #define PCX_CNN_NPARAMS (PCX_CNN_HIDDEN * 3 * 27 + PCX_CNN_HIDDEN * PCX_CNN_HIDDEN * 27 + 3 * PCX_CNN_HIDDEN * 27 + \
                          2 * (PCX_CNN_HIDDEN * 9 * 27 + PCX_CNN_HIDDEN))
 
+/* Form of the correction in this context (flags; default 0: g in FP32):
+ *   PCX_CNN_HERMITIAN  g_s = (g + g^T) / 2 in place of g, with the transpose
+ *                      g^T(u) = conv^T(g1 * conv^T(g2 * conv^T(u, W3), W2), W1)
+ *                      (conv^T the adjoint of conv): a symmetric real map,
+ *                      so T = T0 + B^H g_s B (B = F3_3 K_A^H / |k|^2) is
+ *                      Hermitian like T0;
+ *   PCX_CNN_BF16       every convolution uses its weights rounded to BF16
+ *                      (round to nearest even), accumulating in FP32; the
+ *                      parameters themselves stay FP32 (the master copy that
+ *                      pcx_cnn_adam updates), and pcx_cnn_grad returns the
+ *                      gradient of the rounded network (straight through).
+ * Applies to pcx_cnn_forward, pcx_cnn_grad, pcx_cnn_precond and the learned
+ * path of pcx_solve.  PCX_EINVAL for other bits. */
+#define PCX_CNN_HERMITIAN 1
+#define PCX_CNN_BF16 2
+pcx_status pcx_set_cnn_form(pcx_ctx* ctx, int flags);
+
 /* Random initial parameters (seeded): W1, W2, V1, V2 normal with variance
  * 1/fan-in, W3 = 0 and c = 0 (so T starts as K_P^{-1}). */
 pcx_status pcx_cnn_init(uint64_t seed, float* params, void* stream);
@@ -598,9 +620,11 @@ typedef struct {
                          rank-deficient block gives PCX_ENUMERIC.  NULL: random */
   int k_concurrency;  /* k-points solved at the same time (0 or 1: one after the
                          other).  Each k in flight gets its own host thread,
-                         stream, search-space buffers and apply scratch (about
-                         13 block x 3 N^3 complex entries per precision in use:
-                         10.5 GB at 128^3, block 16, complex64), so the GPU
+                         stream, search-space buffers and apply scratch (13
+                         block x 3 N^3 complex entries in the working
+                         precision, plus 5 block x 3 N^3 complex128 for the
+                         FP64 refinement of PCX_FP32: 10.5 + 8 GB at 128^3,
+                         block 16), so the GPU
                          runs one k's kernels while another k's host does its
                          Rayleigh-Ritz step.  Same results as one after the
                          other.  Not with cnn_params or dump_R (they share the

@@ -31,6 +31,16 @@ the real-space field e = F3_3 (K_A^H r / |k|^2):
 
 g is linear in u for a fixed structure and acts on the real and imaginary
 parts of the complex field with the same weights, so T is complex-linear.
+
+Hermitian form (symmetric=True): g_s = (g + g^T) / 2 with the transpose
+
+    g^T(u) = conv^T(g1 * conv^T(g2 * conv^T(u, W3), W2), W1)
+
+(conv^T the adjoint of conv).  g_s is a symmetric real map, so T(r) =
+T0 r + B^H g_s B r with B = F3_3 K_A^H / |k|^2 is Hermitian like T0 (F3_3 is
+unitary): the form a conjugate-gradient-type eigensolver expects of its
+preconditioner.
+
 conv is a cross-correlation with 3 x 3 x 3 taps and periodic wrap-around:
 conv(x, w)[o, z, y, x] = sum_{i, dz, dy, dx} w[o, i, dz+1, dy+1, dx+1]
 x[i, z+dz, y+dy, x+dx].
@@ -42,7 +52,9 @@ range of K_A, whose complement T0 already inverts exactly; the loss is
 sum_v w_v ||g(U_v) - T_v||^2 with w_v = 1 / (count ||K_A^H e_v||^2).
 
 Parameters are one flat vector in the order W1, W2, W3, V1, c1, V2, c2, each
-in C order (param_shapes).
+in C order (param_shapes).  The BF16 form evaluates the network with every
+convolution weight rounded to bfloat16 (rounded(p)); its gradient is the
+gradient of that network, applied to the unrounded parameters.
 """
 from __future__ import annotations
 
@@ -114,6 +126,21 @@ def conv_weight_grad(dy: np.ndarray, x: np.ndarray) -> np.ndarray:
     return g
 
 
+def to_bf16(x) -> np.ndarray:
+    """Round to the nearest bfloat16 (8 exponent, 7 fraction bits), ties to
+    even, from the float32 value of x: keep the top 16 bits of the float32
+    encoding after adding 0x7FFF plus the lowest kept bit."""
+    b = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def rounded(p: dict) -> dict:
+    """The parameters with every convolution weight rounded to bfloat16 (the
+    biases c1, c2 stay as they are): the network the BF16 form evaluates."""
+    return {k: (to_bf16(v) if k[0] in "WV" else v) for k, v in p.items()}
+
+
 def sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
 
@@ -135,21 +162,39 @@ def forward_real(p: dict, f: np.ndarray, u: np.ndarray, g=None):
     return y, dict(u=u, g1=g1, g2=g2, a1=a1, h1=h1, a2=a2, h2=h2)
 
 
-def forward(p: dict, f: np.ndarray, U: np.ndarray) -> np.ndarray:
-    """Complex field U (..., 3, N, N, N): g(Re U) + i g(Im U)."""
+def transpose_real(p: dict, f: np.ndarray, u: np.ndarray, g=None):
+    """g^T(u) for one real (3, N, N, N) sample; returns (y, cache)."""
+    g1, g2 = gates(p, f) if g is None else g
+    b3 = conv_adjoint(u, p["W3"])
+    k2 = b3 * g2
+    b2 = conv_adjoint(k2, p["W2"])
+    k1 = b2 * g1
+    y = conv_adjoint(k1, p["W1"])
+    return y, dict(u=u, b3=b3, k2=k2, b2=b2, k1=k1)
+
+
+def forward(p: dict, f: np.ndarray, U: np.ndarray, symmetric: bool = False) -> np.ndarray:
+    """Complex field U (..., 3, N, N, N): g(Re U) + i g(Im U), or with
+    symmetric=True the same with g_s = (g + g^T) / 2."""
     g = gates(p, f)
     flat = U.reshape((-1,) + U.shape[-4:])
     out = np.empty(flat.shape, dtype=np.complex128)
+
+    def one(u):
+        y, _ = forward_real(p, f, u, g)
+        if symmetric:
+            y = 0.5 * (y + transpose_real(p, f, u, g)[0])
+        return y
+
     for v in range(flat.shape[0]):
-        yr, _ = forward_real(p, f, flat[v].real, g)
-        yi, _ = forward_real(p, f, flat[v].imag, g)
-        out[v] = yr + 1j * yi
+        out[v] = one(flat[v].real) + 1j * one(flat[v].imag)
     return out.reshape(U.shape)
 
 
-def loss_and_grad(p: dict, f: np.ndarray, U: np.ndarray, T: np.ndarray, w: np.ndarray):
+def loss_and_grad(p: dict, f: np.ndarray, U: np.ndarray, T: np.ndarray, w: np.ndarray, symmetric: bool = False):
     """L = sum_v w_v ||g(U_v) - T_v||^2 over complex samples (nvec, 3, N, N, N)
-    and dL/dparams (dict), by the chain rule through every layer."""
+    (g_s in place of g with symmetric=True) and dL/dparams (dict), by the
+    chain rule through every layer of both paths."""
     g1, g2 = gates(p, f)
     grads = {name: np.zeros(shape) for name, shape in param_shapes(p["W1"].shape[0])}
     dg1 = np.zeros_like(g1)
@@ -158,9 +203,12 @@ def loss_and_grad(p: dict, f: np.ndarray, U: np.ndarray, T: np.ndarray, w: np.nd
     for v in range(U.shape[0]):
         for part in (np.real, np.imag):
             y, cch = forward_real(p, f, part(U[v]), (g1, g2))
+            if symmetric:
+                yt, cct = transpose_real(p, f, part(U[v]), (g1, g2))
+                y = 0.5 * (y + yt)
             diff = y - part(T[v])
             loss += w[v] * np.sum(diff ** 2)
-            dy = 2.0 * w[v] * diff
+            dy = 2.0 * w[v] * diff * (0.5 if symmetric else 1.0)
             grads["W3"] += conv_weight_grad(dy, cch["h2"])
             dh2 = conv_adjoint(dy, p["W3"])
             da2 = dh2 * g2
@@ -170,6 +218,18 @@ def loss_and_grad(p: dict, f: np.ndarray, U: np.ndarray, T: np.ndarray, w: np.nd
             da1 = dh1 * g1
             dg1 += dh1 * cch["a1"]
             grads["W1"] += conv_weight_grad(da1, cch["u"])
+            if symmetric:
+                # the transpose path y' = conv^T(k1, W1): <dy, conv^T(k1, W1)>
+                # = <conv(dy, W1), k1>, so dW1 = conv_weight_grad(k1, dy)
+                grads["W1"] += conv_weight_grad(cct["k1"], dy)
+                dk1 = conv(dy, p["W1"])
+                db2 = dk1 * g1
+                dg1 += dk1 * cct["b2"]
+                grads["W2"] += conv_weight_grad(cct["k2"], db2)
+                dk2 = conv(db2, p["W2"])
+                db3 = dk2 * g2
+                dg2 += dk2 * cct["b3"]
+                grads["W3"] += conv_weight_grad(cct["u"], db3)
     dz1 = dg1 * g1 * (1.0 - g1)
     dz2 = dg2 * g2 * (1.0 - g2)
     grads["V1"] = conv_weight_grad(dz1, f)
@@ -204,10 +264,11 @@ def sandwich_precondition(r, kap, blocks, gamma):
     return curl_scaled(fourier.f3h(m), kap) + longi
 
 
-def precondition(p: dict, f: np.ndarray, r: np.ndarray, kap, gamma, blocks) -> np.ndarray:
-    """T(r) = T0 r + K_A F3_3^H g(F3_3 K_A^H r / |k|^2) / |k|^2."""
+def precondition(p: dict, f: np.ndarray, r: np.ndarray, kap, gamma, blocks, symmetric: bool = False) -> np.ndarray:
+    """T(r) = T0 r + K_A F3_3^H g(F3_3 K_A^H r / |k|^2) / |k|^2 (g_s with
+    symmetric=True)."""
     e = fourier.f3(curl_h_scaled(r, kap))
-    return sandwich_precondition(r, kap, blocks, gamma) + curl_scaled(fourier.f3h(forward(p, f, e)), kap)
+    return sandwich_precondition(r, kap, blocks, gamma) + curl_scaled(fourier.f3h(forward(p, f, e, symmetric)), kap)
 
 
 def training_pair(r: np.ndarray, e: np.ndarray, kap, gamma, blocks):

@@ -328,6 +328,13 @@ pcx_status pcx_set_apply_graphs(pcx_ctx* c, int enable) {
   return PCX_OK;
 }
 
+pcx_status pcx_set_cnn_form(pcx_ctx* c, int flags) {
+  if (!c) return inval(nullptr, "pcx_set_cnn_form: NULL context");
+  if (flags & ~(PCX_CNN_HERMITIAN | PCX_CNN_BF16)) return inval(c, "pcx_set_cnn_form: unknown flag");
+  c->cnn_form = flags;
+  return PCX_OK;
+}
+
 pcx_status pcx_set_apply_path(pcx_ctx* c, int path) {
   if (!c) return inval(nullptr, "pcx_set_apply_path: NULL context");
   if (path != PCX_APPLY_AUTO && path != PCX_APPLY_FIVE_PASS && path != PCX_APPLY_THREE_PASS)

@@ -472,7 +472,7 @@ cudaError_t launch_combine(const void* S, int ns, const double* C, int ny, doubl
     if (precision == PCX_FP64) {
       const size_t smem = (size_t)ns * CY * sizeof(float4);
       if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(combine_ff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(combine_ff_kernel), smem);
         if (e != cudaSuccess) return e;
       }
       combine_ff_kernel<<<grid_for(L, 128, 152u * 16u), 128, smem, s>>>(static_cast<const double2*>(S), ns, C, ny,

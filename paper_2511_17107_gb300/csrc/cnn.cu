@@ -11,11 +11,13 @@
 // it wraps are eqs. matrixfree_diagP / matrixfree_finalform (K_P^{-1}) and
 // the Fourier basis x = F3_3^H H of Sec. 2.4.
 //
-// Everything is FP32 (FP32 weights and accumulation).  A convolution CTA
+// Arithmetic and accumulation are FP32; the convolutions optionally round
+// their weights to BF16 as they load them (the learned form's BF16 flag).  A convolution CTA
 // produces an 8 x 8 x 8 tile of output voxels for every output channel of
 // one sample, from a 10 x 10 x 10 halo tile of all input channels staged in
 // shared memory (periodic wrap on load).  The weight gradient is a
 // per-CTA sum over tiles written to scratch and reduced in a fixed order.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -62,7 +64,7 @@ __device__ __forceinline__ void load_halo(float (*sx)[HV], const View& in, int b
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(CT) conv_fwd_kernel(View in, View out, const float* __restrict__ w,
                                                       const float* __restrict__ bias, View gate, View pre, int n,
-                                                      float out_scale) {
+                                                      float out_scale, int wbf16) {
   // Each thread produces two neighbouring voxels along x for every output
   // channel.  The weights sit in shared memory as [ci][tap][co] (co padded
   // to a multiple of 4), so one 16-byte broadcast load feeds 8 FMAs, and
@@ -77,7 +79,9 @@ __global__ void __launch_bounds__(CT) conv_fwd_kernel(View in, View out, const f
   tile_origin(blockIdx.x, n, z0, y0, x0);
   for (int i = threadIdx.x; i < CIN * 27 * CP; i += CT) {
     const int co = i % CP, t = (i / CP) % 27, ci = i / (CP * 27);
-    sw[i] = co < COUT ? w[(co * CIN + ci) * 27 + t] : 0.f;
+    float wv = co < COUT ? w[(co * CIN + ci) * 27 + t] : 0.f;
+    if (wbf16) wv = __bfloat162float(__float2bfloat16_rn(wv));   // BF16 weights, FP32 accumulation
+    sw[i] = wv;
   }
   load_halo<CIN>(sx, in, b, n, z0, y0, x0);
   __syncthreads();
@@ -376,12 +380,12 @@ unsigned grid_for(size_t n, int threads, unsigned cap) {
 
 #define PCX_CONV_CASE(CI, CO, MD)                                                                       \
   if (cin == CI && cout == CO && mode == MD) {                                                          \
-    conv_fwd_kernel<CI, CO, MD><<<grid, CT, 0, s>>>(in, out, w, bias, gate, pre, n, out_scale);        \
+    conv_fwd_kernel<CI, CO, MD><<<grid, CT, 0, s>>>(in, out, w, bias, gate, pre, n, out_scale, wbf16); \
     return cudaGetLastError();                                                                          \
   }
 
 cudaError_t conv_fwd(int cin, int cout, int mode, const View& in, const View& out, const float* w, const float* bias,
-                     const View& gate, const View& pre, int nb, int n, float out_scale, cudaStream_t s) {
+                     const View& gate, const View& pre, int nb, int n, float out_scale, cudaStream_t s, int wbf16) {
   if (n < TS || (n & (n - 1)) != 0 || nb < 1 || nb > 65535) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((n / TS) * (n / TS) * (n / TS)), (unsigned)nb);
   PCX_CONV_CASE(3, HIDDEN, MODE_GATE)
@@ -407,9 +411,7 @@ static cudaError_t wgrad_t(const View& dy, const View& x, int nb, int n, float* 
   long long grid = 4LL * (sms < 152 ? sms : 152);
   if (grid > jobs) grid = jobs;
   const size_t smem = (size_t)(CIN * HV + COUT * TV) * sizeof(float);
-  if ((e = cudaFuncSetAttribute(conv_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
-    return e;
+  if ((e = raise_dyn_smem(reinterpret_cast<const void*>(conv_wgrad_kernel<CIN, COUT>), smem)) != cudaSuccess) return e;
   conv_wgrad_kernel<CIN, COUT><<<(unsigned)grid, CT, smem, s>>>(dy, x, nb, n, scratch);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   constexpr int NE = COUT * CIN * 27;

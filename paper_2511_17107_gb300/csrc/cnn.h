@@ -44,9 +44,10 @@ inline View complex_view(void* p, size_t n3) {
   return View{static_cast<float*>(p), 6 * (long long)n3, 1, 2 * (long long)n3, 2, 2};
 }
 
-// out = conv(in, w) (+ gate / sigmoid), nb samples on the n^3 grid
+// out = conv(in, w) (+ gate / sigmoid), nb samples on the n^3 grid; wbf16:
+// the weights rounded to BF16 (round to nearest even) before use
 cudaError_t conv_fwd(int cin, int cout, int mode, const View& in, const View& out, const float* w, const float* bias,
-                     const View& gate, const View& pre, int nb, int n, float out_scale, cudaStream_t s);
+                     const View& gate, const View& pre, int nb, int n, float out_scale, cudaStream_t s, int wbf16 = 0);
 // dw (+)= sum over samples of the weight gradient; scratch >= wgrad_scratch_floats(...)
 cudaError_t conv_wgrad(int cin, int cout, const View& dy, const View& x, int nb, int n, float* dw, int accumulate,
                        float* scratch, cudaStream_t s);

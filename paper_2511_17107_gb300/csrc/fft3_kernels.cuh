@@ -49,11 +49,20 @@ template <> struct YSplit<128> { static constexpr int RA = 16, RB = 8; };
 // the pass fills whole 32-byte sectors.  At N = 128 that is 32 pencils
 // (96 KB of complex64 for the three components), two CTAs per SM with 32
 // elements per thread and stage.
+#ifndef PCX_Z128_TN
+#define PCX_Z128_TN 4096
+#endif
+#ifndef PCX_Z128_E
+#define PCX_Z128_E 32
+#endif
+#ifndef PCX_Z128_MINB
+#define PCX_Z128_MINB 2
+#endif
 template <int N>
 struct ZGeom {
   static constexpr int TN = 2048, E = 16, MINB = 3;
 };
-template <> struct ZGeom<128> { static constexpr int TN = 4096, E = 32, MINB = 2; };
+template <> struct ZGeom<128> { static constexpr int TN = PCX_Z128_TN, E = PCX_Z128_E, MINB = PCX_Z128_MINB; };
 
 template <typename T, int N>
 struct Cfg3 {
@@ -72,7 +81,7 @@ struct Cfg3 {
   static constexpr int ZI_PER_THREAD = 3 * N * (TPX / 2) / THREADSZ;  // row-DFT items (2 x RB points)
   static constexpr int MI_PER_THREAD = (TPZ * N + THREADSZ - 1) / THREADSZ;   // cells per thread in the M step
   static_assert(RA * RB == N && G >= 1 && G * RA == TP && TPX * RB == TPZ, "tile split");
-  static_assert(TPX % 4 == 0 && XI_PER_THREAD >= 1 && ZI_PER_THREAD >= 1, "work split");
+  static_assert(TPX % 2 == 0 && XI_PER_THREAD >= 1 && ZI_PER_THREAD >= 1, "work split");
   static_assert(XI_PER_THREAD * THREADS == 3 * G * N && ZI_PER_THREAD * THREADSZ == 3 * N * (TPX / 2),
                 "work split");
   // shared memory of the z tile: three components at stride CS (Tile)
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
   cx<T>* tw = s + 3 * C::CS;    // the three components at stride CS (see Tile)
   cx<T>* ka = tw + N;          // [3][N]   (x tiles)
   cx<T>* kb = ka + 3 * N;      // [TP][3]  (x tiles)
-  T* mtab = reinterpret_cast<T*>(tw + N);   // [n_mat][9] (z tiles)
+  T* mtab = reinterpret_cast<T*>(tw + N);   // [n_mat][12] (z tiles, 16-byte aligned)
 
   constexpr int TILES = ZP ? C3::ZTILES : C3::TILES;
   const size_t v = blockIdx.x / TILES;
@@ -172,28 +181,28 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
       const T gam = (T)kp.gamma;
       const T igam = (T)(1.0 / kp.gamma);
-      // the tile's rows land in shared memory by asynchronous copies
-      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
-        const int t = e / N, n = e % N;
-        int z, y, j;
-        x_row<T, N>(tile, t, z, y, j);
-        const int g = z * N2 + y * N + n;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_cx<T>(&s[TL::sidx(c, t, n)], &in[c * N3 + g]);
-      }
-      cp_async_commit_wait_all();
-      __syncthreads();
       // u = -conj(kappa) x x per mode and gamma kappa.x to the scratch
-      // (T0: u / |k|^2 and kappa.x / (gamma |k|^4))
-      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
-        const int t = e / N, n = e % N;
+      // (T0: u / |k|^2 and kappa.x / (gamma |k|^4)), straight from global
+      // memory into the tile.  THREADS is a multiple of N, so every thread
+      // keeps one point n and walks the rows t = t0, t0 + THREADS / N, ...
+      static_assert(C::THREADS % N == 0, "x tiles: whole rows per thread sweep");
+      constexpr int TSTEP = C::THREADS / N;
+      const int n = threadIdx.x % N, t0 = threadIdx.x / N;
+      __syncthreads();   // kappa tables
+      cx<T> kan[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
+#pragma unroll
+      for (int i = 0; i < (TP + TSTEP - 1) / TSTEP; ++i) {
+        const int t = t0 + i * TSTEP;
+        if (t >= TP) break;
         int z, y, j;
         x_row<T, N>(tile, t, z, y, j);
         const int g = z * N2 + y * N + n;
-        const cx<T> x0 = s[TL::sidx(0, t, n)], x1 = s[TL::sidx(1, t, n)], x2 = s[TL::sidx(2, t, n)];
+        const cx<T> x0 = in[g], x1 = in[N3 + g], x2 = in[2 * N3 + g];
         cx<T> kap[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
+        for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
         T su = (T)1, ss = gam;
         if constexpr (T0) {
           const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
@@ -237,16 +246,8 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
         }
       }
     } else {
-      // pass C: gamma kappa.x of the tile is fetched into shared memory while
-      // the rows are transformed
+      // pass C
       const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
-      cx<T>* ssb = kb + 3 * TP;   // [TP * N]
-      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
-        const int t = e / N, n = e % N;
-        int z, y, j;
-        x_row<T, N>(tile, t, z, y, j);
-        cp_async_cx<T>(&ssb[e], &sb[z * N2 + y * N + n]);
-      }
       // RA-point forward y DFT: rows RB k1 + m1 -> Fourier rows m1 + RB m2
 #pragma unroll
       for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
@@ -264,17 +265,25 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       }
       __syncthreads();
       fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
-      cp_async_commit_wait_all();
-      __syncthreads();
-      for (int e = threadIdx.x; e < TP * N; e += C::THREADS) {
-        const int t = e / N, n = e % N;
+      // C w + gamma conj(kappa) (kappa . x) per mode, the scratch read
+      // straight from global memory; one point n per thread, as in pass A
+      static_assert(C::THREADS % N == 0, "x tiles: whole rows per thread sweep");
+      constexpr int TSTEP = C::THREADS / N;
+      const int n = threadIdx.x % N, t0 = threadIdx.x / N;
+      cx<T> kan[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
+#pragma unroll
+      for (int i = 0; i < (TP + TSTEP - 1) / TSTEP; ++i) {
+        const int t = t0 + i * TSTEP;
+        if (t >= TP) break;
         int z, y, j;
         x_row<T, N>(tile, t, z, y, j);
         const int g = z * N2 + y * N + n;
-        const cx<T> sk = ssb[e];
+        const cx<T> sk = sb[g];
         cx<T> kap[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) kap[i] = ka[i * N + n] + kb[3 * t + i];
+        for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
         const cx<T> w0 = s[TL::sidx(0, t, n)], w1 = s[TL::sidx(1, t, n)], w2 = s[TL::sidx(2, t, n)];
         cx<T> c0 = cfma(kap[1], w2, scale(kap[2] * w1, (T)-1));
         cx<T> c1 = cfma(kap[2], w0, scale(kap[0] * w2, (T)-1));
@@ -297,9 +306,15 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
     // row y = k1 + RA k2 at x = xr TPX + xo
     constexpr int TPX = C3::TPX;
     const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
+    // the material table repacked to 12 entries per material: d1 d2 d3 -
+    // re12 im12 re13 im13 re23 im23 - -, so that the off-diagonals of a
+    // cell come in one 16-byte and one 8-byte load
     if (a.mid) {
       const T* gt = static_cast<const T*>(a.mtab);
-      for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) mtab[i] = gt[i];
+      for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) {
+        const int m = i / 9, f = i % 9;
+        mtab[12 * m + (f < 3 ? f : f + 1)] = gt[i];
+      }
     }
     const T* M = static_cast<const T*>(a.M);
     const uchar4* mid3 = static_cast<const uchar4*>(a.mid3);
@@ -343,13 +358,21 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       cx<T> o12, o13, o23;
       if (mid3) {
         const uchar4 id = idr[i];
-        d1 = mtab[9 * id.x];
-        d2 = mtab[9 * id.y + 1];
-        d3 = mtab[9 * id.z + 2];
-        const T* o = mtab + 9 * id.w;
-        o12 = mk(o[3], o[4]);
-        o13 = mk(o[5], o[6]);
-        o23 = mk(o[7], o[8]);
+        d1 = mtab[12 * id.x];
+        d2 = mtab[12 * id.y + 1];
+        d3 = mtab[12 * id.z + 2];
+        const T* o = mtab + 12 * id.w;
+        if constexpr (sizeof(T) == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(o + 4);
+          const float2 r = *reinterpret_cast<const float2*>(o + 8);
+          o12 = mk(q.x, q.y);
+          o13 = mk(q.z, q.w);
+          o23 = mk(r.x, r.y);
+        } else {
+          o12 = mk(o[4], o[5]);
+          o13 = mk(o[6], o[7]);
+          o23 = mk(o[8], o[9]);
+        }
       } else {
         const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
         d1 = M[cell];
@@ -428,22 +451,20 @@ __global__ void pass3_ids_kernel(const uchar4* __restrict__ mid, uchar4* __restr
 
 // One pass of the three-pass chain over nv vectors; the shared memory of
 // each tile kind is fixed by its geometry (x tiles: the five-pass x layout
-// plus the kappa tables and, for pass C, the scratch tile; z tiles: the
-// tile, the twiddles and the material table).
+// plus the kappa tables; z tiles: the tile, the twiddles and the material
+// table).
 template <typename T, int N, int OP>
 cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st) {
   using C3 = Cfg3<T, N>;
   constexpr bool ZP = is_z_op<OP>();
   size_t smem;
   if constexpr (ZP)
-    smem = C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) + (((size_t)9 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);
+    smem = C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) + (((size_t)12 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);
   else
-    smem = C3::C::SMEM + ((OP == OP_POST || OP == OP_POST_T0) ? (size_t)C3::TP * N * sizeof(cx<T>) : 0);
+    smem = C3::C::SMEM;
   const size_t tiles = (size_t)nv * (ZP ? C3::ZTILES : C3::TILES);
   auto kern = pass3_kernel<T, N, OP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)tiles, pass3_threads<T, N, OP>(), smem, st>>>(a);
   return cudaGetLastError();

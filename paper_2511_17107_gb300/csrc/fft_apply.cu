@@ -56,6 +56,32 @@ int apply_chunk(const pcx_ctx* c, int precision) {
   return (int)(k < 1 ? 1 : (k > 64 ? 64 : k));
 }
 
+cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
+  struct Entry {
+    const void* f;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> seen;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (Entry& en : seen)
+    if (en.f == func && en.dev == dev) {
+      if (bytes <= en.bytes) return cudaSuccess;
+      e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e == cudaSuccess) en.bytes = bytes;
+      return e;
+    }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess) seen.push_back(Entry{func, dev, bytes});
+  return e;
+}
+
 int effective_apply_path(const pcx_ctx* c, int precision) {
   if (c->m_kind == PCX_M_CROSSDOF) return 7;
   const bool three = precision == PCX_FP32 && (c->n == 32 || c->n == 64 || c->n == 128);

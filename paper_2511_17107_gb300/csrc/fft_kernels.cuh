@@ -814,9 +814,7 @@ __global__ void crossdof_kernel(const cx<T>* __restrict__ E, cx<T>* __restrict__
 template <typename T, int N, int AXIS, int OP>
 cudaError_t launch_pass(const PassArgs& a, size_t tiles, size_t smem, cudaStream_t st) {
   auto kern = pass_kernel<T, N, AXIS, OP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)tiles, Cfg<T, N>::THREADS, smem, st>>>(a);
   return cudaGetLastError();

@@ -227,9 +227,7 @@ cudaError_t run(const float4* A, int na, const float4* B, int nb, long long L2, 
   const size_t smem = (size_t)2 * nrow * RS * sizeof(float4);
   auto kern = gram_cc_kernel<TA, TB, SYM, MAXT, MINB>;
   if (threads > MAXT) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;

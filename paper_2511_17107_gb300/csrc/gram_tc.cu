@@ -311,8 +311,7 @@ cudaError_t launch_gram_tc(const void* A, int na, const void* B, int nb, size_t 
   const int ncol = g.same ? na : na + nb;
   const size_t smem = 2 * (size_t)stage_bytes + (size_t)NRAW * ncol * KC * 8 + 64;
   if ((e = cudaMemsetAsync(g.err, 0, sizeof(int), s)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
+  if ((e = raise_dyn_smem(reinterpret_cast<const void*>(gram_tc_kernel), smem)) != cudaSuccess) return e;
   gram_tc_kernel<<<(unsigned)nctas, THREADS, smem, s>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   gram_reduce_kernel<<<(unsigned)(na * nb), RED_THREADS, 0, s>>>(g.partial, (int)nctas, na, nb, g.np, g.err, G);

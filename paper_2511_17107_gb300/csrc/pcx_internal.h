@@ -74,6 +74,7 @@ struct pcx_ctx {
   // workspace of the learned-correction kernels (learned.cpp)
   void* cnn_ws = nullptr;
   size_t cnn_ws_bytes = 0;
+  int cnn_form = 0;   // PCX_CNN_HERMITIAN | PCX_CNN_BF16 flags
   // staging for pcx_apply_host: two slots of X and Y chunks, copy streams
   // and slot events (created on first use)
   void* stage_x = nullptr;
@@ -202,5 +203,13 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol,
                  void* vec_out, cudaStream_t s);
 
 inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Raise the dynamic shared-memory limit of a kernel (on the current device)
+// to at least `bytes`.  The limit is a property of the kernel, shared by
+// every thread that launches it, so it only ever grows: a launch sized
+// under the limit stays valid when another thread raises it (several
+// k-points of pcx_solve in flight launch the same kernels with different
+// sizes).
+cudaError_t raise_dyn_smem(const void* func, size_t bytes);
 
 }  // namespace pcx

@@ -111,8 +111,10 @@ struct Run {
   }
   char* col(DevBuf& b, int j) { return static_cast<char*>(b.p) + (size_t)j * L * es; }
 
-  pcx_status alloc_all() {
-    const size_t blk = (size_t)3 * n * L * es;
+  // x_only: the FP64 run of the mixed scheme, which keeps only X and AX
+  // (n columns each, with their combination targets) in FP64
+  pcx_status alloc_all(bool x_only = false) {
+    const size_t blk = (size_t)(x_only ? 1 : 3) * n * L * es;
     CK(S.alloc(blk));
     CK(AS.alloc(blk));
     CK(S2.alloc(blk));
@@ -669,7 +671,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
   r64.k_zero = kz;
   r64.verbose = ks.o->verbose;
   if (ks.o->stats) r64.tm = ks.t64;
-  if ((st = r64.alloc_all()) != PCX_OK) {
+  if ((st = r64.alloc_all(ks.o->precision == PCX_FP32)) != PCX_OK) {
     *ks.err = r64.err;
     return st;
   }

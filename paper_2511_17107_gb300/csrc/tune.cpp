@@ -1,6 +1,7 @@
-// Autotuner of the apply launch configuration: vectors per launch chunk
-// (how much of the block sweeps the five passes while L2-resident) and
-// whether the launch chain replays as a CUDA graph.  Each candidate is timed
+// Autotuner of the apply launch configuration: the pass structure (five
+// passes, or the three-pass form where it exists), vectors per launch chunk
+// (how much of the block sweeps the passes while L2-resident) and whether
+// the launch chain replays as a CUDA graph.  Each candidate is timed
 // with CUDA events on the caller's stream; the choice is cached per
 // (device, SM count, N, precision, block) in the process and, when the
 // environment variable PCX_TUNE_CACHE names a file, in that file (one line
@@ -51,12 +52,14 @@ bool file_lookup(const std::string& key, pcx_tune_result* r) {
   bool found = false;
   while (std::fgets(line, sizeof(line), f)) {
     char k[400];
-    int chunk = 0, graphs = 0;
+    int chunk = 0, graphs = 0, path = PCX_APPLY_FIVE_PASS;
     double us = 0;
-    if (std::sscanf(line, "%399s %d %d %lf", k, &chunk, &graphs, &us) == 4 && key == k && chunk > 0) {
+    const int got = std::sscanf(line, "%399s %d %d %lf %d", k, &chunk, &graphs, &us, &path);
+    if (got >= 4 && key == k && chunk > 0) {
       r->chunk = chunk;
       r->graphs = graphs;
       r->us_per_vector = us;
+      r->path = got == 5 ? path : PCX_APPLY_FIVE_PASS;
       found = true;   // the last line for a key wins
     }
   }
@@ -69,7 +72,7 @@ void file_store(const std::string& key, const pcx_tune_result& r) {
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), r.chunk, r.graphs, r.us_per_vector);
+  std::fprintf(f, "%s %d %d %.6f %d\n", key.c_str(), r.chunk, r.graphs, r.us_per_vector, r.path);
   std::fclose(f);
 }
 
@@ -102,6 +105,7 @@ cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, 
   if (r.from_cache) {
     c->apply_chunk = r.chunk;
     c->use_graphs = r.graphs;
+    c->apply_path = r.path;
     if (out) *out = r;
     return cudaSuccess;
   }
@@ -110,12 +114,19 @@ cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, 
   void* Y = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaSuccess;
-  const int saved_chunk = c->apply_chunk, saved_graphs = c->use_graphs;
+  const int saved_chunk = c->apply_chunk, saved_graphs = c->use_graphs, saved_path = c->apply_path;
   const double k[3] = {0.31, 0.67, 1.13};
   const KParams kp = make_kparams(c, k, 0.0);
   std::vector<int> cands;
   double best = 1e300;
-  int best_chunk = 1;
+  int best_chunk = 1, best_path = PCX_APPLY_FIVE_PASS;
+  std::vector<int> paths = {PCX_APPLY_FIVE_PASS};
+  {
+    const int keep = c->apply_path;
+    c->apply_path = PCX_APPLY_THREE_PASS;
+    if (effective_apply_path(c, precision) == PCX_APPLY_THREE_PASS) paths.push_back(PCX_APPLY_THREE_PASS);
+    c->apply_path = keep;
+  }
   const int reps = 3;
   auto time_apply = [&](double* ms) -> cudaError_t {
     cudaError_t e2;
@@ -139,19 +150,25 @@ cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, 
   CKT(cudaEventCreate(&e0));
   CKT(cudaEventCreate(&e1));
   c->use_graphs = 0;
-  for (int ch : cands) {
-    c->apply_chunk = ch;
-    double ms = 0;
-    CKT(time_apply(&ms));
-    ++r.candidates;
-    if (ms < best) {
-      best = ms;
-      best_chunk = ch;
+  for (int path : paths) {
+    c->apply_path = path;
+    for (int ch : cands) {
+      c->apply_chunk = ch;
+      double ms = 0;
+      CKT(time_apply(&ms));
+      ++r.candidates;
+      if (ms < best) {
+        best = ms;
+        best_chunk = ch;
+        best_path = path;
+      }
     }
   }
   r.chunk = best_chunk;
+  r.path = best_path;
   r.graphs = 0;
   if (capturable(s)) {
+    c->apply_path = best_path;
     c->apply_chunk = best_chunk;
     c->use_graphs = 1;
     double ms = 0;
@@ -173,10 +190,12 @@ done:
   if (err != cudaSuccess) {
     c->apply_chunk = saved_chunk;
     c->use_graphs = saved_graphs;
+    c->apply_path = saved_path;
     return err;
   }
   c->apply_chunk = r.chunk;
   c->use_graphs = r.graphs;
+  c->apply_path = r.path;
   {
     std::lock_guard<std::mutex> lock(g_mu);
     g_cache.push_back(Entry{key, r});

@@ -31,10 +31,15 @@ class Sample:
     w: np.ndarray
 
 
-def collect(ctx, k, n_pairs=16, nev=12, block=16, dump_every=3, cg_tol=1e-3, cg_maxit=300, seed=0):
+FORM = pcx.PCX_CNN_HERMITIAN | pcx.PCX_CNN_BF16   # the correction's form used for training and solves
+
+
+def collect(ctx, k, n_pairs=16, nev=12, block=16, dump_every=3, cg_tol=1e-3, cg_maxit=300, seed=0, form=FORM):
     """Residuals from an FP32-phase solve at k, their PCG targets and the
-    training pairs.  Returns a Sample, or None if no residual was dumped."""
+    training pairs; the context is set to the correction's form (see
+    pcx_set_cnn_form).  Returns a Sample, or None if no residual was dumped."""
     import torch
+    pcx.pcx_set_cnn_form(ctx, form)
     n = ctx.n
     R = torch.empty((n_pairs, 3, n, n, n), dtype=torch.complex64, device="cuda")
     stats = pcx.pcx_solve_stats()

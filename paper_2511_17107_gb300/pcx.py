@@ -55,7 +55,7 @@ class pcx_solve_stats(C.Structure):
 
 class pcx_tune_result(C.Structure):
     _fields_ = [("chunk", C.c_int), ("graphs", C.c_int), ("us_per_vector", C.c_double), ("candidates", C.c_int),
-                ("from_cache", C.c_int)]
+                ("from_cache", C.c_int), ("path", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -108,6 +108,7 @@ def lib():
             "pcx_apply_kbatch": (st, [vp, dp, C.c_int, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_set_apply_graphs": (st, [vp, C.c_int]),
             "pcx_set_apply_path": (st, [vp, C.c_int]),
+            "pcx_set_cnn_form": (st, [vp, C.c_int]),
             "pcx_get_apply_path": (C.c_int, [vp, C.c_int]),
             "pcx_autotune": (st, [vp, C.c_int, C.c_int, vp, C.POINTER(pcx_tune_result)]),
             "pcx_sandwich_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
@@ -136,7 +137,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_autotune",
+                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_set_cnn_form", "pcx_autotune",
                         "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
                         "pcx_cg_solve", "pcx_gram", "pcx_set_gram_path", "pcx_get_gram_path", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
@@ -378,6 +379,9 @@ def pcx_div_norms(ctx, k, X, out, stream=None):
 
 
 PCX_CNN_HIDDEN = 8
+PCX_CNN_HERMITIAN, PCX_CNN_BF16 = 1, 2
+
+
 PCX_CNN_NPARAMS = (PCX_CNN_HIDDEN * 3 * 27 + PCX_CNN_HIDDEN * PCX_CNN_HIDDEN * 27 + 3 * PCX_CNN_HIDDEN * 27
                    + 2 * (PCX_CNN_HIDDEN * 9 * 27 + PCX_CNN_HIDDEN))
 
@@ -395,6 +399,10 @@ def pcx_apply_kbatch(ctx, kpts, X, Y, gamma=0.0, stream=None):
 
 def pcx_set_apply_graphs(ctx, enable):
     _check(lib().pcx_set_apply_graphs(ctx.handle, int(bool(enable))), ctx.handle)
+
+
+def pcx_set_cnn_form(ctx, flags):
+    _check(lib().pcx_set_cnn_form(ctx.handle, int(flags)), ctx.handle)
 
 
 def pcx_set_apply_path(ctx, path):

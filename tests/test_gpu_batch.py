@@ -82,11 +82,14 @@ def test_autotune_chooses_and_caches(pcx, tmp_path):
         assert r["from_cache"] == 0 and r["candidates"] >= 4
         assert r["chunk"] in (1, 2, 4, 8) and r["graphs"] in (0, 1) and r["us_per_vector"] > 0
         assert pcx.pcx_get_apply_chunk(ctx, pcx.PCX_FP32) == r["chunk"]
+        # complex64 at 32^3 has both pass structures; the tuner timed both
+        assert r["path"] in (pcx.PCX_APPLY_FIVE_PASS, pcx.PCX_APPLY_THREE_PASS)
+        assert pcx.pcx_get_apply_path(ctx, pcx.PCX_FP32) == r["path"]
         line = (tmp_path / "tune.txt").read_text().strip().split()
-        assert line[-3:-1] == [str(r["chunk"]), str(r["graphs"])]
+        assert line[1:3] == [str(r["chunk"]), str(r["graphs"])] and line[4] == str(r["path"])
         ctx2 = pcx.setup_structure(s, n)
         r2 = pcx.pcx_autotune(ctx2, pcx.PCX_FP32, nvec, stream=stream)
-        assert r2["from_cache"] == 1 and r2["chunk"] == r["chunk"]
+        assert r2["from_cache"] == 1 and r2["chunk"] == r["chunk"] and r2["path"] == r["path"]
     finally:
         del os.environ["PCX_TUNE_CACHE"]
     # the tuned context still computes the same apply
@@ -98,5 +101,6 @@ def test_autotune_chooses_and_caches(pcx, tmp_path):
             pcx.pcx_apply(ctx, k, X, Y)
     stream.synchronize()
     ctx3 = pcx.setup_structure(s, n)
+    pcx.pcx_set_apply_path(ctx3, r["path"])
     pcx.pcx_apply(ctx3, k, X, ref)
     assert torch.equal(Y, ref)

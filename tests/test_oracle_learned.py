@@ -189,3 +189,61 @@ def test_features_layout():
     np.testing.assert_array_equal(f[4], b[..., 0, 1].imag)
     np.testing.assert_array_equal(f[8], b[..., 1, 2].imag)
     assert learned.param_count(8) == 8 * 3 * 27 + 64 * 27 + 3 * 8 * 27 + 2 * (8 * 9 * 27 + 8)
+
+
+def test_symmetric_form_gradient_matches_finite_differences():
+    rng = np.random.default_rng(13)
+    c, n, nv = 2, 4, 2
+    p = _rand_params(rng, c)
+    f = rng.uniform(0.05, 1.0, size=(9, n, n, n))
+    U = rng.standard_normal((nv, 3, n, n, n)) + 1j * rng.standard_normal((nv, 3, n, n, n))
+    T = rng.standard_normal((nv, 3, n, n, n)) + 1j * rng.standard_normal((nv, 3, n, n, n))
+    w = np.array([0.9, 1.1])
+    _, grads = learned.loss_and_grad(p, f, U, T, w, symmetric=True)
+    flat = learned.pack(p, c)
+    gflat = learned.pack(grads, c)
+    h = 1e-4   # the loss is quadratic in each weight entry; 1e-4 keeps the FD rounding small
+    for j in rng.choice(flat.size, size=60, replace=False):
+        fp, fm = flat.copy(), flat.copy()
+        fp[j] += h
+        fm[j] -= h
+        lp, _ = learned.loss_and_grad(learned.unpack(fp, c), f, U, T, w, symmetric=True)
+        lm, _ = learned.loss_and_grad(learned.unpack(fm, c), f, U, T, w, symmetric=True)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (j, fd, gflat[j])
+
+
+def test_symmetric_form_is_symmetric_and_the_preconditioner_hermitian():
+    """<v, g_s u> = <g_s v, u> for real fields (while g itself is not
+    symmetric), and T(r) built on g_s is Hermitian: <x, T y> = conj <y, T x>."""
+    rng = np.random.default_rng(14)
+    c, n = 3, 5
+    p = _rand_params(rng, c)
+    f = rng.uniform(0.05, 1.0, size=(9, n, n, n))
+    u = rng.standard_normal((3, n, n, n))
+    v = rng.standard_normal((3, n, n, n))
+    gs = lambda x: learned.forward(p, f, x[None].astype(complex), symmetric=True)[0].real
+    g = lambda x: learned.forward_real(p, f, x)[0]
+    assert abs(np.sum(v * gs(u)) - np.sum(gs(v) * u)) <= 1e-12 * abs(np.sum(v * gs(u)))
+    assert abs(np.sum(v * g(u)) - np.sum(g(v) * u)) > 1e-3 * abs(np.sum(v * g(u)))
+    fs, blocks, kap, gam = _small_case()
+    nn = fs.shape[-1]
+    ps = _rand_params(rng, learned.HIDDEN, 0.2)
+    x = wl.random_block(1, nn, seed=21)[0]
+    y = wl.random_block(1, nn, seed=22)[0]
+    lhs = np.vdot(x, learned.precondition(ps, fs, y, kap, gam, blocks, symmetric=True))
+    rhs = np.conj(np.vdot(y, learned.precondition(ps, fs, x, kap, gam, blocks, symmetric=True)))
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+
+
+def test_bf16_rounding():
+    """Round to nearest even at 7 fraction bits, checked on exact binary
+    values and against torch's float32 -> bfloat16 conversion."""
+    vals = np.array([1.0, 1 + 2 ** -7, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -8 + 2 ** -20, -3.140625, 0.0])
+    want = np.array([1.0, 1 + 2 ** -7, 1.0, 1 + 2 ** -6, 1 + 2 ** -7, -3.140625, 0.0])
+    np.testing.assert_array_equal(learned.to_bf16(vals), want)
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(31)
+    x = (rng.standard_normal(10000) * 10.0 ** rng.uniform(-6, 6, 10000)).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(learned.to_bf16(x), ref)

@@ -233,6 +233,22 @@ def random_inclusions(seed) -> Structure:
     return Structure(f"random-{seed}", SC.copy(), np.stack(mats), 0, shapes)
 
 
+def bcc_gyroid(double=False, anisotropic=True, eps_lattice=16.0, beta=0.875) -> Structure:
+    """BCC-SG (material where g(x) > 1.1) or BCC-DG (|g(x)| > 1.1) on the BCC
+    lattice (Sec. 4, eq. display:exp_latticeconst), with the paper's
+    permittivity: epsilon_1 = I / eps_lattice (isotropic) or the gyrotropic
+    tensor of eq. display:exp_permittivity (beta = 0.875), eps_lattice = 16
+    for the BCC lattice; vacuum outside."""
+    eps = paper_anisotropic(eps_lattice, beta) if anisotropic else eps_lattice * VACUUM
+    shapes = [Shape(SHAPE_GYROID, 1, (1.1, 1 if double else 0))]
+    name = ("bcc-dg" if double else "bcc-sg") + ("-aniso" if anisotropic else "-iso")
+    return Structure(name, BCC.copy(), np.stack([VACUUM, eps]), 0, shapes)
+
+
+BCC_POINTS = {"H'": (2 * PI, 0.0, 0.0), "G": (0.0, 0.0, 0.0), "P": (PI, PI, PI), "N": (PI, 0.0, PI),
+              "H": (0.0, 2 * PI, 0.0)}
+
+
 def homogeneous(eps, lattice=None) -> Structure:
     """One material filling the whole cell."""
     lat = SC.copy() if lattice is None else np.asarray(lattice, dtype=np.float64)
