@@ -305,6 +305,34 @@ pcx_status pcx_set_apply_path(pcx_ctx* ctx, int path);
  * M_CrossDoF chain); -1 for a NULL context or a bad precision. */
 int pcx_get_apply_path(const pcx_ctx* ctx, int precision);
 
+/*
+ * pcx_set_penalty_form -- how the penalty term of this context weighs the
+ * Fourier modes (every later apply, preconditioner and solve uses it):
+ *   PCX_PENALTY_SCALAR    (default) one coefficient gamma for all modes,
+ *                         gamma K_B (Sec. 2.3, eq. kc_formulation); gamma <= 0
+ *                         in a call selects the rule of Remark 2.6.
+ *   PCX_PENALTY_PER_MODE  mode p carries gamma_p = gamma max(1, 1/|kappa_p|^2),
+ *                         and gamma <= 0 in a call selects gamma = 4 pi^2:
+ *                         the rule of Remark 2.6 applied per mode with the
+ *                         mode's own B eigenvalue |kappa_p|^2 (Lemma
+ *                         kc_ABblock) in place of |k|^2.
+ * Both leave the divergence-free eigenpairs unchanged: the penalty acts only
+ * on span(conj kappa_p) per mode, where Op reduces to gamma_p |kappa_p|^2,
+ * so with the per-mode rule every spurious eigenvalue is at least 4 pi^2
+ * (the condition gamma lambda^B >= lambda_m^A of Prop. 2.5 holds mode by
+ * mode, also for k outside the first zone).  What changes is the top of the
+ * spectrum: the scalar rule puts it at about 12 N^2 4 pi^2 / |k|^2 for
+ * 0 < |k| < 1, the per-mode rule at 12 N^2 4 pi^2 whatever k, which bounds
+ * the FP64 rounding floor of the residual (about 1e-16 times the largest
+ * eigenvalue) below 1e-8 at N = 128 near Gamma.  Switching the form frees
+ * the captured apply graphs.  PCX_EINVAL for another value.
+ */
+#define PCX_PENALTY_SCALAR 0
+#define PCX_PENALTY_PER_MODE 1
+pcx_status pcx_set_penalty_form(pcx_ctx* ctx, int form);
+/* The penalty form of this context; -1 for a NULL context. */
+int pcx_get_penalty_form(const pcx_ctx* ctx);
+
 /* Result of pcx_autotune. */
 typedef struct {
   int chunk;            /* vectors per launch chunk chosen                         */
@@ -445,6 +473,9 @@ pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol
  * K_B = [K_1^H; K_2^H; K_3^H][K_1 K_2 K_3] is the Fourier form of B^H B
  * (Prop. 2.8), so out[j] = ||B h_j||^2 for the real-space field h_j = F3_3 x_j:
  * the penalty share of a Rayleigh quotient is gamma out[j] / (theta out[nvec+j]).
+ * Under PCX_PENALTY_PER_MODE each mode's term is weighted by gamma_p / gamma,
+ * so out[j] = x_j^H (sum_p gamma_p K_B(p)) x_j / gamma and the share formula
+ * stands.
  * Stream-ordered; X as in pcx_apply.
  */
 pcx_status pcx_div_norms(pcx_ctx* ctx, const double k[3], const void* X, int nvec, int precision, double* out,

@@ -32,10 +32,11 @@ def dense_matrix(apply, dim: int, batch: int = 256) -> np.ndarray:
     return np.concatenate(cols, axis=0).T
 
 
-def homogeneous_spectrum(kap: np.ndarray, inv_eps: np.ndarray, gamma: float) -> np.ndarray:
-    """Sorted spectrum of the Fourier-basis operator for a homogeneous medium."""
+def homogeneous_spectrum(kap: np.ndarray, inv_eps: np.ndarray, gamma) -> np.ndarray:
+    """Sorted spectrum of the Fourier-basis operator for a homogeneous medium
+    (gamma a scalar or per-mode (N, N, N) coefficients)."""
     ka = fourier.ka_matrix(kap)
-    hp = ka @ inv_eps @ np.conj(np.swapaxes(ka, -1, -2)) + gamma * fourier.kb_matrix(kap)
+    hp = ka @ inv_eps @ np.conj(np.swapaxes(ka, -1, -2)) + fourier.gamma_blocks(gamma) * fourier.kb_matrix(kap)
     return np.sort(np.linalg.eigvalsh(hp).ravel())
 
 

@@ -85,6 +85,13 @@ def _per_mode(mat: np.ndarray, x: np.ndarray) -> np.ndarray:
     return np.einsum("zyxij,...jzyx->...izyx", mat, x)
 
 
+def gamma_blocks(gamma):
+    """gamma as a factor of (N, N, N, 3, 3) per-mode blocks: a scalar as is,
+    a per-mode (N, N, N) array with two trailing axes added."""
+    g = np.asarray(gamma, dtype=np.float64)
+    return g[..., None, None] if g.ndim else float(g)
+
+
 def f3(u: np.ndarray, explicit: bool = False) -> np.ndarray:
     """F3 applied to every component (last three axes)."""
     n = u.shape[-1]
@@ -115,7 +122,8 @@ def apply_definition(x, yee, apply_m, gamma, explicit=False):
 
 
 def apply_symbols(x, kap, apply_m, gamma, explicit=False):
-    """K_A F3_3^H M F3_3 K_A^H x + gamma K_B x  (Prop. 2.8 factorisation)."""
+    """K_A F3_3^H M F3_3 K_A^H x + gamma K_B x  (Prop. 2.8 factorisation).
+    gamma: a scalar, or per-mode (N, N, N) coefficients gamma_p."""
     ka = ka_matrix(kap)
     kah = np.conj(np.swapaxes(ka, -1, -2))
     u = _per_mode(kah, x)
@@ -124,9 +132,10 @@ def apply_symbols(x, kap, apply_m, gamma, explicit=False):
 
 
 def kp_matrix(kap, gamma) -> np.ndarray:
-    """Per-mode K_P = K_A K_A^H + gamma K_B (eq. matrixfree_diagP)."""
+    """Per-mode K_P = K_A K_A^H + gamma K_B (eq. matrixfree_diagP); gamma a
+    scalar or per-mode (N, N, N) coefficients."""
     ka = ka_matrix(kap)
-    return ka @ np.conj(np.swapaxes(ka, -1, -2)) + gamma * kb_matrix(kap)
+    return ka @ np.conj(np.swapaxes(ka, -1, -2)) + gamma_blocks(gamma) * kb_matrix(kap)
 
 
 def precondition(r, kap, gamma, tiny=0.0):

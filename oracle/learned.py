@@ -256,7 +256,8 @@ def curl_scaled(w, kap):
 
 
 def sandwich_precondition(r, kap, blocks, gamma):
-    """T0 r (the curl-sandwich approximate inverse, module docstring)."""
+    """T0 r (the curl-sandwich approximate inverse, module docstring); gamma a
+    scalar or per-mode (N, N, N) coefficients."""
     eps = np.linalg.inv(blocks)
     e = fourier.f3(curl_h_scaled(r, kap))
     m = np.einsum("zyxij,...jzyx->...izyx", eps, e)

@@ -344,6 +344,17 @@ pcx_status pcx_set_apply_path(pcx_ctx* c, int path) {
   return PCX_OK;
 }
 
+pcx_status pcx_set_penalty_form(pcx_ctx* c, int form) {
+  if (!c) return inval(nullptr, "pcx_set_penalty_form: NULL context");
+  if (form != PCX_PENALTY_SCALAR && form != PCX_PENALTY_PER_MODE)
+    return inval(c, "pcx_set_penalty_form: form must be PCX_PENALTY_SCALAR or PCX_PENALTY_PER_MODE");
+  if (form != c->penalty_form) pcx::free_apply_graphs(c);
+  c->penalty_form = form;
+  return PCX_OK;
+}
+
+int pcx_get_penalty_form(const pcx_ctx* c) { return c ? c->penalty_form : -1; }
+
 int pcx_get_apply_path(const pcx_ctx* c, int precision) {
   if (!c || (precision != PCX_FP64 && precision != PCX_FP32)) return -1;
   return pcx::effective_apply_path(c, precision);

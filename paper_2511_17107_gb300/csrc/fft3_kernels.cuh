@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
       const T gam = (T)kp.gamma;
       const T igam = (T)(1.0 / kp.gamma);
-      // u = -conj(kappa) x x per mode and gamma kappa.x to the scratch
-      // (T0: u / |k|^2 and kappa.x / (gamma |k|^4)), straight from global
+      // u = -conj(kappa) x x per mode and gamma_p kappa.x to the scratch
+      // (T0: u / |k|^2 and kappa.x / (gamma_p |k|^4)), straight from global
       // memory into the tile.  THREADS is a multiple of N, so every thread
       // keeps one point n and walks the rows t = t0, t0 + THREADS / N, ...
       static_assert(C::THREADS % N == 0, "x tiles: whole rows per thread sweep");
@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
         if constexpr (T0) {
           const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
           su = k2 > (T)0 ? (T)1 / k2 : (T)0;
-          ss = su * su * igam;
+          ss = su * su * igam * fftk::penalty_inv_weight(kp, k2);
+        } else if (kp.per_mode) {
+          ss = gam * fftk::penalty_weight(kp, norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]));
         }
         sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), ss);
         const cx<T> zr = mk((T)0, (T)0);

@@ -151,6 +151,22 @@ struct Tile {
   }
 };
 
+// Penalty weight of one Fourier mode relative to kp.gamma: 1 in the scalar
+// form; max(1, 1/|kappa_p|^2) in the per-mode form (k2 = |kappa_p|^2).
+// The mode with kappa_p = 0 gets 0: its penalty term vanishes either way.
+template <typename T>
+__device__ __forceinline__ T penalty_weight(const KParams& kp, T k2) {
+  if (!kp.per_mode || k2 >= (T)1) return (T)1;
+  return k2 > (T)0 ? (T)1 / k2 : (T)0;
+}
+
+// Reciprocal of that weight, min(1, |kappa_p|^2) (per-mode form) or 1: it
+// scales 1/gamma into 1/gamma_p without a division.
+template <typename T>
+__device__ __forceinline__ T penalty_inv_weight(const KParams& kp, T k2) {
+  return kp.per_mode && k2 < (T)1 ? k2 : (T)1;
+}
+
 // kappa_i(p) = sum_j b_ji (L1(p_j) + i kt_j L0(p_j)) + i kq_i L0(p_i)
 template <typename T>
 __device__ __forceinline__ void kappa_at(const cx<T>* lam, int n, const KParams& kp, int p1, int p2, int p3,
@@ -365,8 +381,8 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
     // ---- x-axis passes: staged through shared memory, points fastest ----
     __syncthreads();   // tables visible
     if constexpr (OP == OP_PRE || OP == OP_PRE_T0) {
-      // u = -conj(kappa) x x per mode, and gamma kappa.x to the scratch
-      // (T0: u / |k|^2 and kappa.x / (gamma |k|^4))
+      // u = -conj(kappa) x x per mode, and gamma_p kappa.x to the scratch
+      // (T0: u / |k|^2 and kappa.x / (gamma_p |k|^4))
       cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
       const T gam = (T)kp.gamma;
       const T igam = (T)(1.0 / kp.gamma);
@@ -391,7 +407,9 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
         if constexpr (OP == OP_PRE_T0) {
           const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
           su = k2 > (T)0 ? (T)1 / k2 : (T)0;
-          ss = su * su * igam;
+          ss = su * su * igam * penalty_inv_weight(kp, k2);
+        } else if (kp.per_mode) {
+          ss = gam * penalty_weight(kp, norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]));
         }
         sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), ss);
         const cx<T> z = mk((T)0, (T)0);
@@ -522,14 +540,14 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
   }
 }
 
-// W = K_P^{-1} R per mode: r/|k|^2 + (1/gamma - 1) conj(k) (k . r) / |k|^4.
+// W = K_P^{-1} R per mode: r/|k|^2 + (1/gamma_p - 1) conj(k) (k . r) / |k|^4.
 template <typename T>
 __global__ void precond_kernel(const cx<T>* __restrict__ R, cx<T>* __restrict__ W, const cx<T>* __restrict__ lam,
                                int n, int nvec, KParams kp) {
   const size_t n3 = (size_t)n * n * n;
   const int lg = __ffs(n) - 1;   // n is a power of two
   const size_t total = n3 * nvec;
-  const T cg = (T)(1.0 / kp.gamma - 1.0);
+  const T ig = (T)(1.0 / kp.gamma);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const size_t v = e >> (3 * lg), mode = e & (n3 - 1);
     const int p1 = (int)(mode & (n - 1)), p2 = (int)((mode >> lg) & (n - 1)), p3 = (int)(mode >> (2 * lg));
@@ -541,6 +559,7 @@ __global__ void precond_kernel(const cx<T>* __restrict__ R, cx<T>* __restrict__ 
     cx<T> w0, w1, w2;
     if (k2 > (T)0) {
       const T ik2 = (T)1 / k2;
+      const T cg = ig * penalty_inv_weight(kp, k2) - (T)1;
       cx<T> sk = cfma(kap[2], r2, cfma(kap[1], r1, kap[0] * r0));
       sk = scale(sk, cg * ik2 * ik2);
       w0 = cfma_conj(kap[0], sk, scale(r0, ik2));
@@ -557,7 +576,8 @@ __global__ void precond_kernel(const cx<T>* __restrict__ R, cx<T>* __restrict__ 
 
 // Quadratic form of the penalty term per column: out[v] += sum over modes
 // |kappa(p) . x_v(p)|^2 = x_v^H K_B x_v (= ||B x||^2 for the real-space
-// field, Prop. 2.8), and out[nvec + v] += ||x_v||^2.  One block row per
+// field, Prop. 2.8), each mode weighted by gamma_p / gamma in the per-mode
+// form, and out[nvec + v] += ||x_v||^2.  One block row per
 // column (blockIdx.y); block sums are added with FP64 atomics.
 template <typename T>
 __global__ void __launch_bounds__(256) div_norm_kernel(const cx<T>* __restrict__ X, const cx<T>* __restrict__ lam,
@@ -573,7 +593,9 @@ __global__ void __launch_bounds__(256) div_norm_kernel(const cx<T>* __restrict__
     kappa_at<T>(lam, n, kp, p1, p2, p3, kap);
     const cx<T> x0 = x[mode], x1 = x[mode + n3], x2 = x[mode + 2 * n3];
     const cx<T> d = cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0));
-    sb += (double)norm2(d);
+    T wb = (T)1;
+    if (kp.per_mode) wb = penalty_weight(kp, norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]));
+    sb += (double)(wb * norm2(d));
     sx += (double)norm2(x0) + (double)norm2(x1) + (double)norm2(x2);
   }
 #pragma unroll
@@ -627,7 +649,7 @@ __global__ void curl_h_kernel(const cx<T>* __restrict__ X, cx<T>* __restrict__ U
   }
 }
 
-// Y (+)= s K_A Wm / |k|^2 + [R given] conj(kappa) (kappa . r) / (gamma |k|^4)
+// Y (+)= s K_A Wm / |k|^2 + [R given] conj(kappa) (kappa . r) / (gamma_p |k|^4)
 template <typename T>
 __global__ void curl_add_kernel(const cx<T>* __restrict__ Wm, const cx<T>* __restrict__ R, cx<T>* __restrict__ Y,
                                 const cx<T>* __restrict__ lam, int n, int nvec, KParams kp, T s, int accumulate) {
@@ -652,7 +674,8 @@ __global__ void curl_add_kernel(const cx<T>* __restrict__ Wm, const cx<T>* __res
       y2 = scale(cfma(kap[0], w1, scale(kap[1] * w0, (T)-1)), sw);
       if (R) {
         const cx<T> r0 = R[base], r1 = R[base + n3], r2 = R[base + 2 * n3];
-        const cx<T> sk = scale(cfma(kap[2], r2, cfma(kap[1], r1, kap[0] * r0)), ig * ik2 * ik2);
+        const cx<T> sk =
+            scale(cfma(kap[2], r2, cfma(kap[1], r1, kap[0] * r0)), ig * penalty_inv_weight(kp, k2) * ik2 * ik2);
         y0 = cfma_conj(kap[0], sk, y0);
         y1 = cfma_conj(kap[1], sk, y1);
         y2 = cfma_conj(kap[2], sk, y2);

@@ -22,8 +22,9 @@ struct KParams {
   double b[9];      // b = A^{-1}, row-major: b[3*j + i] = b_ji
   double kt[3];     // coefficient of i Lambda_0 inside S_j
   double kq[3];     // coefficient of i Lambda_0(p_i) added to kappa_i
-  double gamma;
+  double gamma;     // penalty coefficient (per-mode form: its scale, see per_mode)
   int diag_b;       // 1 when b is diagonal (simple cubic fast path)
+  int per_mode;     // 1: mode p carries gamma_p = gamma max(1, 1/|kappa_p|^2)
 };
 
 // Device-resident, k-independent tables of one context.
@@ -75,6 +76,7 @@ struct pcx_ctx {
   void* cnn_ws = nullptr;
   size_t cnn_ws_bytes = 0;
   int cnn_form = 0;   // PCX_CNN_HERMITIAN | PCX_CNN_BF16 flags
+  int penalty_form = 0;   // PCX_PENALTY_SCALAR or PCX_PENALTY_PER_MODE
   // staging for pcx_apply_host: two slots of X and Y chunks, copy streams
   // and slot events (created on first use)
   void* stage_x = nullptr;

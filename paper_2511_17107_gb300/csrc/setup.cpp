@@ -235,7 +235,7 @@ double gamma_rule(const double k[3]) {
 }
 
 KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma) {
-  KParams kp;
+  KParams kp{};   // value-initialised: graph keys compare KParams bytewise
   std::memcpy(kp.b, c->b, sizeof(kp.b));
   for (int j = 0; j < 3; ++j) {
     double kt = c->A[0 * 3 + j] * k[0] + c->A[1 * 3 + j] * k[1] + c->A[2 * 3 + j] * k[2];   // (A^T k)_j
@@ -247,7 +247,12 @@ KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma) {
       kp.kq[j] = k[j];
     }
   }
-  kp.gamma = gamma > 0 ? gamma : gamma_rule(k);
+  // Per-mode form: the rule of Remark 2.6 applied to every Fourier mode with
+  // that mode's own B eigenvalue |kappa_p|^2 (Lemma kc_ABblock) in place of
+  // |k|^2, so gamma_p |kappa_p|^2 = 4 pi^2 max(1, |kappa_p|^2) >= 4 pi^2 for
+  // every mode; the kernels take gamma_p = gamma max(1, 1/|kappa_p|^2).
+  kp.per_mode = c->penalty_form == PCX_PENALTY_PER_MODE;
+  kp.gamma = gamma > 0 ? gamma : kp.per_mode ? 4.0 * M_PI * M_PI : gamma_rule(k);
   kp.diag_b = (c->b[1] == 0 && c->b[2] == 0 && c->b[3] == 0 && c->b[5] == 0 && c->b[6] == 0 && c->b[7] == 0);
   return kp;
 }

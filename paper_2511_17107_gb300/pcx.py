@@ -19,6 +19,7 @@ PCX_OK, PCX_EINVAL, PCX_ENOMEM, PCX_ENOTHPD, PCX_ENOCONV, PCX_ENUMERIC, PCX_ECUD
 PCX_FP64, PCX_FP32 = 0, 1
 PCX_CT_SUMMED, PCX_CT_LITERAL = 0, 1
 PCX_APPLY_AUTO, PCX_APPLY_FIVE_PASS, PCX_APPLY_THREE_PASS = 0, 1, 2
+PCX_PENALTY_SCALAR, PCX_PENALTY_PER_MODE = 0, 1
 STATUS_NAMES = {0: "PCX_OK", -1: "PCX_EINVAL", -2: "PCX_ENOMEM", -3: "PCX_ENOTHPD", -4: "PCX_ENOCONV",
                 -5: "PCX_ENUMERIC", -6: "PCX_ECUDA"}
 
@@ -110,6 +111,8 @@ def lib():
             "pcx_set_apply_path": (st, [vp, C.c_int]),
             "pcx_set_cnn_form": (st, [vp, C.c_int]),
             "pcx_get_apply_path": (C.c_int, [vp, C.c_int]),
+            "pcx_set_penalty_form": (st, [vp, C.c_int]),
+            "pcx_get_penalty_form": (C.c_int, [vp]),
             "pcx_autotune": (st, [vp, C.c_int, C.c_int, vp, C.POINTER(pcx_tune_result)]),
             "pcx_sandwich_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
             "pcx_cnn_init": (st, [C.c_uint64, vp, vp]),
@@ -137,7 +140,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_set_cnn_form", "pcx_autotune",
+                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_set_penalty_form", "pcx_get_penalty_form", "pcx_set_cnn_form", "pcx_autotune",
                         "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
                         "pcx_cg_solve", "pcx_gram", "pcx_set_gram_path", "pcx_get_gram_path", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
@@ -411,6 +414,14 @@ def pcx_set_apply_path(ctx, path):
 
 def pcx_get_apply_path(ctx, precision):
     return int(lib().pcx_get_apply_path(ctx.handle, int(precision)))
+
+
+def pcx_set_penalty_form(ctx, form):
+    _check(lib().pcx_set_penalty_form(ctx.handle, int(form)), ctx.handle)
+
+
+def pcx_get_penalty_form(ctx):
+    return int(lib().pcx_get_penalty_form(ctx.handle))
 
 
 def pcx_autotune(ctx, precision, nvec, stream=None):
