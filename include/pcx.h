@@ -225,12 +225,11 @@ pcx_status pcx_apply(pcx_ctx* ctx, const double k[3], double gamma, const void* 
  * pcx_apply_noalloc -- pcx_apply for callers that cannot allocate device
  * memory.  The paper has no counterpart: this entry point exists for
  * integration, not for the method.  Some callers must not call cudaMalloc or
- * cudaFree during their steady state: a host thread that is capturing a CUDA
- * stream into a graph (allocation calls are not capturable and break the
- * capture), an application whose device memory is carved out up front by
- * its own pool or framework allocator and must not be fragmented or
- * oversubscribed by a library, or a real-time loop where an allocation's
- * latency (and its implicit device synchronisation) is not acceptable.
+ * cudaFree during their steady state: an application whose device memory is
+ * carved out up front by its own pool or framework allocator and must not be
+ * fragmented or oversubscribed by a library, or a real-time loop where an
+ * allocation's latency (and its implicit device synchronisation) is not
+ * acceptable.
  * pcx_apply may allocate (its scratch grows on demand); this variant never
  * does: no cudaMalloc, no cudaFree, no allocating library routine.
  *
@@ -245,8 +244,8 @@ pcx_status pcx_apply(pcx_ctx* ctx, const double k[3], double gamma, const void* 
  * processed in chunks that fit the array.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The address is kept for the life of the
+ * (cudaGetSymbolAddress) with that device current.  The address is kept
+ * for the life of the
  * process: a cudaDeviceReset while the library is loaded is not supported.
  * The context's device must be current (PCX_EINVAL otherwise).
  * The array is shared by every call and keeps the last call's contents;

@@ -102,13 +102,14 @@ void pcx_destroy(pcx_ctx* c) {
     pcx::gram_cc_release_stream(st);
     pcx::gram_tc_release_stream(st);
     pcx::gram_x_release_stream(st);
+    pcx::cnn_release_stream(st);
     cudaStreamDestroy(st);
   }
   for (auto& row : c->slot_event)
     for (auto& ev : row)
       if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64,  c->dev.tw32, c->dev.m64,  c->dev.m32,
-                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->cnn_ws, c->ktab,
+                  c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->ktab,
                   c->dev.mid3};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -15,25 +15,24 @@
 
 #include "cnn.h"
 #include "pcx_internal.h"
+#include "stream_scratch.h"
 
 namespace pcx {
 
 namespace {
 
-// context-owned workspace, grown on demand (the previous one may still be in
-// use by queued work, so growth synchronises the device)
-cudaError_t ws_get(pcx_ctx* c, size_t bytes, char** out) {
-  if (bytes > c->cnn_ws_bytes) {
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return e;
-    if (c->cnn_ws) cudaFree(c->cnn_ws);
-    c->cnn_ws = nullptr;
-    c->cnn_ws_bytes = 0;
-    if ((e = cudaMalloc(&c->cnn_ws, bytes)) != cudaSuccess) return e;
-    c->cnn_ws_bytes = bytes;
-  }
-  *out = static_cast<char*>(c->cnn_ws);
-  return cudaSuccess;
+// Workspace of the learned-correction kernels, keyed by (device, stream)
+// and shared by every context: a training loop over many structures (one
+// context each) holds one buffer, not one per context.  Grown on demand;
+// growth synchronises the device, since queued work may still read the old
+// buffer.
+StreamScratch g_cnn_ws;
+
+cudaError_t ws_get(cudaStream_t s, size_t bytes, char** out) {
+  void* p = nullptr;
+  cudaError_t e = g_cnn_ws.get(s, bytes, &p);
+  *out = static_cast<char*>(p);
+  return e;
 }
 
 size_t align_up(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -53,6 +52,8 @@ constexpr int C = cnn::HIDDEN;
 
 }  // namespace
 
+void cnn_release_stream(cudaStream_t s) { g_cnn_ws.release(s); }
+
 #define CKE(x)                                 \
   do {                                         \
     cudaError_t _e = (x);                      \
@@ -62,7 +63,7 @@ constexpr int C = cnn::HIDDEN;
 cudaError_t cnn_gates(pcx_ctx* c, const float* params, float* gates, cudaStream_t s) {
   const size_t n3 = (size_t)c->n * c->n * c->n;
   char* ws;
-  CKE(ws_get(c, align_up(9 * n3 * sizeof(float)), &ws));
+  CKE(ws_get(s, align_up(9 * n3 * sizeof(float)), &ws));
   float* f = reinterpret_cast<float*>(ws);
   CKE(cnn::features(c, f, s));
   const cnn::View fv = cnn::shared_view(f, n3), none{};
@@ -133,7 +134,7 @@ cudaError_t cnn_forward(pcx_ctx* c, const float* params, const float* gates, con
   const int chunk = forward_chunk_size(c, nvec);
   const size_t hb = align_up(2 * (size_t)chunk * C * n3 * sizeof(float));
   char* ws;
-  CKE(ws_get(c, 2 * hb + align_up(ADJ_FLOATS * sizeof(float)), &ws));
+  CKE(ws_get(s, 2 * hb + align_up(ADJ_FLOATS * sizeof(float)), &ws));
   float* h1 = reinterpret_cast<float*>(ws);
   float* h2 = reinterpret_cast<float*>(ws + hb);
   float* adj = reinterpret_cast<float*>(ws + 2 * hb);
@@ -169,7 +170,7 @@ cudaError_t cnn_grad(pcx_ctx* c, const float* params, const void* U, const void*
   need += align_up(cnn::wgrad_scratch_floats(9, C) * 4);             // the largest wgrad scratch
   need += 2 * align_up(C * C * 27 * 4) + align_up(ADJ_FLOATS * 4) + align_up(nvec * 8 + 8);   // weights, w, loss
   char* ws;
-  CKE(ws_get(c, need, &ws));
+  CKE(ws_get(s, need, &ws));
   Carve cv{ws};
   float* f = cv.take<float>(9 * n3);
   float* g = cv.take<float>(2 * C * n3);
@@ -293,7 +294,7 @@ cudaError_t cnn_precond(pcx_ctx* c, const KParams& kp, const float* params, cons
   const size_t hb = align_up(2 * (size_t)chunk * C * n3 * sizeof(float));
   const size_t tb = align_up((size_t)chunk * 3 * n3 * sizeof(float2));
   char* ws;
-  CKE(ws_get(c, 2 * hb + 2 * tb + align_up(ADJ_FLOATS * sizeof(float)), &ws));
+  CKE(ws_get(s, 2 * hb + 2 * tb + align_up(ADJ_FLOATS * sizeof(float)), &ws));
   float* h1 = reinterpret_cast<float*>(ws);
   float* h2 = reinterpret_cast<float*>(ws + hb);
   float2* e = reinterpret_cast<float2*>(ws + 2 * hb);
@@ -332,7 +333,7 @@ cudaError_t cnn_pairs(pcx_ctx* c, const KParams& kp, const void* R, const void* 
   if (enorm2_host) {
     CKE(launch_curl_h(c, kp, E, U, nvec, 0, PCX_FP32, s));
     char* ws;
-    CKE(ws_get(c, align_up(2 * nvec * sizeof(double)), &ws));
+    CKE(ws_get(s, align_up(2 * nvec * sizeof(double)), &ws));
     double* d = reinterpret_cast<double*>(ws);
     CKE(cnn::col_dots(U, U, nvec, 3 * n3, d, s));
     std::vector<double> h(2 * (size_t)nvec);
@@ -355,7 +356,7 @@ cudaError_t cg_solve(pcx_ctx* c, const KParams& kp, const void* R, void* E, int 
   const size_t n3 = (size_t)c->n * c->n * c->n, len = 3 * n3;
   const size_t vb = align_up((size_t)nvec * len * sizeof(float2));
   char* ws;
-  CKE(ws_get(c, 4 * vb + align_up(6 * (size_t)nvec * sizeof(double)), &ws));
+  CKE(ws_get(s, 4 * vb + align_up(6 * (size_t)nvec * sizeof(double)), &ws));
   float2* res = reinterpret_cast<float2*>(ws);
   float2* z = reinterpret_cast<float2*>(ws + vb);
   float2* p = reinterpret_cast<float2*>(ws + 2 * vb);

@@ -72,9 +72,6 @@ struct pcx_ctx {
   // CUDA graphs of the apply launch chain (fft_apply.cu), when enabled
   int use_graphs = 0;
   void* graphs = nullptr;
-  // workspace of the learned-correction kernels (learned.cpp)
-  void* cnn_ws = nullptr;
-  size_t cnn_ws_bytes = 0;
   int cnn_form = 0;   // PCX_CNN_HERMITIAN | PCX_CNN_BF16 flags
   int penalty_form = 0;   // PCX_PENALTY_SCALAR or PCX_PENALTY_PER_MODE
   // staging for pcx_apply_host: two slots of X and Y chunks, copy streams
@@ -178,6 +175,7 @@ void set_gram_path(int path);
 void gram_cc_release_stream(cudaStream_t s);
 void gram_tc_release_stream(cudaStream_t s);
 void gram_x_release_stream(cudaStream_t s);
+void cnn_release_stream(cudaStream_t s);
 int get_gram_path();
 // G = [A1 | A2]^H B: A1 (na1 columns) and A2 (na2 columns) complex128, B
 // complex64; double-float accumulation on the FP32 pipes.

@@ -1,7 +1,6 @@
 """pcx_apply_noalloc: the apply variant for callers that cannot allocate
-device memory (for example while a stream is being captured into a CUDA
-graph, or when the application owns all device memory through its own
-pool).  Its scratch is a 32 MiB file-scope device array instead of a
+device memory (for example when the application owns all device memory
+through its own pool).  Its scratch is a 32 MiB file-scope device array instead of a
 cudaMalloc'd buffer.
 
 The test calls the entry point through the C ABI twice in a row and checks
