@@ -47,20 +47,22 @@ template <> struct YSplit<128> { static constexpr int RA = 16, RB = 8; };
 // Geometry of the z tiles (pass B): RB rows x TPX columns of z pencils, at
 // least 32 bytes of consecutive x per row so that every global access of
 // the pass fills whole 32-byte sectors.  At N = 128 that is 32 pencils
-// (96 KB of complex64 for the three components), two CTAs per SM with 32
-// elements per thread and stage.
+// (96 KB of complex64 for the three components), two CTAs per SM of 256
+// threads with 48 elements per thread and stage: the fused inverse-stage /
+// M / forward-stage step holds three components of eight points, which
+// needs more than the 80 registers a 384-thread CTA could have.
 #ifndef PCX_Z128_TN
 #define PCX_Z128_TN 4096
 #endif
 #ifndef PCX_Z128_E
-#define PCX_Z128_E 32
+#define PCX_Z128_E 48
 #endif
 #ifndef PCX_Z128_MINB
 #define PCX_Z128_MINB 2
 #endif
 template <int N>
 struct ZGeom {
-  static constexpr int TN = 2048, E = 16, MINB = 3;
+  static constexpr int TN = 2048, E = 16, MINB = 2;
 };
 template <> struct ZGeom<128> { static constexpr int TN = PCX_Z128_TN, E = PCX_Z128_E, MINB = PCX_Z128_MINB; };
 
@@ -79,7 +81,6 @@ struct Cfg3 {
   static constexpr int ZTILES = N * N / TPZ;        // z tiles per vector
   static constexpr int XI_PER_THREAD = 3 * G * N / THREADS;           // row-DFT items (RA points)
   static constexpr int ZI_PER_THREAD = 3 * N * (TPX / 2) / THREADSZ;  // row-DFT items (2 x RB points)
-  static constexpr int MI_PER_THREAD = (TPZ * N + THREADSZ - 1) / THREADSZ;   // cells per thread in the M step
   static_assert(RA * RB == N && G >= 1 && G * RA == TP && TPX * RB == TPZ, "tile split");
   static_assert(TPX % 2 == 0 && XI_PER_THREAD >= 1 && ZI_PER_THREAD >= 1, "work split");
   static_assert(XI_PER_THREAD * THREADS == 3 * G * N && ZI_PER_THREAD * THREADSZ == 3 * N * (TPX / 2),
@@ -96,9 +97,17 @@ template <typename T, int N, int OP>
 __host__ __device__ constexpr int pass3_threads() {
   return is_z_op<OP>() ? Cfg3<T, N>::THREADSZ : Cfg3<T, N>::THREADS;
 }
+// x tiles (passes A and C): CTAs per SM the registers are sized for, and
+// rows whose global loads are issued together before their arithmetic
+#ifndef PCX_X3_MINB
+#define PCX_X3_MINB 3
+#endif
+#ifndef PCX_X3_PF
+#define PCX_X3_PF 1
+#endif
 template <typename T, int N, int OP>
 __host__ __device__ constexpr int pass3_minb() {
-  return is_z_op<OP>() ? ZGeom<N>::MINB : 3;
+  return is_z_op<OP>() ? ZGeom<N>::MINB : PCX_X3_MINB;
 }
 
 // Row of pencil t of x tile `tile` (within one vector): z, y, and the n2
@@ -192,14 +201,31 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       cx<T> kan[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
+      constexpr int NI = (TP + TSTEP - 1) / TSTEP;
+      constexpr int PF = PCX_X3_PF < NI ? PCX_X3_PF : NI;
 #pragma unroll
-      for (int i = 0; i < (TP + TSTEP - 1) / TSTEP; ++i) {
-        const int t = t0 + i * TSTEP;
-        if (t >= TP) break;
-        int z, y, j;
-        x_row<T, N>(tile, t, z, y, j);
-        const int g = z * N2 + y * N + n;
-        const cx<T> x0 = in[g], x1 = in[N3 + g], x2 = in[2 * N3 + g];
+      for (int i0 = 0; i0 < NI; i0 += PF) {
+      // the rows of this batch: their loads in flight together
+      cx<T> xv[PF][3];
+      int gv[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u < NI && t < TP) {
+          int z, y, j;
+          x_row<T, N>(tile, t, z, y, j);
+          gv[u] = z * N2 + y * N + n;
+          xv[u][0] = in[gv[u]];
+          xv[u][1] = in[N3 + gv[u]];
+          xv[u][2] = in[2 * N3 + gv[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u >= NI || t >= TP) break;
+        const int g = gv[u];
+        const cx<T> x0 = xv[u][0], x1 = xv[u][1], x2 = xv[u][2];
         cx<T> kap[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
@@ -224,6 +250,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
         s[TL::sidx(0, t, n)] = u0;
         s[TL::sidx(1, t, n)] = u1;
         s[TL::sidx(2, t, n)] = u2;
+      }
       }
       __syncthreads();
       fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
@@ -275,14 +302,28 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       cx<T> kan[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
+      constexpr int NI = (TP + TSTEP - 1) / TSTEP;
+      constexpr int PF = PCX_X3_PF < NI ? PCX_X3_PF : NI;
 #pragma unroll
-      for (int i = 0; i < (TP + TSTEP - 1) / TSTEP; ++i) {
-        const int t = t0 + i * TSTEP;
-        if (t >= TP) break;
-        int z, y, j;
-        x_row<T, N>(tile, t, z, y, j);
-        const int g = z * N2 + y * N + n;
-        const cx<T> sk = sb[g];
+      for (int i0 = 0; i0 < NI; i0 += PF) {
+      cx<T> skv[PF];
+      int gv[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u < NI && t < TP) {
+          int z, y, j;
+          x_row<T, N>(tile, t, z, y, j);
+          gv[u] = z * N2 + y * N + n;
+          skv[u] = sb[gv[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u >= NI || t >= TP) break;
+        const int g = gv[u];
+        const cx<T> sk = skv[u];
         cx<T> kap[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
@@ -300,6 +341,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
         out[g] = cfma_conj(kap[0], sk, c0);
         out[N3 + g] = cfma_conj(kap[1], sk, c1);
         out[2 * N3 + g] = cfma_conj(kap[2], sk, c2);
+      }
       }
     }
   } else {
@@ -338,79 +380,130 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       }
     }
     __syncthreads();
-    fft_tile<T, N, 2, +1, 0, 0, C>(s, tw, nullptr, nullptr, 0);
-    // material ids of the tile's cells in the pass's own order (mid3: one
-    // contiguous run of TP N ids per tile), all loads in flight at once
-    uchar4 idr[C3::MI_PER_THREAD];
-    if (mid3) {
-      const uchar4* tid3 = mid3 + (size_t)tile * TP * N;
-#pragma unroll
-      for (int i = 0; i < C3::MI_PER_THREAD; ++i) {
-        const int w = threadIdx.x + i * C::THREADS;
-        if (w < TP * N) idr[i] = tid3[w];
-      }
-    }
+    // z transforms of the tile with plan (R0, R1): the inverse as two
+    // Stockham stages (radix R0 at Ns = 1, radix R1 at Ns = R0), the forward
+    // as radix R1 at Ns = 1 then radix R0 at Ns = R1.  The inverse's second
+    // stage reads and writes the R1 points j + R0 r of a pencil, which are
+    // also the inputs of the forward's first stage, so those two stages and
+    // the cell-by-cell M between them run in registers on the same points
+    // (all three components): two shared-memory round trips fewer.  The
+    // forward's first stage leaves element r of butterfly j at position
+    // j + R0 r (not at j R1 + r), which its second stage reads back.
+    using P = typename C::P;
+    constexpr int R0 = P::R0, R1 = P::R1;
+    static_assert(P::NST == 2 && R0 * R1 == N, "two-stage z plan");
+    stage<T, N, 2, R0, +1, 0, 0, C>(s, tw, 1, nullptr, nullptr, 0);
     const T inv_n3 = (T)(1.0 / (double)N3);
+    const uchar4* tid3 = mid3 ? mid3 + (size_t)tile * TP * N : nullptr;
+    for (int w = threadIdx.x; w < TP * R0; w += C::THREADS) {
+      const int t = w % TP, j = w / TP;
+      cx<T> v[3][R1];
 #pragma unroll
-    for (int i = 0; i < C3::MI_PER_THREAD; ++i) {   // pencils fastest
-      const int w = threadIdx.x + i * C::THREADS;
-      if (w >= TP * N) break;
-      const int t = w % TP, n = w / TP;
-      T d1, d2, d3;
-      cx<T> o12, o13, o23;
-      if (mid3) {
-        const uchar4 id = idr[i];
-        d1 = mtab[12 * id.x];
-        d2 = mtab[12 * id.y + 1];
-        d3 = mtab[12 * id.z + 2];
-        const T* o = mtab + 12 * id.w;
-        if constexpr (sizeof(T) == 4) {
-          const float4 q = *reinterpret_cast<const float4*>(o + 4);
-          const float2 r = *reinterpret_cast<const float2*>(o + 8);
-          o12 = mk(q.x, q.y);
-          o13 = mk(q.z, q.w);
-          o23 = mk(r.x, r.y);
+      for (int c = 0; c < 3; ++c) {
+        const cx<T>* sp = s + TL::sidx(c, t, j);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[c][r] = sp[r * R0 * TL::SN];
+      }
+#pragma unroll
+      for (int r = 1; r < R1; ++r) {
+        cx<T> wt = tw[r * j];   // inverse: e^{+2 pi i r j / N}
+        wt.y = -wt.y;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * wt;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dft<R1, +1>(v[c]);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int n = j + R0 * r;
+        T d1, d2, d3;
+        cx<T> o12, o13, o23;
+        if (tid3) {
+          const uchar4 id = tid3[n * TP + t];
+          d1 = mtab[12 * id.x];
+          d2 = mtab[12 * id.y + 1];
+          d3 = mtab[12 * id.z + 2];
+          const T* o = mtab + 12 * id.w;
+          if constexpr (sizeof(T) == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(o + 4);
+            const float2 q2 = *reinterpret_cast<const float2*>(o + 8);
+            o12 = mk(q.x, q.y);
+            o13 = mk(q.z, q.w);
+            o23 = mk(q2.x, q2.y);
+          } else {
+            o12 = mk(o[4], o[5]);
+            o13 = mk(o[6], o[7]);
+            o23 = mk(o[8], o[9]);
+          }
         } else {
-          o12 = mk(o[4], o[5]);
-          o13 = mk(o[6], o[7]);
-          o23 = mk(o[8], o[9]);
+          const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
+          d1 = M[cell];
+          d2 = M[N3 + cell];
+          d3 = M[2 * N3 + cell];
+          o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
+          o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
+          o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
         }
-      } else {
-        const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
-        d1 = M[cell];
-        d2 = M[N3 + cell];
-        d3 = M[2 * N3 + cell];
-        o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
-        o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
-        o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
+        T sc = inv_n3;
+        if constexpr (OP == OP_SANDWICH_EPS) {
+          // eps = M^{-1} = adj(M) / det(M) on the Hermitian block
+          const T a11 = d2 * d3 - norm2(o23), a22 = d1 * d3 - norm2(o13), a33 = d1 * d2 - norm2(o12);
+          const cx<T> a12 = o13 * conjg(o23) - scale(o12, d3);
+          const cx<T> a13 = o12 * o23 - scale(o13, d2);
+          const cx<T> a23 = o13 * conjg(o12) - scale(o23, d1);
+          const T det = d1 * a11 + (o12 * conjg(a12)).x + (o13 * conjg(a13)).x;
+          sc = inv_n3 / det;
+          d1 = a11;
+          d2 = a22;
+          d3 = a33;
+          o12 = a12;
+          o13 = a13;
+          o23 = a23;
+        }
+        const cx<T> e0 = v[0][r], e1 = v[1][r], e2 = v[2][r];
+        v[0][r] = scale(cfma(o13, e2, cfma(o12, e1, scale(e0, d1))), sc);
+        v[1][r] = scale(cfma(o23, e2, cfma_conj(o12, e0, scale(e1, d2))), sc);
+        v[2][r] = scale(cfma_conj(o23, e1, cfma_conj(o13, e0, scale(e2, d3))), sc);
       }
-      const int i0 = TL::sidx(0, t, n), i1 = TL::sidx(1, t, n), i2 = TL::sidx(2, t, n);
-      const cx<T> e0 = s[i0], e1 = s[i1], e2 = s[i2];
-      T sc = inv_n3;
-      if constexpr (OP == OP_SANDWICH_EPS) {
-        // eps = M^{-1} = adj(M) / det(M) on the Hermitian block
-        const T a11 = d2 * d3 - norm2(o23), a22 = d1 * d3 - norm2(o13), a33 = d1 * d2 - norm2(o12);
-        const cx<T> a12 = o13 * conjg(o23) - scale(o12, d3);
-        const cx<T> a13 = o12 * o23 - scale(o13, d2);
-        const cx<T> a23 = o13 * conjg(o12) - scale(o23, d1);
-        const T det = d1 * a11 + (o12 * conjg(a12)).x + (o13 * conjg(a13)).x;
-        sc = inv_n3 / det;
-        d1 = a11;
-        d2 = a22;
-        d3 = a33;
-        o12 = a12;
-        o13 = a13;
-        o23 = a23;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dft<R1, -1>(v[c]);
+        cx<T>* sp = s + TL::sidx(c, t, j);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) sp[r * R0 * TL::SN] = v[c][r];
       }
-      const cx<T> m0 = cfma(o13, e2, cfma(o12, e1, scale(e0, d1)));
-      const cx<T> m1 = cfma(o23, e2, cfma_conj(o12, e0, scale(e1, d2)));
-      const cx<T> m2 = cfma_conj(o23, e1, cfma_conj(o13, e0, scale(e2, d3)));
-      s[i0] = scale(m0, sc);
-      s[i1] = scale(m1, sc);
-      s[i2] = scale(m2, sc);
     }
     __syncthreads();
-    fft_tile<T, N, 2, -1, 0, 0, C>(s, tw, nullptr, nullptr, 0);
+    // forward second stage (radix R0 at Ns = R1): butterfly jj reads its R0
+    // inputs from the consecutive positions R0 jj + q, twiddle
+    // e^{-2 pi i q jj / N}, and writes the transform in natural order,
+    // positions jj + R1 q
+    {
+      constexpr int PER = 3 * TP * R1 / C::THREADS;
+      static_assert(PER * C::THREADS == 3 * TP * R1, "forward second stage: whole items per thread");
+      cx<T> v[PER][R0];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int w = threadIdx.x + i * C::THREADS;
+        const int t = w % TP, jj = (w / TP) % R1, c = w / (TP * R1);
+        const cx<T>* sp = s + TL::sidx(c, t, R0 * jj);
+#pragma unroll
+        for (int q = 0; q < R0; ++q) v[i][q] = sp[q * TL::SN];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int w = threadIdx.x + i * C::THREADS;
+        const int t = w % TP, jj = (w / TP) % R1, c = w / (TP * R1);
+#pragma unroll
+        for (int q = 1; q < R0; ++q) v[i][q] = v[i][q] * tw[q * jj];
+        dft<R0, -1>(v[i]);
+        cx<T>* sp = s + TL::sidx(c, t, jj);
+#pragma unroll
+        for (int q = 0; q < R0; ++q) sp[q * R1 * TL::SN] = v[i][q];
+      }
+      __syncthreads();
+    }
     // RB-point forward y DFT over k2, twiddle e^{-2 pi i k1 m1 / N}, store
     // to rows RB k1 + m1
 #pragma unroll

@@ -62,6 +62,7 @@ template <> struct Plan<32, 8> { static constexpr int R0 = 8, R1 = 4, R2 = 0, NS
 template <> struct Plan<64, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 0, NST = 2; };
 template <> struct Plan<128, 8> { static constexpr int R0 = 8, R1 = 4, R2 = 4, NST = 3; };
 template <> struct Plan<128, 32> { static constexpr int R0 = 16, R1 = 8, R2 = 0, NST = 2; };
+template <> struct Plan<128, 48> { static constexpr int R0 = 16, R1 = 8, R2 = 0, NST = 2; };
 template <> struct Plan<256, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 4, NST = 3; };
 
 // Tile shape of the complex64 passes (elements per thread, pencils x points

@@ -31,6 +31,13 @@
 #include "linalg.h"
 #include "pcx_internal.h"
 
+// Projection-and-Cholesky-QR passes of the refinement's [P W] block against
+// X (two: the second removes what FP32 rounding left of X in the first);
+// a build-time choice for tuning builds.
+#ifndef PCX_ORTH_PASSES
+#define PCX_ORTH_PASSES 2
+#endif
+
 namespace pcx {
 namespace {
 
@@ -513,7 +520,7 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     // the identity; P is dropped when [P W] is numerically rank deficient.
     auto orth_block = [&](int c0, int cnt, bool& okb) -> pcx_status {
       okb = true;
-      for (int pass = 0; pass < 2 && okb; ++pass) {
+      for (int pass = 0; pass < PCX_ORTH_PASSES && okb; ++pass) {
         std::vector<cd> xw;
         pcx_status s2;
         if ((s2 = r32.gram(r32.S.p, n, r32.col(r32.S, c0), cnt, xw)) != PCX_OK) return s2;
