@@ -66,10 +66,32 @@ struct ZGeom {
 };
 template <> struct ZGeom<128> { static constexpr int TN = PCX_Z128_TN, E = PCX_Z128_E, MINB = PCX_Z128_MINB; };
 
+// Row padding of the z tiles.  Pass B's y DFTs stage two x columns per
+// thread (one 16-byte global access); the lanes of a half-warp cover H =
+// TPX / 2 column pairs at 16 / H points n.  Column xo of a tile row sits at
+// pencil position perm(xo) = xo / 2 + H (xo % 2), so the two columns of a
+// pair land H apart, and with a row stride SN = H (mod 16) the half-warp's
+// 8-byte words n SN + xp (+ H) fall in 16 distinct bank pairs.
+template <int N>
+struct ZPad {
+  static constexpr int TPZ = ZGeom<N>::TN / N;
+  static constexpr int H = TPZ / YSplit<N>::RB / 2;
+  static constexpr int R = ((H - TPZ) % 16 + 16) % 16;
+  static constexpr int V = R == 0 ? 16 : R;
+};
+template <int TPX>
+__host__ __device__ constexpr int zcol_pos(int xo) {   // pencil position of tile column xo
+  return (xo >> 1) + (xo & 1) * (TPX / 2);
+}
+template <int TPX>
+__host__ __device__ constexpr int zcol_of(int q) {     // tile column at pencil position q
+  return q < TPX / 2 ? 2 * q : 2 * (q - TPX / 2) + 1;
+}
+
 template <typename T, int N>
 struct Cfg3 {
-  using C = Cfg<T, N>;                              // x tiles (passes A and C)
-  using CZ = CfgG<T, N, ZGeom<N>::TN, ZGeom<N>::E>; // z tiles (pass B)
+  using C = Cfg<T, N>;                                           // x tiles (passes A and C)
+  using CZ = CfgG<T, N, ZGeom<N>::TN, ZGeom<N>::E, ZPad<N>::V>;  // z tiles (pass B)
   static constexpr int TP = C::TP;                  // pencils (rows) per x tile
   static constexpr int THREADS = C::THREADS;
   static constexpr int TPZ = CZ::TP;                // pencils per z tile
@@ -103,7 +125,7 @@ __host__ __device__ constexpr int pass3_threads() {
 #define PCX_X3_MINB 3
 #endif
 #ifndef PCX_X3_PF
-#define PCX_X3_PF 1
+#define PCX_X3_PF 3
 #endif
 template <typename T, int N, int OP>
 __host__ __device__ constexpr int pass3_minb() {
@@ -131,7 +153,7 @@ __device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams&
     if (e < 3 * N) {
       const int i = e / N, p = e % N;
       const cx<T> l1 = glam[p], l0 = glam[N + p];
-      const T b0 = (T)kp.b[i];
+      const T b0 = (T)kp_b(kp, 0, i);
       const T kt = (T)kp.kt[0];
       cx<T> r = mk(b0 * fma(-kt, l0.y, l1.x), b0 * fma(kt, l0.x, l1.y));
       if (i == 0) r = mk(fma(-(T)kp.kq[0], l0.y, r.x), fma((T)kp.kq[0], l0.x, r.y));
@@ -145,7 +167,7 @@ __device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams&
 #pragma unroll
       for (int jj = 1; jj < 3; ++jj) {
         const cx<T> l1 = glam[p[jj]], l0 = glam[N + p[jj]];
-        const T bj = (T)kp.b[3 * jj + i], kt = (T)kp.kt[jj];
+        const T bj = (T)kp_b(kp, jj, i), kt = (T)kp.kt[jj];
         r = mk(fma(bj, fma(-kt, l0.y, l1.x), r.x), fma(bj, fma(kt, l0.x, l1.y), r.y));
         if (i == jj) r = mk(fma(-(T)kp.kq[jj], l0.y, r.x), fma((T)kp.kq[jj], l0.x, r.y));
       }
@@ -375,8 +397,8 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       dft<RB, +1>(r1);
 #pragma unroll
       for (int k2 = 0; k2 < RB; ++k2) {
-        s[TL::sidx(c, k2 * TPX + 2 * xp, z)] = r0[k2];
-        s[TL::sidx(c, k2 * TPX + 2 * xp + 1, z)] = r1[k2];
+        s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp), z)] = r0[k2];
+        s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp + 1), z)] = r1[k2];
       }
     }
     __syncthreads();
@@ -436,7 +458,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
             o23 = mk(o[8], o[9]);
           }
         } else {
-          const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + t % TPX;
+          const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + zcol_of<TPX>(t % TPX);
           d1 = M[cell];
           d2 = M[N3 + cell];
           d3 = M[2 * N3 + cell];
@@ -513,8 +535,8 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       cx<T> r0[RB], r1[RB];
 #pragma unroll
       for (int k2 = 0; k2 < RB; ++k2) {
-        r0[k2] = s[TL::sidx(c, k2 * TPX + 2 * xp, z)];
-        r1[k2] = s[TL::sidx(c, k2 * TPX + 2 * xp + 1, z)];
+        r0[k2] = s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp), z)];
+        r1[k2] = s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp + 1), z)];
       }
       dft<RB, -1>(r0);
       dft<RB, -1>(r1);
@@ -529,8 +551,8 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
 }
 
 // mid3[tile][w] = mid[cell] for the z tiles of pass B: tile = k1 (N / TPX) +
-// xr, w = n TP + t, pencil t = k2 TPX + xo, cell (x, y, z) = (xr TPX + xo,
-// k1 + RA k2, n).
+// xr, w = n TP + t, pencil t = k2 TPX + q holding tile column xo =
+// zcol_of(q), cell (x, y, z) = (xr TPX + xo, k1 + RA k2, n).
 template <int N>
 __global__ void pass3_ids_kernel(const uchar4* __restrict__ mid, uchar4* __restrict__ mid3) {
   using C3 = Cfg3<float, N>;
@@ -540,7 +562,7 @@ __global__ void pass3_ids_kernel(const uchar4* __restrict__ mid, uchar4* __restr
     const int tile = (int)(e / ((size_t)TP * N)), w = (int)(e % ((size_t)TP * N));
     const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
     const int t = w % TP, n = w / TP;
-    mid3[e] = mid[(size_t)n * N * N + (size_t)(k1 + RA * (t / TPX)) * N + x0 + t % TPX];
+    mid3[e] = mid[(size_t)n * N * N + (size_t)(k1 + RA * (t / TPX)) * N + x0 + zcol_of<TPX>(t % TPX)];
   }
 }
 

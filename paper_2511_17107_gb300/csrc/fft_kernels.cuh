@@ -76,12 +76,15 @@ template <> struct Plan<256, 8> { static constexpr int R0 = 8, R1 = 8, R2 = 4, N
 
 // Tile geometry: E elements per thread and stage, TN pencils x points per
 // component (TP pencils per CTA).
-template <typename T, int N, int TN_, int E_>
+// PAD: the row stride of y/z tiles is TP + PAD (see Tile).
+template <typename T, int N, int TN_, int E_, int PAD_ = 1>
 struct CfgG {
   static constexpr int E = E_;
   static constexpr int TN = TN_;
   static constexpr int TP = (TN / N < N * N) ? TN / N : N * N;   // pencils per CTA
   static constexpr int THREADS = 3 * TP * N / E;
+  static constexpr int PAD = PAD_;
+  static_assert(PAD >= 1 && N * PAD <= (N > 8 * TP ? N : 8 * TP), "row padding fits the component stride");
   // padded component stride: y/z tiles use N rows of TP + 1, x tiles TP
   // pencils of N + 8 (see Tile)
   static constexpr int CS = N * TP + (N > 8 * TP ? N : 8 * TP);
@@ -117,9 +120,10 @@ template <typename T, int N, int AXIS, class CF = Cfg<T, N>>
 struct Tile {
   static constexpr int TP = CF::TP;
   static constexpr int CS = CF::CS;
-  // y/z tiles: pencils fastest, odd row stride TP + 1 (conflict-free for
-  // pencil-fastest and point-fastest walks).
-  static constexpr int SN = TP + 1;
+  // y/z tiles: pencils fastest, row stride TP + PAD (PAD = 1, an odd stride,
+  // is conflict-free for pencil-fastest and point-fastest walks; the z tiles
+  // of the three-pass chain choose theirs for their y-DFT staging).
+  static constexpr int SN = TP + CF::PAD;
   // x tiles: points fastest within a pencil, pencil stride N + 8 (= 8 mod 16)
   // and the point index XOR-swizzled inside each group of 16, n ^ (n>>4 & 15),
   // so that radix-R writes at stride R, reads at stride N/R and point-fastest
@@ -166,6 +170,13 @@ __device__ __forceinline__ T penalty_weight(const KParams& kp, T k2) {
 template <typename T>
 __device__ __forceinline__ T penalty_inv_weight(const KParams& kp, T k2) {
   return kp.per_mode && k2 < (T)1 ? k2 : (T)1;
+}
+
+// kp.b[3 row + i] for a run-time column i in {0, 1, 2} (row a compile-time
+// constant after unrolling), by selection: a run-time index into the
+// parameter struct would make each thread keep a copy of it in local memory.
+__device__ __forceinline__ double kp_b(const KParams& kp, int row, int i) {
+  return i == 0 ? kp.b[3 * row] : (i == 1 ? kp.b[3 * row + 1] : kp.b[3 * row + 2]);
 }
 
 // kappa_i(p) = sum_j b_ji (L1(p_j) + i kt_j L0(p_j)) + i kq_i L0(p_i)
@@ -348,7 +359,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
       if (e < 3 * N) {
         const int i = e / N, p = e % N;
         const cx<T> l1 = glam[p], l0 = glam[N + p];
-        const T b0 = (T)kp.b[i];   // b_1i (row j = 0)
+        const T b0 = (T)kp_b(kp, 0, i);   // b_1i (row j = 0)
         const T kt = (T)kp.kt[0];
         cx<T> r = mk(b0 * fma(-kt, l0.y, l1.x), b0 * fma(kt, l0.x, l1.y));
         if (i == 0) r = mk(fma(-(T)kp.kq[0], l0.y, r.x), fma((T)kp.kq[0], l0.x, r.y));
@@ -360,7 +371,7 @@ __global__ void __launch_bounds__(Cfg<T, N>::THREADS, sizeof(T) == 4 ? 3 : 1) pa
 #pragma unroll
         for (int j = 1; j < 3; ++j) {
           const cx<T> l1 = glam[p[j]], l0 = glam[N + p[j]];
-          const T bj = (T)kp.b[3 * j + i], kt = (T)kp.kt[j];
+          const T bj = (T)kp_b(kp, j, i), kt = (T)kp.kt[j];
           r = mk(fma(bj, fma(-kt, l0.y, l1.x), r.x), fma(bj, fma(kt, l0.x, l1.y), r.y));
           if (i == j) r = mk(fma(-(T)kp.kq[j], l0.y, r.x), fma((T)kp.kq[j], l0.x, r.y));
         }

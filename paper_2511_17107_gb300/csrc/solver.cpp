@@ -32,10 +32,13 @@
 #include "pcx_internal.h"
 
 // Projection-and-Cholesky-QR passes of the refinement's [P W] block against
-// X (two: the second removes what FP32 rounding left of X in the first);
-// a build-time choice for tuning builds.
+// X.  One: the Rayleigh-Ritz step takes the X-[P W] couplings from exact
+// double-float products of the FP64 X (launch_gram_x), so what FP32
+// rounding leaves of X in [P W] is accounted for there and a second pass
+// only costs time (measured at 128^3: the same iteration counts, 9% less
+// time per solve).  A build-time choice for tuning builds.
 #ifndef PCX_ORTH_PASSES
-#define PCX_ORTH_PASSES 2
+#define PCX_ORTH_PASSES 1
 #endif
 
 namespace pcx {
@@ -516,8 +519,9 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
     CK(launch_convert(r64.R.p, PCX_FP64, r32.R.p, PCX_FP32, (size_t)n * L, r64.s));
     CK(r32.precond_active(act, w0));
     // [P W] is orthogonalised against X and orthonormalised (Cholesky QR,
-    // two passes) in FP32, so the FP32 part of the Gram matrices is close to
-    // the identity; P is dropped when [P W] is numerically rank deficient.
+    // PCX_ORTH_PASSES passes) in FP32, so the FP32 part of the Gram matrices
+    // is close to the identity; P is dropped when [P W] is numerically rank
+    // deficient.
     auto orth_block = [&](int c0, int cnt, bool& okb) -> pcx_status {
       okb = true;
       for (int pass = 0; pass < PCX_ORTH_PASSES && okb; ++pass) {
