@@ -176,6 +176,210 @@ __device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams&
   }
 }
 
+// The three steps of pass B on one z tile, shared by the one-tile-per-CTA
+// kernel and the warp-specialised persistent one.  tile = k1 (N / TPX) + xr;
+// pencil t = k2 TPX + q holds tile column xo = zcol_of(q) of real row
+// y = k1 + RA k2, at x = xr TPX + xo.
+template <typename T, int N, int OP>
+struct ZTile {
+  using C3 = Cfg3<T, N>;
+  using C = typename C3::CZ;
+  using TL = Tile<T, N, 2, C>;
+  static constexpr int TP = C::TP, RA = C3::RA, RB = C3::RB, TPX = C3::TPX;
+  static constexpr int N2 = N * N, N3 = N2 * N;
+  static constexpr int ITEMS = 3 * N * (TPX / 2);   // y-DFT items (two x columns each)
+
+  // RB-point inverse y DFT of rows RB k1 + n2 of the tile's columns into
+  // the shared tile s, by NTHR threads (tid < NTHR): items tid + it NTHR
+  template <int NTHR>
+  static __device__ __forceinline__ void load(cx<T>* s, const cx<T>* in, int k1, int x0, int tid) {
+    static_assert(ITEMS % NTHR == 0, "whole y-DFT items per thread");
+#pragma unroll
+    for (int it = 0; it < ITEMS / NTHR; ++it) {
+      const int w = tid + it * NTHR;
+      const int xp = w % (TPX / 2), z = (w / (TPX / 2)) % N, c = w / ((TPX / 2) * N);
+      const cx<T>* ip = in + (size_t)c * N3 + z * N2 + (RB * k1) * N + x0 + 2 * xp;
+      cx<T> r0[RB], r1[RB];
+#pragma unroll
+      for (int n2 = 0; n2 < RB; ++n2) ld2(ip + n2 * N, r0[n2], r1[n2]);
+      dft<RB, +1>(r0);
+      dft<RB, +1>(r1);
+#pragma unroll
+      for (int k2 = 0; k2 < RB; ++k2) {
+        s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp), z)] = r0[k2];
+        s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp + 1), z)] = r1[k2];
+      }
+    }
+  }
+
+  // RB-point forward y DFT over k2 with twiddle e^{-2 pi i k1 m1 / N}, from
+  // the shared tile to rows RB k1 + m1
+  template <int NTHR>
+  static __device__ __forceinline__ void store(const cx<T>* s, const cx<T>* tw, cx<T>* out, int k1, int x0, int tid) {
+    static_assert(ITEMS % NTHR == 0, "whole y-DFT items per thread");
+#pragma unroll
+    for (int it = 0; it < ITEMS / NTHR; ++it) {
+      const int w = tid + it * NTHR;
+      const int xp = w % (TPX / 2), z = (w / (TPX / 2)) % N, c = w / ((TPX / 2) * N);
+      cx<T> r0[RB], r1[RB];
+#pragma unroll
+      for (int k2 = 0; k2 < RB; ++k2) {
+        r0[k2] = s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp), z)];
+        r1[k2] = s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp + 1), z)];
+      }
+      dft<RB, -1>(r0);
+      dft<RB, -1>(r1);
+      cx<T>* op = out + (size_t)c * N3 + z * N2 + (RB * k1) * N + x0 + 2 * xp;
+#pragma unroll
+      for (int m1 = 0; m1 < RB; ++m1) {
+        const cx<T> wt = tw[k1 * m1];
+        st2(op + m1 * N, r0[m1] * wt, r1[m1] * wt);
+      }
+    }
+  }
+
+  // z transforms of the tile with plan (R0, R1): the inverse as two
+  // Stockham stages (radix R0 at Ns = 1, radix R1 at Ns = R0), the forward
+  // as radix R1 at Ns = 1 then radix R0 at Ns = R1.  The inverse's second
+  // stage reads and writes the R1 points j + R0 r of a pencil, which are
+  // also the inputs of the forward's first stage, so those two stages and
+  // the cell-by-cell M between them run in registers on the same points
+  // (all three components): two shared-memory round trips fewer.  The
+  // forward's first stage leaves element r of butterfly j at position
+  // j + R0 r (not at j R1 + r), which its second stage reads back.  Run by
+  // the C::THREADS threads tid = threadIdx.x < C::THREADS; SYNC is their
+  // barrier.  The tile must be complete in s on entry (the caller's
+  // barrier); on return it holds the forward transform, visible to the
+  // group.
+  template <class SYNC>
+  static __device__ __forceinline__ void transform(cx<T>* s, const cx<T>* tw, const T* mtab, const uchar4* tid3,
+                                                   const T* M, int k1, int x0) {
+    using P = typename C::P;
+    constexpr int R0 = P::R0, R1 = P::R1;
+    static_assert(P::NST == 2 && R0 * R1 == N, "two-stage z plan");
+    stage<T, N, 2, R0, +1, 0, 0, C, SYNC>(s, tw, 1, nullptr, nullptr, 0);
+    const T inv_n3 = (T)(1.0 / (double)N3);
+    for (int w = threadIdx.x; w < TP * R0; w += C::THREADS) {
+      const int t = w % TP, j = w / TP;
+      cx<T> v[3][R1];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const cx<T>* sp = s + TL::sidx(c, t, j);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) v[c][r] = sp[r * R0 * TL::SN];
+      }
+#pragma unroll
+      for (int r = 1; r < R1; ++r) {
+        cx<T> wt = tw[r * j];   // inverse: e^{+2 pi i r j / N}
+        wt.y = -wt.y;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * wt;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dft<R1, +1>(v[c]);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        const int n = j + R0 * r;
+        T d1, d2, d3;
+        cx<T> o12, o13, o23;
+        if (tid3) {
+          const uchar4 id = tid3[n * TP + t];
+          d1 = mtab[12 * id.x];
+          d2 = mtab[12 * id.y + 1];
+          d3 = mtab[12 * id.z + 2];
+          const T* o = mtab + 12 * id.w;
+          if constexpr (sizeof(T) == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(o + 4);
+            const float2 q2 = *reinterpret_cast<const float2*>(o + 8);
+            o12 = mk(q.x, q.y);
+            o13 = mk(q.z, q.w);
+            o23 = mk(q2.x, q2.y);
+          } else {
+            o12 = mk(o[4], o[5]);
+            o13 = mk(o[6], o[7]);
+            o23 = mk(o[8], o[9]);
+          }
+        } else {
+          const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + zcol_of<TPX>(t % TPX);
+          d1 = M[cell];
+          d2 = M[N3 + cell];
+          d3 = M[2 * N3 + cell];
+          o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
+          o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
+          o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
+        }
+        T sc = inv_n3;
+        if constexpr (OP == OP_SANDWICH_EPS) {
+          // eps = M^{-1} = adj(M) / det(M) on the Hermitian block
+          const T a11 = d2 * d3 - norm2(o23), a22 = d1 * d3 - norm2(o13), a33 = d1 * d2 - norm2(o12);
+          const cx<T> a12 = o13 * conjg(o23) - scale(o12, d3);
+          const cx<T> a13 = o12 * o23 - scale(o13, d2);
+          const cx<T> a23 = o13 * conjg(o12) - scale(o23, d1);
+          const T det = d1 * a11 + (o12 * conjg(a12)).x + (o13 * conjg(a13)).x;
+          sc = inv_n3 / det;
+          d1 = a11;
+          d2 = a22;
+          d3 = a33;
+          o12 = a12;
+          o13 = a13;
+          o23 = a23;
+        }
+        const cx<T> e0 = v[0][r], e1 = v[1][r], e2 = v[2][r];
+        v[0][r] = scale(cfma(o13, e2, cfma(o12, e1, scale(e0, d1))), sc);
+        v[1][r] = scale(cfma(o23, e2, cfma_conj(o12, e0, scale(e1, d2))), sc);
+        v[2][r] = scale(cfma_conj(o23, e1, cfma_conj(o13, e0, scale(e2, d3))), sc);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dft<R1, -1>(v[c]);
+        cx<T>* sp = s + TL::sidx(c, t, j);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) sp[r * R0 * TL::SN] = v[c][r];
+      }
+    }
+    SYNC::sync();
+    // forward second stage (radix R0 at Ns = R1): butterfly jj reads its R0
+    // inputs from the consecutive positions R0 jj + q, twiddle
+    // e^{-2 pi i q jj / N}, and writes the transform in natural order,
+    // positions jj + R1 q
+    constexpr int PER = 3 * TP * R1 / C::THREADS;
+    static_assert(PER * C::THREADS == 3 * TP * R1, "forward second stage: whole items per thread");
+    cx<T> v[PER][R0];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int w = threadIdx.x + i * C::THREADS;
+      const int t = w % TP, jj = (w / TP) % R1, c = w / (TP * R1);
+      const cx<T>* sp = s + TL::sidx(c, t, R0 * jj);
+#pragma unroll
+      for (int q = 0; q < R0; ++q) v[i][q] = sp[q * TL::SN];
+    }
+    SYNC::sync();
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int w = threadIdx.x + i * C::THREADS;
+      const int t = w % TP, jj = (w / TP) % R1, c = w / (TP * R1);
+#pragma unroll
+      for (int q = 1; q < R0; ++q) v[i][q] = v[i][q] * tw[q * jj];
+      dft<R0, -1>(v[i]);
+      cx<T>* sp = s + TL::sidx(c, t, jj);
+#pragma unroll
+      for (int q = 0; q < R0; ++q) sp[q * R1 * TL::SN] = v[i][q];
+    }
+    SYNC::sync();
+  }
+
+  // the material table repacked to 12 entries per material: d1 d2 d3 -
+  // re12 im12 re13 im13 re23 im23 - -, so that the off-diagonals of a cell
+  // come in one 16-byte and one 8-byte load
+  static __device__ __forceinline__ void stage_mtab(T* mtab, const void* gmtab, int n_mat, int tid, int nthr) {
+    const T* gt = static_cast<const T*>(gmtab);
+    for (int i = tid; i < 9 * n_mat; i += nthr) {
+      const int m = i / 9, f = i % 9;
+      mtab[12 * m + (f < 3 ? f : f + 1)] = gt[i];
+    }
+  }
+};
+
 template <typename T, int N, int OP>
 __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP>()) pass3_kernel(PassArgs a) {
   constexpr bool ZP = is_z_op<OP>();
@@ -368,183 +572,102 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
     }
   } else {
     // ================= z tiles: pass B =================
-    // tile = k1 * (N / TPX) + xr; pencil t = k2 * TPX + xo holds the real
-    // row y = k1 + RA k2 at x = xr TPX + xo
+    using ZT = ZTile<T, N, OP>;
     constexpr int TPX = C3::TPX;
     const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
-    // the material table repacked to 12 entries per material: d1 d2 d3 -
-    // re12 im12 re13 im13 re23 im23 - -, so that the off-diagonals of a
-    // cell come in one 16-byte and one 8-byte load
-    if (a.mid) {
-      const T* gt = static_cast<const T*>(a.mtab);
-      for (int i = threadIdx.x; i < 9 * a.n_mat; i += C::THREADS) {
-        const int m = i / 9, f = i % 9;
-        mtab[12 * m + (f < 3 ? f : f + 1)] = gt[i];
-      }
-    }
-    const T* M = static_cast<const T*>(a.M);
+    if (a.mid) ZT::stage_mtab(mtab, a.mtab, a.n_mat, threadIdx.x, C::THREADS);
+    ZT::template load<C::THREADS>(s, in, k1, x0, threadIdx.x);
+    __syncthreads();   // the tile, the twiddles and the material table
     const uchar4* mid3 = static_cast<const uchar4*>(a.mid3);
-    // RB-point inverse y DFT of rows RB k1 + n2 (two x columns per item)
-#pragma unroll
-    for (int it = 0; it < C3::ZI_PER_THREAD; ++it) {
-      const int w = threadIdx.x + it * C::THREADS;
-      const int xp = w % (TPX / 2), z = (w / (TPX / 2)) % N, c = w / ((TPX / 2) * N);
-      const cx<T>* ip = in + (size_t)c * N3 + z * N2 + (RB * k1) * N + x0 + 2 * xp;
-      cx<T> r0[RB], r1[RB];
-#pragma unroll
-      for (int n2 = 0; n2 < RB; ++n2) ld2(ip + n2 * N, r0[n2], r1[n2]);
-      dft<RB, +1>(r0);
-      dft<RB, +1>(r1);
-#pragma unroll
-      for (int k2 = 0; k2 < RB; ++k2) {
-        s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp), z)] = r0[k2];
-        s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp + 1), z)] = r1[k2];
-      }
+    ZT::template transform<CtaSync>(s, tw, mtab, mid3 ? mid3 + (size_t)tile * TP * N : nullptr,
+                                    static_cast<const T*>(a.M), k1, x0);
+    ZT::template store<C::THREADS>(s, tw, out, k1, x0, threadIdx.x);
+  }
+}
+
+// Pass B as a persistent warp-specialised kernel: one CTA per SM walks z
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... with two tile buffers in
+// shared memory.  The first C::THREADS threads (the transform group) run
+// the z transforms and M of tile i on buffer i % 2 while the other
+// 512 - C::THREADS threads (the I/O group) store tile i - 1 from the other
+// buffer and load tile i + 1 into it, so that global traffic and the
+// transforms overlap inside the SM.  Hardware named barriers hand the
+// buffers over (no spin loop): FULL[b] -- the I/O group arrives once it
+// has loaded buffer b, the transform group waits on it; EMPTY[b] -- the
+// transform group arrives once it has transformed buffer b, the I/O group
+// waits on it before storing that tile and reusing the buffer.  ZB_T is the
+// transform group's own barrier between stages, ZB_IO the I/O group's
+// between reading a buffer out and refilling it.  Both groups walk the same
+// tile sequence, so every phase of every barrier gets all 512 arrivals.
+constexpr int ZB_T = 1, ZB_IO = 2, ZB_FULL = 3, ZB_EMPTY = 5;   // FULL 3, 4; EMPTY 5, 6
+constexpr int ZWS_THREADS = 512;
+
+__device__ __forceinline__ void zb_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void zb_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+
+template <typename T, int N, int OP>
+__global__ void __launch_bounds__(ZWS_THREADS, 1) pass3z_ws_kernel(PassArgs a, int total_tiles) {
+  using C3 = Cfg3<T, N>;
+  using C = typename C3::CZ;
+  using ZT = ZTile<T, N, OP>;
+  constexpr int CT = C::THREADS, IOT = ZWS_THREADS - CT;
+  static_assert(CT % 32 == 0 && IOT >= 32 && IOT % 32 == 0, "whole warps in both groups");
+  constexpr int TP = C::TP, TPX = C3::TPX, ZT_N = C3::ZTILES, N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* buf1 = buf0 + 3 * C::CS;
+  cx<T>* tw = buf1 + 3 * C::CS;
+  T* mtab = reinterpret_cast<T*>(tw + N);   // 16-byte aligned: 3 CS and N are even
+  const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
+  for (int i = threadIdx.x; i < N; i += ZWS_THREADS) tw[i] = gtw[i];
+  if (a.mid) ZT::stage_mtab(mtab, a.mtab, a.n_mat, threadIdx.x, ZWS_THREADS);
+  __syncthreads();
+  const uchar4* mid3 = static_cast<const uchar4*>(a.mid3);
+  if (threadIdx.x < CT) {
+    // transform group
+    const T* M = static_cast<const T*>(a.M);
+    int i = 0;
+    for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++i) {
+      const int b = i & 1;
+      const int tile = g % ZT_N;
+      const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
+      zb_sync(ZB_FULL + b, ZWS_THREADS);
+      ZT::template transform<GroupSync<ZB_T, CT>>(b ? buf1 : buf0, tw, mtab,
+                                                  mid3 ? mid3 + (size_t)tile * TP * N : nullptr, M, k1, x0);
+      zb_arrive(ZB_EMPTY + b, ZWS_THREADS);
     }
-    __syncthreads();
-    // z transforms of the tile with plan (R0, R1): the inverse as two
-    // Stockham stages (radix R0 at Ns = 1, radix R1 at Ns = R0), the forward
-    // as radix R1 at Ns = 1 then radix R0 at Ns = R1.  The inverse's second
-    // stage reads and writes the R1 points j + R0 r of a pencil, which are
-    // also the inputs of the forward's first stage, so those two stages and
-    // the cell-by-cell M between them run in registers on the same points
-    // (all three components): two shared-memory round trips fewer.  The
-    // forward's first stage leaves element r of butterfly j at position
-    // j + R0 r (not at j R1 + r), which its second stage reads back.
-    using P = typename C::P;
-    constexpr int R0 = P::R0, R1 = P::R1;
-    static_assert(P::NST == 2 && R0 * R1 == N, "two-stage z plan");
-    stage<T, N, 2, R0, +1, 0, 0, C>(s, tw, 1, nullptr, nullptr, 0);
-    const T inv_n3 = (T)(1.0 / (double)N3);
-    const uchar4* tid3 = mid3 ? mid3 + (size_t)tile * TP * N : nullptr;
-    for (int w = threadIdx.x; w < TP * R0; w += C::THREADS) {
-      const int t = w % TP, j = w / TP;
-      cx<T> v[3][R1];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const cx<T>* sp = s + TL::sidx(c, t, j);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) v[c][r] = sp[r * R0 * TL::SN];
+  } else {
+    // I/O group: step i stores tile i - 2 (the previous user of buffer
+    // i % 2) and loads tile i into it
+    const int tid = threadIdx.x - CT;
+    const cx<T>* in = static_cast<const cx<T>*>(a.in);
+    cx<T>* out = static_cast<cx<T>*>(a.out);
+    // this CTA's tile count; steps 0 .. nt + 1 (the last two only store)
+    const int nt = (int)blockIdx.x < total_tiles ? (total_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                                                 : 0;
+    for (int i = 0; i < nt + 2; ++i) {
+      const long long gs = (long long)blockIdx.x + (long long)(i - 2) * gridDim.x;
+      const long long gl = (long long)blockIdx.x + (long long)i * gridDim.x;
+      const bool st = i >= 2;
+      const bool ld = i < nt;
+      const int b = i & 1;
+      cx<T>* s = b ? buf1 : buf0;
+      if (st) {
+        const int tile = (int)(gs % ZT_N);
+        const size_t v = (size_t)(gs / ZT_N);
+        zb_sync(ZB_EMPTY + b, ZWS_THREADS);
+        ZT::template store<IOT>(s, tw, out + v * 3 * N3, tile / (N / TPX), (tile % (N / TPX)) * TPX, tid);
       }
-#pragma unroll
-      for (int r = 1; r < R1; ++r) {
-        cx<T> wt = tw[r * j];   // inverse: e^{+2 pi i r j / N}
-        wt.y = -wt.y;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * wt;
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) dft<R1, +1>(v[c]);
-#pragma unroll
-      for (int r = 0; r < R1; ++r) {
-        const int n = j + R0 * r;
-        T d1, d2, d3;
-        cx<T> o12, o13, o23;
-        if (tid3) {
-          const uchar4 id = tid3[n * TP + t];
-          d1 = mtab[12 * id.x];
-          d2 = mtab[12 * id.y + 1];
-          d3 = mtab[12 * id.z + 2];
-          const T* o = mtab + 12 * id.w;
-          if constexpr (sizeof(T) == 4) {
-            const float4 q = *reinterpret_cast<const float4*>(o + 4);
-            const float2 q2 = *reinterpret_cast<const float2*>(o + 8);
-            o12 = mk(q.x, q.y);
-            o13 = mk(q.z, q.w);
-            o23 = mk(q2.x, q2.y);
-          } else {
-            o12 = mk(o[4], o[5]);
-            o13 = mk(o[6], o[7]);
-            o23 = mk(o[8], o[9]);
-          }
-        } else {
-          const int cell = n * N2 + (k1 + RA * (t / TPX)) * N + x0 + zcol_of<TPX>(t % TPX);
-          d1 = M[cell];
-          d2 = M[N3 + cell];
-          d3 = M[2 * N3 + cell];
-          o12 = mk(M[3 * N3 + cell], M[4 * N3 + cell]);
-          o13 = mk(M[5 * N3 + cell], M[6 * N3 + cell]);
-          o23 = mk(M[7 * N3 + cell], M[8 * N3 + cell]);
-        }
-        T sc = inv_n3;
-        if constexpr (OP == OP_SANDWICH_EPS) {
-          // eps = M^{-1} = adj(M) / det(M) on the Hermitian block
-          const T a11 = d2 * d3 - norm2(o23), a22 = d1 * d3 - norm2(o13), a33 = d1 * d2 - norm2(o12);
-          const cx<T> a12 = o13 * conjg(o23) - scale(o12, d3);
-          const cx<T> a13 = o12 * o23 - scale(o13, d2);
-          const cx<T> a23 = o13 * conjg(o12) - scale(o23, d1);
-          const T det = d1 * a11 + (o12 * conjg(a12)).x + (o13 * conjg(a13)).x;
-          sc = inv_n3 / det;
-          d1 = a11;
-          d2 = a22;
-          d3 = a33;
-          o12 = a12;
-          o13 = a13;
-          o23 = a23;
-        }
-        const cx<T> e0 = v[0][r], e1 = v[1][r], e2 = v[2][r];
-        v[0][r] = scale(cfma(o13, e2, cfma(o12, e1, scale(e0, d1))), sc);
-        v[1][r] = scale(cfma(o23, e2, cfma_conj(o12, e0, scale(e1, d2))), sc);
-        v[2][r] = scale(cfma_conj(o23, e1, cfma_conj(o13, e0, scale(e2, d3))), sc);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        dft<R1, -1>(v[c]);
-        cx<T>* sp = s + TL::sidx(c, t, j);
-#pragma unroll
-        for (int r = 0; r < R1; ++r) sp[r * R0 * TL::SN] = v[c][r];
-      }
-    }
-    __syncthreads();
-    // forward second stage (radix R0 at Ns = R1): butterfly jj reads its R0
-    // inputs from the consecutive positions R0 jj + q, twiddle
-    // e^{-2 pi i q jj / N}, and writes the transform in natural order,
-    // positions jj + R1 q
-    {
-      constexpr int PER = 3 * TP * R1 / C::THREADS;
-      static_assert(PER * C::THREADS == 3 * TP * R1, "forward second stage: whole items per thread");
-      cx<T> v[PER][R0];
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        const int w = threadIdx.x + i * C::THREADS;
-        const int t = w % TP, jj = (w / TP) % R1, c = w / (TP * R1);
-        const cx<T>* sp = s + TL::sidx(c, t, R0 * jj);
-#pragma unroll
-        for (int q = 0; q < R0; ++q) v[i][q] = sp[q * TL::SN];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        const int w = threadIdx.x + i * C::THREADS;
-        const int t = w % TP, jj = (w / TP) % R1, c = w / (TP * R1);
-#pragma unroll
-        for (int q = 1; q < R0; ++q) v[i][q] = v[i][q] * tw[q * jj];
-        dft<R0, -1>(v[i]);
-        cx<T>* sp = s + TL::sidx(c, t, jj);
-#pragma unroll
-        for (int q = 0; q < R0; ++q) sp[q * R1 * TL::SN] = v[i][q];
-      }
-      __syncthreads();
-    }
-    // RB-point forward y DFT over k2, twiddle e^{-2 pi i k1 m1 / N}, store
-    // to rows RB k1 + m1
-#pragma unroll
-    for (int it = 0; it < C3::ZI_PER_THREAD; ++it) {
-      const int w = threadIdx.x + it * C::THREADS;
-      const int xp = w % (TPX / 2), z = (w / (TPX / 2)) % N, c = w / ((TPX / 2) * N);
-      cx<T> r0[RB], r1[RB];
-#pragma unroll
-      for (int k2 = 0; k2 < RB; ++k2) {
-        r0[k2] = s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp), z)];
-        r1[k2] = s[TL::sidx(c, k2 * TPX + zcol_pos<TPX>(2 * xp + 1), z)];
-      }
-      dft<RB, -1>(r0);
-      dft<RB, -1>(r1);
-      cx<T>* op = out + (size_t)c * N3 + z * N2 + (RB * k1) * N + x0 + 2 * xp;
-#pragma unroll
-      for (int m1 = 0; m1 < RB; ++m1) {
-        const cx<T> wt = tw[k1 * m1];
-        st2(op + m1 * N, r0[m1] * wt, r1[m1] * wt);
+      if (ld) {
+        if (st) zb_sync(ZB_IO, IOT);   // every read of the buffer done before it is refilled
+        const int tile = (int)(gl % ZT_N);
+        const size_t v = (size_t)(gl / ZT_N);
+        ZT::template load<IOT>(s, in + v * 3 * N3, tile / (N / TPX), (tile % (N / TPX)) * TPX, tid);
+        zb_arrive(ZB_FULL + b, ZWS_THREADS);
       }
     }
   }
@@ -570,10 +693,34 @@ __global__ void pass3_ids_kernel(const uchar4* __restrict__ mid, uchar4* __restr
 // each tile kind is fixed by its geometry (x tiles: the five-pass x layout
 // plus the kappa tables; z tiles: the tile, the twiddles and the material
 // table).
+// Pass B's kernel: one tile per CTA (0) or the warp-specialised persistent
+// one (1); a build-time choice for tuning builds.  Measured at 128^3 the two
+// are within run-to-run noise of each other (both wait on the shared-memory
+// instruction queue at 16 warps per SM), so the simpler one is the default.
+#ifndef PCX_ZWS
+#define PCX_ZWS 0
+#endif
+
 template <typename T, int N, int OP>
 cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st) {
   using C3 = Cfg3<T, N>;
   constexpr bool ZP = is_z_op<OP>();
+  if constexpr (ZP && PCX_ZWS) {
+    const size_t smem = 2 * C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) +
+                        (((size_t)12 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);
+    const long long tiles = (long long)nv * C3::ZTILES;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    auto kern = pass3z_ws_kernel<T, N, OP>;
+    if ((e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem)) != cudaSuccess) return e;
+    const long long grid = tiles < sms ? tiles : sms;
+    if (grid == 0) return cudaSuccess;
+    kern<<<(unsigned)grid, ZWS_THREADS, smem, st>>>(a, (int)tiles);
+    return cudaGetLastError();
+  }
   size_t smem;
   if constexpr (ZP)
     smem = C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) + (((size_t)12 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);

@@ -253,7 +253,20 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // SRC: 0 = shared memory, 1 = global (first stage only, Ns = 1).
 // DST: 0 = shared memory, 1 = global (last stage only, Ns = N / R).
 // Threads walk butterflies with the pencil index fastest.
-template <typename T, int N, int AXIS, int R, int DIR, int SRC, int DST, class CF = Cfg<T, N>>
+// Barrier of the threads that run a stage: the whole CTA by default; a
+// named barrier over the first COUNT threads where one warp group of a
+// warp-specialised kernel runs the stages (bar.sync: every warp of the group
+// arrives and waits; the hardware barrier needs no spin loop).
+struct CtaSync {
+  static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+template <int ID, int COUNT>
+struct GroupSync {
+  static_assert(ID >= 1 && ID < 16 && COUNT % 32 == 0, "named barrier id and warp-multiple count");
+  static __device__ __forceinline__ void sync() { asm volatile("bar.sync %0, %1;\n" ::"n"(ID), "n"(COUNT) : "memory"); }
+};
+
+template <typename T, int N, int AXIS, int R, int DIR, int SRC, int DST, class CF = Cfg<T, N>, class SYNC = CtaSync>
 __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const cx<T>* gin, cx<T>* gout, int qb) {
   using C = CF;
   using TL = Tile<T, N, AXIS, CF>;
@@ -278,7 +291,7 @@ __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const c
       for (int r = 0; r < R; ++r) v[i][r] = sp[r * NB * TL::SN];
     }
   }
-  if constexpr (SRC == 0 && DST == 0) __syncthreads();
+  if constexpr (SRC == 0 && DST == 0) SYNC::sync();
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     int t, j, c;
@@ -308,7 +321,7 @@ __device__ __forceinline__ void stage(cx<T>* s, const cx<T>* tw, int Ns, const c
       for (int r = 0; r < R; ++r) sp[r * Ns * TL::SN] = v[i][r];
     }
   }
-  if constexpr (DST == 0) __syncthreads();
+  if constexpr (DST == 0) SYNC::sync();
 }
 
 // Full 1D transform of the tile.  FROM_G: the first stage reads global
