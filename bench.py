@@ -496,6 +496,49 @@ def study_configs_1_2(pcx, tol=1e-8, k_concurrency=4):
     return 0
 
 
+def study_ill_conditioned(pcx, grids=(32, 64), nev=8, tol=1e-8, maxit=600, long_maxit=4000):
+    """Sec. 4.4 (row f4): the ill-conditioned inverse permittivity
+    U diag(1e-1, 1e-3, 1e-5) U^H in a sphere of the SC cell at
+    k = (1/7, 3/5, 4/13) pi, 8 bands, with M_Trivial and M_CrossDoF (the
+    latter built without the Sec. 3.3 proof, which this material does not
+    meet, as in the paper): per grid and M kind, FP64 and mixed precision
+    with K_P^{-1} and mixed precision with T0 (maxit iterations), and
+    M_CrossDoF again with long_maxit; per run the worst wanted residual of
+    every iteration (every 10th kept), its mean decrease per iteration (log10
+    per iteration, least squares over the history), the final residual and
+    the lowest Ritz values.  One JSON line."""
+    import numpy as np
+
+    import workloads as wl
+    s = wl.ill_conditioned_sphere()
+    k = wl.config_k(s.name)[0]
+    out = {"study": "ill-conditioned", "structure": s.name, "k": "(1/7, 3/5, 4/13) pi", "nev": nev, "tol": tol,
+           "maxit": maxit}
+    for n in grids:
+        for mname, mk in (("trivial", pcx.PCX_M_TRIVIAL), ("crossdof", pcx.PCX_M_CROSSDOF)):
+            ctx = pcx.setup_structure(s, n, m_kind=mk, crossdof_unchecked=True)
+            legs = [("fp64", pcx.PCX_FP64, 0, maxit), ("mixed", pcx.PCX_FP32, 0, maxit),
+                    ("mixed_t0", pcx.PCX_FP32, 1, maxit)]
+            if mk == pcx.PCX_M_CROSSDOF:
+                legs += [("fp64_long", pcx.PCX_FP64, 0, long_maxit), ("mixed_long", pcx.PCX_FP32, 0, long_maxit)]
+            for leg, prec, kind, cap in legs:
+                hist = np.zeros(4 * cap + 64)
+                stats = pcx.pcx_solve_stats()
+                t0 = time.perf_counter()
+                ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, tol, block=nev + 4, maxit=cap, precision=prec,
+                                                 precond_kind=kind, raise_on_noconv=False, stats=stats,
+                                                 res_history=hist, penalty_tol=-1.0)
+                h = hist[:stats.history_len]
+                good = h[np.isfinite(h) & (h > 0)]
+                slope = float(np.polyfit(np.arange(good.size), np.log10(good), 1)[0]) if good.size > 2 else None
+                out[f"N{n}_{mname}_{leg}"] = {
+                    "status": int(st), "iters": int(its[0]), "s": time.perf_counter() - t0,
+                    "max_res": float(np.max(res)), "log10_res_per_iter": slope,
+                    "res_history_every10": [float(v) for v in h[::10]][:200], "omega2": ev[0].tolist()}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def study_woodpile(pcx, n=256, nev=20, tol=1e-8):
     """Configuration 5: the 256^3 simple cubic woodpile of anisotropic rods at
     k = 2 pi (0.1, 0.2, 0.3), 20 bands, mixed precision with the
@@ -787,7 +830,7 @@ def main():
                     help="print pcx_apply timings at 1, 16 and 48 vectors per call, complex64 and complex128, instead")
     ap.add_argument("--study", default="",
                     choices=["", "bcc-convergence", "frequency-difference", "woodpile-256", "learned-64",
-                             "configs-1-2"],
+                             "configs-1-2", "ill-conditioned"],
                     help="run one of the paper's studies or configuration 5 instead of the benchmark (one JSON line)")
     args = ap.parse_args()
     if args.study:
@@ -796,7 +839,7 @@ def main():
         _build.build()
         return {"bcc-convergence": study_bcc_convergence, "frequency-difference": study_frequency_difference,
                 "woodpile-256": study_woodpile, "learned-64": study_learned,
-                "configs-1-2": study_configs_1_2}[args.study](pcx)
+                "configs-1-2": study_configs_1_2, "ill-conditioned": study_ill_conditioned}[args.study](pcx)
     if args.warmup < 3:
         args.warmup = 3
     if args.blockops:

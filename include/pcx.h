@@ -94,6 +94,11 @@ typedef struct {
                             im o23 (M_k = [[d1,o12,o13],[.,d2,o23],[.,.,d3]],
                             Hermitian)                                           */
   int m_kind;            /* PCX_M_TRIVIAL (0, default) or PCX_M_CROSSDOF, below  */
+  int crossdof_unchecked; /* 1: build an M_CrossDoF context even where the
+                            sufficient HPD conditions of Sec. 3.3 do not hold
+                            (as the paper's ill-conditioned case of Sec. 4.4
+                            does); M may then be indefinite.  0 (default):
+                            such a context is refused with PCX_ENOTHPD      */
 } pcx_setup_desc;
 
 /* m_kind: the discrete inverse permittivity M of the apply (Sec. 3.2).
@@ -106,8 +111,12 @@ typedef struct {
  *   crossdof_Tmat read from the componentwise template eq.
  *   crossdof_xytemplate (T_12: mean over x in {i-1, i}, y in {j-1/2,
  *   j+1/2}; T_13, T_23 alike).  It needs a structure sampled from shapes
- *   (not cell_blocks, at most 255 materials); the HPD check stays the
- *   per-cell one of M_Trivial.  The apply then runs seven passes: the
+ *   (not cell_blocks, at most 255 materials).  It is accepted when the
+ *   sufficient conditions of Sec. 3.3 hold: every material's epsilon_1 has
+ *   eigenvalues in (0, 1], and either one off-diagonal position is zero in
+ *   every material or every assembled row is strictly diagonally dominant
+ *   (else PCX_ENOTHPD naming the first failing row, unless
+ *   crossdof_unchecked is set).  The apply then runs seven passes: the
  *   z-axis sandwich is split into an inverse z transform, a real-space
  *   stencil pass and a forward z transform.  pcx_sandwich_precond keeps
  *   the per-cell M_Trivial inverse (an approximate inverse either way). */
@@ -598,6 +607,7 @@ typedef struct {
   double ms_precond;     /* preconditioner (K_P^{-1} or the learned T)              */
   int learned_fallbacks; /* k-points at which the learned correction fell back     */
   int dumped;            /* residual columns written to dump_R                      */
+  int history_len;       /* entries written to opts.res_history                     */
 } pcx_solve_stats;
 
 /* Eigensolver options (pcx_solve).  Zero-initialised fields take defaults. */
@@ -659,6 +669,13 @@ typedef struct {
                          Rayleigh-Ritz step.  Same results as one after the
                          other.  Not with cnn_params or dump_R (they share the
                          context's workspace): those solve one k at a time.  */
+  double* res_history;  /* optional HOST array: the worst wanted residual
+                         max_{j < nev} Res_j after every LOBPCG iteration (FP32
+                         phase and refinement, in the order they run), at most
+                         res_history_cap entries; stats->history_len gives the
+                         count.  With k-points in flight their entries
+                         interleave.                                          */
+  int res_history_cap;
 } pcx_solve_opts;
 
 /*

@@ -459,7 +459,7 @@ pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c) {
   const bool use_ids = !d->cell_blocks && d->n_mat <= 255;
   st = sample_blocks(d, c->A, c->blocks, use_ids ? &ids : nullptr, c->err);
   if (st != PCX_OK) return st;
-  if (c->m_kind == PCX_M_CROSSDOF) {
+  if (c->m_kind == PCX_M_CROSSDOF && !d->crossdof_unchecked) {
     // M_CrossDoF: the sufficient conditions of Sec. 3.3
     std::string why;
     const long long bad = crossdof_unproven(n, d->n_mat, d->eps, ids, &why);

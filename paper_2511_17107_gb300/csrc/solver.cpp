@@ -61,6 +61,18 @@ struct DevBuf {
   }
 };
 
+// Worst wanted residual after every iteration (opts.res_history), in the
+// order the iterations run; k-points in flight append concurrently.
+struct History {
+  double* buf = nullptr;
+  int cap = 0;
+  std::atomic<int> len{0};
+  void add(double v) {
+    const int i = len.fetch_add(1);
+    if (i < cap) buf[i] = v;
+  }
+};
+
 #define CK(x)                                    \
   do {                                           \
     cudaError_t _e = (x);                        \
@@ -107,6 +119,7 @@ struct Run {
   KParams kp;
   bool k_zero;
   int verbose;
+  History* hist = nullptr;   // per-iteration worst residuals (optional)
   double fp32_floor = 0;   // FP32 phase: stop once worst <= fp32_floor 2^-24 theta_top (0: off)
   double theta_top = 0;    // largest Ritz value of the last Rayleigh-Ritz step
   int np = 0;        // P columns at S[n : n+np] (valid when lobpcg returns)
@@ -274,6 +287,7 @@ pcx_status lobpcg(Run& run, int nev, double tol, int maxit, double stop_tol, int
       }
       if (j < nev) worst = std::max(worst, res[j]);
     }
+    if (run.hist) run.hist->add(worst);
     if (run.verbose) {
       std::fprintf(stderr, "[pcx] %s it %d worst %.3e theta0 %.12g theta_top %.4e\n",
                    run.prec == PCX_FP64 ? "fp64" : "fp32", iters, worst, theta[0], run.theta_top);
@@ -480,6 +494,7 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
       }
       if (j < nev) worst = std::max(worst, res[j]);
     }
+    if (r64.hist) r64.hist->add(worst);
     if (r64.verbose)
       std::fprintf(stderr, "[pcx] refine it %d worst %.3e theta0 %.12g%s\n", iters, worst, theta[0],
                    since_fresh == 0 ? " (fresh AX)" : "");
@@ -655,6 +670,7 @@ struct KSolve {
   Times *t32, *t64;
   int iters32 = 0, iters64 = 0;
   Learned* learned = nullptr;
+  History* hist = nullptr;
   std::string* err = nullptr;   // where messages go (the context's, or a worker's own)
 };
 
@@ -681,6 +697,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
   r64.kp = make_kparams(c, k, gamma);
   r64.k_zero = kz;
   r64.verbose = ks.o->verbose;
+  r64.hist = ks.hist;
   if (ks.o->stats) r64.tm = ks.t64;
   if ((st = r64.alloc_all(ks.o->precision == PCX_FP32)) != PCX_OK) {
     *ks.err = r64.err;
@@ -696,6 +713,7 @@ pcx_status solve_one_k(KSolve& ks, const double k[3], double gamma, int ik, Run&
     r32.kp = r64.kp;
     r32.k_zero = kz;
     r32.verbose = ks.o->verbose;
+    r32.hist = ks.hist;
     r32.fp32_floor = ks.o->fp32_floor == 0 ? 1024.0 : (ks.o->fp32_floor > 0 ? ks.o->fp32_floor : 0.0);
     r32.t0 = r64.t0;
     if (ks.o->stats) r32.tm = ks.t32;
@@ -1020,6 +1038,12 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
   const auto t_start = std::chrono::steady_clock::now();
   if (o.stats) std::memset(o.stats, 0, sizeof(*o.stats));
   ks.err = &c->err;
+  History hist;
+  if (o.res_history && o.res_history_cap > 0) {
+    hist.buf = o.res_history;
+    hist.cap = o.res_history_cap;
+    ks.hist = &hist;
+  }
   const KOut kout{eig_out, res_out, iters_out, vec_out};
   const int conc = std::min(o.k_concurrency, nk);
   if (conc > 1 && !o.cnn_params && !o.dump_R) {
@@ -1050,6 +1074,7 @@ pcx_status solve(pcx_ctx* c, const double* kpts, int nk, int nev, double tol, co
     st.ms_precond = t32.precond + t64.precond;
     st.learned_fallbacks = lrn.fallbacks;
     st.dumped = lrn.dumped;
+    st.history_len = std::min(hist.len.load(), hist.cap);
   }
   return result;
 }

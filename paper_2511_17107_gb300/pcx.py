@@ -40,7 +40,7 @@ class pcx_setup_desc(C.Structure):
     _fields_ = [("n", C.c_int), ("stencil_m", C.c_int), ("ct_reading", C.c_int), ("lattice", C.c_double * 9),
                 ("n_mat", C.c_int), ("eps", C.POINTER(C.c_double)), ("background", C.c_int),
                 ("n_shape", C.c_int), ("shapes", C.POINTER(pcx_shape)), ("cell_blocks", C.POINTER(C.c_double)),
-                ("m_kind", C.c_int)]
+                ("m_kind", C.c_int), ("crossdof_unchecked", C.c_int)]
 
 
 class pcx_solve_stats(C.Structure):
@@ -48,7 +48,7 @@ class pcx_solve_stats(C.Structure):
                 ("applies_fp64", C.c_longlong), ("ms_total", C.c_double), ("ms_apply", C.c_double),
                 ("ms_gram", C.c_double), ("ms_rr", C.c_double), ("ms_other", C.c_double),
                 ("gamma_raises", C.c_int), ("gamma_last", C.c_double), ("ms_precond", C.c_double),
-                ("learned_fallbacks", C.c_int), ("dumped", C.c_int)]
+                ("learned_fallbacks", C.c_int), ("dumped", C.c_int), ("history_len", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -68,7 +68,7 @@ class pcx_solve_opts(C.Structure):
                 ("gamma", C.c_double), ("penalty_tol", C.c_double), ("cnn_params", C.c_void_p),
                 ("dump_R", C.c_void_p), ("dump_cap", C.c_int), ("dump_every", C.c_int), ("precond_kind", C.c_int),
                 ("learned_patience", C.c_int), ("fp32_floor", C.c_double), ("x0", C.c_void_p),
-                ("k_concurrency", C.c_int)]
+                ("k_concurrency", C.c_int), ("res_history", C.POINTER(C.c_double)), ("res_history_cap", C.c_int)]
 
 
 _lib = None
@@ -210,10 +210,12 @@ class Context:
 PCX_M_TRIVIAL, PCX_M_CROSSDOF = 0, 1
 
 
-def _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks, m_kind=PCX_M_TRIVIAL):
+def _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks, m_kind=PCX_M_TRIVIAL,
+          crossdof_unchecked=False):
     d = pcx_setup_desc()
     d.n = n
     d.m_kind = m_kind
+    d.crossdof_unchecked = int(bool(crossdof_unchecked))
     d.stencil_m = stencil_m
     d.ct_reading = ct_reading
     lat = np.eye(3) if lattice is None else np.asarray(lattice, dtype=np.float64)
@@ -244,11 +246,12 @@ def _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_block
 
 
 def pcx_setup(n, lattice=None, eps=None, background=0, shapes=(), stencil_m=1, ct_reading=PCX_CT_SUMMED,
-              cell_blocks=None, m_kind=PCX_M_TRIVIAL):
+              cell_blocks=None, m_kind=PCX_M_TRIVIAL, crossdof_unchecked=False):
     """Create a context.  ``eps``: (n_mat, 3, 3) complex permittivities;
     ``shapes``: objects with .kind, .material, .params; ``cell_blocks``:
     optional (N^3, 9) float64 packed blocks overriding the structure."""
-    d, keep = _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks, m_kind)
+    d, keep = _desc(n, lattice, eps, background, shapes, stencil_m, ct_reading, cell_blocks, m_kind,
+                    crossdof_unchecked)
     h = C.c_void_p()
     st = lib().pcx_setup(C.byref(d), C.byref(h))
     if st != PCX_OK:
@@ -259,10 +262,12 @@ def pcx_setup(n, lattice=None, eps=None, background=0, shapes=(), stencil_m=1, c
     return Context(h, n)
 
 
-def setup_structure(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED, m_kind=PCX_M_TRIVIAL):
+def setup_structure(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED, m_kind=PCX_M_TRIVIAL,
+                    crossdof_unchecked=False):
     """pcx_setup from a ``workloads.Structure``."""
     return pcx_setup(n, structure.lattice, structure.eps, structure.background, structure.shapes,
-                     stencil_m=stencil_m, ct_reading=ct_reading, m_kind=m_kind)
+                     stencil_m=stencil_m, ct_reading=ct_reading, m_kind=m_kind,
+                     crossdof_unchecked=crossdof_unchecked)
 
 
 def pcx_sample_host(structure, n, stencil_m=1, ct_reading=PCX_CT_SUMMED, m_kind=PCX_M_TRIVIAL, cell_blocks=None):
@@ -549,9 +554,11 @@ def pcx_rr_eig(ga, gb, drop_tol=1e-13):
 def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_tol=0.0, seed=0, verbose=0,
               vec_out=None, stream=None, raise_on_noconv=True, stats=None, gamma=0.0, penalty_tol=0.0,
               cnn_params=None, dump_R=None, dump_every=0, precond_kind=0, learned_patience=0, fp32_floor=0.0,
-              x0=None, k_concurrency=0):
+              x0=None, k_concurrency=0, res_history=None):
     """Returns (eig (nk, nev), res (nk, nev), iters (nk,), status).  Pass a
-    pcx_solve_stats instance as ``stats`` to receive counters and timings."""
+    pcx_solve_stats instance as ``stats`` to receive counters and timings,
+    and a float64 numpy array as ``res_history`` to receive the worst wanted
+    residual of every iteration (count in stats.history_len)."""
     kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
     nk = kp.shape[0]
     o = pcx_solve_opts(block, maxit, precision, switch_tol, seed, verbose,
@@ -561,6 +568,11 @@ def pcx_solve(ctx, kpts, nev, tol, block=0, maxit=0, precision=PCX_FP64, switch_
                        int(dump_R.shape[0]) if dump_R is not None else 0, int(dump_every), int(precond_kind),
                        int(learned_patience), float(fp32_floor), _devptr(x0) if x0 is not None else None,
                        int(k_concurrency))
+    if res_history is not None:
+        if res_history.dtype != np.float64 or not res_history.flags["C_CONTIGUOUS"]:
+            raise ValueError("res_history must be a contiguous float64 array")
+        o.res_history = _dptr(res_history)
+        o.res_history_cap = int(res_history.size)
     eig = np.zeros((nk, nev))
     res = np.zeros((nk, nev))
     its = np.zeros(nk, dtype=np.int32)

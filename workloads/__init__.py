@@ -249,6 +249,20 @@ BCC_POINTS = {"H'": (2 * PI, 0.0, 0.0), "G": (0.0, 0.0, 0.0), "P": (PI, PI, PI),
               "H": (0.0, 2 * PI, 0.0)}
 
 
+def ill_conditioned_sphere(seed=20251117, radius=0.345) -> Structure:
+    """Sec. 4.4: a material whose inverse permittivity is
+    U diag(1e-1, 1e-3, 1e-5) U^H (U a seeded unitary), so its permittivity
+    is U diag(1e1, 1e3, 1e5) U^H, in a sphere of radius 0.345 at the centre
+    of the simple cubic cell, vacuum outside (the sphere stands in for the
+    SC-CURV geometry, whose cylinder axes the paper does not give)."""
+    rng = np.random.default_rng(seed)
+    u = seeded_unitary(rng)
+    eps = u @ np.diag([1e1, 1e3, 1e5]).astype(np.complex128) @ u.conj().T
+    eps = 0.5 * (eps + eps.conj().T)
+    shapes = [Shape(SHAPE_SPHERE, 1, (0.5, 0.5, 0.5, radius))]
+    return Structure("ill-conditioned-sphere", SC.copy(), np.stack([VACUUM, eps]), 0, shapes)
+
+
 def homogeneous(eps, lattice=None) -> Structure:
     """One material filling the whole cell."""
     lat = SC.copy() if lattice is None else np.asarray(lattice, dtype=np.float64)
@@ -276,6 +290,8 @@ def config_k(name):
         return k_path(FCC_POINTS, ["X", "U", "L", "G", "X", "W", "K"], 40)
     if name == "woodpile":
         return np.array([[2 * PI * 0.1, 2 * PI * 0.2, 2 * PI * 0.3]])
+    if name == "ill-conditioned-sphere":
+        return np.array([[PI / 7, 3 * PI / 5, 4 * PI / 13]])
     if name.startswith("random"):
         return np.array([[PI, PI, PI]])
     raise KeyError(name)
