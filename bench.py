@@ -745,22 +745,28 @@ def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps
     P = None
     if learned_steps > 0 and (not want or "mixed_learned" in want):
         P, out["learned_training"] = train_learned(pcx, n, steps=learned_steps)
-    legs = [("mixed", pcx.PCX_FP32, 0, None), ("mixed_sandwich", pcx.PCX_FP32, 1, None)]
+    scalar, projector = pcx.PCX_PENALTY_SCALAR, pcx.PCX_PENALTY_PROJECTOR
+    legs = [("mixed", pcx.PCX_FP32, 0, None, scalar), ("mixed_sandwich", pcx.PCX_FP32, 1, None, scalar)]
     if P is not None:
         from paper_2511_17107_gb300 import learned as lrn
         pcx.pcx_set_cnn_form(ctx, lrn.FORM)   # the form the correction was trained in
-        legs.append(("mixed_learned", pcx.PCX_FP32, 1, P))
-    legs.append(("fp64", pcx.PCX_FP64, 0, None))
-    legs.append(("fp64_sandwich", pcx.PCX_FP64, 1, None))
+        legs.append(("mixed_learned", pcx.PCX_FP32, 1, P, scalar))
+    legs.append(("fp64", pcx.PCX_FP64, 0, None, scalar))
+    legs.append(("fp64_sandwich", pcx.PCX_FP64, 1, None, scalar))
+    # the projector penalty form (the same physical eigenpairs, every
+    # penalty eigenvalue 4 pi^2): a lower FP32 rounding floor
+    legs.append(("mixed_sandwich_projector", pcx.PCX_FP32, 1, None, projector))
     if want:
         legs = [leg for leg in legs if leg[0] in want]
     eigs = {}
-    for name, prec, kind, params in legs:
+    for name, prec, kind, params, form in legs:
         stats = pcx.pcx_solve_stats()
+        pcx.pcx_set_penalty_form(ctx, form)
         t0 = time.perf_counter()
         ev, res, its, st = pcx.pcx_solve(ctx, ks, nev, tol, block=block, precision=prec, stats=stats,
                                          raise_on_noconv=False, precond_kind=kind, cnn_params=params)
         dt = time.perf_counter() - t0
+        pcx.pcx_set_penalty_form(ctx, scalar)
         eigs[name] = ev
         d = stats.as_dict()
         out[name] = {"s_per_k": dt / nk, "status": int(st), "max_res": float(np.max(res)),

@@ -332,14 +332,42 @@ int pcx_get_apply_path(const pcx_ctx* ctx, int precision);
  * spectrum: the scalar rule puts it at about 12 N^2 4 pi^2 / |k|^2 for
  * 0 < |k| < 1, the per-mode rule at 12 N^2 4 pi^2 whatever k, which bounds
  * the FP64 rounding floor of the residual (about 1e-16 times the largest
- * eigenvalue) below 1e-8 at N = 128 near Gamma.  Switching the form frees
- * the captured apply graphs.  PCX_EINVAL for another value.
+ * eigenvalue) below 1e-8 at N = 128 near Gamma.
+ *   PCX_PENALTY_PROJECTOR gamma_p = gamma / |kappa_p|^2 (gamma <= 0 in a call:
+ *                         4 pi^2): gamma_p K_B(p) is gamma times the
+ *                         projector onto conj(kappa_p), every penalty
+ *                         eigenvalue equals gamma, and the top of the
+ *                         spectrum is that of A M A^H (about 12 N^2 / eps_min)
+ *                         instead of 12 N^2 4 pi^2 -- a lower FP32 rounding
+ *                         floor for the mixed scheme.  Prop. 2.5's condition
+ *                         needs gamma >= lambda_m^A, as with the rule.
+ * Switching the form frees the captured apply graphs.  PCX_EINVAL for
+ * another value.
  */
 #define PCX_PENALTY_SCALAR 0
 #define PCX_PENALTY_PER_MODE 1
+#define PCX_PENALTY_PROJECTOR 2
 pcx_status pcx_set_penalty_form(pcx_ctx* ctx, int form);
 /* The penalty form of this context; -1 for a NULL context. */
 int pcx_get_penalty_form(const pcx_ctx* ctx);
+
+/*
+ * pcx_set_apply_variant -- kernel variants of the three-pass chain in this
+ * context (the arithmetic, and so every result, is the same; only the
+ * schedule differs):
+ *   x_variant (passes A and C): 0 -- one row's global loads at a time, three
+ *     CTAs per SM; 1 -- three rows' loads issued together, three CTAs per
+ *     SM; 2 -- six rows' loads together, two CTAs per SM;
+ *   z_variant (pass B): 0 -- one z tile per CTA; 1 -- a persistent
+ *     warp-specialised kernel, one CTA per SM, in which half the warps
+ *     transform one tile buffer while the other half store the previous
+ *     tile and load the next one into the second buffer.
+ * -1 selects the build's default (x 1, z 0).  pcx_autotune sets both.
+ * Changing them frees the captured apply graphs.  PCX_EINVAL out of range.
+ */
+pcx_status pcx_set_apply_variant(pcx_ctx* ctx, int x_variant, int z_variant);
+/* The variants in effect (defaults resolved); either pointer may be NULL. */
+pcx_status pcx_get_apply_variant(const pcx_ctx* ctx, int* x_variant, int* z_variant);
 
 /* Result of pcx_autotune. */
 typedef struct {
@@ -350,6 +378,8 @@ typedef struct {
   int from_cache;       /* 0 measured, 1 process cache, 2 the PCX_TUNE_CACHE file  */
   int path;             /* pass structure chosen: PCX_APPLY_FIVE_PASS or
                            PCX_APPLY_THREE_PASS                                    */
+  int x_variant;        /* three-pass kernel variants chosen (pcx_set_apply_variant; */
+  int z_variant;        /* -1 when the five-pass chain was chosen)                   */
 } pcx_tune_result;
 
 /*
@@ -358,9 +388,11 @@ typedef struct {
  * context has (the five-pass chain, and the three-pass one where it
  * exists; see pcx_set_apply_path), every chunk size 1, 2, 4, ... <=
  * min(nvec, 64) (and nvec) is timed with CUDA events on `stream` (two warm
- * and three timed applies on random vectors), then graph replay of the best
- * one when `stream` is not the default stream.  The choice is applied to the
- * context (as pcx_set_apply_path / pcx_set_apply_chunk /
+ * and three timed applies on random vectors); when the three-pass chain
+ * wins, every pair of its kernel variants (pcx_set_apply_variant) at the
+ * best chunk; then graph replay of the best configuration when `stream` is
+ * not the default stream.  The choice is applied to the context (as
+ * pcx_set_apply_path / pcx_set_apply_chunk / pcx_set_apply_variant /
  * pcx_set_apply_graphs would) and cached
  * per device, SM count, N, precision and nvec for the process; when the
  * environment variable PCX_TUNE_CACHE names a file, results are read from and
@@ -481,7 +513,7 @@ pcx_status pcx_rr_eig(int m, const double* ga, const double* gb, double drop_tol
  * K_B = [K_1^H; K_2^H; K_3^H][K_1 K_2 K_3] is the Fourier form of B^H B
  * (Prop. 2.8), so out[j] = ||B h_j||^2 for the real-space field h_j = F3_3 x_j:
  * the penalty share of a Rayleigh quotient is gamma out[j] / (theta out[nvec+j]).
- * Under PCX_PENALTY_PER_MODE each mode's term is weighted by gamma_p / gamma,
+ * Under PCX_PENALTY_PER_MODE or _PROJECTOR each mode's term is weighted by gamma_p / gamma,
  * so out[j] = x_j^H (sum_p gamma_p K_B(p)) x_j / gamma and the share formula
  * stands.
  * Stream-ordered; X as in pcx_apply.

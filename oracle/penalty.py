@@ -18,6 +18,11 @@ eigenvalue in place of |k|^2 is
 so every penalty eigenvalue gamma_p |kappa_p|^2 = 4 pi^2 max(1, |kappa_p|^2)
 is at least 4 pi^2 (the condition gamma lambda^B >= lambda_m^A of Prop. 2.5,
 mode by mode) while the divergence-free eigenpairs do not change.
+
+Projector form (also an extension): gamma_p = gamma / |kappa_p|^2, so that
+gamma_p K_B(p) = gamma conj(kappa_p) kappa_p^T / |kappa_p|^2 is gamma times
+the orthogonal projector onto conj(kappa_p) and every penalty eigenvalue is
+gamma itself.
 """
 from __future__ import annotations
 
@@ -50,4 +55,14 @@ def gamma_per_mode(kap: np.ndarray, scale: float = 4.0 * math.pi ** 2) -> np.nda
     g = np.full(k2.shape, float(scale))
     small = (k2 > 0) & (k2 < 1)
     g[small] = scale / k2[small]
+    return g
+
+
+def gamma_projector(kap: np.ndarray, scale: float = 4.0 * math.pi ** 2) -> np.ndarray:
+    """(N, N, N) coefficients gamma_p = scale / |kappa_p|^2 of the projector
+    form; a mode with kappa_p = 0 (no penalty term) gets `scale`."""
+    k2 = np.sum(np.abs(kap) ** 2, axis=0)
+    g = np.full(k2.shape, float(scale))
+    nz = k2 > 0
+    g[nz] = scale / k2[nz]
     return g

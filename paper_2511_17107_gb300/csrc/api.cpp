@@ -345,10 +345,28 @@ pcx_status pcx_set_apply_path(pcx_ctx* c, int path) {
   return PCX_OK;
 }
 
+pcx_status pcx_set_apply_variant(pcx_ctx* c, int x_variant, int z_variant) {
+  if (!c) return inval(nullptr, "pcx_set_apply_variant: NULL context");
+  if (x_variant < -1 || x_variant >= pcx::X3_VARIANTS || z_variant < -1 || z_variant >= pcx::Z3_VARIANTS)
+    return inval(c, "pcx_set_apply_variant: x_variant must be in [-1, 2] and z_variant in [-1, 1]");
+  if (x_variant != c->x3_variant || z_variant != c->z3_variant) pcx::free_apply_graphs(c);
+  c->x3_variant = x_variant;
+  c->z3_variant = z_variant;
+  return PCX_OK;
+}
+
+pcx_status pcx_get_apply_variant(const pcx_ctx* c, int* x_variant, int* z_variant) {
+  if (!c) return inval(nullptr, "pcx_get_apply_variant: NULL context");
+  if (x_variant) *x_variant = c->x3_variant >= 0 ? c->x3_variant : PCX_X3_VARIANT;
+  if (z_variant) *z_variant = c->z3_variant >= 0 ? c->z3_variant : PCX_Z3_VARIANT;
+  return PCX_OK;
+}
+
 pcx_status pcx_set_penalty_form(pcx_ctx* c, int form) {
   if (!c) return inval(nullptr, "pcx_set_penalty_form: NULL context");
-  if (form != PCX_PENALTY_SCALAR && form != PCX_PENALTY_PER_MODE)
-    return inval(c, "pcx_set_penalty_form: form must be PCX_PENALTY_SCALAR or PCX_PENALTY_PER_MODE");
+  if (form != PCX_PENALTY_SCALAR && form != PCX_PENALTY_PER_MODE && form != PCX_PENALTY_PROJECTOR)
+    return inval(c, "pcx_set_penalty_form: form must be PCX_PENALTY_SCALAR, PCX_PENALTY_PER_MODE or "
+                    "PCX_PENALTY_PROJECTOR");
   if (form != c->penalty_form) pcx::free_apply_graphs(c);
   c->penalty_form = form;
   return PCX_OK;

@@ -119,17 +119,22 @@ template <typename T, int N, int OP>
 __host__ __device__ constexpr int pass3_threads() {
   return is_z_op<OP>() ? Cfg3<T, N>::THREADSZ : Cfg3<T, N>::THREADS;
 }
-// x tiles (passes A and C): CTAs per SM the registers are sized for, and
-// rows whose global loads are issued together before their arithmetic
-#ifndef PCX_X3_MINB
-#define PCX_X3_MINB 3
-#endif
-#ifndef PCX_X3_PF
-#define PCX_X3_PF 3
-#endif
-template <typename T, int N, int OP>
+// Kernel variants the autotuner chooses between at run time (the tile
+// shapes themselves are fixed by the geometry above, which the pass-B id
+// table depends on).  x tiles (passes A and C): PF rows whose global loads
+// are issued together before their arithmetic, and the CTAs per SM the
+// registers are sized for (MINB).  z tiles (pass B): one tile per CTA (0) or
+// the warp-specialised persistent kernel (1).
+template <int XV>
+struct XVar;
+template <> struct XVar<0> { static constexpr int PF = 1, MINB = 3; };
+template <> struct XVar<1> { static constexpr int PF = 3, MINB = 3; };
+template <> struct XVar<2> { static constexpr int PF = 6, MINB = 2; };
+// (X3_VARIANTS, Z3_VARIANTS and the defaults PCX_X3_VARIANT, PCX_Z3_VARIANT
+// are in pcx_internal.h, for the host side)
+template <typename T, int N, int OP, int XV>
 __host__ __device__ constexpr int pass3_minb() {
-  return is_z_op<OP>() ? ZGeom<N>::MINB : PCX_X3_MINB;
+  return is_z_op<OP>() ? ZGeom<N>::MINB : XVar<XV>::MINB;
 }
 
 // Row of pencil t of x tile `tile` (within one vector): z, y, and the n2
@@ -380,8 +385,8 @@ struct ZTile {
   }
 };
 
-template <typename T, int N, int OP>
-__global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP>()) pass3_kernel(PassArgs a) {
+template <typename T, int N, int OP, int XV>
+__global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP, XV>()) pass3_kernel(PassArgs a) {
   constexpr bool ZP = is_z_op<OP>();
   using C3 = Cfg3<T, N>;
   using C = std::conditional_t<ZP, typename C3::CZ, typename C3::C>;
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
 #pragma unroll
       for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
       constexpr int NI = (TP + TSTEP - 1) / TSTEP;
-      constexpr int PF = PCX_X3_PF < NI ? PCX_X3_PF : NI;
+      constexpr int PF = XVar<XV>::PF < NI ? XVar<XV>::PF : NI;
 #pragma unroll
       for (int i0 = 0; i0 < NI; i0 += PF) {
       // the rows of this batch: their loads in flight together
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
 #pragma unroll
       for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
       constexpr int NI = (TP + TSTEP - 1) / TSTEP;
-      constexpr int PF = PCX_X3_PF < NI ? PCX_X3_PF : NI;
+      constexpr int PF = XVar<XV>::PF < NI ? XVar<XV>::PF : NI;
 #pragma unroll
       for (int i0 = 0; i0 < NI; i0 += PF) {
       cx<T> skv[PF];
@@ -693,45 +698,60 @@ __global__ void pass3_ids_kernel(const uchar4* __restrict__ mid, uchar4* __restr
 // each tile kind is fixed by its geometry (x tiles: the five-pass x layout
 // plus the kappa tables; z tiles: the tile, the twiddles and the material
 // table).
-// Pass B's kernel: one tile per CTA (0) or the warp-specialised persistent
-// one (1); a build-time choice for tuning builds.  Measured at 128^3 the two
-// are within run-to-run noise of each other (both wait on the shared-memory
-// instruction queue at 16 warps per SM), so the simpler one is the default.
-#ifndef PCX_ZWS
-#define PCX_ZWS 0
-#endif
-
-template <typename T, int N, int OP>
-cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st) {
+template <typename T, int N, int OP, int XV>
+cudaError_t launch_pass3_tile(const PassArgs& a, int nv, cudaStream_t st) {
   using C3 = Cfg3<T, N>;
   constexpr bool ZP = is_z_op<OP>();
-  if constexpr (ZP && PCX_ZWS) {
-    const size_t smem = 2 * C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) +
-                        (((size_t)12 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);
-    const long long tiles = (long long)nv * C3::ZTILES;
-    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    auto kern = pass3z_ws_kernel<T, N, OP>;
-    if ((e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem)) != cudaSuccess) return e;
-    const long long grid = tiles < sms ? tiles : sms;
-    if (grid == 0) return cudaSuccess;
-    kern<<<(unsigned)grid, ZWS_THREADS, smem, st>>>(a, (int)tiles);
-    return cudaGetLastError();
-  }
   size_t smem;
   if constexpr (ZP)
     smem = C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) + (((size_t)12 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);
   else
     smem = C3::C::SMEM;
   const size_t tiles = (size_t)nv * (ZP ? C3::ZTILES : C3::TILES);
-  auto kern = pass3_kernel<T, N, OP>;
+  auto kern = pass3_kernel<T, N, OP, XV>;
   cudaError_t e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)tiles, pass3_threads<T, N, OP>(), smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, int N, int OP>
+cudaError_t launch_pass3_ws(const PassArgs& a, int nv, cudaStream_t st) {
+  using C3 = Cfg3<T, N>;
+  const size_t smem = 2 * C3::ZSMEM_TILE + (size_t)N * sizeof(cx<T>) +
+                      (((size_t)12 * a.n_mat * sizeof(T) + 15) & ~(size_t)15);
+  const long long tiles = (long long)nv * C3::ZTILES;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  auto kern = pass3z_ws_kernel<T, N, OP>;
+  if ((e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem)) != cudaSuccess) return e;
+  const long long grid = tiles < sms ? tiles : sms;
+  if (grid == 0) return cudaSuccess;
+  kern<<<(unsigned)grid, ZWS_THREADS, smem, st>>>(a, (int)tiles);
+  return cudaGetLastError();
+}
+
+// One pass of the three-pass chain over nv vectors; xv / zv pick the kernel
+// variant of the x / z passes (out of range: the build-time default).
+template <typename T, int N, int OP>
+cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st, int xv, int zv) {
+  if constexpr (is_z_op<OP>()) {
+    if (zv < 0 || zv >= Z3_VARIANTS) zv = PCX_Z3_VARIANT;
+    return zv == 1 ? launch_pass3_ws<T, N, OP>(a, nv, st) : launch_pass3_tile<T, N, OP, 0>(a, nv, st);
+  } else {
+    if (xv < 0 || xv >= X3_VARIANTS) xv = PCX_X3_VARIANT;
+    switch (xv) {
+      case 0:
+        return launch_pass3_tile<T, N, OP, 0>(a, nv, st);
+      case 2:
+        return launch_pass3_tile<T, N, OP, 2>(a, nv, st);
+      default:
+        return launch_pass3_tile<T, N, OP, 1>(a, nv, st);
+    }
+  }
 }
 
 // the pass-B order of the material ids (device, N^3 uchar4), built once per context

@@ -156,19 +156,21 @@ struct Tile {
   }
 };
 
-// Penalty weight of one Fourier mode relative to kp.gamma: 1 in the scalar
-// form; max(1, 1/|kappa_p|^2) in the per-mode form (k2 = |kappa_p|^2).
-// The mode with kappa_p = 0 gets 0: its penalty term vanishes either way.
+// Penalty weight of one Fourier mode relative to kp.gamma (k2 = |kappa_p|^2):
+// 1 in the scalar form; max(1, 1/k2) in the per-mode form; 1/k2 in the
+// projector form.  The mode with kappa_p = 0 gets 0: its penalty term
+// vanishes either way.
 template <typename T>
 __device__ __forceinline__ T penalty_weight(const KParams& kp, T k2) {
-  if (!kp.per_mode || k2 >= (T)1) return (T)1;
+  if (!kp.per_mode || (kp.per_mode == 1 && k2 >= (T)1)) return (T)1;
   return k2 > (T)0 ? (T)1 / k2 : (T)0;
 }
 
-// Reciprocal of that weight, min(1, |kappa_p|^2) (per-mode form) or 1: it
-// scales 1/gamma into 1/gamma_p without a division.
+// Reciprocal of that weight (min(1, k2), k2 or 1): it scales 1/gamma into
+// 1/gamma_p without a division.
 template <typename T>
 __device__ __forceinline__ T penalty_inv_weight(const KParams& kp, T k2) {
+  if (kp.per_mode == 2) return k2;
   return kp.per_mode && k2 < (T)1 ? k2 : (T)1;
 }
 
@@ -874,7 +876,7 @@ __host__ __device__ constexpr bool has_pass3() {
   return sizeof(T) == 4 && (N == 32 || N == 64 || N == 128);
 }
 template <typename T, int N, int OP>
-cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st);
+cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st, int xv, int zv);
 
 template <typename T, int N>
 cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void* Y, int nvec, int chunk, void* sbuf,
@@ -939,13 +941,16 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
       if (c->apply_path != PCX_APPLY_FIVE_PASS && (c->dev.mid3 || !c->dev.mid)) {
         // three passes, in place on y after the first
         a.mid3 = c->dev.mid3;
-        if ((e = t0 ? launch_pass3<T, N, OP_PRE_T0>(a, nv, st) : launch_pass3<T, N, OP_PRE>(a, nv, st)) != cudaSuccess)
-          return e;
-        a.in = y;
-        if ((e = t0 ? launch_pass3<T, N, OP_SANDWICH_EPS>(a, nv, st) : launch_pass3<T, N, OP_SANDWICH>(a, nv, st))
+        const int xv = c->x3_variant, zv = c->z3_variant;
+        if ((e = t0 ? launch_pass3<T, N, OP_PRE_T0>(a, nv, st, xv, zv) : launch_pass3<T, N, OP_PRE>(a, nv, st, xv, zv))
             != cudaSuccess)
           return e;
-        if ((e = t0 ? launch_pass3<T, N, OP_POST_T0>(a, nv, st) : launch_pass3<T, N, OP_POST>(a, nv, st)) != cudaSuccess)
+        a.in = y;
+        if ((e = t0 ? launch_pass3<T, N, OP_SANDWICH_EPS>(a, nv, st, xv, zv)
+                    : launch_pass3<T, N, OP_SANDWICH>(a, nv, st, xv, zv)) != cudaSuccess)
+          return e;
+        if ((e = t0 ? launch_pass3<T, N, OP_POST_T0>(a, nv, st, xv, zv) : launch_pass3<T, N, OP_POST>(a, nv, st, xv, zv))
+            != cudaSuccess)
           return e;
         continue;
       }

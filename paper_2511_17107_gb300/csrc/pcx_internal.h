@@ -24,8 +24,20 @@ struct KParams {
   double kq[3];     // coefficient of i Lambda_0(p_i) added to kappa_i
   double gamma;     // penalty coefficient (per-mode form: its scale, see per_mode)
   int diag_b;       // 1 when b is diagonal (simple cubic fast path)
-  int per_mode;     // 1: mode p carries gamma_p = gamma max(1, 1/|kappa_p|^2)
+  int per_mode;     // penalty form: 0 scalar; 1 gamma_p = gamma max(1, 1/|kappa_p|^2);
+                    // 2 gamma_p = gamma / |kappa_p|^2 (gamma times the longitudinal projector)
 };
+
+// Kernel variants of the three-pass chain (fft3_kernels.cuh): x passes
+// 0..X3_VARIANTS-1, z pass 0..Z3_VARIANTS-1, and the build-time defaults
+// used when neither the caller nor the autotuner chose.
+constexpr int X3_VARIANTS = 3, Z3_VARIANTS = 2;
+#ifndef PCX_X3_VARIANT
+#define PCX_X3_VARIANT 1
+#endif
+#ifndef PCX_Z3_VARIANT
+#define PCX_Z3_VARIANT 0
+#endif
 
 // Device-resident, k-independent tables of one context.
 struct DeviceTables {
@@ -63,6 +75,8 @@ struct pcx_ctx {
   int apply_chunk = 0;
   // apply pass structure: PCX_APPLY_AUTO, PCX_APPLY_FIVE_PASS or PCX_APPLY_THREE_PASS
   int apply_path = 0;
+  // kernel variants of the three-pass chain's x and z passes (-1: build default)
+  int x3_variant = -1, z3_variant = -1;
   void* scratch = nullptr;     // gamma kappa.x carried from pass 1 to pass 5
   size_t scratch_bytes = 0;
   size_t l2_bytes = 0;
@@ -73,7 +87,7 @@ struct pcx_ctx {
   int use_graphs = 0;
   void* graphs = nullptr;
   int cnn_form = 0;   // PCX_CNN_HERMITIAN | PCX_CNN_BF16 flags
-  int penalty_form = 0;   // PCX_PENALTY_SCALAR or PCX_PENALTY_PER_MODE
+  int penalty_form = 0;   // PCX_PENALTY_SCALAR, PCX_PENALTY_PER_MODE or PCX_PENALTY_PROJECTOR
   // staging for pcx_apply_host: two slots of X and Y chunks, copy streams
   // and slot events (created on first use)
   void* stage_x = nullptr;

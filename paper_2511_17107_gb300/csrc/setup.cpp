@@ -251,7 +251,10 @@ KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma) {
   // that mode's own B eigenvalue |kappa_p|^2 (Lemma kc_ABblock) in place of
   // |k|^2, so gamma_p |kappa_p|^2 = 4 pi^2 max(1, |kappa_p|^2) >= 4 pi^2 for
   // every mode; the kernels take gamma_p = gamma max(1, 1/|kappa_p|^2).
-  kp.per_mode = c->penalty_form == PCX_PENALTY_PER_MODE;
+  // Projector form: gamma_p = gamma / |kappa_p|^2, so that gamma_p K_B(p) is
+  // gamma times the projector onto conj(kappa_p) and every penalty
+  // eigenvalue equals gamma (4 pi^2 by default, the rule's value).
+  kp.per_mode = c->penalty_form;
   kp.gamma = gamma > 0 ? gamma : kp.per_mode ? 4.0 * M_PI * M_PI : gamma_rule(k);
   kp.diag_b = (c->b[1] == 0 && c->b[2] == 0 && c->b[3] == 0 && c->b[5] == 0 && c->b[6] == 0 && c->b[7] == 0);
   return kp;

@@ -1,7 +1,8 @@
 // Autotuner of the apply launch configuration: the pass structure (five
 // passes, or the three-pass form where it exists), vectors per launch chunk
-// (how much of the block sweeps the passes while L2-resident) and whether
-// the launch chain replays as a CUDA graph.  Each candidate is timed
+// (how much of the block sweeps the passes while L2-resident), the kernel
+// variants of the three-pass chain's x and z passes, and whether the launch
+// chain replays as a CUDA graph.  Each candidate is timed
 // with CUDA events on the caller's stream; the choice is cached per
 // (device, SM count, N, precision, block) in the process and, when the
 // environment variable PCX_TUNE_CACHE names a file, in that file (one line
@@ -52,14 +53,16 @@ bool file_lookup(const std::string& key, pcx_tune_result* r) {
   bool found = false;
   while (std::fgets(line, sizeof(line), f)) {
     char k[400];
-    int chunk = 0, graphs = 0, path = PCX_APPLY_FIVE_PASS;
+    int chunk = 0, graphs = 0, path = PCX_APPLY_FIVE_PASS, xv = -1, zv = -1;
     double us = 0;
-    const int got = std::sscanf(line, "%399s %d %d %lf %d", k, &chunk, &graphs, &us, &path);
+    const int got = std::sscanf(line, "%399s %d %d %lf %d %d %d", k, &chunk, &graphs, &us, &path, &xv, &zv);
     if (got >= 4 && key == k && chunk > 0) {
       r->chunk = chunk;
       r->graphs = graphs;
       r->us_per_vector = us;
-      r->path = got == 5 ? path : PCX_APPLY_FIVE_PASS;
+      r->path = got >= 5 ? path : PCX_APPLY_FIVE_PASS;
+      r->x_variant = got >= 7 ? xv : -1;
+      r->z_variant = got >= 7 ? zv : -1;
       found = true;   // the last line for a key wins
     }
   }
@@ -72,7 +75,8 @@ void file_store(const std::string& key, const pcx_tune_result& r) {
   if (!path || !*path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %.6f %d\n", key.c_str(), r.chunk, r.graphs, r.us_per_vector, r.path);
+  std::fprintf(f, "%s %d %d %.6f %d %d %d\n", key.c_str(), r.chunk, r.graphs, r.us_per_vector, r.path, r.x_variant,
+               r.z_variant);
   std::fclose(f);
 }
 
@@ -106,6 +110,8 @@ cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, 
     c->apply_chunk = r.chunk;
     c->use_graphs = r.graphs;
     c->apply_path = r.path;
+    c->x3_variant = r.x_variant;
+    c->z3_variant = r.z_variant;
     if (out) *out = r;
     return cudaSuccess;
   }
@@ -115,6 +121,7 @@ cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaSuccess;
   const int saved_chunk = c->apply_chunk, saved_graphs = c->use_graphs, saved_path = c->apply_path;
+  const int saved_xv = c->x3_variant, saved_zv = c->z3_variant;
   const double k[3] = {0.31, 0.67, 1.13};
   const KParams kp = make_kparams(c, k, 0.0);
   std::vector<int> cands;
@@ -150,6 +157,7 @@ cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, 
   CKT(cudaEventCreate(&e0));
   CKT(cudaEventCreate(&e1));
   c->use_graphs = 0;
+  c->x3_variant = c->z3_variant = -1;
   for (int path : paths) {
     c->apply_path = path;
     for (int ch : cands) {
@@ -167,6 +175,30 @@ cudaError_t autotune_apply(pcx_ctx* c, int precision, int nvec, cudaStream_t s, 
   r.chunk = best_chunk;
   r.path = best_path;
   r.graphs = 0;
+  r.x_variant = r.z_variant = -1;
+  if (best_path == PCX_APPLY_THREE_PASS) {
+    // the kernel variants at the best chunk (the defaults were timed above)
+    c->apply_path = best_path;
+    c->apply_chunk = best_chunk;
+    r.x_variant = PCX_X3_VARIANT;
+    r.z_variant = PCX_Z3_VARIANT;
+    for (int xv = 0; xv < X3_VARIANTS; ++xv)
+      for (int zv = 0; zv < Z3_VARIANTS; ++zv) {
+        if (xv == PCX_X3_VARIANT && zv == PCX_Z3_VARIANT) continue;
+        c->x3_variant = xv;
+        c->z3_variant = zv;
+        double ms = 0;
+        CKT(time_apply(&ms));
+        ++r.candidates;
+        if (ms < best) {
+          best = ms;
+          r.x_variant = xv;
+          r.z_variant = zv;
+        }
+      }
+    c->x3_variant = r.x_variant;
+    c->z3_variant = r.z_variant;
+  }
   if (capturable(s)) {
     c->apply_path = best_path;
     c->apply_chunk = best_chunk;
@@ -191,11 +223,15 @@ done:
     c->apply_chunk = saved_chunk;
     c->use_graphs = saved_graphs;
     c->apply_path = saved_path;
+    c->x3_variant = saved_xv;
+    c->z3_variant = saved_zv;
     return err;
   }
   c->apply_chunk = r.chunk;
   c->use_graphs = r.graphs;
   c->apply_path = r.path;
+  c->x3_variant = r.x_variant;
+  c->z3_variant = r.z_variant;
   {
     std::lock_guard<std::mutex> lock(g_mu);
     g_cache.push_back(Entry{key, r});

@@ -19,7 +19,7 @@ PCX_OK, PCX_EINVAL, PCX_ENOMEM, PCX_ENOTHPD, PCX_ENOCONV, PCX_ENUMERIC, PCX_ECUD
 PCX_FP64, PCX_FP32 = 0, 1
 PCX_CT_SUMMED, PCX_CT_LITERAL = 0, 1
 PCX_APPLY_AUTO, PCX_APPLY_FIVE_PASS, PCX_APPLY_THREE_PASS = 0, 1, 2
-PCX_PENALTY_SCALAR, PCX_PENALTY_PER_MODE = 0, 1
+PCX_PENALTY_SCALAR, PCX_PENALTY_PER_MODE, PCX_PENALTY_PROJECTOR = 0, 1, 2
 STATUS_NAMES = {0: "PCX_OK", -1: "PCX_EINVAL", -2: "PCX_ENOMEM", -3: "PCX_ENOTHPD", -4: "PCX_ENOCONV",
                 -5: "PCX_ENUMERIC", -6: "PCX_ECUDA"}
 
@@ -56,7 +56,7 @@ class pcx_solve_stats(C.Structure):
 
 class pcx_tune_result(C.Structure):
     _fields_ = [("chunk", C.c_int), ("graphs", C.c_int), ("us_per_vector", C.c_double), ("candidates", C.c_int),
-                ("from_cache", C.c_int), ("path", C.c_int)]
+                ("from_cache", C.c_int), ("path", C.c_int), ("x_variant", C.c_int), ("z_variant", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -112,6 +112,8 @@ def lib():
             "pcx_set_cnn_form": (st, [vp, C.c_int]),
             "pcx_get_apply_path": (C.c_int, [vp, C.c_int]),
             "pcx_set_penalty_form": (st, [vp, C.c_int]),
+            "pcx_set_apply_variant": (st, [vp, C.c_int, C.c_int]),
+            "pcx_get_apply_variant": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
             "pcx_get_penalty_form": (C.c_int, [vp]),
             "pcx_autotune": (st, [vp, C.c_int, C.c_int, vp, C.POINTER(pcx_tune_result)]),
             "pcx_sandwich_precond": (st, [vp, dp, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
@@ -140,7 +142,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_set_penalty_form", "pcx_get_penalty_form", "pcx_set_cnn_form", "pcx_autotune",
+                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_set_penalty_form", "pcx_get_penalty_form", "pcx_set_apply_variant", "pcx_get_apply_variant", "pcx_set_cnn_form", "pcx_autotune",
                         "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
                         "pcx_cg_solve", "pcx_gram", "pcx_set_gram_path", "pcx_get_gram_path", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
@@ -419,6 +421,16 @@ def pcx_set_apply_path(ctx, path):
 
 def pcx_get_apply_path(ctx, precision):
     return int(lib().pcx_get_apply_path(ctx.handle, int(precision)))
+
+
+def pcx_set_apply_variant(ctx, x_variant=-1, z_variant=-1):
+    _check(lib().pcx_set_apply_variant(ctx.handle, int(x_variant), int(z_variant)), ctx.handle)
+
+
+def pcx_get_apply_variant(ctx):
+    xv, zv = C.c_int(), C.c_int()
+    _check(lib().pcx_get_apply_variant(ctx.handle, C.byref(xv), C.byref(zv)), ctx.handle)
+    return xv.value, zv.value
 
 
 def pcx_set_penalty_form(ctx, form):

@@ -144,3 +144,62 @@ def test_apply_path_rejects_unknown_value(pcx):
     with pytest.raises(pcx.PcxError) as e:
         pcx.pcx_set_apply_path(ctx, 7)
     assert e.value.status == pcx.PCX_EINVAL
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_kernel_variants_give_identical_results(pcx, n):
+    """Every x / z kernel variant of the three-pass chain runs the same
+    arithmetic in the same order: outputs bit-identical to the default's,
+    for the apply and for T0; out-of-range variants are refused."""
+    s = wl.diamond_rods()
+    k = wl.config_k(s.name)[5]
+    x = wl.random_block(3, n, seed=21).astype(np.complex64)
+    ctx = pcx.setup_structure(s, n)
+    pcx.pcx_set_apply_path(ctx, pcx.PCX_APPLY_THREE_PASS)
+    pcx.pcx_set_apply_chunk(ctx, 2)   # a ragged last chunk of one vector
+    X = torch.from_numpy(x).cuda()
+    ref = {}
+    for xv in range(3):
+        for zv in range(2):
+            pcx.pcx_set_apply_variant(ctx, xv, zv)
+            assert pcx.pcx_get_apply_variant(ctx) == (xv, zv)
+            Y = torch.empty_like(X)
+            W = torch.empty_like(X)
+            pcx.pcx_apply(ctx, k, X, Y)
+            pcx.pcx_sandwich_precond(ctx, k, X, W)
+            torch.cuda.synchronize()
+            got = (Y.cpu().numpy(), W.cpu().numpy())
+            if not ref:
+                ref = {"y": got[0], "w": got[1]}
+            assert np.array_equal(got[0], ref["y"]) and np.array_equal(got[1], ref["w"]), (xv, zv)
+    pcx.pcx_set_apply_variant(ctx, -1, -1)
+    assert pcx.pcx_get_apply_variant(ctx) == (1, 0)
+    for bad in ((3, 0), (0, 2), (-2, 0)):
+        with pytest.raises(pcx.PcxError) as e:
+            pcx.pcx_set_apply_variant(ctx, *bad)
+        assert e.value.status == pcx.PCX_EINVAL
+
+
+def test_autotune_picks_the_variants(pcx):
+    """At 32^3 (three-pass chain available) the tuner times the kernel
+    variants and leaves the chosen pair in the context; the result is valid
+    and the apply with it matches the oracle."""
+    n = 32
+    s = wl.fcc_air_spheres()
+    k = wl.config_k(s.name)[3]
+    ctx = pcx.setup_structure(s, n)
+    r = pcx.pcx_autotune(ctx, pcx.PCX_FP32, 3, stream=torch.cuda.Stream())
+    if r["path"] == pcx.PCX_APPLY_THREE_PASS:
+        assert 0 <= r["x_variant"] < 3 and 0 <= r["z_variant"] < 2
+        assert pcx.pcx_get_apply_variant(ctx) == (r["x_variant"], r["z_variant"])
+        if not r["from_cache"]:
+            assert r["candidates"] >= 6
+    else:
+        assert (r["x_variant"], r["z_variant"]) == (-1, -1)
+    x = wl.random_block(2, n, seed=22).astype(np.complex64)
+    want = _oracle_apply(s, n, k, x.astype(np.complex128))
+    X = torch.from_numpy(x).cuda()
+    Y = torch.empty_like(X)
+    pcx.pcx_apply(ctx, k, X, Y)
+    torch.cuda.synchronize()
+    assert _err(Y.cpu().numpy(), want) <= TOL

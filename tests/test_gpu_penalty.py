@@ -53,7 +53,7 @@ def _per_mode_ctx(pcx, s, n, **kw):
 def test_penalty_form_rejects_other_values(pcx):
     ctx = pcx.setup_structure(wl.sc_gyro_sphere(), 8)
     with pytest.raises(pcx.PcxError):
-        pcx.pcx_set_penalty_form(ctx, 2)
+        pcx.pcx_set_penalty_form(ctx, 3)
     assert pcx.pcx_get_penalty_form(ctx) == pcx.PCX_PENALTY_SCALAR
 
 
@@ -200,3 +200,62 @@ def test_per_mode_solve_near_gamma_reaches_1e8_at_64(pcx):
         ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-8, block=nev + 4, precision=prec, maxit=400)
         assert st == pcx.PCX_OK and np.all(res <= 1e-8), (prec, res)
         np.testing.assert_allclose(ev[0], ev_s[0], rtol=2e-6)
+
+
+def _projector_ctx(pcx, s, n, **kw):
+    ctx = pcx.setup_structure(s, n, **kw)
+    pcx.pcx_set_penalty_form(ctx, pcx.PCX_PENALTY_PROJECTOR)
+    assert pcx.pcx_get_penalty_form(ctx) == pcx.PCX_PENALTY_PROJECTOR
+    return ctx
+
+
+@pytest.mark.parametrize("dtype,path,tol", [(np.complex128, None, 1e-12), (np.complex64, "three", 2e-5),
+                                            (np.complex64, "five", 2e-5)])
+def test_projector_apply_and_preconditioners(pcx, dtype, path, tol):
+    """The projector form gamma_p = 4 pi^2 / |kappa_p|^2 against the oracle:
+    the apply (both pass structures in complex64), K_P^{-1} and T0."""
+    n = 32
+    s = wl.fcc_air_spheres()
+    k = np.array([0.4, -1.1, 0.7])
+    kap = fourier.kappa(n, s.lattice, k)
+    g = penalty.gamma_projector(kap)
+    blocks = permittivity.cell_blocks(s, n)
+    x = wl.random_block(2, n, seed=47)
+    want = fourier.apply_symbols(x, kap, lambda e: permittivity.apply_m(blocks, e), g)
+    ctx = _projector_ctx(pcx, s, n)
+    if path is not None:
+        pcx.pcx_set_apply_path(ctx, pcx.PCX_APPLY_THREE_PASS if path == "three" else pcx.PCX_APPLY_FIVE_PASS)
+    X = torch.from_numpy(x.astype(dtype)).cuda()
+    Y = torch.empty_like(X)
+    pcx.pcx_apply(ctx, k, X, Y)
+    torch.cuda.synchronize()
+    assert _err(Y.cpu().numpy(), want) <= tol
+    W = torch.empty_like(X)
+    pcx.pcx_precond(ctx, k, X, W)
+    torch.cuda.synchronize()
+    assert _err(W.cpu().numpy(), fourier.precondition(x, kap, g)) <= tol
+    pcx.pcx_sandwich_precond(ctx, k, X, W)
+    torch.cuda.synchronize()
+    assert _err(W.cpu().numpy(), learned.sandwich_precondition(x, kap, blocks, g)) <= tol
+
+
+@pytest.mark.parametrize("prec,rtol", [(0, 1e-10), (1, 1e-6)])
+def test_projector_solve_matches_scalar_form(pcx, prec, rtol):
+    """The projector form keeps the physical eigenpairs: the 8^3 solve
+    returns the lowest eigenvalues of the scalar form's dense operator."""
+    n, nev = 8, 6
+    s = wl.sc_gyro_sphere()
+    k = np.array([0.6, 1.3, -0.5])
+    kap = fourier.kappa(n, s.lattice, k)
+    blocks = permittivity.cell_blocks(s, n)
+    am = lambda e: permittivity.apply_m(blocks, e)
+    shape = (3, n, n, n)
+    mat = eig.dense_matrix(lambda c: fourier.apply_symbols(c.reshape((-1,) + shape), kap, am,
+                                                           penalty.gamma_practical(k)).reshape(c.shape[0], -1),
+                           3 * n ** 3)
+    ev_d = np.linalg.eigvalsh(0.5 * (mat + mat.conj().T))
+    want = ev_d[ev_d > 1e-9 * ev_d.max()][:nev]
+    ctx = _projector_ctx(pcx, s, n)
+    ev, res, its, st = pcx.pcx_solve(ctx, [k], nev, 1e-10, block=nev + 4, precision=prec)
+    assert st == pcx.PCX_OK and np.all(res <= 1e-10)
+    np.testing.assert_allclose(ev[0], want, rtol=rtol)

@@ -119,3 +119,46 @@ def test_per_mode_sandwich_is_exact_for_a_homogeneous_isotropic_medium():
     x = rng.standard_normal((2, 3, n, n, n)) + 1j * rng.standard_normal((2, 3, n, n, n))
     y = fourier.apply_symbols(x, kap, lambda e: permittivity.apply_m(blocks, e), g)
     np.testing.assert_allclose(learned.sandwich_precondition(y, kap, blocks, g), x, atol=1e-9 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("lattice,kvec", [("SC", (0.05, -0.08, 0.03)), ("FCC", (1.3, 0.2, -0.7))])
+def test_projector_spectrum_is_physical_union_constant(lattice, kvec):
+    """Projector form gamma_p = gamma / |kappa_p|^2: the spectrum is the
+    nonzero spectrum of A M A^H (dense real-space stencils) and the value
+    gamma = 4 pi^2 once per mode with kappa_p != 0; the largest eigenvalue
+    is that of A M A^H or gamma, far below the rule's 4 pi^2 max|kappa|^2."""
+    n = 6
+    lat = getattr(wl, lattice)
+    k = np.array(kvec)
+    s = wl.sc_gyro_sphere() if lattice == "SC" else wl.fcc_air_spheres()
+    blocks = permittivity.cell_blocks(s, n)
+    ops = yee.YeeOperators(n, lat, k, 1)
+    am = lambda e: permittivity.apply_m(blocks, e)
+    dim, shape = 3 * n ** 3, (3, n, n, n)
+    ev_a = _eigh(eig.dense_matrix(
+        lambda c: ops.curl(am(ops.curl_adj(c.reshape((-1,) + shape)))).reshape(c.shape[0], -1), dim))
+    phys = ev_a[np.abs(ev_a) > 1e-9 * ev_a.max()]
+    kap = fourier.kappa(n, lat, k)
+    k2 = np.sum(np.abs(kap) ** 2, axis=0)
+    ev = _eigh(eig.dense_matrix(
+        lambda c: fourier.apply_symbols(c.reshape((-1,) + shape), kap, am, penalty.gamma_projector(kap))
+        .reshape(c.shape[0], -1), dim))
+    expect = np.sort(np.concatenate([phys, np.full(int(np.sum(k2 > 0)), FOUR_PI2), np.zeros(int(np.sum(k2 == 0)))]))
+    np.testing.assert_allclose(ev, expect, atol=1e-10 * expect.max())
+    assert ev.max() <= max(ev_a.max(), FOUR_PI2) * (1 + 1e-12)
+
+
+def test_projector_preconditioner_and_sandwich_invert():
+    """K_P^{-1} undoes the projector-form vacuum operator and T0 the
+    projector-form operator of M = m0 I, on every mode with kappa != 0."""
+    rng = np.random.default_rng(7)
+    n, m0 = 8, 0.37
+    k = np.array([0.07, 0.02, -0.05])
+    kap = fourier.kappa(n, wl.FCC, k)
+    g = penalty.gamma_projector(kap)
+    x = rng.standard_normal((2, 3, n, n, n)) + 1j * rng.standard_normal((2, 3, n, n, n))
+    y = fourier.apply_symbols(x, kap, lambda e: e, g)
+    np.testing.assert_allclose(fourier.precondition(y, kap, g), x, atol=1e-10 * np.abs(x).max())
+    blocks = np.broadcast_to(m0 * np.eye(3), (n, n, n, 3, 3)).astype(np.complex128)
+    y = fourier.apply_symbols(x, kap, lambda e: permittivity.apply_m(blocks, e), g)
+    np.testing.assert_allclose(learned.sandwich_precondition(y, kap, blocks, g), x, atol=1e-9 * np.abs(x).max())
