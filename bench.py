@@ -754,7 +754,7 @@ def solve_legs(pcx, ctx, kpath, nk, n, nev=12, block=16, tol=1e-8, learned_steps
     legs.append(("fp64", pcx.PCX_FP64, 0, None, scalar))
     legs.append(("fp64_sandwich", pcx.PCX_FP64, 1, None, scalar))
     # the projector penalty form (the same physical eigenpairs, every
-    # penalty eigenvalue 4 pi^2): a lower FP32 rounding floor
+    # penalty eigenvalue 16 pi^2): a lower FP32 rounding floor
     legs.append(("mixed_sandwich_projector", pcx.PCX_FP32, 1, None, projector))
     if want:
         legs = [leg for leg in legs if leg[0] in want]

@@ -334,7 +334,10 @@ int pcx_get_apply_path(const pcx_ctx* ctx, int precision);
  * the FP64 rounding floor of the residual (about 1e-16 times the largest
  * eigenvalue) below 1e-8 at N = 128 near Gamma.
  *   PCX_PENALTY_PROJECTOR gamma_p = gamma / |kappa_p|^2 (gamma <= 0 in a call:
- *                         4 pi^2): gamma_p K_B(p) is gamma times the
+ *                         16 pi^2, four times the rule's value, since all
+ *                         N^3 penalty eigenvalues sit at gamma and a cluster
+ *                         just above the wanted ones would slow LOBPCG or
+ *                         enter the wanted set): gamma_p K_B(p) is gamma times the
  *                         projector onto conj(kappa_p), every penalty
  *                         eigenvalue equals gamma, and the top of the
  *                         spectrum is that of A M A^H (about 12 N^2 / eps_min)

@@ -58,7 +58,7 @@ def gamma_per_mode(kap: np.ndarray, scale: float = 4.0 * math.pi ** 2) -> np.nda
     return g
 
 
-def gamma_projector(kap: np.ndarray, scale: float = 4.0 * math.pi ** 2) -> np.ndarray:
+def gamma_projector(kap: np.ndarray, scale: float = 16.0 * math.pi ** 2) -> np.ndarray:
     """(N, N, N) coefficients gamma_p = scale / |kappa_p|^2 of the projector
     form; a mode with kappa_p = 0 (no penalty term) gets `scale`."""
     k2 = np.sum(np.abs(kap) ** 2, axis=0)

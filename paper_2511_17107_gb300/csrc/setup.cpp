@@ -253,9 +253,13 @@ KParams make_kparams(const pcx_ctx* c, const double k[3], double gamma) {
   // every mode; the kernels take gamma_p = gamma max(1, 1/|kappa_p|^2).
   // Projector form: gamma_p = gamma / |kappa_p|^2, so that gamma_p K_B(p) is
   // gamma times the projector onto conj(kappa_p) and every penalty
-  // eigenvalue equals gamma (4 pi^2 by default, the rule's value).
+  // eigenvalue equals gamma.  Its default is four times the rule's 4 pi^2:
+  // all N^3 penalty eigenvalues sit at that one value, and a cluster that
+  // close above the wanted ones would slow LOBPCG or enter the wanted set.
   kp.per_mode = c->penalty_form;
-  kp.gamma = gamma > 0 ? gamma : kp.per_mode ? 4.0 * M_PI * M_PI : gamma_rule(k);
+  const double four_pi2 = 4.0 * M_PI * M_PI;
+  kp.gamma = gamma > 0 ? gamma : kp.per_mode == PCX_PENALTY_PROJECTOR ? 4.0 * four_pi2
+                                                                      : kp.per_mode ? four_pi2 : gamma_rule(k);
   kp.diag_b = (c->b[1] == 0 && c->b[2] == 0 && c->b[3] == 0 && c->b[5] == 0 && c->b[6] == 0 && c->b[7] == 0);
   return kp;
 }

@@ -212,7 +212,7 @@ def _projector_ctx(pcx, s, n, **kw):
 @pytest.mark.parametrize("dtype,path,tol", [(np.complex128, None, 1e-12), (np.complex64, "three", 2e-5),
                                             (np.complex64, "five", 2e-5)])
 def test_projector_apply_and_preconditioners(pcx, dtype, path, tol):
-    """The projector form gamma_p = 4 pi^2 / |kappa_p|^2 against the oracle:
+    """The projector form gamma_p = 16 pi^2 / |kappa_p|^2 against the oracle:
     the apply (both pass structures in complex64), K_P^{-1} and T0."""
     n = 32
     s = wl.fcc_air_spheres()

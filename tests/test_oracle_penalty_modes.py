@@ -125,8 +125,9 @@ def test_per_mode_sandwich_is_exact_for_a_homogeneous_isotropic_medium():
 def test_projector_spectrum_is_physical_union_constant(lattice, kvec):
     """Projector form gamma_p = gamma / |kappa_p|^2: the spectrum is the
     nonzero spectrum of A M A^H (dense real-space stencils) and the value
-    gamma = 4 pi^2 once per mode with kappa_p != 0; the largest eigenvalue
-    is that of A M A^H or gamma, far below the rule's 4 pi^2 max|kappa|^2."""
+    gamma (16 pi^2 by default) once per mode with kappa_p != 0; the largest
+    eigenvalue is that of A M A^H or gamma, far below the rule's
+    4 pi^2 max|kappa|^2."""
     n = 6
     lat = getattr(wl, lattice)
     k = np.array(kvec)
@@ -143,9 +144,10 @@ def test_projector_spectrum_is_physical_union_constant(lattice, kvec):
     ev = _eigh(eig.dense_matrix(
         lambda c: fourier.apply_symbols(c.reshape((-1,) + shape), kap, am, penalty.gamma_projector(kap))
         .reshape(c.shape[0], -1), dim))
-    expect = np.sort(np.concatenate([phys, np.full(int(np.sum(k2 > 0)), FOUR_PI2), np.zeros(int(np.sum(k2 == 0)))]))
+    gam = 4 * FOUR_PI2
+    expect = np.sort(np.concatenate([phys, np.full(int(np.sum(k2 > 0)), gam), np.zeros(int(np.sum(k2 == 0)))]))
     np.testing.assert_allclose(ev, expect, atol=1e-10 * expect.max())
-    assert ev.max() <= max(ev_a.max(), FOUR_PI2) * (1 + 1e-12)
+    assert ev.max() <= max(ev_a.max(), gam) * (1 + 1e-12)
 
 
 def test_projector_preconditioner_and_sandwich_invert():
