@@ -46,9 +46,11 @@ WORKLOAD = ("diamond-rods 128^3 FCC, 40 Bloch vectors x block of 16, complex64, 
 METRIC = "compensated-operator applies/s at 128^3"
 # DRAM bytes of one vector through the pass kernels at 16 vectors per
 # launch: dram__bytes_read.sum + dram__bytes_write.sum of the launches of one
-# chunk (five or three passes) in an ncu capture of this benchmark, divided
-# by 16; used only when the run uses that chunk and that pass structure.
-TRAFFIC_BYTES_PER_VECTOR_128_C64 = {5: 8.8128e9 / 16, 3: 5.346921e9 / 16}   # by pass count
+# chunk in an ncu capture of this benchmark, divided by 16; keyed by the pass
+# structure and, for the three-pass chain, pass B's kernel variant (one tile
+# per CTA, or the warp-specialised one); the x-pass variants move the same
+# bytes.  Used only when the run uses that chunk, structure and variant.
+TRAFFIC_BYTES_PER_VECTOR_128_C64 = {(5, None): 8.8128e9 / 16, (3, 0): 5.346921e9 / 16, (3, 1): 5.310127e9 / 16}
 TRAFFIC_CHUNK = 16
 UNIT = "vector-applies/s"
 
@@ -952,8 +954,9 @@ def main():
     chunk = pcx.pcx_get_apply_chunk(ctx, prec)
     passes = pcx.pcx_get_apply_path(ctx, prec)
     passes = 3 if passes == pcx.PCX_APPLY_THREE_PASS else (5 if passes == pcx.PCX_APPLY_FIVE_PASS else passes)
-    traffic = TRAFFIC_BYTES_PER_VECTOR_128_C64[passes] * vecs \
-        if (n, es) == (N, 8) and passes in TRAFFIC_BYTES_PER_VECTOR_128_C64 and chunk == TRAFFIC_CHUNK else None
+    tkey = (passes, pcx.pcx_get_apply_variant(ctx)[1] if passes == 3 else None)
+    traffic = TRAFFIC_BYTES_PER_VECTOR_128_C64[tkey] * vecs \
+        if (n, es) == (N, 8) and tkey in TRAFFIC_BYTES_PER_VECTOR_128_C64 and chunk == TRAFFIC_CHUNK else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -970,7 +973,8 @@ def main():
                      # DRAM bytes the pass chain moves (ncu) over the same launch time
                      "traffic_gbs": traffic / (per_launch_ms / 1e3) / 1e9 if traffic else None,
                      "traffic_frac": traffic / (per_launch_ms / 1e3) / 1e9 / peak if traffic else None,
-                     "kernel": f"pcx_apply pass chain ({passes} pass kernels per chunk of vectors)",
+                     "kernel": f"pcx_apply pass chain ({passes} pass kernels per chunk of vectors"
+                               + (", kernel variants x %d z %d)" % pcx.pcx_get_apply_variant(ctx) if passes == 3 else ")"),
                      "peak_kind": peak_kind + " (burst HBM copy)",
                      "algorithmic_bytes_per_launch": abytes},
         "e2e": e2e,
