@@ -110,7 +110,7 @@ void pcx_destroy(pcx_ctx* c) {
       if (ev) cudaEventDestroy(ev);
   void* ptrs[] = {c->dev.lam64, c->dev.lam32, c->dev.tw64,  c->dev.tw32, c->dev.m64,  c->dev.m32,
                   c->dev.mid,   c->dev.mtab64, c->dev.mtab32, c->scratch, c->stage_x, c->stage_y, c->ktab,
-                  c->dev.mid3};
+                  c->dev.mid3, c->dev.mtab12};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;

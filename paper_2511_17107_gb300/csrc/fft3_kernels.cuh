@@ -181,6 +181,45 @@ __device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams&
   }
 }
 
+// Where pass B reads its twiddles and its per-material table from.  Pass B
+// waits on the queue of shared-memory instructions, and each cell costs five
+// loads of material entries; global loads of the small, L1-resident material
+// table go through the separate load/store queue instead (PCX_ZB_GTAB = 1,
+// FP32, the 16-byte records of DeviceTables::mtab12: 9,554 -> 9,781
+// vector-applies/s at 128^3).  Twiddles from the global table
+// (PCX_ZB_GTW = 1) were slower (9,249): each twiddle feeds a product at
+// once, and the L1 latency sits on that path.
+#ifndef PCX_ZB_GTW
+#define PCX_ZB_GTW 0
+#endif
+#ifndef PCX_ZB_GTAB
+#define PCX_ZB_GTAB 1
+#endif
+
+template <bool G>
+__device__ __forceinline__ cx<float> ld_tab(const cx<float>* p) {
+  if constexpr (G) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return mk(v.x, v.y);
+  } else {
+    return *p;
+  }
+}
+template <bool G>
+__device__ __forceinline__ cx<double> ld_tab(const cx<double>* p) {
+  if constexpr (G) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return mk(v.x, v.y);
+  } else {
+    return *p;
+  }
+}
+template <bool G, typename V>
+__device__ __forceinline__ V ld_tab(const V* p) {
+  if constexpr (G) return __ldg(p);
+  else return *p;
+}
+
 // The three steps of pass B on one z tile, shared by the one-tile-per-CTA
 // kernel and the warp-specialised persistent one.  tile = k1 (N / TPX) + xr;
 // pencil t = k2 TPX + q holds tile column xo = zcol_of(q) of real row
@@ -193,6 +232,8 @@ struct ZTile {
   static constexpr int TP = C::TP, RA = C3::RA, RB = C3::RB, TPX = C3::TPX;
   static constexpr int N2 = N * N, N3 = N2 * N;
   static constexpr int ITEMS = 3 * N * (TPX / 2);   // y-DFT items (two x columns each)
+  static constexpr bool GTW = PCX_ZB_GTW != 0;
+  static constexpr bool GTAB = PCX_ZB_GTAB != 0 && sizeof(T) == 4;
 
   // RB-point inverse y DFT of rows RB k1 + n2 of the tile's columns into
   // the shared tile s, by NTHR threads (tid < NTHR): items tid + it NTHR
@@ -237,7 +278,7 @@ struct ZTile {
       cx<T>* op = out + (size_t)c * N3 + z * N2 + (RB * k1) * N + x0 + 2 * xp;
 #pragma unroll
       for (int m1 = 0; m1 < RB; ++m1) {
-        const cx<T> wt = tw[k1 * m1];
+        const cx<T> wt = ld_tab<GTW>(tw + k1 * m1);
         st2(op + m1 * N, r0[m1] * wt, r1[m1] * wt);
       }
     }
@@ -275,7 +316,7 @@ struct ZTile {
       }
 #pragma unroll
       for (int r = 1; r < R1; ++r) {
-        cx<T> wt = tw[r * j];   // inverse: e^{+2 pi i r j / N}
+        cx<T> wt = ld_tab<GTW>(tw + r * j);   // inverse: e^{+2 pi i r j / N}
         wt.y = -wt.y;
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * wt;
@@ -289,13 +330,13 @@ struct ZTile {
         cx<T> o12, o13, o23;
         if (tid3) {
           const uchar4 id = tid3[n * TP + t];
-          d1 = mtab[12 * id.x];
-          d2 = mtab[12 * id.y + 1];
-          d3 = mtab[12 * id.z + 2];
+          d1 = ld_tab<GTAB>(mtab + 12 * id.x);
+          d2 = ld_tab<GTAB>(mtab + 12 * id.y + 1);
+          d3 = ld_tab<GTAB>(mtab + 12 * id.z + 2);
           const T* o = mtab + 12 * id.w;
           if constexpr (sizeof(T) == 4) {
-            const float4 q = *reinterpret_cast<const float4*>(o + 4);
-            const float2 q2 = *reinterpret_cast<const float2*>(o + 8);
+            const float4 q = ld_tab<GTAB>(reinterpret_cast<const float4*>(o + 4));
+            const float2 q2 = ld_tab<GTAB>(reinterpret_cast<const float2*>(o + 8));
             o12 = mk(q.x, q.y);
             o13 = mk(q.z, q.w);
             o23 = mk(q2.x, q2.y);
@@ -364,7 +405,7 @@ struct ZTile {
       const int w = threadIdx.x + i * C::THREADS;
       const int t = w % TP, jj = (w / TP) % R1, c = w / (TP * R1);
 #pragma unroll
-      for (int q = 1; q < R0; ++q) v[i][q] = v[i][q] * tw[q * jj];
+      for (int q = 1; q < R0; ++q) v[i][q] = v[i][q] * ld_tab<GTW>(tw + q * jj);
       dft<R0, -1>(v[i]);
       cx<T>* sp = s + TL::sidx(c, t, jj);
 #pragma unroll
@@ -580,13 +621,15 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
     using ZT = ZTile<T, N, OP>;
     constexpr int TPX = C3::TPX;
     const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
-    if (a.mid) ZT::stage_mtab(mtab, a.mtab, a.n_mat, threadIdx.x, C::THREADS);
+    if (a.mid && !ZT::GTAB) ZT::stage_mtab(mtab, a.mtab, a.n_mat, threadIdx.x, C::THREADS);
+    const T* mt = ZT::GTAB ? static_cast<const T*>(a.mtab12) : mtab;
+    const cx<T>* twz = ZT::GTW ? gtw : tw;
     ZT::template load<C::THREADS>(s, in, k1, x0, threadIdx.x);
     __syncthreads();   // the tile, the twiddles and the material table
     const uchar4* mid3 = static_cast<const uchar4*>(a.mid3);
-    ZT::template transform<CtaSync>(s, tw, mtab, mid3 ? mid3 + (size_t)tile * TP * N : nullptr,
+    ZT::template transform<CtaSync>(s, twz, mt, mid3 ? mid3 + (size_t)tile * TP * N : nullptr,
                                     static_cast<const T*>(a.M), k1, x0);
-    ZT::template store<C::THREADS>(s, tw, out, k1, x0, threadIdx.x);
+    ZT::template store<C::THREADS>(s, twz, out, k1, x0, threadIdx.x);
   }
 }
 
@@ -629,7 +672,9 @@ __global__ void __launch_bounds__(ZWS_THREADS, 1) pass3z_ws_kernel(PassArgs a, i
   T* mtab = reinterpret_cast<T*>(tw + N);   // 16-byte aligned: 3 CS and N are even
   const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
   for (int i = threadIdx.x; i < N; i += ZWS_THREADS) tw[i] = gtw[i];
-  if (a.mid) ZT::stage_mtab(mtab, a.mtab, a.n_mat, threadIdx.x, ZWS_THREADS);
+  if (a.mid && !ZT::GTAB) ZT::stage_mtab(mtab, a.mtab, a.n_mat, threadIdx.x, ZWS_THREADS);
+  const T* mt = ZT::GTAB ? static_cast<const T*>(a.mtab12) : mtab;
+  const cx<T>* twz = ZT::GTW ? gtw : tw;
   __syncthreads();
   const uchar4* mid3 = static_cast<const uchar4*>(a.mid3);
   if (threadIdx.x < CT) {
@@ -641,7 +686,7 @@ __global__ void __launch_bounds__(ZWS_THREADS, 1) pass3z_ws_kernel(PassArgs a, i
       const int tile = g % ZT_N;
       const int k1 = tile / (N / TPX), x0 = (tile % (N / TPX)) * TPX;
       zb_sync(ZB_FULL + b, ZWS_THREADS);
-      ZT::template transform<GroupSync<ZB_T, CT>>(b ? buf1 : buf0, tw, mtab,
+      ZT::template transform<GroupSync<ZB_T, CT>>(b ? buf1 : buf0, twz, mt,
                                                   mid3 ? mid3 + (size_t)tile * TP * N : nullptr, M, k1, x0);
       zb_arrive(ZB_EMPTY + b, ZWS_THREADS);
     }
@@ -665,7 +710,7 @@ __global__ void __launch_bounds__(ZWS_THREADS, 1) pass3z_ws_kernel(PassArgs a, i
         const int tile = (int)(gs % ZT_N);
         const size_t v = (size_t)(gs / ZT_N);
         zb_sync(ZB_EMPTY + b, ZWS_THREADS);
-        ZT::template store<IOT>(s, tw, out + v * 3 * N3, tile / (N / TPX), (tile % (N / TPX)) * TPX, tid);
+        ZT::template store<IOT>(s, twz, out + v * 3 * N3, tile / (N / TPX), (tile % (N / TPX)) * TPX, tid);
       }
       if (ld) {
         if (st) zb_sync(ZB_IO, IOT);   // every read of the buffer done before it is refilled

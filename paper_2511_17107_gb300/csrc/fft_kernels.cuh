@@ -107,6 +107,7 @@ struct PassArgs {
   const void* mid;     // [N^3] uchar4 material ids (E1, E2, E3, V)
   const void* mid3;    // the same ids in the order of the three-pass z tiles (or null)
   const void* mtab;    // [n_mat][9] block entries per material
+  const void* mtab12;  // [n_mat][12] the same in 16-byte records (FP32; three-pass z tiles)
   int n_mat;
   KParams kp;
   // k-batched sweeps: vector v of the launch (v_base + v overall) uses
@@ -895,6 +896,7 @@ cudaError_t run_apply_n(const pcx_ctx* c, const KParams& kp, const void* X, void
   a.mid = c->dev.mid;
   a.mid3 = nullptr;
   a.mtab = dbl ? c->dev.mtab64 : c->dev.mtab32;
+  a.mtab12 = dbl ? nullptr : c->dev.mtab12;
   a.n_mat = n_mat;
   a.kp = kp;
   a.kps = kps;

@@ -50,6 +50,7 @@ struct DeviceTables {
   void* mid = nullptr;     // [N^3] uchar4
   void* mtab64 = nullptr;  // [n_mat][9] double: e11 e22 e33 re12 im12 re13 im13 re23 im23
   void* mtab32 = nullptr;  // [n_mat][9] float
+  void* mtab12 = nullptr;  // [n_mat][12] float: e11 e22 e33 0 re12 im12 re13 im13 re23 im23 0 0 (16-byte records)
   int n_mat = 0;
   void* mid3 = nullptr;    // [N^3] uchar4: mid in the order of the three-pass z tiles (N = 32, 64, 128)
   // M as dense blocks (caller-supplied cell blocks, or more than 255 materials)

@@ -531,9 +531,15 @@ pcx_status setup_context(const pcx_setup_desc* d, pcx_ctx* c) {
       for (int f = 0; f < 9; ++f) t64[9 * mt + f] = row[f];
     }
     std::vector<float> t32(t64.begin(), t64.end());
+    // the same entries in 16-byte aligned records of 12 (the three-pass z
+    // tiles read a cell's off-diagonals with one 16-byte and one 8-byte load)
+    std::vector<float> t12(12 * (size_t)d->n_mat, 0.f);
+    for (int mt = 0; mt < d->n_mat; ++mt)
+      for (int f = 0; f < 9; ++f) t12[12 * mt + (f < 3 ? f : f + 1)] = t32[9 * mt + f];
     c->dev.n_mat = d->n_mat;
     if ((e = upload(&c->dev.mid, mid)) != cudaSuccess || (e = upload(&c->dev.mtab64, t64)) != cudaSuccess ||
-        (e = upload(&c->dev.mtab32, t32)) != cudaSuccess || (e = build_pass3_ids(c)) != cudaSuccess)
+        (e = upload(&c->dev.mtab32, t32)) != cudaSuccess || (e = upload(&c->dev.mtab12, t12)) != cudaSuccess ||
+        (e = build_pass3_ids(c)) != cudaSuccess)
       goto cuda_error;
   } else {
     std::vector<double> m64(9 * n3);
