@@ -50,7 +50,7 @@ METRIC = "compensated-operator applies/s at 128^3"
 # structure and, for the three-pass chain, pass B's kernel variant (one tile
 # per CTA, or the warp-specialised one); the x-pass variants move the same
 # bytes.  Used only when the run uses that chunk, structure and variant.
-TRAFFIC_BYTES_PER_VECTOR_128_C64 = {(5, None): 8.8128e9 / 16, (3, 0): 5.346921e9 / 16, (3, 1): 5.310127e9 / 16}
+TRAFFIC_BYTES_PER_VECTOR_128_C64 = {(5, None): 8.8128e9 / 16, (3, 0): 5.321861e9 / 16, (3, 1): 5.304722e9 / 16}
 TRAFFIC_CHUNK = 16
 UNIT = "vector-applies/s"
 
@@ -832,6 +832,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="vectors per launch chunk (implies --no-tune)")
     ap.add_argument("--apply-path", default="auto", choices=["auto", "five", "three"],
                     help="pass structure of the apply (pcx_set_apply_path)")
+    ap.add_argument("--apply-variant", default="",
+                    help="X,Z: the three-pass chain's kernel variants (pcx_set_apply_variant; overrides the tuner's)")
     ap.add_argument("--blockops", action="store_true",
                     help="print timings of the eigensolver's Gram products and combinations instead")
     ap.add_argument("--sizes", action="store_true",
@@ -890,6 +892,9 @@ def main():
     tune = None if args.no_tune else pcx.pcx_autotune(ctx, prec, block, stream=stream)
     if args.apply_path != "auto":   # an explicit pass structure overrides the tuner's choice
         pcx.pcx_set_apply_path(ctx, {"five": pcx.PCX_APPLY_FIVE_PASS, "three": pcx.PCX_APPLY_THREE_PASS}[args.apply_path])
+    if args.apply_variant:
+        xv, zv = (int(t) for t in args.apply_variant.split(","))
+        pcx.pcx_set_apply_variant(ctx, xv, zv)
     x = wl.random_block(block, n, seed=20251117 + rank).astype(cdt)
     X = torch.empty((nk, block, 3, n, n, n), dtype=torch.complex64 if es == 8 else torch.complex128, device="cuda")
     X.copy_(torch.from_numpy(x).cuda().unsqueeze(0).expand_as(X))
