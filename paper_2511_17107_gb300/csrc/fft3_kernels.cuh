@@ -31,6 +31,8 @@
 // three run in place on the output buffer.
 #pragma once
 
+#include <atomic>
+#include <cstdint>
 #include <type_traits>
 
 #include "fft_kernels.cuh"
@@ -123,7 +125,9 @@ __host__ __device__ constexpr int pass3_threads() {
 // shapes themselves are fixed by the geometry above, which the pass-B id
 // table depends on).  x tiles (passes A and C): PF rows whose global loads
 // are issued together before their arithmetic, and the CTAs per SM the
-// registers are sized for (MINB).  z tiles (pass B): one tile per CTA (0) or
+// registers are sized for (MINB); variant 3 is the persistent kernel that
+// stages the next tile's rows with asynchronous copies
+// (pass3x_async_kernel).  z tiles (pass B): one tile per CTA (0) or
 // the warp-specialised persistent kernel (1).
 template <int XV>
 struct XVar;
@@ -180,6 +184,230 @@ __device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams&
     }
   }
 }
+
+// The steps of passes A and C on one x tile (16 rows of N points at
+// N = 128), shared by the one-tile-per-CTA kernel and the persistent one
+// that stages the next tile's rows with asynchronous copies.  The rows'
+// input comes either straight from global memory or from such a staged
+// copy raw[c][t][n] in shared memory; the arithmetic and its order are the
+// same in both.
+template <typename T, int N, int OP>
+struct XTile {
+  using C3 = Cfg3<T, N>;
+  using C = typename C3::C;
+  using TL = Tile<T, N, 0, C>;
+  static constexpr int TP = C::TP, RA = C3::RA, RB = C3::RB, G = C3::G;
+  static constexpr int N2 = N * N, N3 = N2 * N;
+  static constexpr bool PRE = OP == OP_PRE || OP == OP_PRE_T0;
+  static constexpr bool T0 = OP == OP_PRE_T0 || OP == OP_POST_T0;
+  // THREADS is a multiple of N, so in the row sweeps every thread keeps one
+  // point n and walks the rows t = t0, t0 + THREADS / N, ...
+  static_assert(C::THREADS % N == 0, "x tiles: whole rows per thread sweep");
+  static constexpr int TSTEP = C::THREADS / N;
+  static constexpr int NI = (TP + TSTEP - 1) / TSTEP;
+  static constexpr int CH = N * (int)sizeof(cx<T>) / 16;   // 16-byte pieces per row
+  static constexpr int RAW = 3 * TP * N;                   // entries of a staged tile
+
+  // global offset (within one vector, component 0) of the row the staged
+  // row t holds: pass A row t of the tile; pass C the input row
+  // RB k1 + m1 of row group gi, t = gi RA + k1
+  static __device__ __forceinline__ int raw_row(int tile, int t) {
+    int z, y, j;
+    if constexpr (PRE) {
+      x_row<T, N>(tile, t, z, y, j);
+      return z * N2 + y * N;
+    } else {
+      x_row<T, N>(tile, (t / RA) * RA, z, y, j);
+      return z * N2 + (j + RB * (t % RA)) * N;
+    }
+  }
+
+  // asynchronous copies of the tile's 3 TP input rows into raw (16-byte
+  // pieces; the vector's base must be 16-byte aligned, which the launcher
+  // checks); completion: cp.async.wait_all by every thread, then a barrier
+  static __device__ __forceinline__ void stage_rows(cx<T>* raw, const cx<T>* in, int tile) {
+    static_assert(CH * 16 == N * (int)sizeof(cx<T>), "whole 16-byte pieces per row");
+    for (int q = threadIdx.x; q < 3 * TP * CH; q += C::THREADS) {
+      const int ch = q % CH, t = (q / CH) % TP, c = q / (CH * TP);
+      const char* src = reinterpret_cast<const char*>(in + (size_t)c * N3 + raw_row(tile, t)) + 16 * ch;
+      const unsigned dst =
+          (unsigned)__cvta_generic_to_shared(reinterpret_cast<char*>(raw + (size_t)(c * TP + t) * N) + 16 * ch);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  static __device__ __forceinline__ void wait_rows() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+  // Pass A, first step: u = -conj(kappa) x x per mode into the tile and
+  // gamma_p kappa.x to the scratch sb (T0: u / |k|^2 and
+  // kappa.x / (gamma_p |k|^4)); x from global memory (FROM_RAW false, PF
+  // rows' loads in flight together) or from the staged rows.  The kappa
+  // tables must be visible.
+  template <int PF, bool FROM_RAW>
+  static __device__ __forceinline__ void pre_rows(cx<T>* s, const cx<T>* in, const cx<T>* raw, cx<T>* sb,
+                                                  const cx<T>* ka, const cx<T>* kb, const KParams& kp, int tile) {
+    const T gam = (T)kp.gamma;
+    const T igam = (T)(1.0 / kp.gamma);
+    const int n = threadIdx.x % N, t0 = threadIdx.x / N;
+    cx<T> kan[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
+    constexpr int PFE = PF < NI ? PF : NI;
+#pragma unroll
+    for (int i0 = 0; i0 < NI; i0 += PFE) {
+      // the rows of this batch: their loads in flight together
+      cx<T> xv[PFE][3];
+      int gv[PFE];
+#pragma unroll
+      for (int u = 0; u < PFE; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u < NI && t < TP) {
+          int z, y, j;
+          x_row<T, N>(tile, t, z, y, j);
+          gv[u] = z * N2 + y * N + n;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if constexpr (FROM_RAW) xv[u][c] = raw[(c * TP + t) * N + n];
+            else xv[u][c] = in[c * N3 + gv[u]];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PFE; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u >= NI || t >= TP) break;
+        const int g = gv[u];
+        const cx<T> x0 = xv[u][0], x1 = xv[u][1], x2 = xv[u][2];
+        cx<T> kap[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
+        T su = (T)1, ss = gam;
+        if constexpr (T0) {
+          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+          su = k2 > (T)0 ? (T)1 / k2 : (T)0;
+          ss = su * su * igam * fftk::penalty_inv_weight(kp, k2);
+        } else if (kp.per_mode) {
+          ss = gam * fftk::penalty_weight(kp, norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]));
+        }
+        sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), ss);
+        const cx<T> zr = mk((T)0, (T)0);
+        cx<T> u0 = cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, zr), (T)-1));
+        cx<T> u1 = cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, zr), (T)-1));
+        cx<T> u2 = cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, zr), (T)-1));
+        if constexpr (T0) {
+          u0 = scale(u0, su);
+          u1 = scale(u1, su);
+          u2 = scale(u2, su);
+        }
+        s[TL::sidx(0, t, n)] = u0;
+        s[TL::sidx(1, t, n)] = u1;
+        s[TL::sidx(2, t, n)] = u2;
+      }
+    }
+  }
+
+  // Pass A, last step: RA-point inverse y DFT over the rows of each group,
+  // twiddle e^{+2 pi i n2 k1 / N}, stored to row RB k1 + n2
+  static __device__ __forceinline__ void pre_ydft(const cx<T>* s, const cx<T>* tw, cx<T>* out, int tile) {
+#pragma unroll
+    for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
+      const int w = threadIdx.x + it * C::THREADS;
+      const int n = w % N, gi = (w / N) % G, c = w / (N * G);
+      int z, y, n2;
+      x_row<T, N>(tile, gi * RA, z, y, n2);
+      cx<T> r[RA];
+#pragma unroll
+      for (int i = 0; i < RA; ++i) r[i] = s[TL::sidx(c, gi * RA + i, n)];
+      dft<RA, +1>(r);
+      cx<T>* o = out + (size_t)c * N3 + z * N2 + n2 * N + n;
+#pragma unroll
+      for (int k1 = 0; k1 < RA; ++k1) {
+        cx<T> wt = tw[n2 * k1];
+        wt.y = -wt.y;
+        o[(RB * k1) * N] = r[k1] * wt;
+      }
+    }
+  }
+
+  // Pass C, first step: RA-point forward y DFT, input rows RB k1 + m1 ->
+  // Fourier rows m1 + RB m2 of the tile (from global memory, or from the
+  // staged rows raw[c][gi RA + k1][n])
+  template <bool FROM_RAW>
+  static __device__ __forceinline__ void post_ydft(cx<T>* s, const cx<T>* in, const cx<T>* raw, int tile) {
+#pragma unroll
+    for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
+      const int w = threadIdx.x + it * C::THREADS;
+      const int n = w % N, gi = (w / N) % G, c = w / (N * G);
+      cx<T> r[RA];
+      if constexpr (FROM_RAW) {
+        const cx<T>* rp = raw + (size_t)(c * TP + gi * RA) * N + n;
+#pragma unroll
+        for (int k1 = 0; k1 < RA; ++k1) r[k1] = rp[k1 * N];
+      } else {
+        int z, y, m1;
+        x_row<T, N>(tile, gi * RA, z, y, m1);
+        const cx<T>* ip = in + (size_t)c * N3 + z * N2 + m1 * N + n;
+#pragma unroll
+        for (int k1 = 0; k1 < RA; ++k1) r[k1] = ip[(RB * k1) * N];
+      }
+      dft<RA, -1>(r);
+#pragma unroll
+      for (int m2 = 0; m2 < RA; ++m2) s[TL::sidx(c, gi * RA + m2, n)] = r[m2];
+    }
+  }
+
+  // Pass C, last step: C w + gamma conj(kappa) (kappa . x) per mode (T0:
+  // (C w) / |k|^2 + conj(kappa) s), the scratch read straight from global
+  // memory with PF rows' loads in flight together; one point n per thread
+  template <int PF>
+  static __device__ __forceinline__ void post_rows(const cx<T>* s, const cx<T>* sb, cx<T>* out, const cx<T>* ka,
+                                                   const cx<T>* kb, int tile) {
+    const int n = threadIdx.x % N, t0 = threadIdx.x / N;
+    cx<T> kan[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
+    constexpr int PFE = PF < NI ? PF : NI;
+#pragma unroll
+    for (int i0 = 0; i0 < NI; i0 += PFE) {
+      cx<T> skv[PFE];
+      int gv[PFE];
+#pragma unroll
+      for (int u = 0; u < PFE; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u < NI && t < TP) {
+          int z, y, j;
+          x_row<T, N>(tile, t, z, y, j);
+          gv[u] = z * N2 + y * N + n;
+          skv[u] = sb[gv[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PFE; ++u) {
+        const int t = t0 + (i0 + u) * TSTEP;
+        if (i0 + u >= NI || t >= TP) break;
+        const int g = gv[u];
+        const cx<T> sk = skv[u];
+        cx<T> kap[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
+        const cx<T> w0 = s[TL::sidx(0, t, n)], w1 = s[TL::sidx(1, t, n)], w2 = s[TL::sidx(2, t, n)];
+        cx<T> c0 = cfma(kap[1], w2, scale(kap[2] * w1, (T)-1));
+        cx<T> c1 = cfma(kap[2], w0, scale(kap[0] * w2, (T)-1));
+        cx<T> c2 = cfma(kap[0], w1, scale(kap[1] * w0, (T)-1));
+        if constexpr (T0) {
+          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
+          const T su = k2 > (T)0 ? (T)1 / k2 : (T)0;
+          c0 = scale(c0, su);
+          c1 = scale(c1, su);
+          c2 = scale(c2, su);
+        }
+        out[g] = cfma_conj(kap[0], sk, c0);
+        out[N3 + g] = cfma_conj(kap[1], sk, c1);
+        out[2 * N3 + g] = cfma_conj(kap[2], sk, c2);
+      }
+    }
+  }
+};
 
 // Where pass B reads its twiddles and its per-material table from.  Pass B
 // waits on the queue of shared-memory instructions, and each cell costs five
@@ -453,168 +681,23 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
 
   if constexpr (!ZP) {
     // ================= x tiles: pass A (PRE) and pass C (POST) =================
+    using XT = XTile<T, N, OP>;
     KParams kp = a.kp;
     if (a.kps) kp = a.kps[(a.v_base + (int)v) / a.vec_per_k];
     x_kappa_tables<T, N>(static_cast<const cx<T>*>(a.lam), kp, tile, ka, kb);
-    constexpr bool PRE = OP == OP_PRE || OP == OP_PRE_T0;
-    constexpr bool T0 = OP == OP_PRE_T0 || OP == OP_POST_T0;
-    if constexpr (PRE) {
+    if constexpr (XT::PRE) {
       cx<T>* sb = static_cast<cx<T>*>(a.sbuf) + v * N3;
-      const T gam = (T)kp.gamma;
-      const T igam = (T)(1.0 / kp.gamma);
-      // u = -conj(kappa) x x per mode and gamma_p kappa.x to the scratch
-      // (T0: u / |k|^2 and kappa.x / (gamma_p |k|^4)), straight from global
-      // memory into the tile.  THREADS is a multiple of N, so every thread
-      // keeps one point n and walks the rows t = t0, t0 + THREADS / N, ...
-      static_assert(C::THREADS % N == 0, "x tiles: whole rows per thread sweep");
-      constexpr int TSTEP = C::THREADS / N;
-      const int n = threadIdx.x % N, t0 = threadIdx.x / N;
       __syncthreads();   // kappa tables
-      cx<T> kan[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
-      constexpr int NI = (TP + TSTEP - 1) / TSTEP;
-      constexpr int PF = XVar<XV>::PF < NI ? XVar<XV>::PF : NI;
-#pragma unroll
-      for (int i0 = 0; i0 < NI; i0 += PF) {
-      // the rows of this batch: their loads in flight together
-      cx<T> xv[PF][3];
-      int gv[PF];
-#pragma unroll
-      for (int u = 0; u < PF; ++u) {
-        const int t = t0 + (i0 + u) * TSTEP;
-        if (i0 + u < NI && t < TP) {
-          int z, y, j;
-          x_row<T, N>(tile, t, z, y, j);
-          gv[u] = z * N2 + y * N + n;
-          xv[u][0] = in[gv[u]];
-          xv[u][1] = in[N3 + gv[u]];
-          xv[u][2] = in[2 * N3 + gv[u]];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < PF; ++u) {
-        const int t = t0 + (i0 + u) * TSTEP;
-        if (i0 + u >= NI || t >= TP) break;
-        const int g = gv[u];
-        const cx<T> x0 = xv[u][0], x1 = xv[u][1], x2 = xv[u][2];
-        cx<T> kap[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
-        T su = (T)1, ss = gam;
-        if constexpr (T0) {
-          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
-          su = k2 > (T)0 ? (T)1 / k2 : (T)0;
-          ss = su * su * igam * fftk::penalty_inv_weight(kp, k2);
-        } else if (kp.per_mode) {
-          ss = gam * fftk::penalty_weight(kp, norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]));
-        }
-        sb[g] = scale(cfma(kap[2], x2, cfma(kap[1], x1, kap[0] * x0)), ss);
-        const cx<T> zr = mk((T)0, (T)0);
-        cx<T> u0 = cfma_conj(kap[2], x1, scale(cfma_conj(kap[1], x2, zr), (T)-1));
-        cx<T> u1 = cfma_conj(kap[0], x2, scale(cfma_conj(kap[2], x0, zr), (T)-1));
-        cx<T> u2 = cfma_conj(kap[1], x0, scale(cfma_conj(kap[0], x1, zr), (T)-1));
-        if constexpr (T0) {
-          u0 = scale(u0, su);
-          u1 = scale(u1, su);
-          u2 = scale(u2, su);
-        }
-        s[TL::sidx(0, t, n)] = u0;
-        s[TL::sidx(1, t, n)] = u1;
-        s[TL::sidx(2, t, n)] = u2;
-      }
-      }
+      XT::template pre_rows<XVar<XV>::PF, false>(s, in, nullptr, sb, ka, kb, kp, tile);
       __syncthreads();
       fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
-      // RA-point inverse y DFT over the rows of each group, twiddle
-      // e^{+2 pi i n2 k1 / N}, store to row RB k1 + n2
-#pragma unroll
-      for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
-        const int w = threadIdx.x + it * C::THREADS;
-        const int n = w % N, gi = (w / N) % C3::G, c = w / (N * C3::G);
-        int z, y, n2;
-        x_row<T, N>(tile, gi * RA, z, y, n2);
-        cx<T> r[RA];
-#pragma unroll
-        for (int i = 0; i < RA; ++i) r[i] = s[TL::sidx(c, gi * RA + i, n)];
-        dft<RA, +1>(r);
-        cx<T>* o = out + (size_t)c * N3 + z * N2 + n2 * N + n;
-#pragma unroll
-        for (int k1 = 0; k1 < RA; ++k1) {
-          cx<T> wt = tw[n2 * k1];
-          wt.y = -wt.y;
-          o[(RB * k1) * N] = r[k1] * wt;
-        }
-      }
+      XT::pre_ydft(s, tw, out, tile);
     } else {
-      // pass C
       const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
-      // RA-point forward y DFT: rows RB k1 + m1 -> Fourier rows m1 + RB m2
-#pragma unroll
-      for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
-        const int w = threadIdx.x + it * C::THREADS;
-        const int n = w % N, gi = (w / N) % C3::G, c = w / (N * C3::G);
-        int z, y, m1;
-        x_row<T, N>(tile, gi * RA, z, y, m1);
-        const cx<T>* ip = in + (size_t)c * N3 + z * N2 + m1 * N + n;
-        cx<T> r[RA];
-#pragma unroll
-        for (int k1 = 0; k1 < RA; ++k1) r[k1] = ip[(RB * k1) * N];
-        dft<RA, -1>(r);
-#pragma unroll
-        for (int m2 = 0; m2 < RA; ++m2) s[TL::sidx(c, gi * RA + m2, n)] = r[m2];
-      }
+      XT::template post_ydft<false>(s, in, nullptr, tile);
       __syncthreads();
       fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
-      // C w + gamma conj(kappa) (kappa . x) per mode, the scratch read
-      // straight from global memory; one point n per thread, as in pass A
-      static_assert(C::THREADS % N == 0, "x tiles: whole rows per thread sweep");
-      constexpr int TSTEP = C::THREADS / N;
-      const int n = threadIdx.x % N, t0 = threadIdx.x / N;
-      cx<T> kan[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) kan[i] = ka[i * N + n];
-      constexpr int NI = (TP + TSTEP - 1) / TSTEP;
-      constexpr int PF = XVar<XV>::PF < NI ? XVar<XV>::PF : NI;
-#pragma unroll
-      for (int i0 = 0; i0 < NI; i0 += PF) {
-      cx<T> skv[PF];
-      int gv[PF];
-#pragma unroll
-      for (int u = 0; u < PF; ++u) {
-        const int t = t0 + (i0 + u) * TSTEP;
-        if (i0 + u < NI && t < TP) {
-          int z, y, j;
-          x_row<T, N>(tile, t, z, y, j);
-          gv[u] = z * N2 + y * N + n;
-          skv[u] = sb[gv[u]];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < PF; ++u) {
-        const int t = t0 + (i0 + u) * TSTEP;
-        if (i0 + u >= NI || t >= TP) break;
-        const int g = gv[u];
-        const cx<T> sk = skv[u];
-        cx<T> kap[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) kap[i] = kan[i] + kb[3 * t + i];
-        const cx<T> w0 = s[TL::sidx(0, t, n)], w1 = s[TL::sidx(1, t, n)], w2 = s[TL::sidx(2, t, n)];
-        cx<T> c0 = cfma(kap[1], w2, scale(kap[2] * w1, (T)-1));
-        cx<T> c1 = cfma(kap[2], w0, scale(kap[0] * w2, (T)-1));
-        cx<T> c2 = cfma(kap[0], w1, scale(kap[1] * w0, (T)-1));
-        if constexpr (T0) {
-          const T k2 = norm2(kap[0]) + norm2(kap[1]) + norm2(kap[2]);
-          const T su = k2 > (T)0 ? (T)1 / k2 : (T)0;
-          c0 = scale(c0, su);
-          c1 = scale(c1, su);
-          c2 = scale(c2, su);
-        }
-        out[g] = cfma_conj(kap[0], sk, c0);
-        out[N3 + g] = cfma_conj(kap[1], sk, c1);
-        out[2 * N3 + g] = cfma_conj(kap[2], sk, c2);
-      }
-      }
+      XT::template post_rows<XVar<XV>::PF>(s, sb, out, ka, kb, tile);
     }
   } else {
     // ================= z tiles: pass B =================
@@ -631,6 +714,73 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
                                     static_cast<const T*>(a.M), k1, x0);
     ZT::template store<C::THREADS>(s, twz, out, k1, x0, threadIdx.x);
   }
+}
+
+// Passes A and C as a persistent kernel: CTA b walks x tiles b, b +
+// gridDim.x, ... and, once a tile's input rows have been consumed, copies
+// the next tile's rows into shared memory with asynchronous copies
+// (cp.async, 16-byte pieces), so that they are in flight during the x FFT
+// and the y DFT of the current tile.  A tile-per-CTA kernel issues its
+// global loads only in its first step.  The arithmetic is XTile's, as in
+// pass3_kernel.  Shared memory: the tile, twiddles, kappa tables and one
+// staged tile of rows (108 KB at N = 128: two CTAs per SM).
+template <typename T, int N>
+__host__ __device__ constexpr size_t xasync_raw_offset() {
+  using C = typename Cfg3<T, N>::C;
+  return (((size_t)3 * C::CS + 4 * N + 3 * C::TP) + 1) & ~(size_t)1;   // entries, 16-byte aligned
+}
+template <typename T, int N>
+__host__ __device__ constexpr size_t xasync_smem() {
+  return (xasync_raw_offset<T, N>() + (size_t)XTile<T, N, OP_PRE>::RAW) * sizeof(cx<T>);
+}
+
+template <typename T, int N, int OP>
+__global__ void __launch_bounds__(Cfg3<T, N>::THREADS, 2) pass3x_async_kernel(PassArgs a, int total_tiles) {
+  using C3 = Cfg3<T, N>;
+  using C = typename C3::C;
+  using XT = XTile<T, N, OP>;
+  static_assert(!is_z_op<OP>(), "x tiles only");
+  constexpr int N3 = N * N * N, TILES = C3::TILES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* tw = s + 3 * C::CS;
+  cx<T>* ka = tw + N;       // [3][N]
+  cx<T>* kb = ka + 3 * N;   // [TP][3]
+  cx<T>* raw = s + xasync_raw_offset<T, N>();
+  const cx<T>* gtw = static_cast<const cx<T>*>(a.tw);
+  for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = gtw[i];
+  const cx<T>* gin = static_cast<const cx<T>*>(a.in);
+  cx<T>* gout = static_cast<cx<T>*>(a.out);
+  const int g0 = blockIdx.x;
+  if (g0 < total_tiles) XT::stage_rows(raw, gin + (size_t)(g0 / TILES) * 3 * N3, g0 % TILES);
+  for (int g = g0; g < total_tiles; g += gridDim.x) {
+    const size_t v = (size_t)(g / TILES);
+    const int tile = g % TILES;
+    cx<T>* out = gout + v * 3 * N3;
+    KParams kp = a.kp;
+    if (a.kps) kp = a.kps[(a.v_base + (int)v) / a.vec_per_k];
+    // the previous tile's last readers of ka, kb and s passed the barrier
+    // at the end of its iteration
+    x_kappa_tables<T, N>(static_cast<const cx<T>*>(a.lam), kp, tile, ka, kb);
+    XT::wait_rows();
+    __syncthreads();   // this tile's rows, the kappa tables (and the twiddles)
+    const int gn = g + (int)gridDim.x;
+    if constexpr (XT::PRE) {
+      XT::template pre_rows<1, true>(s, nullptr, raw, static_cast<cx<T>*>(a.sbuf) + v * N3, ka, kb, kp, tile);
+      __syncthreads();   // the rows are consumed; the tile is complete
+      if (gn < total_tiles) XT::stage_rows(raw, gin + (size_t)(gn / TILES) * 3 * N3, gn % TILES);
+      fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
+      XT::pre_ydft(s, tw, out, tile);
+    } else {
+      XT::template post_ydft<true>(s, nullptr, raw, tile);
+      __syncthreads();
+      if (gn < total_tiles) XT::stage_rows(raw, gin + (size_t)(gn / TILES) * 3 * N3, gn % TILES);
+      fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
+      XT::template post_rows<3>(s, static_cast<const cx<T>*>(a.sbuf) + v * N3, out, ka, kb, tile);
+    }
+    __syncthreads();   // s, ka and kb are rewritten by the next tile
+  }
+  XT::wait_rows();
 }
 
 // Pass B as a persistent warp-specialised kernel: one CTA per SM walks z
@@ -779,8 +929,39 @@ cudaError_t launch_pass3_ws(const PassArgs& a, int nv, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename T, int N, int OP>
+cudaError_t launch_pass3_async(const PassArgs& a, int nv, cudaStream_t st) {
+  using C3 = Cfg3<T, N>;
+  const size_t smem = xasync_smem<T, N>();
+  const long long tiles = (long long)nv * C3::TILES;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (tiles == 0) return cudaSuccess;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  auto kern = pass3x_async_kernel<T, N, OP>;
+  if ((e = raise_dyn_smem(reinterpret_cast<const void*>(kern), smem)) != cudaSuccess) return e;
+  // resident CTAs per SM, queried once per device (not inside a capture)
+  static std::atomic<int> resident[64];
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  per_sm = resident[dev].load();
+  if (per_sm == 0) {
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C3::THREADS, smem)) != cudaSuccess)
+      return e;
+    if (per_sm < 1) per_sm = 1;
+    resident[dev].store(per_sm);
+  }
+  const long long fill = (long long)per_sm * sms;
+  const long long grid = tiles < fill ? tiles : fill;
+  kern<<<(unsigned)grid, C3::THREADS, smem, st>>>(a, (int)tiles);
+  return cudaGetLastError();
+}
+
 // One pass of the three-pass chain over nv vectors; xv / zv pick the kernel
-// variant of the x / z passes (out of range: the build-time default).
+// variant of the x / z passes (out of range: the build-time default).  The
+// asynchronous-copy x kernel (3) needs 16-byte aligned input vectors; other
+// inputs take variant 1.
 template <typename T, int N, int OP>
 cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st, int xv, int zv) {
   if constexpr (is_z_op<OP>()) {
@@ -788,11 +969,14 @@ cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st, int xv, int
     return zv == 1 ? launch_pass3_ws<T, N, OP>(a, nv, st) : launch_pass3_tile<T, N, OP, 0>(a, nv, st);
   } else {
     if (xv < 0 || xv >= X3_VARIANTS) xv = PCX_X3_VARIANT;
+    if (xv == 3 && (reinterpret_cast<uintptr_t>(a.in) & 15) != 0) xv = 1;
     switch (xv) {
       case 0:
         return launch_pass3_tile<T, N, OP, 0>(a, nv, st);
       case 2:
         return launch_pass3_tile<T, N, OP, 2>(a, nv, st);
+      case 3:
+        return launch_pass3_async<T, N, OP>(a, nv, st);
       default:
         return launch_pass3_tile<T, N, OP, 1>(a, nv, st);
     }

@@ -31,7 +31,7 @@ struct KParams {
 // Kernel variants of the three-pass chain (fft3_kernels.cuh): x passes
 // 0..X3_VARIANTS-1, z pass 0..Z3_VARIANTS-1, and the build-time defaults
 // used when neither the caller nor the autotuner chose.
-constexpr int X3_VARIANTS = 3, Z3_VARIANTS = 2;
+constexpr int X3_VARIANTS = 4, Z3_VARIANTS = 2;
 #ifndef PCX_X3_VARIANT
 #define PCX_X3_VARIANT 1
 #endif

@@ -159,7 +159,7 @@ def test_kernel_variants_give_identical_results(pcx, n):
     pcx.pcx_set_apply_chunk(ctx, 2)   # a ragged last chunk of one vector
     X = torch.from_numpy(x).cuda()
     ref = {}
-    for xv in range(3):
+    for xv in range(4):
         for zv in range(2):
             pcx.pcx_set_apply_variant(ctx, xv, zv)
             assert pcx.pcx_get_apply_variant(ctx) == (xv, zv)
@@ -174,7 +174,7 @@ def test_kernel_variants_give_identical_results(pcx, n):
             assert np.array_equal(got[0], ref["y"]) and np.array_equal(got[1], ref["w"]), (xv, zv)
     pcx.pcx_set_apply_variant(ctx, -1, -1)
     assert pcx.pcx_get_apply_variant(ctx) == (1, 0)
-    for bad in ((3, 0), (0, 2), (-2, 0)):
+    for bad in ((4, 0), (0, 2), (-2, 0)):
         with pytest.raises(pcx.PcxError) as e:
             pcx.pcx_set_apply_variant(ctx, *bad)
         assert e.value.status == pcx.PCX_EINVAL
@@ -190,7 +190,7 @@ def test_autotune_picks_the_variants(pcx):
     ctx = pcx.setup_structure(s, n)
     r = pcx.pcx_autotune(ctx, pcx.PCX_FP32, 3, stream=torch.cuda.Stream())
     if r["path"] == pcx.PCX_APPLY_THREE_PASS:
-        assert 0 <= r["x_variant"] < 3 and 0 <= r["z_variant"] < 2
+        assert 0 <= r["x_variant"] < 4 and 0 <= r["z_variant"] < 2
         assert pcx.pcx_get_apply_variant(ctx) == (r["x_variant"], r["z_variant"])
         if not r["from_cache"]:
             assert r["candidates"] >= 6
