@@ -360,15 +360,16 @@ int pcx_get_penalty_form(const pcx_ctx* ctx);
  * schedule differs):
  *   x_variant (passes A and C): 0 -- one row's global loads at a time, three
  *     CTAs per SM; 1 -- three rows' loads issued together, three CTAs per
- *     SM; 2 -- six rows' loads together, two CTAs per SM; 3 -- a
- *     persistent kernel, two CTAs per SM, that copies the next tile's input
- *     rows into shared memory asynchronously (cp.async) while it transforms
- *     the current tile (input vectors not 16-byte aligned run variant 1);
+ *     SM; 2 -- six rows' loads together, two CTAs per SM; 3 -- pass A as
+ *     a persistent kernel, two CTAs per SM, that copies the next tile's
+ *     input rows into shared memory asynchronously (cp.async) while it
+ *     transforms the current tile, pass C as in 1 (input vectors not
+ *     16-byte aligned run variant 1);
  *   z_variant (pass B): 0 -- one z tile per CTA; 1 -- a persistent
  *     warp-specialised kernel, one CTA per SM, in which half the warps
  *     transform one tile buffer while the other half store the previous
  *     tile and load the next one into the second buffer.
- * -1 selects the build's default (x 1, z 0).  pcx_autotune sets both.
+ * -1 selects the build's default (x 3, z 0).  pcx_autotune sets both.
  * Changing them frees the captured apply graphs.  PCX_EINVAL out of range.
  */
 pcx_status pcx_set_apply_variant(pcx_ctx* ctx, int x_variant, int z_variant);

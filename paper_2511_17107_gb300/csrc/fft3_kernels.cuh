@@ -716,7 +716,8 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
   }
 }
 
-// Passes A and C as a persistent kernel: CTA b walks x tiles b, b +
+// Passes A and C as a persistent kernel (x variant 3 runs pass A with it;
+// pass C measured slower this way): CTA b walks x tiles b, b +
 // gridDim.x, ... and, once a tile's input rows have been consumed, copies
 // the next tile's rows into shared memory with asynchronous copies
 // (cp.async, 16-byte pieces), so that they are in flight during the x FFT
@@ -976,7 +977,10 @@ cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st, int xv, int
       case 2:
         return launch_pass3_tile<T, N, OP, 2>(a, nv, st);
       case 3:
-        return launch_pass3_async<T, N, OP>(a, nv, st);
+        // pass A only: staged rows made pass C slower (431 against 386 us
+        // per launch of 16 vectors at 128^3), pass A faster (442 against 453)
+        if constexpr (XTile<T, N, OP>::PRE) return launch_pass3_async<T, N, OP>(a, nv, st);
+        else return launch_pass3_tile<T, N, OP, 1>(a, nv, st);
       default:
         return launch_pass3_tile<T, N, OP, 1>(a, nv, st);
     }

@@ -33,7 +33,7 @@ struct KParams {
 // used when neither the caller nor the autotuner chose.
 constexpr int X3_VARIANTS = 4, Z3_VARIANTS = 2;
 #ifndef PCX_X3_VARIANT
-#define PCX_X3_VARIANT 1
+#define PCX_X3_VARIANT 3
 #endif
 #ifndef PCX_Z3_VARIANT
 #define PCX_Z3_VARIANT 0

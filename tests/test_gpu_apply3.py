@@ -173,7 +173,7 @@ def test_kernel_variants_give_identical_results(pcx, n):
                 ref = {"y": got[0], "w": got[1]}
             assert np.array_equal(got[0], ref["y"]) and np.array_equal(got[1], ref["w"]), (xv, zv)
     pcx.pcx_set_apply_variant(ctx, -1, -1)
-    assert pcx.pcx_get_apply_variant(ctx) == (1, 0)
+    assert pcx.pcx_get_apply_variant(ctx) == (3, 0)
     for bad in ((4, 0), (0, 2), (-2, 0)):
         with pytest.raises(pcx.PcxError) as e:
             pcx.pcx_set_apply_variant(ctx, *bad)
