@@ -125,9 +125,9 @@ __host__ __device__ constexpr int pass3_threads() {
 // shapes themselves are fixed by the geometry above, which the pass-B id
 // table depends on).  x tiles (passes A and C): PF rows whose global loads
 // are issued together before their arithmetic, and the CTAs per SM the
-// registers are sized for (MINB); variant 3 is the persistent kernel that
-// stages the next tile's rows with asynchronous copies
-// (pass3x_async_kernel).  z tiles (pass B): one tile per CTA (0) or
+// registers are sized for (MINB); variant 3 runs pass A as the persistent
+// kernel that stages the next tile's rows with asynchronous copies
+// (pass3x_async_kernel) and pass C as variant 1.  z tiles (pass B): one tile per CTA (0) or
 // the warp-specialised persistent kernel (1).
 template <int XV>
 struct XVar;
@@ -186,9 +186,9 @@ __device__ __forceinline__ void x_kappa_tables(const cx<T>* glam, const KParams&
 }
 
 // The steps of passes A and C on one x tile (16 rows of N points at
-// N = 128), shared by the one-tile-per-CTA kernel and the persistent one
-// that stages the next tile's rows with asynchronous copies.  The rows'
-// input comes either straight from global memory or from such a staged
+// N = 128), shared by the one-tile-per-CTA kernel and pass A's persistent
+// one, which stages the next tile's rows with asynchronous copies.  Pass
+// A's rows come either straight from global memory or from such a staged
 // copy raw[c][t][n] in shared memory; the arithmetic and its order are the
 // same in both.
 template <typename T, int N, int OP>
@@ -208,21 +208,14 @@ struct XTile {
   static constexpr int CH = N * (int)sizeof(cx<T>) / 16;   // 16-byte pieces per row
   static constexpr int RAW = 3 * TP * N;                   // entries of a staged tile
 
-  // global offset (within one vector, component 0) of the row the staged
-  // row t holds: pass A row t of the tile; pass C the input row
-  // RB k1 + m1 of row group gi, t = gi RA + k1
+  // global offset (within one vector, component 0) of pass A's row t of the tile
   static __device__ __forceinline__ int raw_row(int tile, int t) {
     int z, y, j;
-    if constexpr (PRE) {
-      x_row<T, N>(tile, t, z, y, j);
-      return z * N2 + y * N;
-    } else {
-      x_row<T, N>(tile, (t / RA) * RA, z, y, j);
-      return z * N2 + (j + RB * (t % RA)) * N;
-    }
+    x_row<T, N>(tile, t, z, y, j);
+    return z * N2 + y * N;
   }
 
-  // asynchronous copies of the tile's 3 TP input rows into raw (16-byte
+  // asynchronous copies of pass A's 3 TP input rows into raw (16-byte
   // pieces; the vector's base must be 16-byte aligned, which the launcher
   // checks); completion: cp.async.wait_all by every thread, then a barrier
   static __device__ __forceinline__ void stage_rows(cx<T>* raw, const cx<T>* in, int tile) {
@@ -330,26 +323,18 @@ struct XTile {
   }
 
   // Pass C, first step: RA-point forward y DFT, input rows RB k1 + m1 ->
-  // Fourier rows m1 + RB m2 of the tile (from global memory, or from the
-  // staged rows raw[c][gi RA + k1][n])
-  template <bool FROM_RAW>
-  static __device__ __forceinline__ void post_ydft(cx<T>* s, const cx<T>* in, const cx<T>* raw, int tile) {
+  // Fourier rows m1 + RB m2 of the tile
+  static __device__ __forceinline__ void post_ydft(cx<T>* s, const cx<T>* in, int tile) {
 #pragma unroll
     for (int it = 0; it < C3::XI_PER_THREAD; ++it) {
       const int w = threadIdx.x + it * C::THREADS;
       const int n = w % N, gi = (w / N) % G, c = w / (N * G);
+      int z, y, m1;
+      x_row<T, N>(tile, gi * RA, z, y, m1);
+      const cx<T>* ip = in + (size_t)c * N3 + z * N2 + m1 * N + n;
       cx<T> r[RA];
-      if constexpr (FROM_RAW) {
-        const cx<T>* rp = raw + (size_t)(c * TP + gi * RA) * N + n;
 #pragma unroll
-        for (int k1 = 0; k1 < RA; ++k1) r[k1] = rp[k1 * N];
-      } else {
-        int z, y, m1;
-        x_row<T, N>(tile, gi * RA, z, y, m1);
-        const cx<T>* ip = in + (size_t)c * N3 + z * N2 + m1 * N + n;
-#pragma unroll
-        for (int k1 = 0; k1 < RA; ++k1) r[k1] = ip[(RB * k1) * N];
-      }
+      for (int k1 = 0; k1 < RA; ++k1) r[k1] = ip[(RB * k1) * N];
       dft<RA, -1>(r);
 #pragma unroll
       for (int m2 = 0; m2 < RA; ++m2) s[TL::sidx(c, gi * RA + m2, n)] = r[m2];
@@ -661,7 +646,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
   using C = std::conditional_t<ZP, typename C3::CZ, typename C3::C>;
   constexpr int AXIS = ZP ? 2 : 0;
   using TL = Tile<T, N, AXIS, C>;
-  constexpr int TP = C::TP, RA = C3::RA, RB = C3::RB;
+  constexpr int TP = C::TP;
   constexpr int N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
@@ -694,7 +679,7 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
       XT::pre_ydft(s, tw, out, tile);
     } else {
       const cx<T>* sb = static_cast<const cx<T>*>(a.sbuf) + v * N3;
-      XT::template post_ydft<false>(s, in, nullptr, tile);
+      XT::post_ydft(s, in, tile);
       __syncthreads();
       fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
       XT::template post_rows<XVar<XV>::PF>(s, sb, out, ka, kb, tile);
@@ -716,15 +701,16 @@ __global__ void __launch_bounds__(pass3_threads<T, N, OP>(), pass3_minb<T, N, OP
   }
 }
 
-// Passes A and C as a persistent kernel (x variant 3 runs pass A with it;
-// pass C measured slower this way): CTA b walks x tiles b, b +
+// Pass A as a persistent kernel (x variant 3): CTA b walks x tiles b, b +
 // gridDim.x, ... and, once a tile's input rows have been consumed, copies
 // the next tile's rows into shared memory with asynchronous copies
 // (cp.async, 16-byte pieces), so that they are in flight during the x FFT
 // and the y DFT of the current tile.  A tile-per-CTA kernel issues its
 // global loads only in its first step.  The arithmetic is XTile's, as in
 // pass3_kernel.  Shared memory: the tile, twiddles, kappa tables and one
-// staged tile of rows (108 KB at N = 128: two CTAs per SM).
+// staged tile of rows (103 KB at N = 128: two CTAs per SM).  Pass C's
+// strided y DFT measured slower from staged rows (431 against 386 us per
+// launch of 16 vectors at 128^3), so pass C keeps the tile-per-CTA kernel.
 template <typename T, int N>
 __host__ __device__ constexpr size_t xasync_raw_offset() {
   using C = typename Cfg3<T, N>::C;
@@ -740,7 +726,7 @@ __global__ void __launch_bounds__(Cfg3<T, N>::THREADS, 2) pass3x_async_kernel(Pa
   using C3 = Cfg3<T, N>;
   using C = typename C3::C;
   using XT = XTile<T, N, OP>;
-  static_assert(!is_z_op<OP>(), "x tiles only");
+  static_assert(XT::PRE, "pass A only");
   constexpr int N3 = N * N * N, TILES = C3::TILES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
@@ -757,7 +743,6 @@ __global__ void __launch_bounds__(Cfg3<T, N>::THREADS, 2) pass3x_async_kernel(Pa
   for (int g = g0; g < total_tiles; g += gridDim.x) {
     const size_t v = (size_t)(g / TILES);
     const int tile = g % TILES;
-    cx<T>* out = gout + v * 3 * N3;
     KParams kp = a.kp;
     if (a.kps) kp = a.kps[(a.v_base + (int)v) / a.vec_per_k];
     // the previous tile's last readers of ka, kb and s passed the barrier
@@ -765,20 +750,12 @@ __global__ void __launch_bounds__(Cfg3<T, N>::THREADS, 2) pass3x_async_kernel(Pa
     x_kappa_tables<T, N>(static_cast<const cx<T>*>(a.lam), kp, tile, ka, kb);
     XT::wait_rows();
     __syncthreads();   // this tile's rows, the kappa tables (and the twiddles)
+    XT::template pre_rows<1, true>(s, nullptr, raw, static_cast<cx<T>*>(a.sbuf) + v * N3, ka, kb, kp, tile);
+    __syncthreads();   // the rows are consumed; the tile is complete
     const int gn = g + (int)gridDim.x;
-    if constexpr (XT::PRE) {
-      XT::template pre_rows<1, true>(s, nullptr, raw, static_cast<cx<T>*>(a.sbuf) + v * N3, ka, kb, kp, tile);
-      __syncthreads();   // the rows are consumed; the tile is complete
-      if (gn < total_tiles) XT::stage_rows(raw, gin + (size_t)(gn / TILES) * 3 * N3, gn % TILES);
-      fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
-      XT::pre_ydft(s, tw, out, tile);
-    } else {
-      XT::template post_ydft<true>(s, nullptr, raw, tile);
-      __syncthreads();
-      if (gn < total_tiles) XT::stage_rows(raw, gin + (size_t)(gn / TILES) * 3 * N3, gn % TILES);
-      fft_tile<T, N, 0, -1, 0, 0>(s, tw, nullptr, nullptr, 0);
-      XT::template post_rows<3>(s, static_cast<const cx<T>*>(a.sbuf) + v * N3, out, ka, kb, tile);
-    }
+    if (gn < total_tiles) XT::stage_rows(raw, gin + (size_t)(gn / TILES) * 3 * N3, gn % TILES);
+    fft_tile<T, N, 0, +1, 0, 0>(s, tw, nullptr, nullptr, 0);
+    XT::pre_ydft(s, tw, gout + v * 3 * N3, tile);
     __syncthreads();   // s, ka and kb are rewritten by the next tile
   }
   XT::wait_rows();
@@ -976,9 +953,7 @@ cudaError_t launch_pass3(const PassArgs& a, int nv, cudaStream_t st, int xv, int
         return launch_pass3_tile<T, N, OP, 0>(a, nv, st);
       case 2:
         return launch_pass3_tile<T, N, OP, 2>(a, nv, st);
-      case 3:
-        // pass A only: staged rows made pass C slower (431 against 386 us
-        // per launch of 16 vectors at 128^3), pass A faster (442 against 453)
+      case 3:   // pass A persistent with staged rows, pass C as variant 1
         if constexpr (XTile<T, N, OP>::PRE) return launch_pass3_async<T, N, OP>(a, nv, st);
         else return launch_pass3_tile<T, N, OP, 1>(a, nv, st);
       default:
