@@ -246,7 +246,9 @@ cudaError_t launch_gram_dd(const void* A, int na, const void* B, int nb, size_t 
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int T = (na <= 16 && nb <= 16) ? 16 : 32;
+  // tiles of 32 x 32 where both sizes are multiples of 32, else 16 x 16
+  // (48 x 48: 9 tiles of 16 against 4 of 32 that pad 48 to 64)
+  const int T = (na % 32 == 0 && nb % 32 == 0) ? 32 : 16;
   const unsigned gx = (na + T - 1) / T, gy = (nb + T - 1) / T;
   size_t want = (size_t)8 * sms / (gx * gy);   // short double-float chains
   if (want < 1) want = 1;
