@@ -159,6 +159,68 @@ def cpu_oracle_solve16():
     return time.perf_counter() - t0, int(its), float(np.max(res))
 
 
+def cpu_oracle_solve(name, n, ik, nev=12, block=16, tol=1e-8, maxit=600):
+    """The oracle's textbook LOBPCG (FP64 numpy, K_P^{-1}, one thread) on
+    structure `name` at n^3, Bloch vector ik of its path, nev bands to
+    Res <= tol: (seconds, iterations, max residual)."""
+    import numpy as np
+
+    import workloads as wl
+    from oracle import eig, fourier, penalty, permittivity
+    s = {"fcc-air-spheres": wl.fcc_air_spheres, "diamond-rods": wl.diamond_rods}[name]()
+    k = wl.config_k(s.name)[ik]
+    g = penalty.gamma_practical(k)
+    blocks = permittivity.cell_blocks(s, n)
+    kap = fourier.kappa(n, s.lattice, k)
+    t0 = time.perf_counter()
+    th, _, res, its = eig.lobpcg(lambda x: fourier.apply_symbols(x, kap, lambda e: permittivity.apply_m(blocks, e), g),
+                                 lambda r: fourier.precondition(r, kap, g), wl.random_block(block, n, seed=1), nev,
+                                 tol=tol, maxit=maxit)
+    return time.perf_counter() - t0, int(its), float(np.max(res))
+
+
+def study_cpu_solve(k64=(1, 2, 3), k128=(K_INDEX,), it128=5):
+    """CPU solve-time baselines: the oracle's LOBPCG (FP64 numpy, K_P^{-1},
+    12 bands, block 16, Res <= 1e-8) on configuration 2 (64^3 FCC air
+    spheres, three Bloch vectors of its path after Gamma, which the
+    textbook LOBPCG does not deflate; one single-threaded child process per
+    k, all running at once) and configuration 3 (128^3 diamond rods, one
+    Bloch vector, one child, it128 iterations: the time per iteration, with
+    the whole solve projected to the 87 iterations the FP64 GPU solve takes
+    on that k).  Host cores only, no GPU."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    model, ncores = cpu_model()
+
+    def spawn(name, n, ik, maxit):
+        code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench.cpu_oracle_solve(%r, %d, %d, maxit=%d)))" % (ROOT, name, n, ik, maxit))
+        return subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                env=env, text=True)
+
+    out = {"study": "cpu-solve", "kind": "oracle", "cpu_model": model, "nproc": ncores,
+           "solver": "oracle LOBPCG, FP64 numpy, K_P^-1, 12 bands, block 16, Res <= 1e-8, one thread per k"}
+    t0 = time.perf_counter()
+    jobs = [("config2_64", ik, spawn("fcc-air-spheres", 64, ik, 600)) for ik in k64]
+    jobs += [("config3_128", ik, spawn("diamond-rods", 128, ik, it128)) for ik in k128]
+    for label, ik, p in jobs:
+        o, e = p.communicate()
+        entry = out.setdefault(label, {"runs": [], "concurrent_processes": len(jobs)})
+        if p.returncode != 0:
+            entry["runs"].append({"k_index": ik, "error": e.strip().splitlines()[-1] if e.strip() else "failed"})
+            continue
+        sec, its, mres = json.loads(o.strip().splitlines()[-1])
+        run = {"k_index": ik, "s": sec, "iterations": its, "max_res": mres}
+        if label == "config3_128":
+            run["s_per_iteration"] = sec / max(its, 1)
+            run["projected_s_87_iterations"] = 87 * sec / max(its, 1)
+        entry["runs"].append(run)
+    ok = [r["s"] for r in out.get("config2_64", {}).get("runs", []) if "s" in r]
+    if ok:
+        out["config2_64"]["mean_s_per_k"] = sum(ok) / len(ok)
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def cpu_model():
     """The host CPU's model name and core count (lscpu, else the platform)."""
     import platform
@@ -840,9 +902,11 @@ def main():
                     help="print pcx_apply timings at 1, 16 and 48 vectors per call, complex64 and complex128, instead")
     ap.add_argument("--study", default="",
                     choices=["", "bcc-convergence", "frequency-difference", "woodpile-256", "learned-64",
-                             "configs-1-2", "ill-conditioned"],
+                             "configs-1-2", "ill-conditioned", "cpu-solve"],
                     help="run one of the paper's studies or configuration 5 instead of the benchmark (one JSON line)")
     args = ap.parse_args()
+    if args.study == "cpu-solve":
+        return study_cpu_solve()
     if args.study:
         from paper_2511_17107_gb300 import build as _build
         from paper_2511_17107_gb300 import pcx
