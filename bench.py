@@ -8,8 +8,9 @@ block of 16 vectors in one k-batched call (pcx_apply_kbatch: one launch per
 pass sweeps every (k, vector) pair).  The launch configuration comes from
 pcx_autotune on the timing stream.  value = vectors applied per second over
 the whole job.  Inputs (32 GB per step) are far larger than the 129 MB L2,
-so no flush is needed between steps.  e2e: pcx_apply_host on host buffers,
-one Bloch vector x 16 vectors per step, copies inside the timed region.
+so no flush is needed between steps.  e2e: pcx_apply_kbatch_host on host
+buffers, the same 40 Bloch vectors x 16 vectors per step (one pinned host
+block sent for every k), copies inside the timed region.
 
 The line also carries "solve": the per-k time to Res_j <= 1e-8 (12 bands,
 block 16, pcx_solve) on the same structure, in mixed precision with the
@@ -997,25 +998,26 @@ def main():
     per_launch_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps
 
     # end-to-end: the same step (every Bloch vector of the batch x the block)
-    # from pinned host buffers through pcx_apply_host, copies inside the timed
-    # region: per k, the block goes host -> device and its image comes back
-    # into one pinned host buffer (each k's result overwrites the previous one)
+    # from pinned host buffers through pcx_apply_kbatch_host, copies inside
+    # the timed region: for every k the block goes host -> device and its
+    # image comes back into one pinned host buffer (each k's result
+    # overwrites the previous one), in one pipeline per step
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(x).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
-        pcx.pcx_apply_host(ctx, ks[0], xh, yh)
+        pcx.pcx_apply_kbatch_host(ctx, ks[:1], xh, yh, block, x_stride=0, y_stride=0)
         e2e_steps = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            for kk in ks:
-                pcx.pcx_apply_host(ctx, kk, xh, yh)
+            pcx.pcx_apply_kbatch_host(ctx, ks, xh, yh, block, x_stride=0, y_stride=0)
         e2e_dt = time.perf_counter() - t0
         e2e_ms, e2e_rate = whole_job_rate(e2e_dt * 1e3, len(ks) * block, e2e_steps, world, "cuda")
         e2e = {"value": e2e_rate, "unit": UNIT,
                "h2d_bytes_per_step": int(len(ks) * xh.numel() * es), "d2h_bytes_per_step": int(len(ks) * yh.numel() * es),
-               "step": f"{len(ks)} Bloch vectors x {block} vectors from pinned host buffers (pcx_apply_host per k)"}
+               "step": f"{len(ks)} Bloch vectors x {block} vectors from pinned host buffers, one "
+                       "pcx_apply_kbatch_host call per step (one host block, stride 0, sent for every k)"}
 
     peak, peak_kind = peaks()
     abytes = algorithmic_bytes(n, vecs, es, 4)

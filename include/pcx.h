@@ -422,6 +422,23 @@ pcx_status pcx_apply_host(pcx_ctx* ctx, const double k[3], double gamma, const v
                           void* Y_host, int nvec, int precision, void* stream);
 
 /*
+ * pcx_apply_kbatch_host -- pcx_apply_kbatch on HOST buffers: for each of the
+ * nk Bloch vectors kpts[3 i .. 3 i + 2] (i < nk), the vec_per_k vectors
+ * starting at vector i * x_stride of X_host are applied with k_i and their
+ * images written at vector i * y_stride of Y_host (strides in vectors; 0
+ * reuses one block for every k, a later k's images overwriting an
+ * earlier's).  One pipeline for the whole batch, as in pcx_apply_host: chunks
+ * of up to 4 vectors that divide vec_per_k, host->device copy, apply and
+ * device->host copy of consecutive chunks overlapping on three streams, so
+ * the pipeline fills and drains once per call rather than once per k.
+ * Synchronises `stream` before returning.  PCX_EINVAL for negative counts or
+ * strides, more than 2^24 vectors, NULL or misaligned buffers.
+ */
+pcx_status pcx_apply_kbatch_host(pcx_ctx* ctx, const double* kpts, int nk, double gamma, const void* X_host,
+                                 int x_stride, void* Y_host, int y_stride, int vec_per_k, int precision,
+                                 void* stream);
+
+/*
  * pcx_precond -- W = K_P^{-1} R per Fourier mode (device, stream-ordered).
  * Sec. 2.4 eqs. matrixfree_diagP / matrixfree_finalform:
  *   K_P = K_A K_A^H + gamma K_B = |kappa|^2 I + (gamma - 1) conj(kappa) kappa^T,

@@ -221,29 +221,28 @@ pcx_status pcx_apply_noalloc(pcx_ctx* c, const double k[3], double gamma, const 
   return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply_noalloc", e);
 }
 
-pcx_status pcx_apply_host(pcx_ctx* c, const double k[3], double gamma, const void* Xh, void* Yh, int nvec,
-                          int precision, void* stream) {
-  pcx_status st = check_block(c, "pcx_apply_host", Xh, Yh, nvec, precision);
-  if (st != PCX_OK || nvec == 0) return st;
-  if (!k) return inval(c, "pcx_apply_host: NULL k");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// The host-buffer pipeline of pcx_apply_host and pcx_apply_kbatch_host:
+// nk groups of vpk vectors, group g applied with kps[g], its input at
+// vector g * xs of Xh and its image at vector g * ys of Yh (a stride of 0
+// reuses one block).  Chunks of cv vectors (cv divides vpk, so a chunk
+// never spans two groups) go through two device slots: the host->device
+// copy of chunk i + 1, the apply of chunk i and the device->host copy of
+// chunk i - 1 overlap on three streams.
+static pcx_status apply_host_pipeline(pcx_ctx* c, const char* who, const pcx::KParams* kps, int nk, int vpk,
+                                      const void* Xh, size_t xs, void* Yh, size_t ys, int cv, int precision,
+                                      cudaStream_t s) {
   const size_t vbytes = pcx_vector_length(c) * (precision == PCX_FP64 ? 16 : 8);
-  // chunks of about an eighth of the block, at most 4 vectors, in two slots:
-  // host->device of chunk i + 1, apply of chunk i and device->host of chunk
-  // i - 1 overlap on three streams, so only one chunk's copies are exposed
-  int cv = (nvec + 7) / 8;
-  cv = cv > 4 ? 4 : cv;
   const size_t slot = (size_t)cv * vbytes;
   cudaError_t e = cudaSuccess;
   if (2 * slot > c->stage_bytes) {
-    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(c, who, e);
     if (c->stage_x) cudaFree(c->stage_x);
     if (c->stage_y) cudaFree(c->stage_y);
     c->stage_x = c->stage_y = nullptr;
     c->stage_bytes = 0;
     e = cudaMalloc(&c->stage_x, 2 * slot);
     if (e == cudaSuccess) e = cudaMalloc(&c->stage_y, 2 * slot);
-    if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+    if (e != cudaSuccess) return cuda_fail(c, who, e);
     c->stage_bytes = 2 * slot;
   }
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
@@ -251,35 +250,74 @@ pcx_status pcx_apply_host(pcx_ctx* c, const double k[3], double gamma, const voi
   for (int i = 0; i < 3 && e == cudaSuccess; ++i)
     for (int j = 0; j < 2 && e == cudaSuccess; ++j)
       if (!c->slot_event[i][j]) e = cudaEventCreateWithFlags(&c->slot_event[i][j], cudaEventDisableTiming);
-  if (e != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
+  if (e != cudaSuccess) return cuda_fail(c, who, e);
   cudaStream_t h2d = c->copy_stream[0], d2h = c->copy_stream[1];
   cudaEvent_t* loaded = c->slot_event[0];    // chunk in stage_x[slot]
   cudaEvent_t* applied = c->slot_event[1];   // stage_x[slot] read, stage_y[slot] written
   cudaEvent_t* stored = c->slot_event[2];    // stage_y[slot] copied out
   // earlier work of the caller's stream comes first
-  if ((e = cudaEventRecord(applied[0], s)) != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
-  if ((e = cudaStreamWaitEvent(h2d, applied[0], 0)) != cudaSuccess) return cuda_fail(c, "pcx_apply_host", e);
-  const pcx::KParams kp = pcx::make_kparams(c, k, gamma);
-  const int nch = (nvec + cv - 1) / cv;
-  for (int ch = 0; ch < nch && e == cudaSuccess; ++ch) {
-    const int sl = ch & 1, nv = nvec - ch * cv < cv ? nvec - ch * cv : cv;
+  if ((e = cudaEventRecord(applied[0], s)) != cudaSuccess) return cuda_fail(c, who, e);
+  if ((e = cudaStreamWaitEvent(h2d, applied[0], 0)) != cudaSuccess) return cuda_fail(c, who, e);
+  const int per_group = (vpk + cv - 1) / cv;
+  const long long nch = (long long)nk * per_group;
+  for (long long ch = 0; ch < nch && e == cudaSuccess; ++ch) {
+    const int g = (int)(ch / per_group), j0 = (int)(ch % per_group) * cv;
+    const int sl = (int)(ch & 1), nv = vpk - j0 < cv ? vpk - j0 : cv;
     char* sx = static_cast<char*>(c->stage_x) + sl * slot;
     char* sy = static_cast<char*>(c->stage_y) + sl * slot;
-    const size_t off = (size_t)ch * cv * vbytes, bytes = (size_t)nv * vbytes;
+    const size_t xoff = ((size_t)g * xs + j0) * vbytes, yoff = ((size_t)g * ys + j0) * vbytes;
+    const size_t bytes = (size_t)nv * vbytes;
     if (ch >= 2) e = cudaStreamWaitEvent(h2d, applied[sl], 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sx, static_cast<const char*>(Xh) + off, bytes, cudaMemcpyHostToDevice, h2d);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sx, static_cast<const char*>(Xh) + xoff, bytes, cudaMemcpyHostToDevice, h2d);
     if (e == cudaSuccess) e = cudaEventRecord(loaded[sl], h2d);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, loaded[sl], 0);
     if (e == cudaSuccess && ch >= 2) e = cudaStreamWaitEvent(s, stored[sl], 0);
-    if (e == cudaSuccess) e = pcx::launch_apply(c, kp, sx, sy, nv, precision, s);
+    if (e == cudaSuccess) e = pcx::launch_apply(c, kps[g], sx, sy, nv, precision, s);
     if (e == cudaSuccess) e = cudaEventRecord(applied[sl], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, applied[sl], 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(static_cast<char*>(Yh) + off, sy, bytes, cudaMemcpyDeviceToHost, d2h);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<char*>(Yh) + yoff, sy, bytes, cudaMemcpyDeviceToHost, d2h);
     if (e == cudaSuccess) e = cudaEventRecord(stored[sl], d2h);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(d2h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return e == cudaSuccess ? PCX_OK : cuda_fail(c, "pcx_apply_host", e);
+  return e == cudaSuccess ? PCX_OK : cuda_fail(c, who, e);
+}
+
+pcx_status pcx_apply_host(pcx_ctx* c, const double k[3], double gamma, const void* Xh, void* Yh, int nvec,
+                          int precision, void* stream) {
+  pcx_status st = check_block(c, "pcx_apply_host", Xh, Yh, nvec, precision);
+  if (st != PCX_OK || nvec == 0) return st;
+  if (!k) return inval(c, "pcx_apply_host: NULL k");
+  // chunks of about an eighth of the block, at most 4 vectors: only one
+  // chunk's copies are exposed
+  int cv = (nvec + 7) / 8;
+  cv = cv > 4 ? 4 : cv;
+  const pcx::KParams kp = pcx::make_kparams(c, k, gamma);
+  return apply_host_pipeline(c, "pcx_apply_host", &kp, 1, nvec, Xh, 0, Yh, 0, cv, precision,
+                             static_cast<cudaStream_t>(stream));
+}
+
+pcx_status pcx_apply_kbatch_host(pcx_ctx* c, const double* kpts, int nk, double gamma, const void* Xh, int x_stride,
+                                 void* Yh, int y_stride, int vec_per_k, int precision, void* stream) {
+  if (nk < 0 || vec_per_k < 0) return inval(c, "pcx_apply_kbatch_host: nk, vec_per_k must be >= 0");
+  if (x_stride < 0 || y_stride < 0) return inval(c, "pcx_apply_kbatch_host: strides must be >= 0");
+  if ((long long)nk * vec_per_k > (1LL << 24)) return inval(c, "pcx_apply_kbatch_host: too many vectors");
+  pcx_status st = check_block(c, "pcx_apply_kbatch_host", Xh, Yh, nk * vec_per_k, precision);
+  if (st != PCX_OK || nk == 0 || vec_per_k == 0) return st;
+  if (!kpts) return inval(c, "pcx_apply_kbatch_host: NULL kpts");
+  std::vector<pcx::KParams> kps(nk);
+  for (int i = 0; i < nk; ++i) kps[i] = pcx::make_kparams(c, kpts + 3 * i, gamma);
+  // the largest chunk of at most 4 vectors that divides vec_per_k
+  int cv = 1;
+  for (int d = 4; d >= 1; --d)
+    if (vec_per_k % d == 0) {
+      cv = d;
+      break;
+    }
+  return apply_host_pipeline(c, "pcx_apply_kbatch_host", kps.data(), nk, vec_per_k, Xh, (size_t)x_stride, Yh,
+                             (size_t)y_stride, cv, precision, static_cast<cudaStream_t>(stream));
 }
 
 pcx_status pcx_precond(pcx_ctx* c, const double k[3], double gamma, const void* R, void* W, int nvec, int precision,

@@ -107,6 +107,8 @@ def lib():
             "pcx_get_gram_path": (C.c_int, []),
             "pcx_div_norms": (st, [vp, dp, vp, C.c_int, C.c_int, vp, vp]),
             "pcx_apply_kbatch": (st, [vp, dp, C.c_int, C.c_double, vp, vp, C.c_int, C.c_int, vp]),
+            "pcx_apply_kbatch_host": (st, [vp, dp, C.c_int, C.c_double, vp, C.c_int, vp, C.c_int, C.c_int, C.c_int,
+                                           vp]),
             "pcx_set_apply_graphs": (st, [vp, C.c_int]),
             "pcx_set_apply_path": (st, [vp, C.c_int]),
             "pcx_set_cnn_form": (st, [vp, C.c_int]),
@@ -142,7 +144,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("pcx_setup", "pcx_sample_host", "pcx_destroy", "pcx_last_error", "pcx_grid_n", "pcx_vector_length",
                         "pcx_cell_blocks", "pcx_symbols", "pcx_set_apply_chunk", "pcx_get_apply_chunk", "pcx_apply", "pcx_apply_noalloc", "pcx_apply_host", "pcx_precond",
-                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_set_penalty_form", "pcx_get_penalty_form", "pcx_set_apply_variant", "pcx_get_apply_variant", "pcx_set_cnn_form", "pcx_autotune",
+                        "pcx_div_norms", "pcx_apply_kbatch", "pcx_apply_kbatch_host", "pcx_set_apply_graphs", "pcx_set_apply_path", "pcx_get_apply_path", "pcx_set_penalty_form", "pcx_get_penalty_form", "pcx_set_apply_variant", "pcx_get_apply_variant", "pcx_set_cnn_form", "pcx_autotune",
                         "pcx_sandwich_precond", "pcx_cnn_init", "pcx_cnn_gates",
                         "pcx_cnn_forward", "pcx_cnn_grad", "pcx_cnn_adam", "pcx_cnn_precond", "pcx_cnn_pairs",
                         "pcx_cg_solve", "pcx_gram", "pcx_set_gram_path", "pcx_get_gram_path", "pcx_gram_mixed", "pcx_combine", "pcx_residual", "pcx_rr_eig", "pcx_solve")]
@@ -404,6 +406,31 @@ def pcx_apply_kbatch(ctx, kpts, X, Y, gamma=0.0, stream=None):
         raise ValueError("pcx_apply_kbatch: one k per group")
     _check(lib().pcx_apply_kbatch(ctx.handle, _dptr(kp), nk, float(gamma), _devptr(X), _devptr(Y), vpk, _prec_of(X),
                                   _stream(stream)), ctx.handle)
+    return Y
+
+
+def pcx_apply_kbatch_host(ctx, kpts, X, Y, vec_per_k, x_stride=None, y_stride=None, gamma=0.0, stream=None):
+    """Host-buffer k-batched apply: group i (vec_per_k vectors) at vector
+    i * x_stride of X is applied with kpts[i] and written at vector
+    i * y_stride of Y (strides in vectors, default vec_per_k; 0 reuses one
+    block).  X, Y: host numpy arrays or CPU torch tensors (pinned memory
+    copies fastest)."""
+    kp = np.ascontiguousarray(np.asarray(kpts, dtype=np.float64).reshape(-1, 3))
+    nk = kp.shape[0]
+    xs = vec_per_k if x_stride is None else x_stride
+    ys = vec_per_k if y_stride is None else y_stride
+    if isinstance(X, np.ndarray):
+        prec = PCX_FP32 if X.dtype == np.complex64 else PCX_FP64
+        xp, yp = X.ctypes.data, Y.ctypes.data
+        nx, ny = X.size // ctx.vector_length, Y.size // ctx.vector_length
+    else:
+        prec = _prec_of(X)
+        xp, yp = X.data_ptr(), Y.data_ptr()
+        nx, ny = X.numel() // ctx.vector_length, Y.numel() // ctx.vector_length
+    if nk > 0 and ((nk - 1) * xs + vec_per_k > nx or (nk - 1) * ys + vec_per_k > ny):
+        raise ValueError("pcx_apply_kbatch_host: X or Y too small for the strides")
+    _check(lib().pcx_apply_kbatch_host(ctx.handle, _dptr(kp), nk, float(gamma), C.c_void_p(xp), int(xs),
+                                       C.c_void_p(yp), int(ys), int(vec_per_k), prec, _stream(stream)), ctx.handle)
     return Y
 
 

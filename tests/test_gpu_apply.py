@@ -113,6 +113,39 @@ def test_apply_host_pipelined_chunks(pcx, nvec, pinned):
         assert np.array_equal(yh.numpy(), want)
 
 
+@pytest.mark.parametrize("vpk,xs,ys,pinned", [(6, 6, 6, True), (5, 5, 0, False), (3, 0, 3, True), (8, 9, 8, True)])
+def test_apply_kbatch_host(pcx, vpk, xs, ys, pinned):
+    """pcx_apply_kbatch_host: three Bloch vectors, vec_per_k vectors each,
+    input and output groups at the given strides (0: one block reused).
+    Every group's images equal the device k-batched entry's bit for bit
+    (for output stride 0, the last k's)."""
+    n, nk = 32, 3
+    s = wl.fcc_air_spheres()
+    ks = wl.config_k(s.name)[2:2 + nk]
+    nx = (nk - 1) * xs + vpk
+    x = wl.random_block(nx, n, seed=60 + vpk).astype(np.complex64)
+    ctx = pcx.setup_structure(s, n)
+    xg = np.stack([x[i * xs:i * xs + vpk] for i in range(nk)])
+    X = torch.from_numpy(xg).cuda()
+    Y = torch.empty_like(X)
+    pcx.pcx_apply_kbatch(ctx, ks, X, Y)
+    torch.cuda.synchronize()
+    want = Y.cpu().numpy()
+    xh = torch.from_numpy(x)
+    yh = torch.zeros(((nk - 1) * ys + vpk,) + x.shape[1:], dtype=torch.complex64)
+    if pinned:
+        xh, yh = xh.pin_memory(), yh.pin_memory()
+    pcx.pcx_apply_kbatch_host(ctx, ks, xh, yh, vpk, x_stride=xs, y_stride=ys)
+    got = yh.numpy()
+    if ys == 0:
+        assert np.array_equal(got, want[-1])
+    else:
+        for i in range(nk):
+            assert np.array_equal(got[i * ys:i * ys + vpk], want[i]), i
+    with pytest.raises(pcx.PcxError):
+        pcx.pcx_apply_kbatch_host(ctx, ks, xh, yh, vpk, x_stride=-1, y_stride=ys)
+
+
 @pytest.mark.parametrize("name,maker,n,dtype,nvec,chunk", [
     ("sc16-f64", wl.sc_gyro_sphere, 16, np.complex128, 3, 0),
     ("sc16-f64-chunk1", wl.sc_gyro_sphere, 16, np.complex128, 3, 1),
