@@ -219,7 +219,8 @@ def study_cpu_solve(k64=(1, 2, 3), k128=(K_INDEX,), it128=5):
     if ok:
         out["config2_64"]["mean_s_per_k"] = sum(ok) / len(ok)
     out["wall_s"] = time.perf_counter() - t0
-    return out
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def cpu_model():
