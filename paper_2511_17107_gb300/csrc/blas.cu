@@ -376,6 +376,57 @@ __global__ void __launch_bounds__(256) residual_kernel(const cx<T>* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// The residual of the mixed-precision refinement: R_j = AX_j - theta_j X_j
+// formed in FP64 from the FP64 X and AX and stored rounded to complex64,
+// X_j rounded to complex64 alongside, ||R_j||^2 and ||X_j||^2 in FP64 (the
+// same values as residual_kernel<double> followed by two conversions, with
+// one pass over X and AX and no FP64 R written).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) residual_mixed_kernel(const double2* __restrict__ X, const double2* AX,
+                                                             const double* theta, float2* R32, float2* X32,
+                                                             double* norms, int nvec, size_t L) {
+  const int j = blockIdx.y;
+  const double th = theta[j];
+  double rr = 0.0, xx = 0.0;
+  const double2* x = X + (size_t)j * L;
+  const double2* ax = AX + (size_t)j * L;
+  float2* r = R32 + (size_t)j * L;
+  float2* x32 = X32 + (size_t)j * L;
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (size_t)gridDim.x * blockDim.x) {
+    const double2 xv = x[l], av = ax[l];
+    const double rx = fma(-th, xv.x, av.x), ry = fma(-th, xv.y, av.y);
+    r[l] = make_float2((float)rx, (float)ry);
+    x32[l] = make_float2((float)xv.x, (float)xv.y);
+    rr += fma(rx, rx, ry * ry);
+    xx += fma(xv.x, xv.x, xv.y * xv.y);
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    xx += __shfl_down_sync(0xffffffffu, xx, o);
+  }
+  const int lane = threadIdx.x % 32, wid = threadIdx.x / 32;
+  if (lane == 0) {
+    red[0][wid] = rr;
+    red[1][wid] = xx;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x / 32;
+    rr = lane < nw ? red[0][lane] : 0.0;
+    xx = lane < nw ? red[1][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_down_sync(0xffffffffu, rr, o);
+      xx += __shfl_down_sync(0xffffffffu, xx, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&norms[j], rr);
+      atomicAdd(&norms[nvec + j], xx);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Seeded complex Gaussian fill: SplitMix64 hash of (seed, index) -> two
 // uniforms -> Box-Muller (uses the CUDA math library's log, sqrt, sincos).
 // ---------------------------------------------------------------------------
@@ -522,6 +573,16 @@ cudaError_t launch_residual(const void* X, const void* AX, const double* theta, 
   else
     residual_kernel<float><<<grid, 256, 0, s>>>(static_cast<const cx<float>*>(X), static_cast<const cx<float>*>(AX),
                                                 theta, static_cast<cx<float>*>(R), norms, nvec, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_mixed(const void* X, const void* AX, const double* theta, void* R32, void* X32,
+                                  double* norms, int nvec, size_t L, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(norms, 0, sizeof(double) * 2 * nvec, s);
+  if (e != cudaSuccess || nvec == 0) return e;
+  dim3 grid(grid_for(L, 256, 152u * 4u), nvec);
+  residual_mixed_kernel<<<grid, 256, 0, s>>>(static_cast<const double2*>(X), static_cast<const double2*>(AX), theta,
+                                             static_cast<float2*>(R32), static_cast<float2*>(X32), norms, nvec, L);
   return cudaGetLastError();
 }
 

@@ -206,6 +206,10 @@ cudaError_t launch_combine_add32(const void* S32, int ns, const double* C, int n
                                 cudaStream_t s);
 cudaError_t launch_residual(const void* X, const void* AX, const double* theta, void* R,
                             double* norms, int nvec, size_t L, int precision, cudaStream_t s);
+// complex128 X, AX -> complex64 R = AX - X theta and X, FP64 norms (the
+// mixed-precision refinement's residual)
+cudaError_t launch_residual_mixed(const void* X, const void* AX, const double* theta, void* R32, void* X32,
+                                  double* norms, int nvec, size_t L, cudaStream_t s);
 cudaError_t launch_fill_random(void* X, int nvec, size_t L, uint64_t seed, int precision,
                                cudaStream_t s);
 cudaError_t launch_deflate_p0(void* X, int nvec, int n, int precision, cudaStream_t s);

@@ -480,8 +480,11 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
   for (iters = 0;; ++iters) {
     // FP64 residual
     CK(cudaMemcpyAsync(r64.theta.p, theta.data(), sizeof(double) * n, cudaMemcpyHostToDevice, r64.s));
-    CK(launch_residual(r64.S.p, r64.AS.p, static_cast<double*>(r64.theta.p), r64.R.p,
-                       static_cast<double*>(r64.norms.p), n, L, PCX_FP64, r64.s));
+    // FP64 residual of the FP64 X and AX, stored rounded to FP32 (the
+    // directions and the AX rows below use it), with X rounded to FP32 in the
+    // same pass
+    CK(launch_residual_mixed(r64.S.p, r64.AS.p, static_cast<double*>(r64.theta.p), r32.R.p, r32.S.p,
+                             static_cast<double*>(r64.norms.p), n, L, r64.s));
     std::vector<double> nrm(2 * n);
     CK(cudaMemcpyAsync(nrm.data(), r64.norms.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, r64.s));
     CK(cudaStreamSynchronize(r64.s));
@@ -528,10 +531,7 @@ pcx_status lobpcg_refine(Run& r64, Run& r32, int nev, double tol, int maxit, int
       if (res[j] > tol) act.push_back(j);
     const int na = (int)act.size();
     const int w0 = n + np;
-    // X32 rounded from the FP64 columns; W32 = K_P^{-1} R (FP32)
-    CK(launch_convert(r64.S.p, PCX_FP64, r32.S.p, PCX_FP32, (size_t)n * L, r64.s));
-    // all n residual columns in FP32 (the AX rows below use them too)
-    CK(launch_convert(r64.R.p, PCX_FP64, r32.R.p, PCX_FP32, (size_t)n * L, r64.s));
+    // W32 = K_P^{-1} R (FP32; X32 and R32 come from the residual pass)
     CK(r32.precond_active(act, w0));
     // [P W] is orthogonalised against X and orthonormalised (Cholesky QR,
     // PCX_ORTH_PASSES passes) in FP32, so the FP32 part of the Gram matrices
