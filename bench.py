@@ -391,6 +391,35 @@ def apply_sizes_table(n, reps=5):
                 row["fp64_gemm_peak_tflops"] = round(fp64_tflops, 3)
             print(json.dumps(row), flush=True)
             del x, y
+    # M_CrossDoF (Sec. 3.2.2): the seven-pass chain with the real-space
+    # cross-DoF stencil pass, on the same workload and k at 16 vectors (the
+    # diamond materials fail the sufficient HPD conditions of Sec. 3.3, so
+    # the context is built without that proof; the timing does not depend
+    # on it)
+    cctx = pcx.setup_structure(s, n, m_kind=pcx.PCX_M_CROSSDOF, crossdof_unchecked=True)
+    for dt, es in ((torch.complex64, 8), (torch.complex128, 16)):
+        nv = 16
+        x = torch.complex(torch.randn(nv, 3, n, n, n, device="cuda", dtype=torch.float64),
+                          torch.randn(nv, 3, n, n, n, device="cuda", dtype=torch.float64)).to(dt)
+        y = torch.empty_like(x)
+        tune = pcx.pcx_autotune(cctx, pcx.PCX_FP32 if es == 8 else pcx.PCX_FP64, nv)
+        pcx.pcx_apply(cctx, k, x, y)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pcx.pcx_apply(cctx, k, x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        print(json.dumps({"op": "apply", "m_kind": "crossdof", "N": n, "dtype": "c64" if es == 8 else "c128",
+                          "vectors": nv, "us_per_vector": round(1e3 * ms / nv, 2),
+                          "applies_per_s": round(nv / (ms / 1e3), 1),
+                          "algorithmic_gbs": round(2 * nv * 3 * n ** 3 * es / (ms / 1e3) / 1e9, 1),
+                          "chunk": tune["chunk"] if isinstance(tune, dict) else None}), flush=True)
+        del x, y
     return 0
 
 
