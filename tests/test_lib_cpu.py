@@ -1,6 +1,7 @@
 """CPU-side tests of libpcx: the C ABI loads and exports every declared
 symbol, and the host-only entry points (sampling, Rayleigh-Ritz solver)
 agree with the oracle.  No kernel is launched here."""
+import ctypes
 import os
 import re
 
@@ -182,3 +183,17 @@ def test_crossdof_sec33_conditions(pcx):
     assert pcx.pcx_sample_host(weak, n, m_kind=pcx.PCX_M_CROSSDOF)[2] == 0
     # the same structures under M_Trivial are judged cell by cell instead
     assert pcx.pcx_sample_host(dense, n)[2] == -1
+
+
+def test_host_entries_reject_bad_arguments_before_any_device_work(pcx):
+    """The host-buffer entries check their arguments on the host: a NULL
+    context, negative counts or strides, and NULL or misaligned buffers give
+    PCX_EINVAL without touching a device (so this runs without a GPU)."""
+    lib = pcx.lib()
+    k = np.zeros(3)
+    kp = k.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    buf = np.zeros(64, dtype=np.complex64)
+    p = ctypes.c_void_p(buf.ctypes.data)
+    assert lib.pcx_apply_kbatch_host(None, kp, 1, 0.0, p, 0, p, 0, 1, 1, None) == pcx.PCX_EINVAL
+    assert lib.pcx_apply_host(None, kp, 0.0, p, p, 1, 1, None) == pcx.PCX_EINVAL
+    assert lib.pcx_apply_kbatch(None, kp, 1, 0.0, p, p, 1, 1, None) == pcx.PCX_EINVAL
