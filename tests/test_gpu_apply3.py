@@ -83,6 +83,33 @@ def test_three_pass_full_size_bench_workload(pcx):
     assert _err(Y.cpu().numpy()[0:1], want) <= TOL
 
 
+def test_bench_launch_configuration_sampled_against_oracle(pcx):
+    """The benchmark's launch as timed: 40 Bloch vectors of the diamond-rod
+    path x 16 vectors at 128^3 in one pcx_apply_kbatch (complex64, three-pass
+    chain, 16 vectors per launch, the default kernel variants), inputs seeded
+    on the device; three sampled (k, vector) outputs, the first, a middle and
+    the last, against the oracle's operator one by one."""
+    n, nk, vpk = 128, 40, 16
+    s = wl.diamond_rods()
+    ks = wl.config_k(s.name)[:nk]
+    ctx = pcx.setup_structure(s, n)
+    pcx.pcx_set_apply_path(ctx, pcx.PCX_APPLY_THREE_PASS)
+    pcx.pcx_set_apply_chunk(ctx, 16)
+    g = torch.Generator(device="cuda").manual_seed(20251117)
+    X = torch.randn((nk, vpk, 3, n, n, n), dtype=torch.complex64, device="cuda", generator=g)
+    Y = torch.empty_like(X)
+    pcx.pcx_apply_kbatch(ctx, ks, X, Y)
+    torch.cuda.synchronize()
+    blocks = permittivity.cell_blocks(s, n)
+    for i, j in ((0, 0), (17, 9), (39, 15)):
+        x = X[i, j:j + 1].cpu().numpy().astype(np.complex128)
+        ops = yee.YeeOperators(n, s.lattice, ks[i])
+        want = fourier.apply_definition(x, ops, lambda e: permittivity.apply_m(blocks, e),
+                                        penalty.gamma_practical(ks[i]))
+        assert _err(Y[i, j:j + 1].cpu().numpy(), want) <= TOL, (i, j)
+    del X, Y
+
+
 def test_three_pass_at_k_zero(pcx):
     n = 32
     s = wl.fcc_air_spheres()
