@@ -33,6 +33,11 @@
  * Errors: every call returns a pcx_status; nothing aborts, nothing traps on
  *   the device.  pcx_last_error() gives a message for the last failing call
  *   on a context.  Invalid arguments never reach a kernel.
+ * Threads: a context serves one host thread at a time (its apply scratch,
+ *   host staging slots, graph cache, kernel choices and error message are
+ *   shared state); use one context per thread for concurrent calls.
+ *   pcx_solve's k-points in flight run on threads of its own, each with its
+ *   own buffers.
  */
 #ifndef PCX_H
 #define PCX_H
