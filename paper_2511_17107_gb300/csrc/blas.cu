@@ -376,30 +376,54 @@ __global__ void __launch_bounds__(256) residual_kernel(const cx<T>* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// The residual of the mixed-precision refinement: R_j = AX_j - theta_j X_j
-// formed in FP64 from the FP64 X and AX and stored rounded to complex64,
-// X_j rounded to complex64 alongside, ||R_j||^2 and ||X_j||^2 in FP64 (the
-// same values as residual_kernel<double> followed by two conversions, with
-// one pass over X and AX and no FP64 R written).
+// The residual of the mixed-precision refinement, R_j = AX_j - theta_j X_j,
+// from the FP64 X and AX, stored rounded to complex64, with X_j rounded to
+// complex64 alongside and ||R_j||^2, ||X_j||^2 summed from the rounded
+// values (FP32 within a thread, FP64 across threads).  The difference is
+// formed in double-float on the FP32 pipes: every FP64 operand split into
+// FP32 hi + lo, theta x as TwoProd of the hi parts plus the cross terms,
+// ax - theta x by TwoSum (Knuth), about 2^-48 of |ax| before the final
+// rounding to FP32, the same as FP64 for a result stored in FP32 (GB300's
+// FP64 pipes made the FP64 form three times slower than the memory traffic).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float dd_residual(float ah, float al, float th, float tl, float xh, float xl) {
+  const float p = __fmul_rn(th, xh);
+  float e = fmaf(th, xh, -p);   // p + e == th * xh exactly
+  e = fmaf(th, xl, e);
+  e = fmaf(tl, xh, e);
+  const float sm = __fsub_rn(ah, p);   // TwoSum(ah, -p)
+  const float bb = __fsub_rn(sm, ah);
+  const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(sm, bb)), __fsub_rn(-p, bb));
+  const float lo = __fadd_rn(__fsub_rn(al, e), err);
+  return __fadd_rn(sm, lo);
+}
+
 __global__ void __launch_bounds__(256) residual_mixed_kernel(const double2* __restrict__ X, const double2* AX,
                                                              const double* theta, float2* R32, float2* X32,
                                                              double* norms, int nvec, size_t L) {
   const int j = blockIdx.y;
-  const double th = theta[j];
-  double rr = 0.0, xx = 0.0;
+  float th, tl;
+  dfloat::split(theta[j], th, tl);
+  float rrf = 0.f, xxf = 0.f;
   const double2* x = X + (size_t)j * L;
   const double2* ax = AX + (size_t)j * L;
   float2* r = R32 + (size_t)j * L;
   float2* x32 = X32 + (size_t)j * L;
   for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < L; l += (size_t)gridDim.x * blockDim.x) {
     const double2 xv = x[l], av = ax[l];
-    const double rx = fma(-th, xv.x, av.x), ry = fma(-th, xv.y, av.y);
-    r[l] = make_float2((float)rx, (float)ry);
-    x32[l] = make_float2((float)xv.x, (float)xv.y);
-    rr += fma(rx, rx, ry * ry);
-    xx += fma(xv.x, xv.x, xv.y * xv.y);
+    float xh, xl, yh, yl, ah, al, bh, bl;
+    dfloat::split(xv.x, xh, xl);
+    dfloat::split(xv.y, yh, yl);
+    dfloat::split(av.x, ah, al);
+    dfloat::split(av.y, bh, bl);
+    const float rx = dd_residual(ah, al, th, tl, xh, xl), ry = dd_residual(bh, bl, th, tl, yh, yl);
+    const float x0 = __fadd_rn(xh, xl), x1 = __fadd_rn(yh, yl);
+    r[l] = make_float2(rx, ry);
+    x32[l] = make_float2(x0, x1);
+    rrf = fmaf(rx, rx, fmaf(ry, ry, rrf));
+    xxf = fmaf(x0, x0, fmaf(x1, x1, xxf));
   }
+  double rr = rrf, xx = xxf;
   __shared__ double red[2][32];
   for (int o = 16; o > 0; o >>= 1) {
     rr += __shfl_down_sync(0xffffffffu, rr, o);
