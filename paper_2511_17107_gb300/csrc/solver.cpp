@@ -135,14 +135,15 @@ struct Run {
   char* col(DevBuf& b, int j) { return static_cast<char*>(b.p) + (size_t)j * L * es; }
 
   // x_only: the FP64 run of the mixed scheme, which keeps only X and AX
-  // (n columns each, with their combination targets) in FP64
+  // (n columns each, with their combination targets) in FP64; its residual
+  // goes straight to the FP32 run's R
   pcx_status alloc_all(bool x_only = false) {
     const size_t blk = (size_t)(x_only ? 1 : 3) * n * L * es;
     CK(S.alloc(blk));
     CK(AS.alloc(blk));
     CK(S2.alloc(blk));
     CK(AS2.alloc(blk));
-    CK(R.alloc((size_t)n * L * es));
+    if (!x_only) CK(R.alloc((size_t)n * L * es));
     CK(G.alloc(sizeof(double) * 2 * (size_t)9 * n * n));
     CK(C.alloc(sizeof(double) * 2 * (size_t)9 * n * n));
     CK(theta.alloc(sizeof(double) * n));
