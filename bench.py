@@ -756,8 +756,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD.replace("block of 16", "1 vector per step"),
-                                            "N": N, "vectors_per_step": 1},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "N": N, "vectors_per_step": 1,
+                                            "sample_per_step": "one whole vector of the workload (Bloch vector "
+                                                               f"{K_INDEX} of the path) through the oracle's FP64 "
+                                                               "operator, numpy, one thread"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} whole-vector FP64 oracle applies at 128^3"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
